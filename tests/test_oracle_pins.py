@@ -1,0 +1,177 @@
+"""Pins of the FP64 oracle against what the mathematics fixes (no GPU).
+
+Each test ties one part of the oracle to something other than itself:
+closed forms of the difference operators on polynomials, the RK4 stability
+polynomial on a Fourier mode, hand-derived hyper-diffusion values on cubic
+and compressive profiles, and the signal speed of a uniform state.
+"""
+import math
+
+import numpy as np
+import pytest
+
+BC_P, BC_F, BC_O = 0, 1, 2
+
+
+def _uniform(ny, nx, rho=1.0, vx=0.0, vy=0.0, p=1.0, bx=0.0, by=0.0, gamma=5 / 3):
+    from paper_1710_06423_b300.inputs import conserved
+    o = np.ones((ny, nx))
+    return conserved(rho * o, vx * o, vy * o, p * o, bx * o, by * o, gamma)
+
+
+def test_central_difference_exact_on_quartic(oracle_mod):
+    """Section 2 fourth-order central difference: exact on degree <= 4 (textbook)."""
+    o = oracle_mod
+    nx = 40
+    pr = o.Problem(nx=nx, ny=1, x0=0.0, x1=4.0, bc_x=BC_O, hyperdiffusion=0)
+    x = pr.x0 + (np.arange(nx) + 0.5) * pr.dx
+    for coeffs in ([0.3], [1.0, -2.0], [0.5, 0.1, -0.7], [0.2, 0.0, 0.3, -0.05],
+                   [1.0, -0.5, 0.25, 0.1, -0.03]):
+        P = np.polynomial.Polynomial(coeffs)
+        w = _uniform(1, nx, rho=1.0, p=10.0)
+        w[1, 0, :] = P(x)                     # m_x = P(x)  =>  k_rho = -D_x P
+        k = o.rhs(pr, w)
+        inner = slice(3, nx - 3)
+        exact = -P.deriv()(x)
+        np.testing.assert_allclose(k[0, 0, inner], exact[inner], rtol=0, atol=1e-12 * (1 + abs(exact).max()))
+
+
+def test_central_difference_error_term_quintic(oracle_mod):
+    """Leading error of the 5-point derivative on x^5 is -h^4 f^(5)/30 = -4 h^4 (closed form)."""
+    o = oracle_mod
+    nx = 40
+    pr = o.Problem(nx=nx, ny=1, x0=0.0, x1=2.0, bc_x=BC_O, hyperdiffusion=0)
+    x = pr.x0 + (np.arange(nx) + 0.5) * pr.dx
+    w = _uniform(1, nx, rho=1.0, p=10.0)
+    w[1, 0, :] = x ** 5
+    k = o.rhs(pr, w)
+    inner = slice(3, nx - 3)
+    got = -k[0, 0, inner] - 5 * x[inner] ** 4
+    np.testing.assert_allclose(got, -4.0 * pr.dx ** 4, rtol=1e-6)
+
+
+def test_y_derivative_matches_x(oracle_mod):
+    """The y operator is the x operator transposed: k_rho from m_y = P(y)."""
+    o = oracle_mod
+    ny = 32
+    pr = o.Problem(nx=1, ny=ny, y0=-1.0, y1=1.0, bc_y=BC_O, hyperdiffusion=0)
+    y = pr.y0 + (np.arange(ny) + 0.5) * pr.dy
+    P = np.polynomial.Polynomial([0.1, -0.3, 0.2, 0.05, 0.01])
+    w = _uniform(ny, 1, rho=1.0, p=10.0)
+    w[2, :, 0] = P(y)
+    k = o.rhs(pr, w)
+    inner = slice(3, ny - 3)
+    np.testing.assert_allclose(k[0, inner, 0], -P.deriv()(y)[inner], atol=1e-12)
+
+
+def _rk4_poly(z):
+    return 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+@pytest.mark.parametrize("nx,cfl", [(16, 0.9), (24, 1.6), (32, 0.5)])
+def test_rk4_amplification_sound_mode(oracle_mod, nx, cfl):
+    """One RK4 step on a linear sound mode equals the RK4 polynomial R(z) of the
+    semi-discrete eigenvalue z = -i c dt (8 sin kh - sin 2kh)/(6h) (closed form).
+
+    Run in split form (uniform background rho_b=1, e_b=p0/(gamma-1)) with an
+    amplitude of 1e-9 so the nonlinear remainder is ~1e-9 relative."""
+    o = oracle_mod
+    gamma = 5 / 3
+    amp = 1e-9
+    pr = o.Problem(nx=nx, ny=1, gamma=gamma, hyperdiffusion=0)
+    x = (np.arange(nx) + 0.5) / nx
+    kw = 2 * math.pi
+    s = np.sin(kw * x)[None, :]
+    p0 = 1.0 / gamma                          # c_s = 1
+    bg = np.zeros((4, 1, nx))
+    bg[0] = 1.0
+    bg[1] = p0 / (gamma - 1.0)
+    w = np.zeros((6, 1, nx))
+    w[0] = amp * s                            # rho'
+    w[1] = amp * s                            # m' = rho0 c_s rho'/rho0
+    w[3] = amp * s / (gamma - 1.0)            # e' = p'/(gamma-1), p' = c_s^2 rho'
+    h = 1.0 / nx
+    dt = cfl * h
+    wn = o.rk4_step(pr, w, dt, bg=bg, cmax_xy=(1.0, 1.0))
+    keff = (8 * math.sin(kw * h) - math.sin(2 * kw * h)) / (6 * h)
+    R = _rk4_poly(-1j * keff * dt)
+    # project rho' onto sin / cos:  rho'_new = A (Re R sin kx + Im R cos kx)
+    c = np.cos(kw * x)
+    re = 2.0 / nx * np.sum(wn[0, 0] * s[0]) / amp
+    im = 2.0 / nx * np.sum(wn[0, 0] * c) / amp
+    assert abs(re - R.real) < 1e-7 and abs(im - R.imag) < 1e-7, (re, im, R)
+
+
+def test_hyperdiffusion_zero_on_linear_and_quadratic(oracle_mod):
+    """Third differences vanish on linear and quadratic data => nu_HD = 0 exactly."""
+    o = oracle_mod
+    nx = 24
+    pr = o.Problem(nx=nx, ny=1, bc_x=BC_O, c_shk=0.0)
+    i = np.arange(nx, dtype=float)
+    # dyadic coefficients: every value and difference is exact in binary
+    for prof in (0.5 + i / 64.0, 0.5 + i / 64.0 + i * i / 512.0):
+        w = _uniform(1, nx, rho=1.0, p=1.0)
+        w[0, 0] = prof                        # rho varies, v = B = 0, e uniform
+        k = o.rhs(pr, w, cmax=(2.0, 2.0))
+        assert np.all(k[:, 0, 3:nx - 3] == 0.0)
+
+
+def test_hyperdiffusion_cubic_closed_form(oracle_mod):
+    """Cubic rho_i = a + b i^3: d3 = 6b on every face, d1_f = b(3f^2+3f+1); the
+    flux nu_f d1_f with nu_f = c2 dx cmax 6|b| / max(|d1_{f-1}|,|d1_f|,|d1_{f+1}|)."""
+    o = oracle_mod
+    nx, a, b, c2, cm = 30, 1.0, 2.0 ** -13, 0.07, 1.7   # b dyadic: data and differences exact
+    pr = o.Problem(nx=nx, ny=1, bc_x=BC_O, c2=(c2, 0, 0, 0, 0, 0), c_shk=0.0)
+    i = np.arange(nx, dtype=float)
+    w = _uniform(1, nx, rho=1.0, p=1.0)
+    w[0, 0] = a + b * i ** 3
+    k = o.rhs(pr, w, cmax=(cm, 0.0))
+    dx = pr.dx
+
+    def d1(f):                                 # exact difference of the cubic at face f
+        return b * (3 * f * f + 3 * f + 1)
+
+    def G(f):                                  # face flux nu_f d1_f
+        m1 = max(abs(d1(f - 1)), abs(d1(f)), abs(d1(f + 1)))
+        return c2 * dx * cm * (6 * abs(b) / m1) * d1(f)
+
+    for ii in range(4, nx - 4):
+        expect = (G(ii) - G(ii - 1)) / (dx * dx)
+        assert abs(k[0, 0, ii] - expect) <= 1e-10 * abs(expect), (ii, k[0, 0, ii], expect)
+
+
+def test_shock_viscosity_linear_compression(oracle_mod):
+    """v_x = -a x => div v = -a exactly => s = a; with B_x = q i^2 (no ideal flux
+    along x or y when v_y = B_y = 0) the diffusion is c_shk dx^2 a * 2q / dx^2."""
+    o = oracle_mod
+    nx, av, q, csh = 30, 0.8, 1e-3, 0.6
+    pr = o.Problem(nx=nx, ny=1, bc_x=BC_O, c2=(0,) * 6, c_shk=csh)
+    x = (np.arange(nx) + 0.5) * pr.dx
+    i = np.arange(nx, dtype=float)
+    w = _uniform(1, nx, rho=1.0, p=5.0)
+    w[1, 0] = -av * x                          # m_x with rho = 1
+    w[4, 0] = 0.3 + q * i * i                  # B_x
+    k = o.rhs(pr, w, cmax=(3.0, 0.0))
+    np.testing.assert_allclose(k[4, 0, 3:nx - 3], 2.0 * csh * av * q, rtol=1e-9)
+
+
+def test_signal_speed_and_dt_uniform(oracle_mod):
+    """cmax_d = |v_d| + sqrt((gamma p + B^2)/rho); dt = C min(dx/cx, dy/cy)."""
+    o = oracle_mod
+    g, rho, p, vx, vy, bx, by = 1.4, 0.7, 2.0, -0.3, 0.45, 0.2, -0.9
+    pr = o.Problem(nx=12, ny=10, x1=3.0, y1=1.0, gamma=g, courant=0.4)
+    w = _uniform(10, 12, rho=rho, vx=vx, vy=vy, p=p, bx=bx, by=by, gamma=g)
+    cx, cy = o.cmax(pr, w)
+    cf = math.sqrt((g * p + bx * bx + by * by) / rho)
+    assert abs(cx - (abs(vx) + cf)) < 1e-14 and abs(cy - (abs(vy) + cf)) < 1e-14
+    dt = o.cfl_dt(pr, cx, cy)
+    assert abs(dt - 0.4 * min(0.25 / cx, 0.1 / cy)) < 1e-16
+
+
+def test_uniform_state_stays_uniform(oracle_mod):
+    """A uniform state has zero RHS in every variable: one step leaves it bitwise equal."""
+    o = oracle_mod
+    pr = o.Problem(nx=16, ny=12)
+    w = _uniform(12, 16, rho=1.3, vx=0.2, vy=-0.4, p=0.9, bx=0.3, by=0.6)
+    w1, t, n = o.run(pr, w, max_steps=3)
+    assert n == 3 and np.array_equal(w1, w)
