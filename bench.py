@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Benchmark of the SAC-family ideal-MHD RK4 step on B300 (one JSON line).
+
+Workload (the paper's section 5.1 Orszag-Tang vortex at the sizes of its
+Table 1): a periodic N x N grid on [0,1]^2, gamma 5/3, seeded 1e-3 relative
+noise on rho and p, hyper-diffusion and shock viscosity on, FP32 perturbation
+arithmetic with FP64 time/dt.  A "step" is one classical RK4 step: the
+step-control kernel plus the four fused stage kernels, graph-replayed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--size 8000] [--impl ours|reference]
+
+Multi-GPU (torchrun): each rank advances its own independent replica of the
+grid (the single-grid step has no sharded form here: replicas only), the
+timed region is bracketed by barriers and the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PAPER_8000_HD = 8000 * 8000 * 100 / 163.60   # Table 1: 8000^2, 100 iterations with HD, 100 K20c GPUs
+# algorithmic values moved per cell in each FP32 stage (A-scheme registers, 6 fields):
+#   s1: read U0 (stencil) / write S1;  s2: read S1, U0 / write S2, A;
+#   s3: read S2, U0, A / write S3, A;   s4: read S3, A / write U0
+STAGE_VALUES_FP32 = (12, 24, 30, 18)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--size", type=int, default=8000)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other sizes and the HD-off line")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        loaded = sorted(sm)[len(sm) // 4:] or sm      # drop the idle head of the sampling
+        return {"sm_mhz": float(np.median(loaded)), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_oracle_rate(side: int, steps: int, budget_s: float = 20.0):
+    """Oracle cell-updates/s (per RK4 step) on a side x side sample of the workload."""
+    import oracle
+    from paper_1710_06423_b300 import inputs
+    oracle.build()
+    threads = os.cpu_count() or 1
+    pr = oracle.Problem(nx=side, ny=side, nthreads=threads)
+    w = inputs.orszag_tang(side, noise=1e-3, seed=20171018)
+    done, t0 = 0, time.perf_counter()
+    while done < steps:
+        w, _, n = oracle.run(pr, w, max_steps=1)
+        done += n
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return side * side * done / el, threads, done, el
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    side = 512
+    # calibrate so that warmup + steps stay within about two minutes
+    rate, threads, _, _ = cpu_oracle_rate(side, 1, budget_s=60)
+    per_step = side * side / rate
+    while side > 128 and per_step * (args.steps + args.warmup) > 120.0:
+        side //= 2
+        per_step /= 4.0
+    import oracle
+    from paper_1710_06423_b300 import inputs
+    pr = oracle.Problem(nx=side, ny=side, nthreads=threads)
+    w = inputs.orszag_tang(side, noise=1e-3, seed=20171018)
+    w, _, _ = oracle.run(pr, w, max_steps=args.warmup)
+    t0 = time.perf_counter()
+    w, _, n = oracle.run(pr, w, max_steps=args.steps)
+    el = time.perf_counter() - t0
+    value = side * side * n / el
+    sample = f"orszag-tang {side}x{side} window of the workload, {n} RK4 steps, FP64 oracle"
+    line = {
+        "impl": "reference", "metric": "cell-updates/s per RK step", "value": value,
+        "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / max(n, 1) * (args.size * args.size) / (side * side),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_8000_HD,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"orszag-tang {args.size}x{args.size} periodic, HD on, 1e-3 noise",
+                   "nx": args.size, "ny": args.size, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_device_steps(solver, steps, warmup, pg, torch):
+    """Device time of `steps` graph-replayed RK4 steps (CUDA events, max over ranks)."""
+    stream = torch.cuda.current_stream()
+    solver.steps(warmup)
+    solver.sync()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    solver.steps(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    solver.sync()
+    if pg:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def run_ours(args, ws, rank, local, pg):
+    import torch
+    from paper_1710_06423_b300 import inputs
+    from paper_1710_06423_b300.sac import FP32, Solver
+
+    torch.cuda.set_device(local)
+    n = args.size
+    cells = n * n
+    kw = dict(nx=n, ny=n, precision=FP32, device=local)
+    w0 = inputs.orszag_tang(n, noise=1e-3, seed=20171018)
+    state_bytes = w0.nbytes
+    pinned = torch.from_numpy(w0).pin_memory()
+    out_pinned = torch.empty_like(pinned).pin_memory()
+    del w0
+
+    s = Solver(**kw)
+    s.set_state(pinned.numpy(), None, 0.0)
+    with Clocks(local) as clk:
+        ms = time_device_steps(s, args.steps, args.warmup, pg, torch)
+    clocks = clk.summary()
+    value = ws * cells * args.steps / (ms * 1e-3)
+
+    # per-kernel durations (CUDA events on the context's stream) for the roofline
+    prof = s.profile_stages(max(3, min(10, args.steps)))
+    stage_ms = [float(x) for x in prof[1:]]
+    stage_bytes = [v * 4 * cells for v in STAGE_VALUES_FP32]
+    peak, peak_kind = measured_peaks()
+    achieved = sum(stage_bytes) / (sum(stage_ms) * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "stage_generic<float> (all four RK stages)",
+                "bytes_per_cell_stage": 4 * sum(STAGE_VALUES_FP32) / 4,
+                "stage_ms": stage_ms, "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "of fallback"}
+    del s
+
+    # end to end through the C ABI with host buffers: pinned FP64 state in,
+    # K synchronous sac_step calls (each reads dt and status back), state out
+    s2 = Solver(**kw)
+    s2.set_state(pinned.numpy(), None, 0.0)
+    s2.steps(args.warmup)
+    s2.sync()
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    s2.set_state(pinned.numpy(), None, 0.0)
+    for _ in range(args.steps):
+        s2.step(0.0)
+    s2.get_state_into(out_pinned.numpy())
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    scal = 96   # device scalar record read back by every synchronous step
+    e2e = {"value": ws * cells * args.steps / e2e_s, "unit": "cell-updates/s",
+           "h2d_bytes_per_step": state_bytes / args.steps,
+           "d2h_bytes_per_step": state_bytes / args.steps + scal,
+           "how": "sac_set_state(pinned FP64 host) + K x sac_step (dt/status read back) + sac_get_state(pinned FP64 host)"}
+    del s2
+
+    extra = {}
+    if not args.no_extra:
+        # HD off at the same size (the paper's second Table 1 column)
+        s3 = Solver(**kw, hyperdiffusion=0)
+        s3.set_state(pinned.numpy(), None, 0.0)
+        ms3 = time_device_steps(s3, args.steps, args.warmup, pg, torch)
+        extra["hd_off"] = {"value": ws * cells * args.steps / (ms3 * 1e-3), "ms_per_step": ms3 / args.steps}
+        del s3
+        for m in (2044, 4000):
+            if m >= n:
+                continue
+            sm_ = Solver(nx=m, ny=m, precision=FP32, device=local)
+            sm_.set_state(inputs.orszag_tang(m, noise=1e-3, seed=20171018), None, 0.0)
+            msm = time_device_steps(sm_, args.steps, args.warmup, pg, torch)
+            extra[f"ot{m}"] = {"value": ws * m * m * args.steps / (msm * 1e-3), "ms_per_step": msm / args.steps}
+            del sm_
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, threads, done, el = cpu_oracle_rate(1000, 30, budget_s=20.0)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+               "sample": f"orszag-tang 1000x1000 window of the workload, {done} RK4 steps in {el:.1f} s (FP64 oracle, OpenMP over rows)"}
+
+    line = {
+        "metric": "cell-updates/s per RK step", "value": value, "unit": "cell-updates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_8000_HD,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"orszag-tang {n}x{n} periodic, HD on, 1e-3 noise on rho and p, FP32 perturbations",
+                   "nx": n, "ny": n, "rk": "classical RK4, graph-replayed steps",
+                   "l2": "inputs larger than L2 (1.5 GB per RK register at 8000^2)",
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "vs_baseline_basis": "paper Table 1, 8000^2 with HD, 100 iterations on 100 K20c: 3.91e7 cell-steps/s"},
+        "cell_stage_rate": 4 * value,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 5 * args.steps,
+        "clocks": clocks,
+        "extra": extra,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, ws, rank)
+        else:
+            run_ours(args, ws, rank, local, pg)
+    finally:
+        if pg:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

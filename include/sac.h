@@ -1,0 +1,174 @@
+/*
+ * sac.h -- C ABI of the B300 SAC-family 2D ideal-MHD step (arXiv 1710.06423).
+ *
+ * The library advances the 2D ideal-MHD equations of section 2 of the paper
+ * (mass, momentum, energy and induction in conservative form, total pressure
+ * p_t = p_k + B^2/2, kinetic pressure p_k = (gamma-1)(e - rho v^2/2 - B^2/2),
+ * units with mu0 = 1) in perturbation/background split form, with the
+ * section 2 numerics: fourth-order central differences of the fluxes,
+ * hyper-diffusion / hyper-resistivity scaled by the maximum wave speed plus a
+ * compression-activated shock viscosity, and classical fourth-order
+ * Runge-Kutta stepping whose CFL step comes from a grid-wide maximum of the
+ * signal speed.  Every step runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SAC_OK (0) or a negative SAC_ERR_* code; sac_last_error()
+ *     gives a one-line description of the last failure of a context.
+ *   - State arrays are conserved PERTURBATION variables, field-major,
+ *     w[f][j][i] with f in (rho~, m_x, m_y, e~, B~_x, B~_y), j the row (y) and
+ *     i the column (x, fastest), nx*ny cells per field, no ghost cells.
+ *     Background arrays are bg[f][j][i] with f in (rho_b, e_b, B_bx, B_by).
+ *     With no background the perturbations are the full variables.
+ *   - Host buffers belong to the caller; the library copies in and out and
+ *     keeps no host pointer after the call returns.  Device memory of a
+ *     context belongs to the context and is released by sac_free().
+ *   - A context is bound to one device and one CUDA stream (params.stream,
+ *     NULL = the legacy default stream).  Calls on one context are not thread
+ *     safe.  Calls marked ASYNC only enqueue work on that stream.
+ *   - Errors found on the device (non-finite state or step) are recorded in
+ *     the context and reported by the next synchronising call
+ *     (sac_run_to, sac_step, sac_get_state*, sac_dt, sac_time, sac_sync).
+ *     After SAC_ERR_NONFINITE the state is left as computed, for inspection,
+ *     and further steps are skipped until sac_set_state*.
+ */
+#ifndef SAC_H
+#define SAC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sac_ctx sac_ctx;
+
+enum {
+    SAC_OK = 0,
+    SAC_ERR_ARG = -1,        /* invalid argument or parameter */
+    SAC_ERR_STATE = -2,      /* call out of order (e.g. step before set_state) */
+    SAC_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    SAC_ERR_OOM = -4,        /* device allocation failed */
+    SAC_ERR_NONFINITE = -5,  /* the state or the CFL step became NaN/Inf or dt <= 0 */
+    SAC_ERR_TIMEOUT = -6     /* a bounded device wait gave up */
+};
+
+enum { SAC_BC_PERIODIC = 0, SAC_BC_FIXED = 1, SAC_BC_OUTFLOW = 2 };
+enum { SAC_FP64 = 0, SAC_FP32 = 1 };
+
+/*
+ * Run parameters (section 2 numerics; section 5 test problems).
+ *   nx, ny            interior cells (ny = 1 for a 1D run); 1 <= nx, ny <= 65536
+ *   x0,x1,y0,y1       domain; cell-centred grid, dx = (x1-x0)/nx, dy = (y1-y0)/ny
+ *   gamma             adiabatic index (> 1)
+ *   courant           CFL number C of dt = C min(dx/cmax_x, dy/cmax_y)
+ *   bc_x, bc_y        SAC_BC_*: periodic = wrapped interior; outflow = nearest
+ *                     interior cell of the current stage; fixed = nearest
+ *                     interior cell of the state given to sac_set_state, held
+ *   precision         SAC_FP64: all arithmetic in FP64, same operation order as
+ *                     the FP64 oracle.  SAC_FP32: stencil arithmetic and storage
+ *                     in FP32 on the perturbations; time, dt and the
+ *                     conservation sums in FP64.
+ *   hyperdiffusion    1: hyper-diffusion and shock viscosity on; 0: ideal fluxes
+ *   c2[6]             hyper-diffusion coefficient per conserved variable
+ *   c_shk             shock-viscosity coefficient
+ *   has_background    1: a static background (bg) is supplied to sac_set_state
+ *   device            CUDA device ordinal
+ *   stream            cudaStream_t the context enqueues on (NULL = default)
+ */
+typedef struct {
+    int nx, ny;
+    double x0, x1, y0, y1;
+    double gamma, courant;
+    int bc_x, bc_y;
+    int precision;
+    int hyperdiffusion;
+    double c2[6];
+    double c_shk;
+    int has_background;
+    int device;
+    void *stream;
+} sac_params;
+
+/* Fill *p with defaults: 64x64 periodic on [0,1]^2, gamma 5/3, C 0.3, FP64,
+ * HD on, c2 = (0.02, 0.1, 0.1, 0.02, 0.02, 0.02), c_shk = 0.5, no background,
+ * device 0, default stream. */
+void sac_default_params(sac_params *p);
+
+/* Validate *p, allocate the device buffers of one run and return a context in
+ * *out (NULL on failure).  Errors: SAC_ERR_ARG, SAC_ERR_OOM, SAC_ERR_CUDA. */
+int sac_init(const sac_params *p, sac_ctx **out);
+
+/* Release every device and host resource of c (NULL is ignored). */
+void sac_free(sac_ctx *c);
+
+/* Text of the last error recorded in c ("" if none); static string for NULL. */
+const char *sac_last_error(const sac_ctx *c);
+
+/* Name of a status code. */
+const char *sac_status_string(int code);
+
+/*
+ * Load the state at time t from HOST FP64 arrays: w [6][ny][nx] (required),
+ * bg [4][ny][nx] (required iff has_background, else must be NULL).  Fills the
+ * ghost cells (fixed sides are taken from this state and then held), resets
+ * the step counter and error status and computes the signal speeds of this
+ * state, so sac_dt() is valid.  Synchronous.
+ */
+int sac_set_state(sac_ctx *c, const double *w, const double *bg, double t);
+
+/* Copy the current state to HOST FP64 w [6][ny][nx] and its time to *t (either
+ * may be NULL).  Synchronous; reports a pending device error. */
+int sac_get_state(sac_ctx *c, double *w, double *t);
+
+/* As sac_set_state / sac_get_state with DEVICE arrays of the context's
+ * precision (double for SAC_FP64, float for SAC_FP32), same packed layout, on
+ * the context's device.  ASYNC on the context's stream (sac_get_state_dev
+ * returns *t only after synchronising when t != NULL). */
+int sac_set_state_dev(sac_ctx *c, const void *w_dev, const void *bg_dev, double t);
+int sac_get_state_dev(sac_ctx *c, void *w_dev, double *t);
+
+/*
+ * One classical RK4 step (section 2).  dt > 0: take that step; dt <= 0: take
+ * the CFL step C min(dx/cmax_x, dy/cmax_y) of the current state.  The signal
+ * speeds of the step-start state scale the hyper-diffusion of all four
+ * stages.  *dt_taken (may be NULL) receives the step size.  Synchronous.
+ */
+int sac_step(sac_ctx *c, double dt, double *dt_taken);
+
+/* nsteps CFL steps.  ASYNC: no host synchronisation; errors surface at the
+ * next synchronising call.  Steps are CUDA-graph replays after the first. */
+int sac_steps(sac_ctx *c, long nsteps);
+
+/*
+ * Advance with CFL steps until t_end (the last step is clipped so that the
+ * time lands exactly on t_end) or until max_steps steps (max_steps < 0: no
+ * limit).  *steps_taken (may be NULL) receives the number of steps.  The host
+ * polls the device every few steps; steps after t_end are skipped on the device.
+ */
+int sac_run_to(sac_ctx *c, double t_end, long max_steps, long *steps_taken);
+
+/* CFL step the next sac_step(c, 0, ...) would take.  Synchronous. */
+int sac_dt(sac_ctx *c, double *dt);
+
+/* Time and steps taken since the last set_state.  Synchronous. */
+int sac_time(sac_ctx *c, double *t, long *steps);
+
+/* Maximum signal speeds |v_d| + c_fast of the current state.  Synchronous. */
+int sac_cmax(sac_ctx *c, double *cmax_x, double *cmax_y);
+
+/* Conservation sums over the interior of the current state, accumulated in
+ * FP64 on the device: sums[f] = sum_ij w[f][j][i] for the six fields.
+ * Synchronous. */
+int sac_sums(sac_ctx *c, double sums[6]);
+
+/* Per-kernel timing: nsteps CFL steps launched kernel by kernel (no graph)
+ * with CUDA events around every launch on the context's stream.  ms[0] is
+ * the mean duration of the step-control kernel, ms[1..4] those of the RK
+ * stage 1..4 kernels, in milliseconds.  Advances the state; synchronous. */
+int sac_profile_stages(sac_ctx *c, int nsteps, double ms[5]);
+
+/* Wait for the context's stream and report a pending device error. */
+int sac_sync(sac_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAC_H */

@@ -1,0 +1,64 @@
+// kernels_fp64.cu -- FP64 instantiation of the fused RK stage kernel.
+// Built with --fmad=false (no FMA contraction) and IEEE division and square
+// root so that every value follows the FP64 reference operation order.
+#include "stage_generic.cuh"
+
+namespace sac {
+namespace {
+constexpr int TX = 32, TY = 16;
+
+template <int S, bool BG, bool HD>
+cudaError_t set_attr()
+{
+    return cudaFuncSetAttribute(stage_generic<double, S, BG, HD, TX, TY>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)GenericSmem<double, TX, TY, BG>::bytes);
+}
+
+template <int S, bool BG, bool HD>
+cudaError_t launch(const StageArgs<double>& a, cudaStream_t s)
+{
+    dim3 grid((a.L.nx + TX - 1) / TX, (a.L.ny + TY - 1) / TY);
+    stage_generic<double, S, BG, HD, TX, TY>
+        <<<grid, TX * TY / 2, GenericSmem<double, TX, TY, BG>::bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool BG, bool HD>
+cudaError_t by_stage(const StageArgs<double>& a, int stage, cudaStream_t s)
+{
+    switch (stage) {
+        case 1: return launch<1, BG, HD>(a, s);
+        case 2: return launch<2, BG, HD>(a, s);
+        case 3: return launch<3, BG, HD>(a, s);
+        default: return launch<4, BG, HD>(a, s);
+    }
+}
+
+template <bool BG, bool HD>
+cudaError_t attr_all()
+{
+    cudaError_t e = set_attr<1, BG, HD>();
+    if (e == cudaSuccess) e = set_attr<2, BG, HD>();
+    if (e == cudaSuccess) e = set_attr<3, BG, HD>();
+    if (e == cudaSuccess) e = set_attr<4, BG, HD>();
+    return e;
+}
+}  // namespace
+
+cudaError_t prepare_stage_fp64()
+{
+    cudaError_t e = attr_all<false, false>();
+    if (e == cudaSuccess) e = attr_all<false, true>();
+    if (e == cudaSuccess) e = attr_all<true, false>();
+    if (e == cudaSuccess) e = attr_all<true, true>();
+    return e;
+}
+
+cudaError_t launch_stage_fp64(const StageArgs<double>& a, int stage, bool hd, bool bg, cudaStream_t s)
+{
+    if (bg) return hd ? by_stage<true, true>(a, stage, s) : by_stage<true, false>(a, stage, s);
+    return hd ? by_stage<false, true>(a, stage, s) : by_stage<false, false>(a, stage, s);
+}
+
+}  // namespace sac

@@ -1,0 +1,743 @@
+// sac_engine.cu -- host engine and C ABI (include/sac.h) of the B300 SAC-family
+// ideal-MHD step: context and device buffers, state import/export with ghost
+// filling, the per-step control kernel, CUDA-graph replay of RK steps, FP64
+// conservation sums and error reporting.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+
+#include "../../include/sac.h"
+#include "sac_internal.cuh"
+#include "speed.cuh"
+
+using namespace sac;
+
+namespace {
+
+constexpr int kChunk = 16;          // steps per captured multi-step graph
+constexpr int kSumBlocks = 296;     // 2 x 148 SMs
+
+__host__ __device__ inline int wrapi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+__host__ __device__ inline int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+// interior index read by padded index i (ghosts included) under the
+// set-up rule: periodic wraps, fixed and outflow take the nearest cell
+__device__ inline int src_index(int i, int n, int bc) {
+    return bc == BC_PERIODIC ? wrapi(i, n) : clampi(i, n);
+}
+
+// ---- state import / export --------------------------------------------------
+// Packed [nf][ny][nx] (double or T) -> ghost-padded T, every ghost filled by
+// the set-up rule (fixed sides become the held values).
+template <typename T, typename S>
+__global__ void import_kernel(const S* __restrict__ src, T* __restrict__ dst, Layout L, int nf,
+                              int bc_x, int bc_y)
+{
+    const long long ex = L.nx + 2 * GY, ey = L.ny + 2 * GY;
+    const long long total = (long long)nf * ex * ey;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total;
+         v += (long long)gridDim.x * blockDim.x) {
+        int f = (int)(v / (ex * ey));
+        long long r = v - (long long)f * ex * ey;
+        int j = (int)(r / ex) - GY, i = (int)(r % ex) - GY;
+        int si = src_index(i, L.nx, bc_x), sj = src_index(j, L.ny, bc_y);
+        dst[(long long)f * L.fstride + L.at(i, j)] = (T)src[((long long)f * L.ny + sj) * L.nx + si];
+    }
+}
+
+template <typename T, typename D>
+__global__ void export_kernel(const T* __restrict__ src, D* __restrict__ dst, Layout L, int nf)
+{
+    const long long n = (long long)L.nx * L.ny, total = n * nf;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total;
+         v += (long long)gridDim.x * blockDim.x) {
+        int f = (int)(v / n);
+        long long r = v - (long long)f * n;
+        int j = (int)(r / L.nx), i = (int)(r % L.nx);
+        dst[v] = (D)src[(long long)f * L.fstride + L.at(i, j)];
+    }
+}
+
+// ---- signal speed of the current state (section 2: the maximum wave speed
+// sets the hyper-viscosity and the step) ---------------------------------------
+template <typename T, bool BG>
+__global__ void cmax_kernel(const T* __restrict__ w, const T* __restrict__ bg, Layout L, double gamma,
+                            DevScalars* sc)
+{
+    __shared__ unsigned long long red[2][32];
+    unsigned long long m[2] = {0ull, 0ull};
+    const long long n = (long long)L.nx * L.ny;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        int j = (int)(v / L.nx), i = (int)(v % L.nx);
+        long long g = L.at(i, j);
+        const long long S = L.fstride;
+        T sx, sy;
+        if (BG)
+            signal_speeds<T, true>(w[g], w[S + g], w[2 * S + g], w[3 * S + g], w[4 * S + g], w[5 * S + g],
+                                   bg[g], bg[S + g], bg[2 * S + g], bg[3 * S + g], (T)gamma, sx, sy);
+        else
+            signal_speeds<T, false>(w[g], w[S + g], w[2 * S + g], w[3 * S + g], w[4 * S + g], w[5 * S + g],
+                                    (T)0, (T)0, (T)0, (T)0, (T)gamma, sx, sy);
+        unsigned long long a = speed_key(sx), b = speed_key(sy);
+        m[0] = a > m[0] ? a : m[0];
+        m[1] = b > m[1] ? b : m[1];
+    }
+    for (int d = 0; d < 2; ++d) {
+        unsigned long long x = m[d];
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = y > x ? y : x;
+        }
+        if ((threadIdx.x & 31) == 0) red[d][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        unsigned long long x = 0ull;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) x = red[threadIdx.x][k] > x ? red[threadIdx.x][k] : x;
+        atomicMax(&sc->cmax_bits[threadIdx.x], x);
+    }
+}
+
+// ---- step control -------------------------------------------------------------
+__global__ void reset_kernel(DevScalars* sc, double t)
+{
+    sc->t = t; sc->t_end = CUDART_INF; sc->dt = 0.0; sc->fixed_dt = 0.0;
+    sc->cmax_step[0] = sc->cmax_step[1] = 0.0;
+    sc->cmax_bits[0] = sc->cmax_bits[1] = 0ull;
+    sc->steps = 0; sc->skip = 0; sc->done = 0; sc->status = ST_OK;
+}
+
+__global__ void control_kernel(DevScalars* sc, double t_end)
+{
+    sc->t_end = t_end;
+    sc->done = (sc->t >= t_end) ? 1 : 0;
+}
+
+__device__ inline double decode_speed(unsigned long long b, int fp32)
+{
+    return fp32 ? (double)__uint_as_float((unsigned)b) : __longlong_as_double((long long)b);
+}
+
+// Start one RK step: CFL step from the signal speeds of the current state
+// (dt = C min(dx/cmax_x, dy/cmax_y)), clipped to land on t_end; those speeds
+// scale the hyper-diffusion of the step's four stages.
+__global__ void begin_step_kernel(DevScalars* sc, double dx, double dy, double courant, int fp32,
+                                  double dt_override)
+{
+    if (sc->status != ST_OK || sc->done) { sc->skip = 1; return; }
+    double cx = decode_speed(sc->cmax_bits[0], fp32), cy = decode_speed(sc->cmax_bits[1], fp32);
+    double dt;
+    if (dt_override > 0.0) dt = dt_override;
+    else if (sc->fixed_dt > 0.0) dt = sc->fixed_dt;
+    else { double tx = dx / cx, ty = dy / cy; dt = courant * fmin(tx, ty); }
+    if (!(dt > 0.0) || !isfinite(dt) || !isfinite(cx) || !isfinite(cy)) {
+        sc->status = ST_ERR_NONFINITE; sc->skip = 1; return;
+    }
+    int last = 0;
+    if (sc->t + dt >= sc->t_end) { dt = sc->t_end - sc->t; last = 1; }
+    sc->dt = dt;
+    sc->cmax_step[0] = cx; sc->cmax_step[1] = cy;
+    sc->t = last ? sc->t_end : sc->t + dt;
+    sc->steps += 1;
+    if (last) sc->done = 1;
+    sc->cmax_bits[0] = sc->cmax_bits[1] = 0ull;
+    sc->skip = 0;
+}
+
+// ---- FP64 conservation sums (deterministic two-pass) ---------------------------
+template <typename T>
+__global__ void sums_partial_kernel(const T* __restrict__ w, Layout L, double* __restrict__ part)
+{
+    __shared__ double red[NF][32];
+    double acc[NF] = {0, 0, 0, 0, 0, 0};
+    const long long n = (long long)L.nx * L.ny;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        int j = (int)(v / L.nx), i = (int)(v % L.nx);
+        long long g = L.at(i, j);
+        for (int f = 0; f < NF; ++f) acc[f] += (double)w[(long long)f * L.fstride + g];
+    }
+    for (int f = 0; f < NF; ++f) {
+        double x = acc[f];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) red[f][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NF) {
+        double x = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) x += red[threadIdx.x][k];
+        part[blockIdx.x * NF + threadIdx.x] = x;
+    }
+}
+
+__global__ void sums_final_kernel(const double* __restrict__ part, int nb, double* __restrict__ out)
+{
+    if (threadIdx.x < NF) {
+        double x = 0.0;
+        for (int b = 0; b < nb; ++b) x += part[b * NF + threadIdx.x];
+        out[threadIdx.x] = x;
+    }
+}
+
+int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    return (int)(g < 1 ? 1 : (g > 148 * 16 ? 148 * 16 : g));
+}
+
+}  // namespace
+
+// ============================================================================
+struct sac_ctx {
+    sac_params p;
+    Layout L;
+    bool fp32 = false;
+    size_t esz = 8;                 // element size of the working precision
+    cudaStream_t stream = nullptr;  // user stream (may be the legacy default)
+    cudaStream_t cap = nullptr;     // private stream used only for graph capture
+    void* u0 = nullptr;
+    void* sa = nullptr;
+    void* sb = nullptr;
+    void* acc = nullptr;
+    void* bg = nullptr;
+    DevScalars* sc = nullptr;
+    DevScalars* hsc = nullptr;      // pinned host mirror
+    double* staging = nullptr;      // packed FP64 [6][ny][nx] for host transfers
+    double* part = nullptr;         // [kSumBlocks][6] partial sums + [6] result
+    cudaGraphExec_t g1 = nullptr;   // one CFL step
+    cudaGraphExec_t gN = nullptr;   // kChunk CFL steps
+    bool have_state = false;
+    double t_end_host = std::numeric_limits<double>::infinity();
+    char err[512] = {0};
+};
+
+static const char* kStatusNames[] = {"SAC_OK", "SAC_ERR_ARG", "SAC_ERR_STATE", "SAC_ERR_CUDA",
+                                     "SAC_ERR_OOM", "SAC_ERR_NONFINITE", "SAC_ERR_TIMEOUT"};
+
+static int fail(sac_ctx* c, int code, const char* fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? SAC_ERR_OOM : SAC_ERR_CUDA,  \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                  \
+    } while (0)
+
+static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+// Enqueue the kernel of one RK stage (1..4).
+static cudaError_t enqueue_stage_one(sac_ctx* c, cudaStream_t s, int stage)
+{
+    const bool hd = c->p.hyperdiffusion != 0, bgp = c->p.has_background != 0;
+    // stage input / output buffers (ping-pong SA, SB; U0 written by stage 4)
+    void* sin = stage == 1 ? c->u0 : (stage == 2 ? c->sa : (stage == 3 ? c->sb : c->sa));
+    void* sout = stage == 1 ? c->sa : (stage == 2 ? c->sb : (stage == 3 ? c->sa : c->u0));
+    const double dx = (c->p.x1 - c->p.x0) / c->p.nx, dy = (c->p.y1 - c->p.y0) / c->p.ny;
+    if (c->fp32) {
+        StageArgs<float> a;
+        a.sin = (const float*)sin; a.u0 = (const float*)c->u0; a.acc = (float*)c->acc;
+        a.sout = (float*)sout; a.bg = (const float*)c->bg; a.sc = c->sc; a.L = c->L;
+        a.dx = dx; a.dy = dy; a.gamma = c->p.gamma;
+        for (int f = 0; f < NF; ++f) a.c2[f] = c->p.c2[f];
+        a.c_shk = c->p.c_shk; a.bc_x = c->p.bc_x; a.bc_y = c->p.bc_y;
+        return launch_stage_fp32(a, stage, hd, bgp, s);
+    }
+    StageArgs<double> a;
+    a.sin = (const double*)sin; a.u0 = (const double*)c->u0; a.acc = (double*)c->acc;
+    a.sout = (double*)sout; a.bg = (const double*)c->bg; a.sc = c->sc; a.L = c->L;
+    a.dx = dx; a.dy = dy; a.gamma = c->p.gamma;
+    for (int f = 0; f < NF; ++f) a.c2[f] = c->p.c2[f];
+    a.c_shk = c->p.c_shk; a.bc_x = c->p.bc_x; a.bc_y = c->p.bc_y;
+    return launch_stage_fp64(a, stage, hd, bgp, s);
+}
+
+// Enqueue the four stage kernels of one step (after begin_step).
+static cudaError_t enqueue_stages(sac_ctx* c, cudaStream_t s)
+{
+    for (int stage = 1; stage <= 4; ++stage) {
+        cudaError_t e = enqueue_stage_one(c, s, stage);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t enqueue_step(sac_ctx* c, cudaStream_t s, double dt_override)
+{
+    const double dx = (c->p.x1 - c->p.x0) / c->p.nx, dy = (c->p.y1 - c->p.y0) / c->p.ny;
+    begin_step_kernel<<<1, 1, 0, s>>>(c->sc, dx, dy, c->p.courant, c->fp32 ? 1 : 0, dt_override);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return enqueue_stages(c, s);
+}
+
+static cudaError_t capture(sac_ctx* c, int nsteps, cudaGraphExec_t* out)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = enqueue_step(c, c->cap, 0.0);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+static int launch_cmax(sac_ctx* c)
+{
+    const int block = 256;
+    long long n = (long long)c->p.nx * c->p.ny;
+    int grid = grid_for(n, block);
+    // the running maximum was zeroed by reset_kernel; reduce the current state into it
+    if (c->fp32) {
+        if (c->p.has_background)
+            cmax_kernel<float, true><<<grid, block, 0, c->stream>>>((const float*)c->u0, (const float*)c->bg, c->L, c->p.gamma, c->sc);
+        else
+            cmax_kernel<float, false><<<grid, block, 0, c->stream>>>((const float*)c->u0, nullptr, c->L, c->p.gamma, c->sc);
+    } else {
+        if (c->p.has_background)
+            cmax_kernel<double, true><<<grid, block, 0, c->stream>>>((const double*)c->u0, (const double*)c->bg, c->L, c->p.gamma, c->sc);
+        else
+            cmax_kernel<double, false><<<grid, block, 0, c->stream>>>((const double*)c->u0, nullptr, c->L, c->p.gamma, c->sc);
+    }
+    CK(cudaGetLastError());
+    return SAC_OK;
+}
+
+// Read the device scalars (synchronises the context's stream).
+static int pull_scalars(sac_ctx* c)
+{
+    CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->hsc->status == ST_ERR_NONFINITE)
+        return fail(c, SAC_ERR_NONFINITE, "non-finite state or step after %lld steps (t = %.17g)",
+                    (long long)c->hsc->steps, c->hsc->t);
+    if (c->hsc->status != ST_OK)
+        return fail(c, SAC_ERR_TIMEOUT, "device status %d", c->hsc->status);
+    return SAC_OK;
+}
+
+static int set_t_end(sac_ctx* c, double t_end)
+{
+    control_kernel<<<1, 1, 0, c->stream>>>(c->sc, t_end);
+    CK(cudaGetLastError());
+    c->t_end_host = t_end;
+    return SAC_OK;
+}
+
+static int finish_set_state(sac_ctx* c, double t)
+{
+    // every stage buffer carries the same ghosts (fixed sides are never rewritten)
+    const size_t bytes = NF * (size_t)c->L.fstride * c->esz;
+    CK(cudaMemcpyAsync(c->sa, c->u0, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->sb, c->u0, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    reset_kernel<<<1, 1, 0, c->stream>>>(c->sc, t);
+    CK(cudaGetLastError());
+    c->t_end_host = std::numeric_limits<double>::infinity();
+    int rc = launch_cmax(c);
+    if (rc != SAC_OK) return rc;
+    c->have_state = true;
+    return SAC_OK;
+}
+
+template <typename S>
+static int import_fields(sac_ctx* c, const S* src, void* dst, int nf, bool background)
+{
+    const int block = 256;
+    long long n = (long long)nf * (c->p.nx + 2 * GY) * (c->p.ny + 2 * GY);
+    int bcx = c->p.bc_x, bcy = c->p.bc_y;
+    (void)background;
+    if (c->fp32)
+        import_kernel<float, S><<<grid_for(n, block), block, 0, c->stream>>>(src, (float*)dst, c->L, nf, bcx, bcy);
+    else
+        import_kernel<double, S><<<grid_for(n, block), block, 0, c->stream>>>(src, (double*)dst, c->L, nf, bcx, bcy);
+    CK(cudaGetLastError());
+    return SAC_OK;
+}
+
+// ============================================================================
+extern "C" {
+
+void sac_default_params(sac_params* p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->nx = 64; p->ny = 64;
+    p->x0 = 0.0; p->x1 = 1.0; p->y0 = 0.0; p->y1 = 1.0;
+    p->gamma = 5.0 / 3.0; p->courant = 0.3;
+    p->bc_x = SAC_BC_PERIODIC; p->bc_y = SAC_BC_PERIODIC;
+    p->precision = SAC_FP64;
+    p->hyperdiffusion = 1;
+    const double c2[6] = {0.02, 0.1, 0.1, 0.02, 0.02, 0.02};
+    for (int f = 0; f < 6; ++f) p->c2[f] = c2[f];
+    p->c_shk = 0.5;
+    p->has_background = 0;
+    p->device = 0;
+    p->stream = nullptr;
+}
+
+const char* sac_status_string(int code)
+{
+    if (code > 0 || code < -6) return "SAC_UNKNOWN";
+    return kStatusNames[-code];
+}
+
+const char* sac_last_error(const sac_ctx* c) { return c ? c->err : "no context"; }
+
+void sac_free(sac_ctx* c)
+{
+    if (!c) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->p.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->g1) cudaGraphExecDestroy(c->g1);
+    if (c->gN) cudaGraphExecDestroy(c->gN);
+    cudaFree(c->u0); cudaFree(c->sa); cudaFree(c->sb); cudaFree(c->acc); cudaFree(c->bg);
+    cudaFree(c->sc); cudaFree(c->staging); cudaFree(c->part);
+    if (c->hsc) cudaFreeHost(c->hsc);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    cudaSetDevice(prev);
+    delete c;
+}
+
+int sac_init(const sac_params* p, sac_ctx** out)
+{
+    if (out) *out = nullptr;
+    sac_ctx* c = nullptr;
+    if (!p || !out) return SAC_ERR_ARG;
+    if (p->nx < 1 || p->ny < 1 || p->nx > 65536 || p->ny > 65536) return SAC_ERR_ARG;
+    if (!(p->x1 > p->x0) || !(p->y1 > p->y0) || !(p->gamma > 1.0) || !(p->courant > 0.0)) return SAC_ERR_ARG;
+    if (p->bc_x < 0 || p->bc_x > 2 || p->bc_y < 0 || p->bc_y > 2) return SAC_ERR_ARG;
+    if (p->precision != SAC_FP64 && p->precision != SAC_FP32) return SAC_ERR_ARG;
+    for (int f = 0; f < 6; ++f) if (!(p->c2[f] >= 0.0)) return SAC_ERR_ARG;
+    if (!(p->c_shk >= 0.0)) return SAC_ERR_ARG;
+
+    c = new sac_ctx();
+    c->p = *p;
+    c->fp32 = p->precision == SAC_FP32;
+    c->esz = c->fp32 ? 4 : 8;
+    c->stream = (cudaStream_t)p->stream;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device < 0 || p->device >= ndev) {
+        fail(c, SAC_ERR_ARG, "device %d not available", p->device);
+        sac_free(c);
+        return SAC_ERR_ARG;
+    }
+    int rc = SAC_OK;
+    do {
+        cudaError_t e = cudaSetDevice(p->device);
+        if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e)); break; }
+        Layout& L = c->L;
+        L.nx = p->nx; L.ny = p->ny;
+        L.pitch = (int)round_up(round_up(p->nx, TILE_X_MAX) + 2 * GX, 32);
+        L.rows = (int)(round_up(p->ny, TILE_Y_MAX) + 2 * GY);
+        L.fstride = round_up((long long)L.pitch * L.rows, 64);
+        const size_t fbytes = (size_t)L.fstride * c->esz;
+        void** bufs[4] = {&c->u0, &c->sa, &c->sb, &c->acc};
+        for (int b = 0; b < 4 && rc == SAC_OK; ++b) {
+            e = cudaMalloc(bufs[b], NF * fbytes);
+            if (e != cudaSuccess) rc = fail(c, SAC_ERR_OOM, "cudaMalloc of %zu bytes: %s", NF * fbytes, cudaGetErrorString(e));
+            else e = cudaMemset(*bufs[b], 0, NF * fbytes);
+        }
+        if (rc != SAC_OK) break;
+        if (p->has_background) {
+            e = cudaMalloc(&c->bg, NBG * fbytes);
+            if (e != cudaSuccess) { rc = fail(c, SAC_ERR_OOM, "background alloc: %s", cudaGetErrorString(e)); break; }
+            cudaMemset(c->bg, 0, NBG * fbytes);
+        }
+        if (cudaMalloc(&c->sc, sizeof(DevScalars)) != cudaSuccess ||
+            cudaMallocHost(&c->hsc, sizeof(DevScalars)) != cudaSuccess ||
+            cudaMalloc(&c->part, (kSumBlocks + 1) * NF * sizeof(double)) != cudaSuccess) {
+            rc = fail(c, SAC_ERR_OOM, "scalar allocation failed");
+            break;
+        }
+        e = prepare_stage_fp64();
+        if (e == cudaSuccess) e = prepare_stage_fp32();
+        if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e)); break; }
+        e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "stream: %s", cudaGetErrorString(e)); break; }
+        reset_kernel<<<1, 1, 0, c->stream>>>(c->sc, 0.0);
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "init: %s", cudaGetErrorString(e)); break; }
+    } while (0);
+    if (rc != SAC_OK) {
+        sac_free(c);
+        return rc;
+    }
+    *out = c;
+    return SAC_OK;
+}
+
+int sac_set_state(sac_ctx* c, const double* w, const double* bg, double t)
+{
+    if (!c || !w) return fail(c, SAC_ERR_ARG, "null state");
+    if ((bg != nullptr) != (c->p.has_background != 0))
+        return fail(c, SAC_ERR_ARG, "background must be given iff has_background");
+    if (!std::isfinite(t)) return fail(c, SAC_ERR_ARG, "time must be finite");
+    CK(cudaSetDevice(c->p.device));
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    if (!c->staging) CK(cudaMalloc(&c->staging, NF * n * sizeof(double)));
+    if (bg) {
+        CK(cudaMemcpyAsync(c->staging, bg, NBG * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        int rc = import_fields<double>(c, c->staging, c->bg, NBG, true);
+        if (rc != SAC_OK) return rc;
+    }
+    CK(cudaMemcpyAsync(c->staging, w, NF * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    int rc = import_fields<double>(c, c->staging, c->u0, NF, false);
+    if (rc != SAC_OK) return rc;
+    rc = finish_set_state(c, t);
+    if (rc != SAC_OK) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    return SAC_OK;
+}
+
+int sac_set_state_dev(sac_ctx* c, const void* w, const void* bg, double t)
+{
+    if (!c || !w) return fail(c, SAC_ERR_ARG, "null state");
+    if ((bg != nullptr) != (c->p.has_background != 0))
+        return fail(c, SAC_ERR_ARG, "background must be given iff has_background");
+    if (!std::isfinite(t)) return fail(c, SAC_ERR_ARG, "time must be finite");
+    CK(cudaSetDevice(c->p.device));
+    int rc;
+    if (c->fp32) {
+        if (bg && (rc = import_fields<float>(c, (const float*)bg, c->bg, NBG, true)) != SAC_OK) return rc;
+        if ((rc = import_fields<float>(c, (const float*)w, c->u0, NF, false)) != SAC_OK) return rc;
+    } else {
+        if (bg && (rc = import_fields<double>(c, (const double*)bg, c->bg, NBG, true)) != SAC_OK) return rc;
+        if ((rc = import_fields<double>(c, (const double*)w, c->u0, NF, false)) != SAC_OK) return rc;
+    }
+    return finish_set_state(c, t);
+}
+
+int sac_get_state(sac_ctx* c, double* w, double* t)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
+    CK(cudaSetDevice(c->p.device));
+    if (w) {
+        const size_t n = (size_t)c->p.nx * c->p.ny;
+        if (!c->staging) CK(cudaMalloc(&c->staging, NF * n * sizeof(double)));
+        const int block = 256;
+        int grid = grid_for((long long)NF * n, block);
+        if (c->fp32)
+            export_kernel<float, double><<<grid, block, 0, c->stream>>>((const float*)c->u0, c->staging, c->L, NF);
+        else
+            export_kernel<double, double><<<grid, block, 0, c->stream>>>((const double*)c->u0, c->staging, c->L, NF);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(w, c->staging, NF * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    int rc = pull_scalars(c);
+    if (t) *t = c->hsc->t;
+    return rc;
+}
+
+int sac_get_state_dev(sac_ctx* c, void* w, double* t)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
+    CK(cudaSetDevice(c->p.device));
+    if (w) {
+        const long long n = (long long)c->p.nx * c->p.ny;
+        const int block = 256;
+        int grid = grid_for(NF * n, block);
+        if (c->fp32)
+            export_kernel<float, float><<<grid, block, 0, c->stream>>>((const float*)c->u0, (float*)w, c->L, NF);
+        else
+            export_kernel<double, double><<<grid, block, 0, c->stream>>>((const double*)c->u0, (double*)w, c->L, NF);
+        CK(cudaGetLastError());
+    }
+    if (t) {
+        int rc = pull_scalars(c);
+        *t = c->hsc->t;
+        return rc;
+    }
+    return SAC_OK;
+}
+
+int sac_step(sac_ctx* c, double dt, double* dt_taken)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "step before set_state");
+    if (!(dt <= 0.0) && !std::isfinite(dt)) return fail(c, SAC_ERR_ARG, "dt must be finite");
+    CK(cudaSetDevice(c->p.device));
+    int rc = set_t_end(c, std::numeric_limits<double>::infinity());
+    if (rc != SAC_OK) return rc;
+    CK(enqueue_step(c, c->stream, dt > 0.0 ? dt : 0.0));
+    rc = pull_scalars(c);
+    if (dt_taken) *dt_taken = c->hsc->dt;
+    return rc;
+}
+
+int sac_steps(sac_ctx* c, long nsteps)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "step before set_state");
+    if (nsteps < 0) return fail(c, SAC_ERR_ARG, "nsteps < 0");
+    CK(cudaSetDevice(c->p.device));
+    if (c->t_end_host != std::numeric_limits<double>::infinity()) {
+        int rc = set_t_end(c, std::numeric_limits<double>::infinity());
+        if (rc != SAC_OK) return rc;
+    }
+    if (!c->g1) CK(capture(c, 1, &c->g1));
+    if (!c->gN && nsteps >= kChunk) CK(capture(c, kChunk, &c->gN));
+    long left = nsteps;
+    while (left >= kChunk) { CK(cudaGraphLaunch(c->gN, c->stream)); left -= kChunk; }
+    while (left > 0) { CK(cudaGraphLaunch(c->g1, c->stream)); --left; }
+    return SAC_OK;
+}
+
+int sac_run_to(sac_ctx* c, double t_end, long max_steps, long* steps_taken)
+{
+    if (steps_taken) *steps_taken = 0;
+    if (!c) return SAC_ERR_ARG;
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "run before set_state");
+    if (!std::isfinite(t_end)) return fail(c, SAC_ERR_ARG, "t_end must be finite");
+    CK(cudaSetDevice(c->p.device));
+    int rc = pull_scalars(c);
+    if (rc != SAC_OK) return rc;
+    const long long s0 = c->hsc->steps;
+    rc = set_t_end(c, t_end);
+    if (rc != SAC_OK) return rc;
+    if (!c->g1) CK(capture(c, 1, &c->g1));
+    long launched = 0;
+    double t = c->hsc->t, dt_last = c->hsc->dt;
+    while ((max_steps < 0 || launched < max_steps) && t < t_end) {
+        // enqueue about as many steps as remain (steps past t_end are skipped on the device)
+        long want = 1;
+        if (dt_last > 0.0) {
+            double est = (t_end - t) / dt_last;
+            want = est > 4096.0 ? 4096 : (long)est + 1;
+        }
+        if (max_steps >= 0 && want > max_steps - launched) want = max_steps - launched;
+        if (want >= kChunk && !c->gN) CK(capture(c, kChunk, &c->gN));
+        long n = 0;
+        while (want - n >= kChunk) { CK(cudaGraphLaunch(c->gN, c->stream)); n += kChunk; }
+        while (n < want) { CK(cudaGraphLaunch(c->g1, c->stream)); ++n; }
+        launched += n;
+        rc = pull_scalars(c);
+        if (rc != SAC_OK) break;
+        t = c->hsc->t;
+        dt_last = c->hsc->dt;
+        if (c->hsc->done) break;
+    }
+    if (steps_taken) *steps_taken = (long)(c->hsc->steps - s0);
+    return rc;
+}
+
+int sac_dt(sac_ctx* c, double* dt)
+{
+    if (!c || !dt) return SAC_ERR_ARG;
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
+    double cx, cy;
+    int rc = sac_cmax(c, &cx, &cy);
+    if (rc != SAC_OK) return rc;
+    const double dx = (c->p.x1 - c->p.x0) / c->p.nx, dy = (c->p.y1 - c->p.y0) / c->p.ny;
+    double tx = dx / cx, ty = dy / cy;
+    *dt = c->p.courant * std::fmin(tx, ty);
+    return SAC_OK;
+}
+
+int sac_time(sac_ctx* c, double* t, long* steps)
+{
+    if (!c) return SAC_ERR_ARG;
+    CK(cudaSetDevice(c->p.device));
+    int rc = pull_scalars(c);
+    if (t) *t = c->hsc->t;
+    if (steps) *steps = (long)c->hsc->steps;
+    return rc;
+}
+
+int sac_cmax(sac_ctx* c, double* cx, double* cy)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
+    CK(cudaSetDevice(c->p.device));
+    int rc = pull_scalars(c);
+    if (rc != SAC_OK) return rc;
+    unsigned long long b[2] = {c->hsc->cmax_bits[0], c->hsc->cmax_bits[1]};
+    double v[2];
+    for (int d = 0; d < 2; ++d) {
+        if (c->fp32) { unsigned u = (unsigned)b[d]; float f; memcpy(&f, &u, 4); v[d] = f; }
+        else memcpy(&v[d], &b[d], 8);
+    }
+    if (cx) *cx = v[0];
+    if (cy) *cy = v[1];
+    return SAC_OK;
+}
+
+int sac_sums(sac_ctx* c, double sums[6])
+{
+    if (!c || !sums) return SAC_ERR_ARG;
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
+    CK(cudaSetDevice(c->p.device));
+    if (c->fp32)
+        sums_partial_kernel<float><<<kSumBlocks, 256, 0, c->stream>>>((const float*)c->u0, c->L, c->part);
+    else
+        sums_partial_kernel<double><<<kSumBlocks, 256, 0, c->stream>>>((const double*)c->u0, c->L, c->part);
+    CK(cudaGetLastError());
+    sums_final_kernel<<<1, 32, 0, c->stream>>>(c->part, kSumBlocks, c->part + kSumBlocks * NF);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(sums, c->part + kSumBlocks * NF, NF * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return pull_scalars(c);
+}
+
+int sac_profile_stages(sac_ctx* c, int nsteps, double ms[5])
+{
+    if (!c || !ms || nsteps < 1) return fail(c, SAC_ERR_ARG, "bad arguments");
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
+    CK(cudaSetDevice(c->p.device));
+    int rc = set_t_end(c, std::numeric_limits<double>::infinity());
+    if (rc != SAC_OK) return rc;
+    cudaEvent_t ev[6];
+    for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&ev[k]));
+    double acc[5] = {0, 0, 0, 0, 0};
+    const double dx = (c->p.x1 - c->p.x0) / c->p.nx, dy = (c->p.y1 - c->p.y0) / c->p.ny;
+    for (int it = 0; it < nsteps && rc == SAC_OK; ++it) {
+        cudaEventRecord(ev[0], c->stream);
+        begin_step_kernel<<<1, 1, 0, c->stream>>>(c->sc, dx, dy, c->p.courant, c->fp32 ? 1 : 0, 0.0);
+        cudaEventRecord(ev[1], c->stream);
+        for (int stage = 1; stage <= 4; ++stage) {
+            cudaError_t e = enqueue_stage_one(c, c->stream, stage);
+            if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "stage launch: %s", cudaGetErrorString(e)); break; }
+            cudaEventRecord(ev[1 + stage], c->stream);
+        }
+        if (rc != SAC_OK) break;
+        cudaError_t e = cudaEventSynchronize(ev[5]);
+        if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "profile: %s", cudaGetErrorString(e)); break; }
+        for (int k = 0; k < 5; ++k) {
+            float m = 0.f;
+            cudaEventElapsedTime(&m, ev[k], ev[k + 1]);
+            acc[k] += m;
+        }
+    }
+    for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
+    for (int k = 0; k < 5; ++k) ms[k] = acc[k] / nsteps;
+    if (rc != SAC_OK) return rc;
+    return pull_scalars(c);
+}
+
+int sac_sync(sac_ctx* c)
+{
+    if (!c) return SAC_ERR_ARG;
+    CK(cudaSetDevice(c->p.device));
+    return pull_scalars(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+"""ctypes binding of ``libsac.so`` (include/sac.h): argument marshalling only.
+
+Every step of the MHD path runs in the library's CUDA kernels; this module
+converts numpy arrays / torch tensors to pointers and status codes to
+exceptions.  There is no CPU fallback: if the library is missing the import
+of the solver fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsac.so")
+
+SAC_OK, SAC_ERR_ARG, SAC_ERR_STATE, SAC_ERR_CUDA, SAC_ERR_OOM, SAC_ERR_NONFINITE, SAC_ERR_TIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6
+BC_PERIODIC, BC_FIXED, BC_OUTFLOW = 0, 1, 2
+FP64, FP32 = 0, 1
+NF, NB = 6, 4
+
+#: every function the C header declares, in header order
+EXPORTS = (
+    "sac_default_params", "sac_init", "sac_free", "sac_last_error", "sac_status_string",
+    "sac_set_state", "sac_get_state", "sac_set_state_dev", "sac_get_state_dev",
+    "sac_step", "sac_steps", "sac_run_to", "sac_dt", "sac_time", "sac_cmax", "sac_sums",
+    "sac_profile_stages", "sac_sync",
+)
+
+
+class SacError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} [{code}]")
+        self.code = code
+
+
+class SacParams(ctypes.Structure):
+    """Mirror of ``sac_params``."""
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("courant", ctypes.c_double),
+        ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("hyperdiffusion", ctypes.c_int),
+        ("c2", ctypes.c_double * 6),
+        ("c_shk", ctypes.c_double),
+        ("has_background", ctypes.c_int),
+        ("device", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libsac.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1710_06423_b300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, i, d, L = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_long
+    P = ctypes.POINTER(SacParams)
+    sig = {
+        "sac_default_params": (None, [P]),
+        "sac_init": (i, [P, ctypes.POINTER(vp)]),
+        "sac_free": (None, [vp]),
+        "sac_last_error": (ctypes.c_char_p, [vp]),
+        "sac_status_string": (ctypes.c_char_p, [i]),
+        "sac_set_state": (i, [vp, dp, dp, d]),
+        "sac_get_state": (i, [vp, dp, dp]),
+        "sac_set_state_dev": (i, [vp, vp, vp, d]),
+        "sac_get_state_dev": (i, [vp, vp, dp]),
+        "sac_step": (i, [vp, d, dp]),
+        "sac_steps": (i, [vp, L]),
+        "sac_run_to": (i, [vp, d, L, ctypes.POINTER(L)]),
+        "sac_dt": (i, [vp, dp]),
+        "sac_time": (i, [vp, dp, ctypes.POINTER(L)]),
+        "sac_cmax": (i, [vp, dp, dp]),
+        "sac_sums": (i, [vp, dp]),
+        "sac_profile_stages": (i, [vp, i, dp]),
+        "sac_sync": (i, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_params() -> SacParams:
+    p = SacParams()
+    load().sac_default_params(ctypes.byref(p))
+    return p
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Solver:
+    """One run on one GPU: ``Solver(nx=..., ny=..., precision=FP32, ...)``.
+
+    Keyword arguments are ``sac_params`` fields; ``stream`` may be a
+    ``torch.cuda.Stream`` or a raw handle (default: torch's current stream).
+    """
+
+    def __init__(self, **kw):
+        lib = load()
+        p = default_params()
+        stream = kw.pop("stream", "current")
+        for k, v in kw.items():
+            if k == "c2":
+                for j, x in enumerate(v):
+                    p.c2[j] = x
+            else:
+                setattr(p, k, v)
+        if stream == "current":
+            import torch
+            stream = torch.cuda.current_stream(p.device)
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        p.stream = stream or None
+        self.params = p
+        self._ctx = ctypes.c_void_p()
+        rc = lib.sac_init(ctypes.byref(p), ctypes.byref(self._ctx))
+        if rc != SAC_OK:
+            raise SacError(rc, f"sac_init failed: {lib.sac_status_string(rc).decode()}")
+        self.nx, self.ny = p.nx, p.ny
+        self.fp32 = p.precision == FP32
+
+    # -- helpers --------------------------------------------------------------
+    def _check(self, rc: int, what: str):
+        if rc != SAC_OK:
+            lib = load()
+            raise SacError(rc, f"{what}: {lib.sac_status_string(rc).decode()}: "
+                               f"{lib.sac_last_error(self._ctx).decode()}")
+
+    def close(self):
+        if self._ctx:
+            load().sac_free(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- C ABI ----------------------------------------------------------------
+    def set_state(self, w, bg=None, t: float = 0.0):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != (NF, self.ny, self.nx):
+            raise ValueError(f"state shape {w.shape} != {(NF, self.ny, self.nx)}")
+        if bg is not None:
+            bg = np.ascontiguousarray(bg, dtype=np.float64)
+            if bg.shape != (NB, self.ny, self.nx):
+                raise ValueError(f"background shape {bg.shape} != {(NB, self.ny, self.nx)}")
+        self._check(load().sac_set_state(self._ctx, _dp(w), _dp(bg), float(t)), "sac_set_state")
+
+    def get_state(self):
+        w = np.empty((NF, self.ny, self.nx), dtype=np.float64)
+        t = ctypes.c_double()
+        self._check(load().sac_get_state(self._ctx, _dp(w), ctypes.byref(t)), "sac_get_state")
+        return w, t.value
+
+    def get_state_into(self, w: np.ndarray) -> float:
+        """Copy the state into an existing C-contiguous float64 host array (e.g. pinned)."""
+        assert w.dtype == np.float64 and w.flags.c_contiguous and w.size == NF * self.nx * self.ny
+        t = ctypes.c_double()
+        self._check(load().sac_get_state(self._ctx, _dp(w), ctypes.byref(t)), "sac_get_state")
+        return t.value
+
+    def set_state_dev(self, w, bg=None, t: float = 0.0):
+        """Device tensors of the context's dtype, shape (6, ny, nx) / (4, ny, nx), contiguous."""
+        self._check(load().sac_set_state_dev(self._ctx, ctypes.c_void_p(w.data_ptr()),
+                                             None if bg is None else ctypes.c_void_p(bg.data_ptr()),
+                                             float(t)), "sac_set_state_dev")
+
+    def get_state_dev(self, w) -> None:
+        self._check(load().sac_get_state_dev(self._ctx, ctypes.c_void_p(w.data_ptr()), None),
+                    "sac_get_state_dev")
+
+    def step(self, dt: float = 0.0) -> float:
+        out = ctypes.c_double()
+        self._check(load().sac_step(self._ctx, float(dt), ctypes.byref(out)), "sac_step")
+        return out.value
+
+    def steps(self, n: int):
+        self._check(load().sac_steps(self._ctx, int(n)), "sac_steps")
+
+    def run_to(self, t_end: float, max_steps: int = -1) -> int:
+        n = ctypes.c_long()
+        self._check(load().sac_run_to(self._ctx, float(t_end), int(max_steps), ctypes.byref(n)), "sac_run_to")
+        return n.value
+
+    def dt(self) -> float:
+        out = ctypes.c_double()
+        self._check(load().sac_dt(self._ctx, ctypes.byref(out)), "sac_dt")
+        return out.value
+
+    def time(self):
+        t, n = ctypes.c_double(), ctypes.c_long()
+        self._check(load().sac_time(self._ctx, ctypes.byref(t), ctypes.byref(n)), "sac_time")
+        return t.value, n.value
+
+    def cmax(self):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(load().sac_cmax(self._ctx, ctypes.byref(a), ctypes.byref(b)), "sac_cmax")
+        return a.value, b.value
+
+    def sums(self) -> np.ndarray:
+        out = np.zeros(6)
+        self._check(load().sac_sums(self._ctx, _dp(out)), "sac_sums")
+        return out
+
+    def profile_stages(self, nsteps: int) -> np.ndarray:
+        """Mean CUDA-event durations [ms]: step control, stage 1..4 kernels."""
+        out = np.zeros(5)
+        self._check(load().sac_profile_stages(self._ctx, int(nsteps), _dp(out)), "sac_profile_stages")
+        return out
+
+    def sync(self):
+        self._check(load().sac_sync(self._ctx), "sac_sync")

@@ -1,0 +1,96 @@
+"""Full-size workloads against the oracle.
+
+* Orszag-Tang 1000 x 1000, 200 RK4 steps, FP64 and FP32, against the FP64
+  oracle run to the same horizon (element by element), with the vortex's
+  point symmetry and periodic conservation checked on the GPU results.
+* Orszag-Tang 2044^2 and 8000^2 with 1e-3 noise, FP32, in the launch
+  configuration the benchmark times (graph-replayed CFL steps): one step
+  compared with the oracle on sampled windows.  One RK4 step reads 3 cells
+  per stage, so a cell depends only on cells within 12 of it; the oracle run
+  on a periodically-wrapped window with a 12-cell margin is exact inside the
+  margin when given the GPU's step size and signal speeds.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL_FP32_L1, TOL_FP64, l1rel, maxrel, oracle_problem, problem_kwargs, solver
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+FP64, FP32 = 0, 1
+SIGN = np.array([1, -1, -1, 1, -1, -1])[:, None, None]
+
+
+@pytest.fixture(scope="module")
+def ot1000(oracle_mod, inputs_mod):
+    n = 1000
+    w0 = inputs_mod.orszag_tang(n)
+    w0 = 0.5 * (w0 + SIGN * w0[:, ::-1, ::-1])      # exactly point-symmetric start
+    kw = problem_kwargs(n, n)
+    ref, t, steps = oracle_mod.run(oracle_problem(oracle_mod, kw), w0, max_steps=200)
+    assert steps == 200
+    return kw, w0, ref, t
+
+
+def test_ot1000_fp64_200_steps(ot1000):
+    kw, w0, ref, t_ref = ot1000
+    with solver(kw, FP64) as s:
+        s.set_state(w0, None, 0.0)
+        s0 = s.sums()
+        s.steps(200)
+        got, t = s.get_state()
+        s1 = s.sums()
+    assert t == t_ref
+    err = maxrel(got, ref)
+    assert np.all(err <= TOL_FP64), err
+    assert np.array_equal(got, SIGN * got[:, ::-1, ::-1])
+    scale = np.abs(w0).reshape(6, -1).sum(axis=1)
+    assert np.all(np.abs(s1 - s0) <= 1e-12 * scale), (s1 - s0) / scale
+
+
+def test_ot1000_fp32_200_steps(ot1000):
+    kw, w0, ref, t_ref = ot1000
+    with solver(kw, FP32) as s:
+        s.set_state(w0, None, 0.0)
+        s0 = s.sums()
+        s.steps(200)
+        got, t = s.get_state()
+        s1 = s.sums()
+    assert abs(t - t_ref) <= 1e-5 * t_ref
+    err = l1rel(got, ref)
+    assert np.all(err <= TOL_FP32_L1), err
+    sym = np.abs(got - SIGN * got[:, ::-1, ::-1]).reshape(6, -1).max(axis=1) / np.abs(got).reshape(6, -1).max(axis=1)
+    assert np.all(sym <= 1e-5), sym
+    scale = np.abs(w0).reshape(6, -1).sum(axis=1)
+    assert np.all(np.abs(s1 - s0) <= 1e-5 * scale), (s1 - s0) / scale
+
+
+def _window(w, j0, i0, size, margin):
+    """Periodic window [j0-margin, j0+size+margin) x [i0-margin, i0+size+margin)."""
+    ny, nx = w.shape[1:]
+    jj = np.arange(j0 - margin, j0 + size + margin) % ny
+    ii = np.arange(i0 - margin, i0 + size + margin) % nx
+    return np.ascontiguousarray(w[:, jj][:, :, ii])
+
+
+@pytest.mark.parametrize("n", [2044, 8000])
+def test_bench_config_one_step_windows(oracle_mod, inputs_mod, n):
+    kw = problem_kwargs(n, n)
+    w0 = inputs_mod.orszag_tang(n, noise=1e-3, seed=20171018)
+    with solver(kw, FP32) as s:
+        s.set_state(w0, None, 0.0)
+        cx, cy = s.cmax()
+        s.steps(1)                       # the graph-replayed step the benchmark times
+        got, t = s.get_state()
+    dt = t
+    size, margin = 48, 12
+    starts = [(0, 0), (n - 20, n - 30), (n // 2 + 7, n // 3 + 5), (5, n - 1), (n - 1, 17)]
+    for j0, i0 in starts:
+        win = _window(w0, j0, i0, size, margin)
+        wk = problem_kwargs(size + 2 * margin, size + 2 * margin,
+                            x1=(size + 2 * margin) / n, y1=(size + 2 * margin) / n)
+        pr = oracle_problem(oracle_mod, wk)
+        ref = oracle_mod.rk4_step(pr, win, dt, cmax_xy=(cx, cy))[:, margin:-margin, margin:-margin]
+        g = _window(got, j0, i0, size, 0)
+        err = l1rel(g, ref)
+        assert np.all(err <= TOL_FP32_L1), (j0, i0, err)
+        assert np.all(maxrel(g, ref) <= 1e-4), (j0, i0, maxrel(g, ref))

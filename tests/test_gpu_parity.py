@@ -1,0 +1,232 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Small and ragged grids (several tiles plus a partial one), every boundary
+kind, with and without background and hyper-diffusion, FP64 (operation-order
+parity, 1e-12) and FP32 (relative L1 per field <= 1e-5).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import (TOL_FP32_L1, TOL_FP64, l1rel, maxrel, oracle_problem, problem_kwargs,
+                         smooth_background, solver)
+
+pytestmark = pytest.mark.gpu
+FP64, FP32 = 0, 1
+
+
+def _ot_state(inputs, nx, ny, noise=1e-3, seed=11):
+    w = inputs.orszag_tang(nx, ny, noise=noise, seed=seed)
+    return w
+
+
+def _perturbed_split(w, bg):
+    """Turn a full state into perturbations about bg (rho, e, Bx, By)."""
+    wp = w.copy()
+    wp[0] -= bg[0]
+    wp[3] -= bg[1]
+    wp[4] -= bg[2]
+    wp[5] -= bg[3]
+    return wp
+
+
+CASES = [
+    # name, nx, ny, kwargs, steps, background
+    ("ot_ragged_periodic", 70, 45, {}, 12, False),
+    ("ot_multi_tile", 96, 64, {}, 8, False),
+    ("ot_no_hd", 40, 40, {"hyperdiffusion": 0}, 10, False),
+    ("mixed_fixed_periodic", 50, 33, {"bc_x": 1}, 10, False),
+    ("outflow_both", 37, 29, {"bc_x": 2, "bc_y": 2}, 10, False),
+    ("background_split", 37, 29, {"bc_y": 2}, 8, True),
+    ("tiny_5x3", 5, 3, {}, 6, False),
+    ("strip_1xN", 1, 40, {"bc_y": 2}, 6, False),
+    ("strip_Nx1", 33, 1, {}, 6, False),
+]
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("name,nx,ny,kw,steps,has_bg", CASES, ids=[c[0] for c in CASES])
+def test_parity_small(oracle_mod, inputs_mod, precision, name, nx, ny, kw, steps, has_bg):
+    kw = problem_kwargs(nx, ny, **kw)
+    pr = oracle_problem(oracle_mod, kw)
+    w = _ot_state(inputs_mod, nx, ny)
+    bg = None
+    if has_bg:
+        bg = smooth_background(ny, nx)
+        w = _perturbed_split(w, bg)
+        w[0] += 0.3            # keep total density and pressure comfortably positive
+        w[3] += 0.5
+    ref, t_ref, n_ref = oracle_mod.run(pr, w, bg=bg, max_steps=steps)
+    with solver(kw, precision, has_background=int(has_bg)) as s:
+        s.set_state(w, bg, 0.0)
+        for _ in range(steps):
+            s.step(0.0)
+        got, t = s.get_state()
+    assert abs(t - t_ref) <= (1e-12 if precision == FP64 else 1e-6) * t_ref
+    if precision == FP64:
+        err = maxrel(got, ref)
+        assert np.all(err <= TOL_FP64), err
+    else:
+        err = l1rel(got, ref)
+        assert np.all(err <= TOL_FP32_L1), err
+
+
+def test_brio_wu_fp64_full_config(oracle_mod, inputs_mod):
+    """Brio-Wu, 800 cells, fixed ends, gamma 2, HD on, to t = 0.1 (about 1040 CFL steps)."""
+    kw = problem_kwargs(800, 1, gamma=2.0, bc_x=1)
+    pr = oracle_problem(oracle_mod, kw)
+    w0 = inputs_mod.brio_wu()
+    ref, t_ref, n_ref = oracle_mod.run(pr, w0, t_end=0.1)
+    with solver(kw, FP64) as s:
+        s.set_state(w0, None, 0.0)
+        n = s.run_to(0.1)
+        got, t = s.get_state()
+    assert n == n_ref and t == 0.1 and t_ref == 0.1
+    err = maxrel(got, ref)
+    assert np.all(err <= TOL_FP64), err
+
+
+def test_brio_wu_fp32(oracle_mod, inputs_mod):
+    """Same shock tube in FP32; the step count may differ by one at most (CFL in FP32 speeds)."""
+    kw = problem_kwargs(800, 1, gamma=2.0, bc_x=1)
+    pr = oracle_problem(oracle_mod, kw)
+    w0 = inputs_mod.brio_wu()
+    ref, _, n_ref = oracle_mod.run(pr, w0, t_end=0.1)
+    with solver(kw, FP32) as s:
+        s.set_state(w0, None, 0.0)
+        n = s.run_to(0.1)
+        got, t = s.get_state()
+    assert t == 0.1 and abs(n - n_ref) <= 1
+    err = l1rel(got, ref)
+    assert np.all(err[[0, 1, 3, 5]] <= 1e-4), err
+
+
+def test_run_to_lands_on_t_end_and_matches_step_count(oracle_mod, inputs_mod):
+    kw = problem_kwargs(48, 40)
+    pr = oracle_problem(oracle_mod, kw)
+    w0 = _ot_state(inputs_mod, 48, 40)
+    ref, t_ref, n_ref = oracle_mod.run(pr, w0, t_end=0.0123)
+    with solver(kw, FP64) as s:
+        s.set_state(w0, None, 0.0)
+        n = s.run_to(0.0123)
+        t, steps = s.time()
+        got, _ = s.get_state()
+        assert n == n_ref == steps and t == 0.0123
+        # a second run_to continues from there
+        n2 = s.run_to(0.02, max_steps=3)
+        t2, steps2 = s.time()
+    assert np.all(maxrel(got, ref) <= TOL_FP64)
+    assert n2 == 3 and steps2 == n_ref + 3 and t2 < 0.02
+
+
+def test_dt_and_cmax_match_oracle(oracle_mod, inputs_mod):
+    kw = problem_kwargs(64, 50, courant=0.4)
+    pr = oracle_problem(oracle_mod, kw)
+    w0 = _ot_state(inputs_mod, 64, 50)
+    cx, cy = oracle_mod.cmax(pr, w0)
+    dt = oracle_mod.cfl_dt(pr, cx, cy)
+    with solver(kw, FP64) as s:
+        s.set_state(w0, None, 0.0)
+        gcx, gcy = s.cmax()
+        assert (gcx, gcy) == (cx, cy)
+        assert s.dt() == dt
+        assert s.step(0.0) == dt
+        # after one step the fused stage-4 reduction gives the new state's speeds
+        w1 = oracle_mod.rk4_step(pr, w0, dt)
+        assert s.cmax() == oracle_mod.cmax(pr, w1)
+
+
+def test_explicit_dt_step(oracle_mod, inputs_mod):
+    kw = problem_kwargs(32, 32)
+    pr = oracle_problem(oracle_mod, kw)
+    w0 = _ot_state(inputs_mod, 32, 32)
+    ref = oracle_mod.rk4_step(pr, w0, 1e-4)
+    with solver(kw, FP64) as s:
+        s.set_state(w0, None, 0.0)
+        assert s.step(1e-4) == 1e-4
+        got, t = s.get_state()
+    assert t == 1e-4 and np.all(maxrel(got, ref) <= TOL_FP64)
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32], ids=["fp64", "fp32"])
+def test_checkpoint_resume_bitwise(inputs_mod, precision):
+    """get_state after k steps -> new context -> continue == uninterrupted run, bit for bit."""
+    kw = problem_kwargs(80, 72)
+    w0 = _ot_state(inputs_mod, 80, 72)
+    with solver(kw, precision) as a:
+        a.set_state(w0, None, 0.0)
+        a.steps(10)
+        full, tf = a.get_state()
+    with solver(kw, precision) as b:
+        b.set_state(w0, None, 0.0)
+        b.steps(4)
+        mid, tm = b.get_state()
+    with solver(kw, precision) as c:
+        c.set_state(mid, None, tm)
+        c.steps(6)
+        res, tr = c.get_state()
+    assert np.array_equal(res, full) and tr == tf
+
+
+def test_conservation_sums_match_host(inputs_mod):
+    kw = problem_kwargs(100, 90)
+    w0 = _ot_state(inputs_mod, 100, 90)
+    with solver(kw, FP64) as s:
+        s.set_state(w0, None, 0.0)
+        s0 = s.sums()
+        s.steps(20)
+        s1 = s.sums()
+        w1, _ = s.get_state()
+    host0 = np.array([math.fsum(w0[f].ravel()) for f in range(6)])
+    host1 = np.array([math.fsum(w1[f].ravel()) for f in range(6)])
+    scale = np.abs(w0).reshape(6, -1).sum(axis=1)
+    assert np.all(np.abs(s0 - host0) <= 1e-13 * scale)
+    assert np.all(np.abs(s1 - host1) <= 1e-13 * scale)
+    assert np.all(np.abs(s1 - s0) <= 1e-12 * scale)      # periodic conservation
+
+
+def test_nonfinite_state_reports_error(inputs_mod):
+    from paper_1710_06423_b300.sac import SAC_ERR_NONFINITE, SacError
+    kw = problem_kwargs(32, 32)
+    w0 = _ot_state(inputs_mod, 32, 32)
+    w0[0, 5, 7] = np.nan
+    with solver(kw, FP32) as s:
+        s.set_state(w0, None, 0.0)
+        with pytest.raises(SacError) as ei:
+            s.step(0.0)
+        assert ei.value.code == SAC_ERR_NONFINITE
+        # the context stays usable: a clean state runs again
+        s.set_state(_ot_state(inputs_mod, 32, 32), None, 0.0)
+        s.step(0.0)
+
+
+def test_call_order_errors():
+    from paper_1710_06423_b300.sac import SAC_ERR_STATE, SAC_ERR_ARG, SacError
+    kw = problem_kwargs(16, 16)
+    with solver(kw, FP64) as s:
+        with pytest.raises(SacError) as ei:
+            s.step(0.0)
+        assert ei.value.code == SAC_ERR_STATE
+        with pytest.raises(SacError) as ei:
+            s.set_state(np.ones((6, 16, 16)), np.ones((4, 16, 16)), 0.0)   # bg without has_background
+        assert ei.value.code == SAC_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32], ids=["fp64", "fp32"])
+def test_device_state_roundtrip(inputs_mod, precision):
+    import torch
+    kw = problem_kwargs(64, 40)
+    w0 = _ot_state(inputs_mod, 64, 40)
+    dt = torch.float64 if precision == FP64 else torch.float32
+    with solver(kw, precision) as s:
+        s.set_state(w0, None, 0.0)
+        s.steps(3)
+        host, _ = s.get_state()
+        dev = torch.empty((6, 40, 64), dtype=dt, device="cuda")
+        s.get_state_dev(dev)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.double().cpu().numpy(), host)
+        s.set_state_dev(dev, None, 0.0)
+        back, _ = s.get_state()
+        assert np.array_equal(back, host)
