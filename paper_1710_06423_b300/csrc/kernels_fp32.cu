@@ -1,26 +1,29 @@
-// kernels_fp32.cu -- FP32 instantiation of the fused RK stage kernel.
-// FP32 perturbation arithmetic (A-scheme RK registers); built with FMA
-// contraction on.
-#include "stage_generic.cuh"
+// kernels_fp32.cu -- launchers of the FP32 fused RK stage kernel (field-pair
+// layout, packed f32x2 arithmetic, D-scheme RK registers).
+#include "stage_fp32.cuh"
 
 namespace sac {
 namespace {
-constexpr int TX = 32, TY = 16;
+using f32k::NT;
+using f32k::TX;
+using f32k::TY;
 
 template <int S, bool BG, bool HD>
 cudaError_t set_attr()
 {
-    return cudaFuncSetAttribute(stage_generic<float, S, BG, HD, TX, TY>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)GenericSmem<float, TX, TY, BG>::bytes);
+    cudaError_t e = cudaFuncSetAttribute(f32k::stage_fp32<S, BG, HD>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(f32k::Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f32k::stage_fp32<S, BG, HD>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 template <int S, bool BG, bool HD>
 cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
 {
     dim3 grid((a.L.nx + TX - 1) / TX, (a.L.ny + TY - 1) / TY);
-    stage_generic<float, S, BG, HD, TX, TY>
-        <<<grid, TX * TY / 2, GenericSmem<float, TX, TY, BG>::bytes, s>>>(a);
+    f32k::stage_fp32<S, BG, HD><<<grid, NT, sizeof(f32k::Smem), s>>>(a);
     return cudaGetLastError();
 }
 

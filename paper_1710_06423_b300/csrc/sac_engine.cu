@@ -20,8 +20,6 @@ using namespace sac;
 
 namespace {
 
-constexpr int kChunk = 16;          // steps per captured multi-step graph
-constexpr int kSumBlocks = 296;     // 2 x 148 SMs
 
 __host__ __device__ inline int wrapi(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
 __host__ __device__ inline int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
@@ -37,7 +35,7 @@ __device__ inline int src_index(int i, int n, int bc) {
 // the set-up rule (fixed sides become the held values).
 template <typename T, typename S>
 __global__ void import_kernel(const S* __restrict__ src, T* __restrict__ dst, Layout L, int nf,
-                              int bc_x, int bc_y)
+                              int bc_x, int bc_y, bool bgfield)
 {
     const long long ex = L.nx + 2 * GY, ey = L.ny + 2 * GY;
     const long long total = (long long)nf * ex * ey;
@@ -47,12 +45,12 @@ __global__ void import_kernel(const S* __restrict__ src, T* __restrict__ dst, La
         long long r = v - (long long)f * ex * ey;
         int j = (int)(r / ex) - GY, i = (int)(r % ex) - GY;
         int si = src_index(i, L.nx, bc_x), sj = src_index(j, L.ny, bc_y);
-        dst[(long long)f * L.fstride + L.at(i, j)] = (T)src[((long long)f * L.ny + sj) * L.nx + si];
+        dst[L.idx(f, i, j, bgfield)] = (T)src[((long long)f * L.ny + sj) * L.nx + si];
     }
 }
 
 template <typename T, typename D>
-__global__ void export_kernel(const T* __restrict__ src, D* __restrict__ dst, Layout L, int nf)
+__global__ void export_kernel(const T* __restrict__ src, D* __restrict__ dst, Layout L, int nf, bool bgfield)
 {
     const long long n = (long long)L.nx * L.ny, total = n * nf;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total;
@@ -60,7 +58,7 @@ __global__ void export_kernel(const T* __restrict__ src, D* __restrict__ dst, La
         int f = (int)(v / n);
         long long r = v - (long long)f * n;
         int j = (int)(r / L.nx), i = (int)(r % L.nx);
-        dst[v] = (D)src[(long long)f * L.fstride + L.at(i, j)];
+        dst[v] = (D)src[L.idx(f, i, j, bgfield)];
     }
 }
 
@@ -76,14 +74,15 @@ __global__ void cmax_kernel(const T* __restrict__ w, const T* __restrict__ bg, L
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
          v += (long long)gridDim.x * blockDim.x) {
         int j = (int)(v / L.nx), i = (int)(v % L.nx);
-        long long g = L.at(i, j);
-        const long long S = L.fstride;
+        T q[NF];
+        for (int f = 0; f < NF; ++f) q[f] = w[L.idx(f, i, j, false)];
         T sx, sy;
         if (BG)
-            signal_speeds<T, true>(w[g], w[S + g], w[2 * S + g], w[3 * S + g], w[4 * S + g], w[5 * S + g],
-                                   bg[g], bg[S + g], bg[2 * S + g], bg[3 * S + g], (T)gamma, sx, sy);
+            signal_speeds<T, true>(q[0], q[1], q[2], q[3], q[4], q[5],
+                                   bg[L.idx(0, i, j, true)], bg[L.idx(1, i, j, true)],
+                                   bg[L.idx(2, i, j, true)], bg[L.idx(3, i, j, true)], (T)gamma, sx, sy);
         else
-            signal_speeds<T, false>(w[g], w[S + g], w[2 * S + g], w[3 * S + g], w[4 * S + g], w[5 * S + g],
+            signal_speeds<T, false>(q[0], q[1], q[2], q[3], q[4], q[5],
                                     (T)0, (T)0, (T)0, (T)0, (T)gamma, sx, sy);
         unsigned long long a = speed_key(sx), b = speed_key(sy);
         m[0] = a > m[0] ? a : m[0];
@@ -120,35 +119,11 @@ __global__ void control_kernel(DevScalars* sc, double t_end)
     sc->done = (sc->t >= t_end) ? 1 : 0;
 }
 
-__device__ inline double decode_speed(unsigned long long b, int fp32)
-{
-    return fp32 ? (double)__uint_as_float((unsigned)b) : __longlong_as_double((long long)b);
-}
-
-// Start one RK step: CFL step from the signal speeds of the current state
-// (dt = C min(dx/cmax_x, dy/cmax_y)), clipped to land on t_end; those speeds
-// scale the hyper-diffusion of the step's four stages.
+// Start one RK step (see step_begin in sac_internal.cuh).
 __global__ void begin_step_kernel(DevScalars* sc, double dx, double dy, double courant, int fp32,
                                   double dt_override)
 {
-    if (sc->status != ST_OK || sc->done) { sc->skip = 1; return; }
-    double cx = decode_speed(sc->cmax_bits[0], fp32), cy = decode_speed(sc->cmax_bits[1], fp32);
-    double dt;
-    if (dt_override > 0.0) dt = dt_override;
-    else if (sc->fixed_dt > 0.0) dt = sc->fixed_dt;
-    else { double tx = dx / cx, ty = dy / cy; dt = courant * fmin(tx, ty); }
-    if (!(dt > 0.0) || !isfinite(dt) || !isfinite(cx) || !isfinite(cy)) {
-        sc->status = ST_ERR_NONFINITE; sc->skip = 1; return;
-    }
-    int last = 0;
-    if (sc->t + dt >= sc->t_end) { dt = sc->t_end - sc->t; last = 1; }
-    sc->dt = dt;
-    sc->cmax_step[0] = cx; sc->cmax_step[1] = cy;
-    sc->t = last ? sc->t_end : sc->t + dt;
-    sc->steps += 1;
-    if (last) sc->done = 1;
-    sc->cmax_bits[0] = sc->cmax_bits[1] = 0ull;
-    sc->skip = 0;
+    step_begin(sc, dx, dy, courant, fp32, dt_override);
 }
 
 // ---- FP64 conservation sums (deterministic two-pass) ---------------------------
@@ -161,8 +136,7 @@ __global__ void sums_partial_kernel(const T* __restrict__ w, Layout L, double* _
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
          v += (long long)gridDim.x * blockDim.x) {
         int j = (int)(v / L.nx), i = (int)(v % L.nx);
-        long long g = L.at(i, j);
-        for (int f = 0; f < NF; ++f) acc[f] += (double)w[(long long)f * L.fstride + g];
+        for (int f = 0; f < NF; ++f) acc[f] += (double)w[L.idx(f, i, j, false)];
     }
     for (int f = 0; f < NF; ++f) {
         double x = acc[f];
@@ -193,29 +167,7 @@ int grid_for(long long n, int block) {
 
 }  // namespace
 
-// ============================================================================
-struct sac_ctx {
-    sac_params p;
-    Layout L;
-    bool fp32 = false;
-    size_t esz = 8;                 // element size of the working precision
-    cudaStream_t stream = nullptr;  // user stream (may be the legacy default)
-    cudaStream_t cap = nullptr;     // private stream used only for graph capture
-    void* u0 = nullptr;
-    void* sa = nullptr;
-    void* sb = nullptr;
-    void* acc = nullptr;
-    void* bg = nullptr;
-    DevScalars* sc = nullptr;
-    DevScalars* hsc = nullptr;      // pinned host mirror
-    double* staging = nullptr;      // packed FP64 [6][ny][nx] for host transfers
-    double* part = nullptr;         // [kSumBlocks][6] partial sums + [6] result
-    cudaGraphExec_t g1 = nullptr;   // one CFL step
-    cudaGraphExec_t gN = nullptr;   // kChunk CFL steps
-    bool have_state = false;
-    double t_end_host = std::numeric_limits<double>::infinity();
-    char err[512] = {0};
-};
+#include "sac_ctx.h"
 
 static const char* kStatusNames[] = {"SAC_OK", "SAC_ERR_ARG", "SAC_ERR_STATE", "SAC_ERR_CUDA",
                                      "SAC_ERR_OOM", "SAC_ERR_NONFINITE", "SAC_ERR_TIMEOUT"};
@@ -241,29 +193,40 @@ static int fail(sac_ctx* c, int code, const char* fmt, ...)
 
 static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
+// Stage input / output buffers of RK stage 1..4: ping-pong SA, SB; U0 is the
+// stencil input of stage 1 and is rewritten by stage 4.
+static void stage_buffers(const sac_ctx* c, int stage, void** sin, void** sout)
+{
+    *sin = stage == 1 ? c->u0 : (stage == 2 ? c->sa : (stage == 3 ? c->sb : c->sa));
+    *sout = stage == 1 ? c->sa : (stage == 2 ? c->sb : (stage == 3 ? c->sa : c->u0));
+}
+
+template <typename T>
+static void fill_stage_args(const sac_ctx* c, int stage, StageArgs<T>* a)
+{
+    void *sin, *sout;
+    stage_buffers(c, stage, &sin, &sout);
+    a->sin = (const T*)sin; a->u0 = (const T*)c->u0; a->acc = (T*)c->acc;
+    a->sout = (T*)sout; a->bg = (const T*)c->bg; a->sc = c->sc; a->L = c->L;
+    a->dx = (c->p.x1 - c->p.x0) / c->p.nx; a->dy = (c->p.y1 - c->p.y0) / c->p.ny;
+    a->gamma = c->p.gamma;
+    for (int f = 0; f < NF; ++f) a->c2[f] = c->p.c2[f];
+    a->c_shk = c->p.c_shk; a->bc_x = c->p.bc_x; a->bc_y = c->p.bc_y;
+}
+
+void sac_fp32_stage_args(const sac_ctx* c, int stage, StageArgs<float>* out) { fill_stage_args<float>(c, stage, out); }
+
 // Enqueue the kernel of one RK stage (1..4).
 static cudaError_t enqueue_stage_one(sac_ctx* c, cudaStream_t s, int stage)
 {
     const bool hd = c->p.hyperdiffusion != 0, bgp = c->p.has_background != 0;
-    // stage input / output buffers (ping-pong SA, SB; U0 written by stage 4)
-    void* sin = stage == 1 ? c->u0 : (stage == 2 ? c->sa : (stage == 3 ? c->sb : c->sa));
-    void* sout = stage == 1 ? c->sa : (stage == 2 ? c->sb : (stage == 3 ? c->sa : c->u0));
-    const double dx = (c->p.x1 - c->p.x0) / c->p.nx, dy = (c->p.y1 - c->p.y0) / c->p.ny;
     if (c->fp32) {
         StageArgs<float> a;
-        a.sin = (const float*)sin; a.u0 = (const float*)c->u0; a.acc = (float*)c->acc;
-        a.sout = (float*)sout; a.bg = (const float*)c->bg; a.sc = c->sc; a.L = c->L;
-        a.dx = dx; a.dy = dy; a.gamma = c->p.gamma;
-        for (int f = 0; f < NF; ++f) a.c2[f] = c->p.c2[f];
-        a.c_shk = c->p.c_shk; a.bc_x = c->p.bc_x; a.bc_y = c->p.bc_y;
+        fill_stage_args<float>(c, stage, &a);
         return launch_stage_fp32(a, stage, hd, bgp, s);
     }
     StageArgs<double> a;
-    a.sin = (const double*)sin; a.u0 = (const double*)c->u0; a.acc = (double*)c->acc;
-    a.sout = (double*)sout; a.bg = (const double*)c->bg; a.sc = c->sc; a.L = c->L;
-    a.dx = dx; a.dy = dy; a.gamma = c->p.gamma;
-    for (int f = 0; f < NF; ++f) a.c2[f] = c->p.c2[f];
-    a.c_shk = c->p.c_shk; a.bc_x = c->p.bc_x; a.bc_y = c->p.bc_y;
+    fill_stage_args<double>(c, stage, &a);
     return launch_stage_fp64(a, stage, hd, bgp, s);
 }
 
@@ -362,11 +325,10 @@ static int import_fields(sac_ctx* c, const S* src, void* dst, int nf, bool backg
     const int block = 256;
     long long n = (long long)nf * (c->p.nx + 2 * GY) * (c->p.ny + 2 * GY);
     int bcx = c->p.bc_x, bcy = c->p.bc_y;
-    (void)background;
     if (c->fp32)
-        import_kernel<float, S><<<grid_for(n, block), block, 0, c->stream>>>(src, (float*)dst, c->L, nf, bcx, bcy);
+        import_kernel<float, S><<<grid_for(n, block), block, 0, c->stream>>>(src, (float*)dst, c->L, nf, bcx, bcy, background);
     else
-        import_kernel<double, S><<<grid_for(n, block), block, 0, c->stream>>>(src, (double*)dst, c->L, nf, bcx, bcy);
+        import_kernel<double, S><<<grid_for(n, block), block, 0, c->stream>>>(src, (double*)dst, c->L, nf, bcx, bcy, background);
     CK(cudaGetLastError());
     return SAC_OK;
 }
@@ -449,6 +411,7 @@ int sac_init(const sac_params* p, sac_ctx** out)
         L.pitch = (int)round_up(round_up(p->nx, TILE_X_MAX) + 2 * GX, 32);
         L.rows = (int)(round_up(p->ny, TILE_Y_MAX) + 2 * GY);
         L.fstride = round_up((long long)L.pitch * L.rows, 64);
+        L.paired = c->fp32 ? 1 : 0;   // FP32: three float2 planes of fstride elements each
         const size_t fbytes = (size_t)L.fstride * c->esz;
         void** bufs[4] = {&c->u0, &c->sa, &c->sb, &c->acc};
         for (int b = 0; b < 4 && rc == SAC_OK; ++b) {
@@ -537,9 +500,9 @@ int sac_get_state(sac_ctx* c, double* w, double* t)
         const int block = 256;
         int grid = grid_for((long long)NF * n, block);
         if (c->fp32)
-            export_kernel<float, double><<<grid, block, 0, c->stream>>>((const float*)c->u0, c->staging, c->L, NF);
+            export_kernel<float, double><<<grid, block, 0, c->stream>>>((const float*)c->u0, c->staging, c->L, NF, false);
         else
-            export_kernel<double, double><<<grid, block, 0, c->stream>>>((const double*)c->u0, c->staging, c->L, NF);
+            export_kernel<double, double><<<grid, block, 0, c->stream>>>((const double*)c->u0, c->staging, c->L, NF, false);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(w, c->staging, NF * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     }
@@ -558,9 +521,9 @@ int sac_get_state_dev(sac_ctx* c, void* w, double* t)
         const int block = 256;
         int grid = grid_for(NF * n, block);
         if (c->fp32)
-            export_kernel<float, float><<<grid, block, 0, c->stream>>>((const float*)c->u0, (float*)w, c->L, NF);
+            export_kernel<float, float><<<grid, block, 0, c->stream>>>((const float*)c->u0, (float*)w, c->L, NF, false);
         else
-            export_kernel<double, double><<<grid, block, 0, c->stream>>>((const double*)c->u0, (double*)w, c->L, NF);
+            export_kernel<double, double><<<grid, block, 0, c->stream>>>((const double*)c->u0, (double*)w, c->L, NF, false);
         CK(cudaGetLastError());
     }
     if (t) {

@@ -16,18 +16,33 @@ constexpr int TILE_Y_MAX = 32;
 enum { BC_PERIODIC = 0, BC_FIXED = 1, BC_OUTFLOW = 2 };
 enum { ST_OK = 0, ST_ERR_NONFINITE = -5, ST_ERR_TIMEOUT = -6 };
 
-// Ghost-padded field-major layout: interior cell (i, j) of field f sits at
-//   f * fstride + (j + GY) * pitch + (i + GX).
-// pitch is a multiple of 32 elements (128 B for FP32) so every tile row
-// starts 16-byte aligned; rows and pitch leave room for the largest tile so
-// a ragged last tile reads only inside its own field.
+// field index -> (plane, component) of the FP32 pair layout:
+// planes (rho~, e~), (m_x, m_y), (B~x, B~y); background (rho_b, e_b), (B_bx, B_by)
+__host__ __device__ constexpr int pair_plane(int f) { return f == 0 || f == 3 ? 0 : (f <= 2 ? 1 : 2); }
+__host__ __device__ constexpr int pair_comp(int f) { return f == 0 || f == 1 || f == 4 ? 0 : 1; }
+
+// Ghost-padded layouts.  Interior cell (i, j) has the in-plane offset
+//   at(i, j) = (j + GY) * pitch + (i + GX).
+//  planar (FP64): field f is plane f, element f * fstride + at(i, j);
+//  paired (FP32): the fields are three float2 planes (pair_plane/pair_comp),
+//                 float index 2 * (plane * fstride + at(i, j)) + comp.
+// pitch is a multiple of 32 elements so every tile row starts 16-byte
+// aligned; rows and pitch leave room for the largest tile so a ragged last
+// tile reads only inside its own plane.
 struct Layout {
     int nx, ny;
-    int pitch;          // elements per padded row
-    int rows;           // padded rows per field
-    long long fstride;  // elements per field
+    int pitch;          // elements (doubles or float2) per padded row
+    int rows;           // padded rows per plane
+    long long fstride;  // elements per plane
+    int paired;         // 1: FP32 field-pair planes
     __host__ __device__ long long at(int i, int j) const {
         return (long long)(j + GY) * pitch + (i + GX);
+    }
+    // scalar index of field f (background field when bgfield) at (i, j)
+    __host__ __device__ long long idx(int f, int i, int j, bool bgfield) const {
+        if (!paired) return (long long)f * fstride + at(i, j);
+        const int pl = bgfield ? (f >> 1) : pair_plane(f), cp = bgfield ? (f & 1) : pair_comp(f);
+        return 2 * ((long long)pl * fstride + at(i, j)) + cp;
     }
 };
 
@@ -47,6 +62,39 @@ struct DevScalars {
     int status;               // ST_OK or an error code
     int pad;
 };
+
+__device__ __forceinline__ double decode_speed(unsigned long long b, int fp32)
+{
+    return fp32 ? (double)__uint_as_float((unsigned)b) : __longlong_as_double((long long)b);
+}
+
+// Start one RK step of one run: the CFL step dt = C min(dx/cmax_x, dy/cmax_y)
+// from the signal speeds of the current state (section 2: the maximum wave
+// speed sets the step and the hyper-viscosity), clipped so that t lands on
+// t_end; those speeds scale the hyper-diffusion of the step's four stages.
+// A non-finite speed or step marks the run failed and skips its stages.
+__device__ __forceinline__ void step_begin(DevScalars* sc, double dx, double dy, double courant, int fp32,
+                                           double dt_override)
+{
+    if (sc->status != ST_OK || sc->done) { sc->skip = 1; return; }
+    double cx = decode_speed(sc->cmax_bits[0], fp32), cy = decode_speed(sc->cmax_bits[1], fp32);
+    double dt;
+    if (dt_override > 0.0) dt = dt_override;
+    else if (sc->fixed_dt > 0.0) dt = sc->fixed_dt;
+    else { double tx = dx / cx, ty = dy / cy; dt = courant * fmin(tx, ty); }
+    if (!(dt > 0.0) || !isfinite(dt) || !isfinite(cx) || !isfinite(cy)) {
+        sc->status = ST_ERR_NONFINITE; sc->skip = 1; return;
+    }
+    int last = 0;
+    if (sc->t + dt >= sc->t_end) { dt = sc->t_end - sc->t; last = 1; }
+    sc->dt = dt;
+    sc->cmax_step[0] = cx; sc->cmax_step[1] = cy;
+    sc->t = last ? sc->t_end : sc->t + dt;
+    sc->steps += 1;
+    if (last) sc->done = 1;
+    sc->cmax_bits[0] = sc->cmax_bits[1] = 0ull;
+    sc->skip = 0;
+}
 
 template <typename T>
 struct StageArgs {

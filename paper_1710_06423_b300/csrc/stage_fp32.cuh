@@ -1,0 +1,446 @@
+// stage_fp32.cuh -- the FP32 fused RK stage of the split ideal-MHD system
+// (section 2 of arXiv 1710.06423), built for B300 (sm_103a).
+//
+// Data layout ("field pairs"): the six conserved perturbations are stored as
+// three float2 planes P0 = (rho~, e~), P1 = (m_x, m_y), P2 = (B~x, B~y) (and
+// the background as (rho_b, e_b), (B_bx, B_by)).  Every variable gets the same
+// hyper-diffusion arithmetic and the flux of each pair has a common form, so
+// one packed f32x2 instruction (fma/add/sub/mul.rn.f32x2) advances two
+// variables at once and every stencil offset stays an aligned 8-byte access.
+//
+// One CTA (128 threads) owns a 32 x 32 tile:
+//   0. stage the tile + 3-cell halo of the three planes into shared memory
+//      with 8-byte cp.async (odd row strides keep row-mapped phases free of
+//      bank conflicts);
+//   1. per staged cell: v = m/rho, total pressure, energy-flux factor, B.v,
+//      the x fluxes (cells x0-2..x0+TX+1 of the tile rows) and y fluxes
+//      (rows y0-2..y0+TY+1 of the tile columns) of all three pairs;
+//   2. shock indicator s = max(0, -div v) around the tile;
+//   3. X sweep: each thread walks 8 cells of one row with register windows:
+//      face differences d1, d3, the max over three faces, the face
+//      hyper-diffusion flux and the x flux derivative -> k_x (kept in shared
+//      memory over the dead x-flux buffer);
+//   4. Y sweep: each thread walks 8 cells of one column the same way, adds
+//      k_x, applies the RK stage update (D scheme, see below), stores the
+//      stage output with its ghost copies and, in stage 4, reduces the
+//      maximum signal speed of the new state.
+//
+// RK registers (D scheme, 22.5 values moved per cell-stage):
+//   s1: S1 = U0 + dt/2 k1
+//   s2: D = (S1 - U0)/3 + dt/3 k2,  S2 = U0 + dt/2 k2
+//   s3: D += dt/3 k3,               S3 = U0 + dt k3
+//   s4: U0 = U0 + (D + dt/6 k4)
+// (S1 - U0 is exact when both are within a factor of two, so the new state is
+// rounded once per step.)
+#pragma once
+#include "sac_internal.cuh"
+#include "speed.cuh"
+
+namespace sac {
+namespace f32k {
+
+// ---- packed f32x2 arithmetic ------------------------------------------------
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{.reg .b64 A, B, D; mov.b64 A, {%2, %3}; mov.b64 B, {%4, %5};"
+        " add.rn.f32x2 D, A, B; mov.b64 {%0, %1}, D;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{.reg .b64 A, B, D; mov.b64 A, {%2, %3}; mov.b64 B, {%4, %5};"
+        " sub.rn.f32x2 D, A, B; mov.b64 {%0, %1}, D;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{.reg .b64 A, B, D; mov.b64 A, {%2, %3}; mov.b64 B, {%4, %5};"
+        " mul.rn.f32x2 D, A, B; mov.b64 {%0, %1}, D;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 r;
+    asm("{.reg .b64 A, B, C, D; mov.b64 A, {%2, %3}; mov.b64 B, {%4, %5}; mov.b64 C, {%6, %7};"
+        " fma.rn.f32x2 D, A, B, C; mov.b64 {%0, %1}, D;}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float max3abs(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(fabsf(a)), "f"(fabsf(b)), "f"(fabsf(c)));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float v)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
+}
+
+// ---- tile geometry ------------------------------------------------------------
+constexpr int TX = 32, TY = 32, NT = 128, SEG = 8;
+constexpr int RX = TX + 8, RY = TY + 6, RXP = RX + 1;      // staged region (cols x0-4.., rows y0-3..)
+constexpr int FXW = TX + 4, FXP = FXW + 1;                 // x fluxes: cols x0-2 .. x0+TX+1
+constexpr int FYH = TY + 4;                                // y fluxes: rows y0-2 .. y0+TY+1
+constexpr int SW = TX + 2, SH = TY + 2, SP = SW + 1;       // shock indicator: x0-1.., y0-1..
+constexpr int KXP = TX + 1;                                // k_x rows (aliases the x fluxes)
+
+struct Smem {
+    float2 u[3][RY][RXP];
+    float2 fx[3][TY][FXP];     // reused as kx[3][TY][KXP] after the X sweep
+    float2 fy[3][FYH][TX];
+    float2 s[SH][SP];          // (s, s): the shock indicator duplicated for packed use
+    float vx[RY][RX];
+    float vy[RY][RX];
+};
+static_assert(sizeof(float2) * 3 * TY * KXP <= sizeof(float2) * 3 * TY * FXP, "kx must fit in fx");
+
+__device__ __forceinline__ int wrap_i(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+__device__ __forceinline__ int ghost_list(int i, int n, int bc, int* list)
+{
+    int cnt = 0;
+    list[cnt++] = i;
+    if (bc == BC_PERIODIC) {
+        for (int g = -GY; g < 0; ++g) if (wrap_i(g, n) == i) list[cnt++] = g;
+        for (int g = n; g < n + GY; ++g) if (wrap_i(g, n) == i) list[cnt++] = g;
+    } else if (bc == BC_OUTFLOW) {
+        if (i == 0) { list[cnt++] = -1; list[cnt++] = -2; list[cnt++] = -3; }
+        if (i == n - 1) { list[cnt++] = n; list[cnt++] = n + 1; list[cnt++] = n + 2; }
+    }
+    return cnt;
+}
+
+// One tile (x0, y0) of one run; every thread of the CTA calls it (it holds
+// barriers).  `red` is a block-shared scratch for the stage-4 reduction.
+template <int STAGE, bool BG, bool HD>
+__device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x0, const int y0, Smem& S,
+                                          unsigned long long (*red)[NT / 32])
+{
+    const Layout L = a.L;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float2* __restrict__ gin = reinterpret_cast<const float2*>(a.sin);
+    const long long P = L.fstride;              // plane stride in float2 elements
+    // region (r, c) <-> interior (x0 - 4 + c, y0 - 3 + r) <-> padded element (y0 + r) * pitch + x0 + c
+    const long long rbase = (long long)y0 * L.pitch + x0;
+
+    // ---- 0. stage the three planes ----------------------------------------
+    for (int v = tid; v < 3 * RY * RX; v += NT) {
+        int p = v / (RY * RX), rem = v - p * (RY * RX);
+        int r = rem / RX, c = rem - r * RX;
+        cp_async8(&S.u[p][r][c], gin + p * P + rbase + (long long)r * L.pitch + c);
+    }
+    // warm L2 with the pointwise registers this stage reads at the end
+    if (STAGE >= 2) {
+        const float2* u0 = reinterpret_cast<const float2*>(a.u0);
+        const float2* dd = reinterpret_cast<const float2*>(a.acc);
+        for (int v = tid; v < 3 * TY * 2; v += NT) {      // 2 lines of 128 B per tile row
+            int p = v / (TY * 2), rem = v - p * TY * 2, r = rem >> 1, h = rem & 1;
+            long long e = p * P + L.at(x0 + 16 * h, y0 + r);
+            prefetch_l2(u0 + e);
+            if (STAGE >= 3) prefetch_l2(dd + e);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    const float gm1 = (float)(a.gamma - 1.0);
+    const float2* __restrict__ gbg = reinterpret_cast<const float2*>(a.bg);
+
+    // ---- 1. primitives and fluxes on the staged box [x0-3, x0+TX+3) x [y0-3, y0+TY+3)
+    for (int v = tid; v < RY * (RX - 2); v += NT) {
+        const int r = v / (RX - 2), c = 1 + (v - r * (RX - 2));
+        const float2 P0 = S.u[0][r][c], P1 = S.u[1][r][c], P2 = S.u[2][r][c];
+        const float mx = P1.x, my = P1.y, btx = P2.x, bty = P2.y, et = P0.y;
+        float ux, uy, pt, etot, bx, by;
+        float2 bb2 = make_float2(0.f, 0.f);
+        if constexpr (BG) {
+            const long long e = rbase + (long long)r * L.pitch + c;
+            const float2 B0 = __ldg(gbg + e), B1 = __ldg(gbg + P + e);   // (rho_b, e_b), (B_bx, B_by)
+            bb2 = B1;
+            const float rinv = rcp_approx(B0.x + P0.x);
+            ux = mx * rinv; uy = my * rinv;
+            const float ekin = 0.5f * (mx * ux + my * uy);
+            const float bb = B1.x * btx + B1.y * bty;
+            const float b2p = 0.5f * (btx * btx + bty * bty);
+            const float pk = gm1 * (((et - ekin) - bb) - b2p);
+            pt = (pk + bb) + b2p;
+            const float b2b = 0.5f * (B1.x * B1.x + B1.y * B1.y);
+            const float ptb = gm1 * (B0.y - b2b) + b2b;
+            etot = ((et + B0.y) + pt) + ptb;
+            bx = B1.x + btx; by = B1.y + bty;
+        } else {
+            const float rinv = rcp_approx(P0.x);
+            ux = mx * rinv; uy = my * rinv;
+            const float ekin = 0.5f * (mx * ux + my * uy);
+            const float b2p = 0.5f * (btx * btx + bty * bty);
+            pt = gm1 * ((et - ekin) - b2p) + b2p;
+            etot = et + pt;
+            bx = btx; by = bty;
+        }
+        S.vx[r][c] = ux; S.vy[r][c] = uy;
+        const float bv = bx * ux + by * uy;
+        if (r >= 3 && r < 3 + TY && c >= 2 && c < 2 + FXW) {
+            // x fluxes: (m_x, F_e), (F_mx, F_my), (0, F_By)
+            float2 f1 = fma2(splat(ux), P1, make_float2(pt, 0.f));
+            f1 = fma2(splat(-btx), P2, f1);
+            if constexpr (BG) { f1 = fma2(splat(-btx), bb2, f1); f1 = fma2(splat(-bb2.x), P2, f1); }
+            S.fx[0][r - 3][c - 2] = make_float2(mx, ux * etot - bx * bv);
+            S.fx[1][r - 3][c - 2] = f1;
+            S.fx[2][r - 3][c - 2] = make_float2(0.f, ux * by - bx * uy);
+        }
+        if (c >= 4 && c < 4 + TX && r >= 1 && r < 1 + FYH) {
+            // y fluxes: (m_y, F_e), (F_mx, F_my), (F_Bx, 0)
+            float2 f1 = fma2(splat(uy), P1, make_float2(0.f, pt));
+            f1 = fma2(splat(-bty), P2, f1);
+            if constexpr (BG) { f1 = fma2(splat(-bty), bb2, f1); f1 = fma2(splat(-bb2.y), P2, f1); }
+            S.fy[0][r - 1][c - 4] = make_float2(my, uy * etot - by * bv);
+            S.fy[1][r - 1][c - 4] = f1;
+            S.fy[2][r - 1][c - 4] = make_float2(uy * bx - by * ux, 0.f);
+        }
+    }
+    __syncthreads();
+
+    const float inv12dx = (float)(1.0 / (12.0 * a.dx)), inv12dy = (float)(1.0 / (12.0 * a.dy));
+
+    // ---- 2. shock indicator on [x0-1, x0+TX] x [y0-1, y0+TY] ---------------------
+    if constexpr (HD) {
+        for (int v = tid; v < SH * SW; v += NT) {
+            const int sr = v / SW, scn = v - sr * SW;
+            const int r = sr + 2, c = scn + 3;
+            const float dvx = (8.f * (S.vx[r][c + 1] - S.vx[r][c - 1]) - (S.vx[r][c + 2] - S.vx[r][c - 2])) * inv12dx;
+            const float dvy = (8.f * (S.vy[r + 1][c] - S.vy[r - 1][c]) - (S.vy[r + 2][c] - S.vy[r - 2][c])) * inv12dy;
+            const float sv = fmaxf(0.f, -(dvx + dvy));
+            S.s[sr][scn] = make_float2(sv, sv);
+        }
+        __syncthreads();
+    }
+
+    // hyper-diffusion face coefficients with 1/d^2 folded in:
+    //   nu_f / d^2 = (c2 cmax / d) R_f + (c_shk / 2) (s_i + s_{i+1})
+    const float cmx = (float)a.sc->cmax_step[0], cmy = (float)a.sc->cmax_step[1];
+    const float2 ax[3] = {make_float2((float)(a.c2[0] / a.dx) * cmx, (float)(a.c2[3] / a.dx) * cmx),
+                          make_float2((float)(a.c2[1] / a.dx) * cmx, (float)(a.c2[2] / a.dx) * cmx),
+                          make_float2((float)(a.c2[4] / a.dx) * cmx, (float)(a.c2[5] / a.dx) * cmx)};
+    const float2 ay[3] = {make_float2((float)(a.c2[0] / a.dy) * cmy, (float)(a.c2[3] / a.dy) * cmy),
+                          make_float2((float)(a.c2[1] / a.dy) * cmy, (float)(a.c2[2] / a.dy) * cmy),
+                          make_float2((float)(a.c2[4] / a.dy) * cmy, (float)(a.c2[5] / a.dy) * cmy)};
+    const float2 bh = splat((float)(0.5 * a.c_shk));
+    const float2 m12x = splat(-inv12dx), m12y = splat(-inv12dy), eight = splat(8.f), m3 = splat(-3.f);
+
+    // ---- 3. X sweep: thread = (row lane, 8-cell segment warp) -------------------
+    {
+        const int row = lane, x_0 = warp * SEG;
+        float2 kx[3][SEG];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            // u at cells x_0-3 .. x_0+SEG+2  (region col = cell + 4)
+            float2 u[SEG + 6];
+#pragma unroll
+            for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][row + 3][x_0 - 3 + q + 4];
+            float2 hx[SEG];
+#pragma unroll
+            for (int q = 0; q < SEG; ++q) hx[q] = make_float2(0.f, 0.f);
+            if constexpr (HD) {
+                // faces f = x_0-2 .. x_0+SEG (face f between cells f, f+1); index q = f - (x_0-2)
+                float2 d1[SEG + 3], d3[SEG + 3];
+#pragma unroll
+                for (int q = 0; q < SEG + 3; ++q) {
+                    // cells f-1, f, f+1, f+2 at u indices q, q+1, q+2, q+3
+                    d1[q] = sub2(u[q + 2], u[q + 1]);
+                    d3[q] = fma2(m3, d1[q], sub2(u[q + 3], u[q]));
+                }
+                float2 G[SEG + 1];   // faces x_0-1 .. x_0+SEG-1 (q = 1 .. SEG+1)
+#pragma unroll
+                for (int q = 1; q <= SEG + 1; ++q) {
+                    float m1x = fmaxf(max3abs(d1[q - 1].x, d1[q].x, d1[q + 1].x), 1e-30f);
+                    float m1y = fmaxf(max3abs(d1[q - 1].y, d1[q].y, d1[q + 1].y), 1e-30f);
+                    float m3x = max3abs(d3[q - 1].x, d3[q].x, d3[q + 1].x);
+                    float m3y = max3abs(d3[q - 1].y, d3[q].y, d3[q + 1].y);
+                    float2 R = mul2(make_float2(m3x, m3y), make_float2(rcp_approx(m1x), rcp_approx(m1y)));
+                    // s at cells f and f+1: shock array col = cell - (x0-1) = f + 1
+                    const int f = x_0 - 2 + q;
+                    float2 sf = add2(S.s[row + 1][f + 1], S.s[row + 1][f + 2]);
+                    float2 nu = fma2(ax[p], R, mul2(bh, sf));
+                    G[q - 1] = mul2(nu, d1[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < SEG; ++q) hx[q] = sub2(G[q + 1], G[q]);
+            }
+            // x flux derivative: F at cells x_0-2 .. x_0+SEG+1 (fx col = cell + 2)
+            float2 F[SEG + 4];
+#pragma unroll
+            for (int q = 0; q < SEG + 4; ++q) F[q] = S.fx[p][row][x_0 + q];
+#pragma unroll
+            for (int q = 0; q < SEG; ++q) {
+                float2 d = fma2(eight, sub2(F[q + 3], F[q + 1]), sub2(F[q], F[q + 4]));
+                kx[p][q] = fma2(m12x, d, hx[q]);
+            }
+        }
+        __syncthreads();   // every thread is done with the x fluxes
+        float2 (*KX)[TY][KXP] = reinterpret_cast<float2 (*)[TY][KXP]>(&S.fx[0][0][0]);
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < SEG; ++q) KX[p][row][x_0 + q] = kx[p][q];
+    }
+    __syncthreads();
+
+    // ---- 4. Y sweep, RK update, stores ---------------------------------------------
+    const float2 (*KX)[TY][KXP] = reinterpret_cast<const float2 (*)[TY][KXP]>(&S.fx[0][0][0]);
+    const int col = lane, y_0 = warp * SEG;
+    const int gi = x0 + col;
+    const double dtd = a.sc->dt;
+    const float2 h2 = splat((float)(0.5 * dtd)), dt2 = splat((float)dtd), d3t = splat((float)(dtd / 3.0)),
+                 d6t = splat((float)(dtd / 6.0)), third = splat((float)(1.0 / 3.0));
+    const bool edge = (x0 < GY) || (x0 + TX > L.nx - GY) || (y0 < GY) || (y0 + TY > L.ny - GY);
+    float2* __restrict__ gout = reinterpret_cast<float2*>(a.sout);
+    const float2* __restrict__ gu0 = reinterpret_cast<const float2*>(a.u0);
+    float2* __restrict__ gacc = reinterpret_cast<float2*>(a.acc);
+    float2 outv[SEG][3];
+
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        float2 u[SEG + 6];
+#pragma unroll
+        for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][y_0 - 3 + q + 3][col + 4];
+        float2 hy[SEG];
+#pragma unroll
+        for (int q = 0; q < SEG; ++q) hy[q] = make_float2(0.f, 0.f);
+        if constexpr (HD) {
+            float2 d1[SEG + 3], d3[SEG + 3];
+#pragma unroll
+            for (int q = 0; q < SEG + 3; ++q) {
+                d1[q] = sub2(u[q + 2], u[q + 1]);
+                d3[q] = fma2(m3, d1[q], sub2(u[q + 3], u[q]));
+            }
+            float2 G[SEG + 1];
+#pragma unroll
+            for (int q = 1; q <= SEG + 1; ++q) {
+                float m1x = fmaxf(max3abs(d1[q - 1].x, d1[q].x, d1[q + 1].x), 1e-30f);
+                float m1y = fmaxf(max3abs(d1[q - 1].y, d1[q].y, d1[q + 1].y), 1e-30f);
+                float m3x = max3abs(d3[q - 1].x, d3[q].x, d3[q + 1].x);
+                float m3y = max3abs(d3[q - 1].y, d3[q].y, d3[q + 1].y);
+                float2 R = mul2(make_float2(m3x, m3y), make_float2(rcp_approx(m1x), rcp_approx(m1y)));
+                const int f = y_0 - 2 + q;   // face between rows f and f+1 (tile coordinates)
+                float2 sf = add2(S.s[f + 1][col + 1], S.s[f + 2][col + 1]);
+                float2 nu = fma2(ay[p], R, mul2(bh, sf));
+                G[q - 1] = mul2(nu, d1[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < SEG; ++q) hy[q] = sub2(G[q + 1], G[q]);
+        }
+        float2 F[SEG + 4];
+#pragma unroll
+        for (int q = 0; q < SEG + 4; ++q) F[q] = S.fy[p][y_0 + q][col];
+#pragma unroll
+        for (int q = 0; q < SEG; ++q) {
+            const int j = y0 + y_0 + q;
+            float2 d = fma2(eight, sub2(F[q + 3], F[q + 1]), sub2(F[q], F[q + 4]));
+            float2 k = add2(fma2(m12y, d, hy[q]), KX[p][y_0 + q][col]);
+            const float2 ucen = u[q + 3];
+            float2 o;
+            if (gi < L.nx && j < L.ny) {
+                const long long e = p * P + L.at(gi, j);
+                if (STAGE == 1) {
+                    o = fma2(h2, k, ucen);
+                } else if (STAGE == 2) {
+                    const float2 u0 = gu0[e];
+                    gacc[e] = fma2(d3t, k, mul2(third, sub2(ucen, u0)));
+                    o = fma2(h2, k, u0);
+                } else if (STAGE == 3) {
+                    const float2 u0 = gu0[e];
+                    gacc[e] = fma2(d3t, k, gacc[e]);
+                    o = fma2(dt2, k, u0);
+                } else {
+                    const float2 u0 = gu0[e];
+                    o = add2(u0, fma2(d6t, k, gacc[e]));
+                }
+                if (!edge) {
+                    gout[e] = o;
+                } else {
+                    int xs[7], ys[7];
+                    const int nxs = ghost_list(gi, L.nx, a.bc_x, xs), nys = ghost_list(j, L.ny, a.bc_y, ys);
+                    for (int yy = 0; yy < nys; ++yy)
+                        for (int xx = 0; xx < nxs; ++xx) gout[p * P + L.at(xs[xx], ys[yy])] = o;
+                }
+            } else {
+                o = make_float2(0.f, 0.f);
+            }
+            outv[q][p] = o;
+        }
+    }
+
+    if (STAGE == 4) {
+        unsigned long long m[2] = {0ull, 0ull};
+#pragma unroll
+        for (int q = 0; q < SEG; ++q) {
+            const int j = y0 + y_0 + q;
+            if (gi < L.nx && j < L.ny) {
+                float sx, sy;
+                const float2 o0 = outv[q][0], o1 = outv[q][1], o2 = outv[q][2];
+                if constexpr (BG) {
+                    const long long e = L.at(gi, j);
+                    const float2 B0 = __ldg(gbg + e), B1 = __ldg(gbg + P + e);
+                    signal_speeds<float, true>(o0.x, o1.x, o1.y, o0.y, o2.x, o2.y, B0.x, B0.y, B1.x, B1.y,
+                                               (float)a.gamma, sx, sy);
+                } else {
+                    signal_speeds<float, false>(o0.x, o1.x, o1.y, o0.y, o2.x, o2.y, 0.f, 0.f, 0.f, 0.f,
+                                                (float)a.gamma, sx, sy);
+                }
+                unsigned long long kx_ = speed_key(sx), ky_ = speed_key(sy);
+                m[0] = kx_ > m[0] ? kx_ : m[0];
+                m[1] = ky_ > m[1] ? ky_ : m[1];
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            unsigned long long v = m[d];
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+                v = w > v ? w : v;
+            }
+            if (lane == 0) red[d][warp] = v;
+        }
+        __syncthreads();
+        if (tid < 2) {
+            unsigned long long v = 0ull;
+            for (int w = 0; w < NT / 32; ++w) v = red[tid][w] > v ? red[tid][w] : v;
+            atomicMax(&a.sc->cmax_bits[tid], v);
+        }
+    }
+}
+
+template <int STAGE, bool BG, bool HD>
+__global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a)
+{
+    if (a.sc->skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long red[2][NT / 32];
+    tile_body<STAGE, BG, HD>(a, blockIdx.x * TX, blockIdx.y * TY, *reinterpret_cast<Smem*>(smem_raw), red);
+}
+
+}  // namespace f32k
+}  // namespace sac

@@ -24,17 +24,30 @@
 
 namespace sac {
 
-// RK register schemes.
-//  FP64 (K scheme, bit-compatible with U0 + dt/6 (((k1+2k2)+2k3)+k4)):
+// RK register schemes (classical RK4, section 2), chosen per precision.
+//  K (FP64; bit-compatible with U0 + dt/6 (((k1+2k2)+2k3)+k4)):
 //    s1: K = k1,      S = U0 + dt/2 k1      s2: K += 2 k2, S = U0 + dt/2 k2
 //    s3: K += 2 k3,   S = U0 + dt k3        s4: U0 = U0 + dt/6 (K + k4)
-//  FP32 (A scheme, 21 values moved per cell-stage instead of 25.5):
+//    25.5 values moved per cell-stage.
+//  A (accumulator of the new state; 21 values per cell-stage):
 //    s1: S1 = U0 + dt/2 k1
 //    s2: A = U0 + (S1 - U0)/3 + dt/3 k2,   S2 = U0 + dt/2 k2
 //    s3: A += dt/3 k3,                     S3 = U0 + dt k3
 //    s4: U0 = A + dt/6 k4
-template <typename T> struct UsesKScheme { static constexpr bool value = false; };
-template <> struct UsesKScheme<double> { static constexpr bool value = true; };
+//  D (accumulator of the increment; 22.5 values per cell-stage):
+//    s1: S1 = U0 + dt/2 k1
+//    s2: D = (S1 - U0)/3 + dt/3 k2,        S2 = U0 + dt/2 k2
+//    s3: D += dt/3 k3,                     S3 = U0 + dt k3
+//    s4: U0 = U0 + (D + dt/6 k4)
+//    S1 - U0 is exact when the two are within a factor of two (Sterbenz), so
+//    D carries dt/6 k1 without the rounding of a state-sized sum; the new
+//    state is rounded once per step, as in the K scheme.
+enum { RK_K = 0, RK_A = 1, RK_D = 2 };
+#ifndef SAC_FP32_RK
+#define SAC_FP32_RK RK_D
+#endif
+template <typename T> struct RkScheme { static constexpr int value = SAC_FP32_RK; };
+template <> struct RkScheme<double> { static constexpr int value = RK_K; };
 
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return fmax(a, b); }
 template <> __device__ __forceinline__ float tmax<float>(float a, float b) { return fmaxf(a, b); }
@@ -330,7 +343,8 @@ stage_generic(const StageArgs<T> a)
         for (int f = 0; f < NF; ++f) {
             const long long gf = (long long)f * L.fstride + g;
             const T kf = k[f][cI];
-            if constexpr (UsesKScheme<T>::value) {
+            constexpr int RK = RkScheme<T>::value;
+            if constexpr (RK == RK_K) {
                 if (STAGE == 1) {
                     T u0 = sU[f * RN + c];
                     a.acc[gf] = kf;
@@ -343,7 +357,7 @@ stage_generic(const StageArgs<T> a)
                     T u0 = a.u0[gf];
                     out[f] = u0 + d6 * (a.acc[gf] + kf);
                 }
-            } else {
+            } else if constexpr (RK == RK_A) {
                 if (STAGE == 1) {
                     out[f] = sU[f * RN + c] + h * kf;
                 } else if (STAGE == 2) {
@@ -357,6 +371,22 @@ stage_generic(const StageArgs<T> a)
                     out[f] = u0 + dt * kf;
                 } else {
                     out[f] = a.acc[gf] + d6 * kf;
+                }
+            } else {
+                if (STAGE == 1) {
+                    out[f] = sU[f * RN + c] + h * kf;
+                } else if (STAGE == 2) {
+                    T u0 = a.u0[gf];
+                    T s1 = sU[f * RN + c];
+                    a.acc[gf] = third * (s1 - u0) + d3 * kf;
+                    out[f] = u0 + h * kf;
+                } else if (STAGE == 3) {
+                    T u0 = a.u0[gf];
+                    a.acc[gf] = a.acc[gf] + d3 * kf;
+                    out[f] = u0 + dt * kf;
+                } else {
+                    T u0 = a.u0[gf];
+                    out[f] = u0 + (a.acc[gf] + d6 * kf);
                 }
             }
         }
