@@ -1,0 +1,415 @@
+// batch.cu -- many independent FP32 runs of uneven grid size advanced
+// together: one kernel launch per RK stage over a shared tile queue, per-run
+// CFL steps, CUDA-graph replay of whole batch steps, and an autotuner over
+// the launch configuration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "sac_ctx.h"
+#include "stage_fp32.cuh"
+
+using namespace sac;
+
+namespace {
+
+struct RunCtl {
+    DevScalars* sc;
+    double dx, dy, courant;
+};
+
+struct BatchArgs {
+    const StageArgs<float>* args;   // [nruns][4]: arguments of each run for stage 1..4
+    const int4* tiles;              // queue order: (run, tile x, tile y, 0)
+    int ntiles;
+    unsigned* counters;             // [4] per-stage queue heads (persistent mode)
+    int persistent;
+};
+
+// Start one step of every run; also re-arms the four stage queues.
+__global__ void batch_begin_kernel(const RunCtl* __restrict__ ctl, int n, unsigned* counters)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 4) counters[i] = 0u;
+    if (i < n) step_begin(ctl[i].sc, ctl[i].dx, ctl[i].dy, ctl[i].courant, 1, 0.0);
+}
+
+template <int STAGE, bool BG, bool HD>
+__global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long red[2][f32k::NW];
+    __shared__ __align__(16) StageArgs<float> sa;
+    __shared__ int tile_s;
+    f32k::Smem& S = *reinterpret_cast<f32k::Smem*>(smem_raw);
+    for (int it = 0;; ++it) {
+        if (threadIdx.x == 0) {
+            if (b.persistent) tile_s = (int)atomicAdd(&b.counters[STAGE - 1], 1u);
+            else tile_s = it == 0 ? (int)blockIdx.x : b.ntiles;
+        }
+        __syncthreads();
+        const int t = tile_s;
+        if (t >= b.ntiles) break;
+        const int4 d = b.tiles[t];
+        {
+            // stage the run's arguments in shared memory (uniform reads from then on)
+            const int* src = reinterpret_cast<const int*>(&b.args[d.x * 4 + (STAGE - 1)]);
+            int* dst = reinterpret_cast<int*>(&sa);
+            for (int k = threadIdx.x; k < (int)(sizeof(StageArgs<float>) / sizeof(int)); k += blockDim.x)
+                dst[k] = src[k];
+        }
+        __syncthreads();
+        if (!sa.sc->skip) f32k::tile_body<STAGE, BG, HD>(sa, d.y * f32k::TX, d.z * f32k::TY, S, red);
+        __syncthreads();   // shared memory and `sa` are reused by the next tile
+    }
+}
+
+template <int S, bool BG, bool HD>
+cudaError_t set_attr()
+{
+    return cudaFuncSetAttribute(stage_fp32_batch<S, BG, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(f32k::Smem));
+}
+
+template <bool BG, bool HD>
+cudaError_t attr_all()
+{
+    cudaError_t e = set_attr<1, BG, HD>();
+    if (e == cudaSuccess) e = set_attr<2, BG, HD>();
+    if (e == cudaSuccess) e = set_attr<3, BG, HD>();
+    if (e == cudaSuccess) e = set_attr<4, BG, HD>();
+    return e;
+}
+
+template <bool BG, bool HD>
+cudaError_t launch(const BatchArgs& a, int stage, int grid, cudaStream_t s)
+{
+    const size_t sm = sizeof(f32k::Smem);
+    switch (stage) {
+        case 1: stage_fp32_batch<1, BG, HD><<<grid, f32k::NT, sm, s>>>(a); break;
+        case 2: stage_fp32_batch<2, BG, HD><<<grid, f32k::NT, sm, s>>>(a); break;
+        case 3: stage_fp32_batch<3, BG, HD><<<grid, f32k::NT, sm, s>>>(a); break;
+        default: stage_fp32_batch<4, BG, HD><<<grid, f32k::NT, sm, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+struct sac_batch {
+    int n = 0;
+    std::vector<sac_ctx*> runs;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    bool hd = true, bg = false;
+    int nsm = 148;
+    StageArgs<float>* d_args = nullptr;
+    RunCtl* d_ctl = nullptr;
+    int4* d_tiles = nullptr;
+    unsigned* d_counters = nullptr;
+    int ntiles = 0;
+    int persistent = 1, ctas_per_sm = 2, order = 1;
+    cudaGraphExec_t g1 = nullptr, gN = nullptr;
+    char err[512] = {0};
+};
+
+static int bfail(sac_batch* b, int code, const char* fmt, ...)
+{
+    if (b) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b->err, sizeof(b->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define BK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? SAC_ERR_OOM : SAC_ERR_CUDA,  \
+                         "%s failed: %s", #call, cudaGetErrorString(e_));                  \
+    } while (0)
+
+// Tile queue for one order:
+//  0: runs in the given order, tiles row-major within a run;
+//  1: runs by decreasing cell count (big runs first balance the tail);
+//  2: runs by decreasing cell count, tiles interleaved round-robin across runs.
+static std::vector<int4> make_tiles(const sac_batch* b, int order)
+{
+    std::vector<int> idx(b->n);
+    for (int i = 0; i < b->n; ++i) idx[i] = i;
+    if (order >= 1)
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) {
+            return (long long)b->runs[a]->p.nx * b->runs[a]->p.ny > (long long)b->runs[c]->p.nx * b->runs[c]->p.ny;
+        });
+    std::vector<std::vector<int4>> per(b->n);
+    for (int r : idx) {
+        const int tx = (b->runs[r]->p.nx + f32k::TX - 1) / f32k::TX, ty = (b->runs[r]->p.ny + f32k::TY - 1) / f32k::TY;
+        for (int y = 0; y < ty; ++y)
+            for (int x = 0; x < tx; ++x) per[r].push_back(make_int4(r, x, y, 0));
+    }
+    std::vector<int4> out;
+    if (order <= 1) {
+        for (int r : idx) out.insert(out.end(), per[r].begin(), per[r].end());
+    } else {
+        size_t most = 0;
+        for (int r : idx) most = std::max(most, per[r].size());
+        for (size_t k = 0; k < most; ++k)
+            for (int r : idx)
+                if (k < per[r].size()) out.push_back(per[r][k]);
+    }
+    return out;
+}
+
+static cudaError_t enqueue_batch_step(sac_batch* b, cudaStream_t s)
+{
+    batch_begin_kernel<<<(b->n + 127) / 128, 128, 0, s>>>(b->d_ctl, b->n, b->d_counters);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    BatchArgs a;
+    a.args = b->d_args; a.tiles = b->d_tiles; a.ntiles = b->ntiles; a.counters = b->d_counters;
+    a.persistent = b->persistent;
+    const int grid = b->persistent ? std::min(b->ntiles, b->ctas_per_sm * b->nsm) : b->ntiles;
+    for (int stage = 1; stage <= 4 && e == cudaSuccess; ++stage) {
+        if (b->bg) e = b->hd ? launch<true, true>(a, stage, grid, s) : launch<true, false>(a, stage, grid, s);
+        else e = b->hd ? launch<false, true>(a, stage, grid, s) : launch<false, false>(a, stage, grid, s);
+    }
+    return e;
+}
+
+static void drop_graphs(sac_batch* b)
+{
+    if (b->g1) cudaGraphExecDestroy(b->g1);
+    if (b->gN) cudaGraphExecDestroy(b->gN);
+    b->g1 = b->gN = nullptr;
+}
+
+static cudaError_t capture_batch(sac_batch* b, int nsteps, cudaGraphExec_t* out)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = enqueue_batch_step(b, b->cap);
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+static int apply_config(sac_batch* b, int persistent, int ctas, int order)
+{
+    if ((persistent != 0 && persistent != 1) || ctas < 1 || ctas > 2 || order < 0 || order > 2)
+        return bfail(b, SAC_ERR_ARG, "bad configuration (%d, %d, %d)", persistent, ctas, order);
+    std::vector<int4> t = make_tiles(b, order);
+    BK(cudaMemcpyAsync(b->d_tiles, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    b->persistent = persistent; b->ctas_per_sm = ctas; b->order = order;
+    drop_graphs(b);
+    return SAC_OK;
+}
+
+extern "C" {
+
+const char* sac_batch_last_error(const sac_batch* b) { return b ? b->err : "no batch"; }
+
+void sac_batch_free(sac_batch* b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    for (sac_ctx* c : b->runs) sac_free(c);
+    cudaFree(b->d_args); cudaFree(b->d_ctl); cudaFree(b->d_tiles); cudaFree(b->d_counters);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+int sac_batch_init(const sac_params* runs, int n, sac_batch** out)
+{
+    if (out) *out = nullptr;
+    if (!runs || !out || n < 1) return SAC_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (runs[i].precision != SAC_FP32 || runs[i].device != runs[0].device || runs[i].stream != runs[0].stream ||
+            runs[i].hyperdiffusion != runs[0].hyperdiffusion || runs[i].has_background != runs[0].has_background)
+            return SAC_ERR_ARG;
+    }
+    sac_batch* b = new sac_batch();
+    b->n = n;
+    b->stream = (cudaStream_t)runs[0].stream;
+    b->hd = runs[0].hyperdiffusion != 0;
+    b->bg = runs[0].has_background != 0;
+    for (int i = 0; i < n; ++i) {
+        sac_ctx* c = nullptr;
+        int rc = sac_init(&runs[i], &c);
+        if (rc != SAC_OK) {
+            bfail(b, rc, "run %d: sac_init failed (%s)", i, sac_status_string(rc));
+            sac_batch_free(b);
+            return rc;
+        }
+        b->runs.push_back(c);
+    }
+    int rc = SAC_OK;
+    do {
+        cudaError_t e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, runs[0].device);
+        if (e == cudaSuccess) e = attr_all<false, false>();
+        if (e == cudaSuccess) e = attr_all<false, true>();
+        if (e == cudaSuccess) e = attr_all<true, false>();
+        if (e == cudaSuccess) e = attr_all<true, true>();
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { rc = bfail(b, SAC_ERR_CUDA, "set-up: %s", cudaGetErrorString(e)); break; }
+        std::vector<StageArgs<float>> args(4 * n);
+        std::vector<RunCtl> ctl(n);
+        long long ntiles = 0;
+        for (int i = 0; i < n; ++i) {
+            const sac_ctx* c = b->runs[i];
+            for (int s = 1; s <= 4; ++s) sac_fp32_stage_args(c, s, &args[4 * i + s - 1]);
+            ctl[i].sc = c->sc;
+            ctl[i].dx = (c->p.x1 - c->p.x0) / c->p.nx;
+            ctl[i].dy = (c->p.y1 - c->p.y0) / c->p.ny;
+            ctl[i].courant = c->p.courant;
+            ntiles += (long long)((c->p.nx + f32k::TX - 1) / f32k::TX) * ((c->p.ny + f32k::TY - 1) / f32k::TY);
+        }
+        if (ntiles > (1LL << 30)) { rc = bfail(b, SAC_ERR_ARG, "too many tiles"); break; }
+        b->ntiles = (int)ntiles;
+        if (cudaMalloc(&b->d_args, args.size() * sizeof(StageArgs<float>)) != cudaSuccess ||
+            cudaMalloc(&b->d_ctl, n * sizeof(RunCtl)) != cudaSuccess ||
+            cudaMalloc(&b->d_tiles, ntiles * sizeof(int4)) != cudaSuccess ||
+            cudaMalloc(&b->d_counters, 4 * sizeof(unsigned)) != cudaSuccess) {
+            rc = bfail(b, SAC_ERR_OOM, "batch tables");
+            break;
+        }
+        e = cudaMemcpy(b->d_args, args.data(), args.size() * sizeof(StageArgs<float>), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_ctl, ctl.data(), n * sizeof(RunCtl), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, 4 * sizeof(unsigned));
+        if (e != cudaSuccess) { rc = bfail(b, SAC_ERR_CUDA, "tables: %s", cudaGetErrorString(e)); break; }
+        rc = apply_config(b, 1, 2, 1);
+    } while (0);
+    if (rc != SAC_OK) {
+        sac_batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return SAC_OK;
+}
+
+int sac_batch_set_state(sac_batch* b, int run, const double* w, const double* bg, double t)
+{
+    if (!b || run < 0 || run >= b->n) return bfail(b, SAC_ERR_ARG, "bad run index");
+    int rc = sac_set_state(b->runs[run], w, bg, t);
+    if (rc != SAC_OK) return bfail(b, rc, "run %d: %s", run, sac_last_error(b->runs[run]));
+    return SAC_OK;
+}
+
+int sac_batch_get_state(sac_batch* b, int run, double* w, double* t)
+{
+    if (!b || run < 0 || run >= b->n) return bfail(b, SAC_ERR_ARG, "bad run index");
+    int rc = sac_get_state(b->runs[run], w, t);
+    if (rc != SAC_OK) return bfail(b, rc, "run %d: %s", run, sac_last_error(b->runs[run]));
+    return SAC_OK;
+}
+
+int sac_batch_time(sac_batch* b, int run, double* t, long* steps)
+{
+    if (!b || run < 0 || run >= b->n) return bfail(b, SAC_ERR_ARG, "bad run index");
+    int rc = sac_time(b->runs[run], t, steps);
+    if (rc != SAC_OK) return bfail(b, rc, "run %d: %s", run, sac_last_error(b->runs[run]));
+    return SAC_OK;
+}
+
+int sac_batch_steps(sac_batch* b, long nsteps)
+{
+    if (!b) return SAC_ERR_ARG;
+    if (nsteps < 0) return bfail(b, SAC_ERR_ARG, "nsteps < 0");
+    for (int i = 0; i < b->n; ++i)
+        if (!b->runs[i]->have_state) return bfail(b, SAC_ERR_STATE, "run %d has no state", i);
+    if (!b->g1) BK(capture_batch(b, 1, &b->g1));
+    if (!b->gN && nsteps >= kChunk) BK(capture_batch(b, kChunk, &b->gN));
+    long left = nsteps;
+    while (left >= kChunk) { BK(cudaGraphLaunch(b->gN, b->stream)); left -= kChunk; }
+    while (left > 0) { BK(cudaGraphLaunch(b->g1, b->stream)); --left; }
+    return SAC_OK;
+}
+
+int sac_batch_sync(sac_batch* b)
+{
+    if (!b) return SAC_ERR_ARG;
+    BK(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->n; ++i) {
+        int rc = sac_sync(b->runs[i]);
+        if (rc != SAC_OK) return bfail(b, rc, "run %d: %s", i, sac_last_error(b->runs[i]));
+    }
+    return SAC_OK;
+}
+
+int sac_batch_set_config(sac_batch* b, int persistent, int ctas_per_sm, int order)
+{
+    if (!b) return SAC_ERR_ARG;
+    return apply_config(b, persistent, ctas_per_sm, order);
+}
+
+int sac_batch_tune(sac_batch* b, int trials, int config[3], double* ms_out)
+{
+    if (!b) return SAC_ERR_ARG;
+    if (trials < 1) return bfail(b, SAC_ERR_ARG, "trials < 1");
+    for (int i = 0; i < b->n; ++i)
+        if (!b->runs[i]->have_state) return bfail(b, SAC_ERR_STATE, "run %d has no state", i);
+    // snapshot every run's state and scalars; trials advance them
+    std::vector<void*> snap(b->n, nullptr);
+    std::vector<DevScalars> ssc(b->n);
+    int rc = SAC_OK;
+    for (int i = 0; i < b->n && rc == SAC_OK; ++i) {
+        sac_ctx* c = b->runs[i];
+        const size_t bytes = NF * (size_t)c->L.fstride * c->esz;
+        if (cudaMalloc(&snap[i], bytes) != cudaSuccess) { rc = bfail(b, SAC_ERR_OOM, "tuner snapshot"); break; }
+        if (cudaMemcpyAsync(snap[i], c->u0, bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&ssc[i], c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+            rc = bfail(b, SAC_ERR_CUDA, "tuner snapshot copy");
+    }
+    if (rc == SAC_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) rc = bfail(b, SAC_ERR_CUDA, "sync");
+    const int cand[9][3] = {{1, 2, 0}, {1, 2, 1}, {1, 2, 2}, {1, 1, 0}, {1, 1, 1}, {1, 1, 2},
+                            {0, 2, 0}, {0, 2, 1}, {0, 2, 2}};
+    double best = 1e300;
+    int bi = 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == SAC_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = bfail(b, SAC_ERR_CUDA, "events");
+    for (int k = 0; k < 9 && rc == SAC_OK; ++k) {
+        if ((rc = apply_config(b, cand[k][0], cand[k][1], cand[k][2])) != SAC_OK) break;
+        if (enqueue_batch_step(b, b->stream) != cudaSuccess) { rc = bfail(b, SAC_ERR_CUDA, "trial"); break; }
+        cudaEventRecord(e0, b->stream);
+        for (int t = 0; t < trials; ++t)
+            if (enqueue_batch_step(b, b->stream) != cudaSuccess) { rc = bfail(b, SAC_ERR_CUDA, "trial"); break; }
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = bfail(b, SAC_ERR_CUDA, "trial sync"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / trials < best) { best = ms / trials; bi = k; }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    // restore states and scalars
+    for (int i = 0; i < b->n; ++i) {
+        sac_ctx* c = b->runs[i];
+        if (snap[i]) {
+            const size_t bytes = NF * (size_t)c->L.fstride * c->esz;
+            cudaMemcpyAsync(c->u0, snap[i], bytes, cudaMemcpyDeviceToDevice, b->stream);
+            cudaMemcpyAsync(c->sc, &ssc[i], sizeof(DevScalars), cudaMemcpyHostToDevice, b->stream);
+        }
+    }
+    cudaStreamSynchronize(b->stream);
+    for (void* p : snap) cudaFree(p);
+    if (rc != SAC_OK) return rc;
+    rc = apply_config(b, cand[bi][0], cand[bi][1], cand[bi][2]);
+    if (rc != SAC_OK) return rc;
+    if (config) { config[0] = cand[bi][0]; config[1] = cand[bi][1]; config[2] = cand[bi][2]; }
+    if (ms_out) *ms_out = best;
+    return SAC_OK;
+}
+
+}  // extern "C"

@@ -100,13 +100,30 @@ __device__ __forceinline__ void prefetch_l2(const void* p)
     asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
 }
 
+// Division flavours (compile-time): the fast path uses rcp.approx for 1/rho and
+// for the hyper-diffusion ratio; SAC_FP32_IEEE_DIV=1 selects correctly rounded
+// division for both (accuracy studies).
+#ifndef SAC_FP32_IEEE_DIV
+#define SAC_FP32_IEEE_DIV 0
+#endif
+__device__ __forceinline__ float fdiv(float a, float b)
+{
+#if SAC_FP32_IEEE_DIV
+    return __fdiv_rn(a, b);
+#else
+    return a * rcp_approx(b);
+#endif
+}
+
 // ---- tile geometry ------------------------------------------------------------
-constexpr int TX = 32, TY = 32, NT = 128, SEG = 8;
+constexpr int TX = 32, TY = 32, NT = 256, NW = NT / 32, SEG = 4;
+static_assert(TX / SEG == NW && TY / SEG == NW, "one segment per warp in both sweeps");
 constexpr int RX = TX + 8, RY = TY + 6, RXP = RX + 1;      // staged region (cols x0-4.., rows y0-3..)
 constexpr int FXW = TX + 4, FXP = FXW + 1;                 // x fluxes: cols x0-2 .. x0+TX+1
 constexpr int FYH = TY + 4;                                // y fluxes: rows y0-2 .. y0+TY+1
 constexpr int SW = TX + 2, SH = TY + 2, SP = SW + 1;       // shock indicator: x0-1.., y0-1..
 constexpr int KXP = TX + 1;                                // k_x rows (aliases the x fluxes)
+constexpr int PW = RX - 2;                                 // primitive columns 1 .. RX-2
 
 struct Smem {
     float2 u[3][RY][RXP];
@@ -115,6 +132,7 @@ struct Smem {
     float2 s[SH][SP];          // (s, s): the shock indicator duplicated for packed use
     float vx[RY][RX];
     float vy[RY][RX];
+    float2 ax[3], ay[3];       // per-pair hyper-diffusion coefficients c2 cmax / d
 };
 static_assert(sizeof(float2) * 3 * TY * KXP <= sizeof(float2) * 3 * TY * FXP, "kx must fit in fx");
 
@@ -133,92 +151,134 @@ __device__ __forceinline__ int ghost_list(int i, int n, int bc, int* list)
     return cnt;
 }
 
+// Face hyper-diffusion fluxes G (already divided by d^2) on the SEG+1 faces
+// around a segment of SEG cells, from the SEG+6 values u of the segment plus
+// a 3-cell halo on each side, and the duplicated shock indicators s2 of the
+// SEG+2 cells around it:
+//   d1_f = u_{f+1} - u_f,   d3_f = (u_{f+2} - u_{f-1}) - 3 d1_f,
+//   R_f  = max(|d3_{f-1}|,|d3_f|,|d3_{f+1}|) / max(|d1_{f-1}|,|d1_f|,|d1_{f+1}|)  (0 if 0/0),
+//   G_f  = (a R_f + (c_shk/2)(s_f + s_{f+1})) d1_f.
+// A zero denominator means d1 is zero on all three faces, so G is zero: the
+// denominator is clamped to 1e-30 and the product with d1 = 0 gives that 0.
+__device__ __forceinline__ void face_fluxes(const float2 (&u)[SEG + 6], const float2 (&s2)[SEG + 2],
+                                            float2 a, float2 bh, float2 (&G)[SEG + 1])
+{
+    const float2 m3 = splat(-3.f);
+    float2 d1[SEG + 3], d3[SEG + 3];
+#pragma unroll
+    for (int q = 0; q < SEG + 3; ++q) {   // face f = q - 2 relative to the first cell
+        d1[q] = sub2(u[q + 2], u[q + 1]);
+        d3[q] = fma2(m3, d1[q], sub2(u[q + 3], u[q]));
+    }
+#pragma unroll
+    for (int q = 1; q <= SEG + 1; ++q) {
+        const float m1x = fmaxf(max3abs(d1[q - 1].x, d1[q].x, d1[q + 1].x), 1e-30f);
+        const float m1y = fmaxf(max3abs(d1[q - 1].y, d1[q].y, d1[q + 1].y), 1e-30f);
+        const float m3x = max3abs(d3[q - 1].x, d3[q].x, d3[q + 1].x);
+        const float m3y = max3abs(d3[q - 1].y, d3[q].y, d3[q + 1].y);
+        const float2 R = make_float2(fdiv(m3x, m1x), fdiv(m3y, m1y));
+        const float2 sf = add2(s2[q - 1], s2[q]);
+        const float2 nu = fma2(a, R, mul2(bh, sf));
+        G[q - 1] = mul2(nu, d1[q]);
+    }
+}
+
 // One tile (x0, y0) of one run; every thread of the CTA calls it (it holds
 // barriers).  `red` is a block-shared scratch for the stage-4 reduction.
 template <int STAGE, bool BG, bool HD>
 __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x0, const int y0, Smem& S,
-                                          unsigned long long (*red)[NT / 32])
+                                          unsigned long long (*red)[NW])
 {
     const Layout L = a.L;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2* __restrict__ gin = reinterpret_cast<const float2*>(a.sin);
+    const float2* __restrict__ gbg = reinterpret_cast<const float2*>(a.bg);
     const long long P = L.fstride;              // plane stride in float2 elements
     // region (r, c) <-> interior (x0 - 4 + c, y0 - 3 + r) <-> padded element (y0 + r) * pitch + x0 + c
     const long long rbase = (long long)y0 * L.pitch + x0;
 
-    // ---- 0. stage the three planes ----------------------------------------
-    for (int v = tid; v < 3 * RY * RX; v += NT) {
-        int p = v / (RY * RX), rem = v - p * (RY * RX);
-        int r = rem / RX, c = rem - r * RX;
-        cp_async8(&S.u[p][r][c], gin + p * P + rbase + (long long)r * L.pitch + c);
-    }
-    // warm L2 with the pointwise registers this stage reads at the end
-    if (STAGE >= 2) {
-        const float2* u0 = reinterpret_cast<const float2*>(a.u0);
-        const float2* dd = reinterpret_cast<const float2*>(a.acc);
-        for (int v = tid; v < 3 * TY * 2; v += NT) {      // 2 lines of 128 B per tile row
-            int p = v / (TY * 2), rem = v - p * TY * 2, r = rem >> 1, h = rem & 1;
-            long long e = p * P + L.at(x0 + 16 * h, y0 + r);
-            prefetch_l2(u0 + e);
-            if (STAGE >= 3) prefetch_l2(dd + e);
+    // ---- 0. stage the three planes (8-byte cp.async; incremental indices) ------
+#pragma unroll 1
+    for (int p = 0; p < 3; ++p) {
+        const float2* src = gin + p * P + rbase;
+        int r = tid / RX, c = tid - (tid / RX) * RX;
+#pragma unroll 1
+        for (int v = tid; v < RY * RX; v += NT) {
+            cp_async8(&S.u[p][r][c], src + (long long)r * L.pitch + c);
+            c += NT % RX; r += NT / RX;
+            if (c >= RX) { c -= RX; ++r; }
         }
+    }
+    if (tid < 3) {
+        const float cmx = (float)a.sc->cmax_step[0], cmy = (float)a.sc->cmax_step[1];
+        const int f0 = tid == 0 ? 0 : (tid == 1 ? 1 : 4), f1 = tid == 0 ? 3 : (tid == 1 ? 2 : 5);
+        S.ax[tid] = make_float2((float)(a.c2[f0] / a.dx) * cmx, (float)(a.c2[f1] / a.dx) * cmx);
+        S.ay[tid] = make_float2((float)(a.c2[f0] / a.dy) * cmy, (float)(a.c2[f1] / a.dy) * cmy);
     }
     cp_async_wait_all();
     __syncthreads();
 
     const float gm1 = (float)(a.gamma - 1.0);
-    const float2* __restrict__ gbg = reinterpret_cast<const float2*>(a.bg);
 
     // ---- 1. primitives and fluxes on the staged box [x0-3, x0+TX+3) x [y0-3, y0+TY+3)
-    for (int v = tid; v < RY * (RX - 2); v += NT) {
-        const int r = v / (RX - 2), c = 1 + (v - r * (RX - 2));
-        const float2 P0 = S.u[0][r][c], P1 = S.u[1][r][c], P2 = S.u[2][r][c];
-        const float mx = P1.x, my = P1.y, btx = P2.x, bty = P2.y, et = P0.y;
-        float ux, uy, pt, etot, bx, by;
-        float2 bb2 = make_float2(0.f, 0.f);
-        if constexpr (BG) {
-            const long long e = rbase + (long long)r * L.pitch + c;
-            const float2 B0 = __ldg(gbg + e), B1 = __ldg(gbg + P + e);   // (rho_b, e_b), (B_bx, B_by)
-            bb2 = B1;
-            const float rinv = rcp_approx(B0.x + P0.x);
-            ux = mx * rinv; uy = my * rinv;
-            const float ekin = 0.5f * (mx * ux + my * uy);
-            const float bb = B1.x * btx + B1.y * bty;
-            const float b2p = 0.5f * (btx * btx + bty * bty);
-            const float pk = gm1 * (((et - ekin) - bb) - b2p);
-            pt = (pk + bb) + b2p;
-            const float b2b = 0.5f * (B1.x * B1.x + B1.y * B1.y);
-            const float ptb = gm1 * (B0.y - b2b) + b2b;
-            etot = ((et + B0.y) + pt) + ptb;
-            bx = B1.x + btx; by = B1.y + bty;
-        } else {
-            const float rinv = rcp_approx(P0.x);
-            ux = mx * rinv; uy = my * rinv;
-            const float ekin = 0.5f * (mx * ux + my * uy);
-            const float b2p = 0.5f * (btx * btx + bty * bty);
-            pt = gm1 * ((et - ekin) - b2p) + b2p;
-            etot = et + pt;
-            bx = btx; by = bty;
-        }
-        S.vx[r][c] = ux; S.vy[r][c] = uy;
-        const float bv = bx * ux + by * uy;
-        if (r >= 3 && r < 3 + TY && c >= 2 && c < 2 + FXW) {
-            // x fluxes: (m_x, F_e), (F_mx, F_my), (0, F_By)
-            float2 f1 = fma2(splat(ux), P1, make_float2(pt, 0.f));
-            f1 = fma2(splat(-btx), P2, f1);
-            if constexpr (BG) { f1 = fma2(splat(-btx), bb2, f1); f1 = fma2(splat(-bb2.x), P2, f1); }
-            S.fx[0][r - 3][c - 2] = make_float2(mx, ux * etot - bx * bv);
-            S.fx[1][r - 3][c - 2] = f1;
-            S.fx[2][r - 3][c - 2] = make_float2(0.f, ux * by - bx * uy);
-        }
-        if (c >= 4 && c < 4 + TX && r >= 1 && r < 1 + FYH) {
-            // y fluxes: (m_y, F_e), (F_mx, F_my), (F_Bx, 0)
-            float2 f1 = fma2(splat(uy), P1, make_float2(0.f, pt));
-            f1 = fma2(splat(-bty), P2, f1);
-            if constexpr (BG) { f1 = fma2(splat(-bty), bb2, f1); f1 = fma2(splat(-bb2.y), P2, f1); }
-            S.fy[0][r - 1][c - 4] = make_float2(my, uy * etot - by * bv);
-            S.fy[1][r - 1][c - 4] = f1;
-            S.fy[2][r - 1][c - 4] = make_float2(uy * bx - by * ux, 0.f);
+    {
+        int r = tid / PW, c = 1 + tid - (tid / PW) * PW;
+#pragma unroll 1
+        for (int v = tid; v < RY * PW; v += NT) {
+            const float2 P0 = S.u[0][r][c], P1 = S.u[1][r][c], P2 = S.u[2][r][c];
+            const float mx = P1.x, my = P1.y, btx = P2.x, bty = P2.y, et = P0.y;
+            float ux, uy, pt, etot, bx, by;
+            float2 bb2 = make_float2(0.f, 0.f);
+            if constexpr (BG) {
+                const long long e = rbase + (long long)r * L.pitch + c;
+                const float2 B0 = __ldg(gbg + e), B1 = __ldg(gbg + P + e);   // (rho_b, e_b), (B_bx, B_by)
+                bb2 = B1;
+                const float rinv = fdiv(1.f, B0.x + P0.x);
+                ux = mx * rinv; uy = my * rinv;
+                const float ekin = 0.5f * (mx * ux + my * uy);
+                const float bb = B1.x * btx + B1.y * bty;
+                const float b2p = 0.5f * (btx * btx + bty * bty);
+                const float pk = gm1 * (((et - ekin) - bb) - b2p);
+                pt = (pk + bb) + b2p;
+                const float b2b = 0.5f * (B1.x * B1.x + B1.y * B1.y);
+                const float ptb = gm1 * (B0.y - b2b) + b2b;
+                etot = ((et + B0.y) + pt) + ptb;
+                bx = B1.x + btx; by = B1.y + bty;
+            } else {
+#if SAC_FP32_IEEE_DIV
+                ux = __fdiv_rn(mx, P0.x); uy = __fdiv_rn(my, P0.x);
+#else
+                const float rinv = rcp_approx(P0.x);
+                ux = mx * rinv; uy = my * rinv;
+#endif
+                const float ekin = 0.5f * (mx * ux + my * uy);
+                const float b2p = 0.5f * (btx * btx + bty * bty);
+                pt = gm1 * ((et - ekin) - b2p) + b2p;
+                etot = et + pt;
+                bx = btx; by = bty;
+            }
+            S.vx[r][c] = ux; S.vy[r][c] = uy;
+            const float bv = bx * ux + by * uy;
+            if (r >= 3 && r < 3 + TY && c >= 2 && c < 2 + FXW) {
+                // x fluxes: (m_x, F_e), (F_mx, F_my), (0, F_By)
+                float2 f1 = fma2(splat(ux), P1, make_float2(pt, 0.f));
+                f1 = fma2(splat(-btx), P2, f1);
+                if constexpr (BG) { f1 = fma2(splat(-btx), bb2, f1); f1 = fma2(splat(-bb2.x), P2, f1); }
+                S.fx[0][r - 3][c - 2] = make_float2(mx, ux * etot - bx * bv);
+                S.fx[1][r - 3][c - 2] = f1;
+                S.fx[2][r - 3][c - 2] = make_float2(0.f, ux * by - bx * uy);
+            }
+            if (c >= 4 && c < 4 + TX && r >= 1 && r < 1 + FYH) {
+                // y fluxes: (m_y, F_e), (F_mx, F_my), (F_Bx, 0)
+                float2 f1 = fma2(splat(uy), P1, make_float2(0.f, pt));
+                f1 = fma2(splat(-bty), P2, f1);
+                if constexpr (BG) { f1 = fma2(splat(-bty), bb2, f1); f1 = fma2(splat(-bb2.y), P2, f1); }
+                S.fy[0][r - 1][c - 4] = make_float2(my, uy * etot - by * bv);
+                S.fy[1][r - 1][c - 4] = f1;
+                S.fy[2][r - 1][c - 4] = make_float2(uy * bx - by * ux, 0.f);
+            }
+            c += NT % PW; r += NT / PW;
+            if (c >= 1 + PW) { c -= PW; ++r; }
         }
     }
     __syncthreads();
@@ -227,75 +287,51 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 
     // ---- 2. shock indicator on [x0-1, x0+TX] x [y0-1, y0+TY] ---------------------
     if constexpr (HD) {
+        int sr = tid / SW, scn = tid - (tid / SW) * SW;
+#pragma unroll 1
         for (int v = tid; v < SH * SW; v += NT) {
-            const int sr = v / SW, scn = v - sr * SW;
             const int r = sr + 2, c = scn + 3;
             const float dvx = (8.f * (S.vx[r][c + 1] - S.vx[r][c - 1]) - (S.vx[r][c + 2] - S.vx[r][c - 2])) * inv12dx;
             const float dvy = (8.f * (S.vy[r + 1][c] - S.vy[r - 1][c]) - (S.vy[r + 2][c] - S.vy[r - 2][c])) * inv12dy;
             const float sv = fmaxf(0.f, -(dvx + dvy));
             S.s[sr][scn] = make_float2(sv, sv);
+            scn += NT % SW; sr += NT / SW;
+            if (scn >= SW) { scn -= SW; ++sr; }
         }
         __syncthreads();
     }
 
-    // hyper-diffusion face coefficients with 1/d^2 folded in:
-    //   nu_f / d^2 = (c2 cmax / d) R_f + (c_shk / 2) (s_i + s_{i+1})
-    const float cmx = (float)a.sc->cmax_step[0], cmy = (float)a.sc->cmax_step[1];
-    const float2 ax[3] = {make_float2((float)(a.c2[0] / a.dx) * cmx, (float)(a.c2[3] / a.dx) * cmx),
-                          make_float2((float)(a.c2[1] / a.dx) * cmx, (float)(a.c2[2] / a.dx) * cmx),
-                          make_float2((float)(a.c2[4] / a.dx) * cmx, (float)(a.c2[5] / a.dx) * cmx)};
-    const float2 ay[3] = {make_float2((float)(a.c2[0] / a.dy) * cmy, (float)(a.c2[3] / a.dy) * cmy),
-                          make_float2((float)(a.c2[1] / a.dy) * cmy, (float)(a.c2[2] / a.dy) * cmy),
-                          make_float2((float)(a.c2[4] / a.dy) * cmy, (float)(a.c2[5] / a.dy) * cmy)};
     const float2 bh = splat((float)(0.5 * a.c_shk));
-    const float2 m12x = splat(-inv12dx), m12y = splat(-inv12dy), eight = splat(8.f), m3 = splat(-3.f);
+    const float2 m12x = splat(-inv12dx), m12y = splat(-inv12dy), eight = splat(8.f);
 
-    // ---- 3. X sweep: thread = (row lane, 8-cell segment warp) -------------------
+    // ---- 3. X sweep: thread = (row lane, SEG-cell segment per warp) ---------------
     {
         const int row = lane, x_0 = warp * SEG;
         float2 kx[3][SEG];
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            // u at cells x_0-3 .. x_0+SEG+2  (region col = cell + 4)
-            float2 u[SEG + 6];
+            float2 u[SEG + 6];   // cells x_0-3 .. x_0+SEG+2 (region col = cell + 4)
 #pragma unroll
-            for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][row + 3][x_0 - 3 + q + 4];
+            for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][row + 3][x_0 + 1 + q];
             float2 hx[SEG];
-#pragma unroll
-            for (int q = 0; q < SEG; ++q) hx[q] = make_float2(0.f, 0.f);
             if constexpr (HD) {
-                // faces f = x_0-2 .. x_0+SEG (face f between cells f, f+1); index q = f - (x_0-2)
-                float2 d1[SEG + 3], d3[SEG + 3];
+                float2 s2[SEG + 2];   // cells x_0-1 .. x_0+SEG (shock col = cell + 1)
 #pragma unroll
-                for (int q = 0; q < SEG + 3; ++q) {
-                    // cells f-1, f, f+1, f+2 at u indices q, q+1, q+2, q+3
-                    d1[q] = sub2(u[q + 2], u[q + 1]);
-                    d3[q] = fma2(m3, d1[q], sub2(u[q + 3], u[q]));
-                }
-                float2 G[SEG + 1];   // faces x_0-1 .. x_0+SEG-1 (q = 1 .. SEG+1)
-#pragma unroll
-                for (int q = 1; q <= SEG + 1; ++q) {
-                    float m1x = fmaxf(max3abs(d1[q - 1].x, d1[q].x, d1[q + 1].x), 1e-30f);
-                    float m1y = fmaxf(max3abs(d1[q - 1].y, d1[q].y, d1[q + 1].y), 1e-30f);
-                    float m3x = max3abs(d3[q - 1].x, d3[q].x, d3[q + 1].x);
-                    float m3y = max3abs(d3[q - 1].y, d3[q].y, d3[q + 1].y);
-                    float2 R = mul2(make_float2(m3x, m3y), make_float2(rcp_approx(m1x), rcp_approx(m1y)));
-                    // s at cells f and f+1: shock array col = cell - (x0-1) = f + 1
-                    const int f = x_0 - 2 + q;
-                    float2 sf = add2(S.s[row + 1][f + 1], S.s[row + 1][f + 2]);
-                    float2 nu = fma2(ax[p], R, mul2(bh, sf));
-                    G[q - 1] = mul2(nu, d1[q]);
-                }
+                for (int q = 0; q < SEG + 2; ++q) s2[q] = S.s[row + 1][x_0 + q];
+                float2 G[SEG + 1];
+                face_fluxes(u, s2, S.ax[p], bh, G);
 #pragma unroll
                 for (int q = 0; q < SEG; ++q) hx[q] = sub2(G[q + 1], G[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < SEG; ++q) hx[q] = make_float2(0.f, 0.f);
             }
-            // x flux derivative: F at cells x_0-2 .. x_0+SEG+1 (fx col = cell + 2)
-            float2 F[SEG + 4];
+            float2 F[SEG + 4];   // cells x_0-2 .. x_0+SEG+1 (fx col = cell + 2)
 #pragma unroll
             for (int q = 0; q < SEG + 4; ++q) F[q] = S.fx[p][row][x_0 + q];
 #pragma unroll
             for (int q = 0; q < SEG; ++q) {
-                float2 d = fma2(eight, sub2(F[q + 3], F[q + 1]), sub2(F[q], F[q + 4]));
+                const float2 d = fma2(eight, sub2(F[q + 3], F[q + 1]), sub2(F[q], F[q + 4]));
                 kx[p][q] = fma2(m12x, d, hx[q]);
             }
         }
@@ -323,60 +359,54 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
-        float2 u[SEG + 6];
+        // pointwise registers of this pair first, so their latency hides behind the sweep
+        float2 u0v[SEG], dv[SEG];
 #pragma unroll
-        for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][y_0 - 3 + q + 3][col + 4];
+        for (int q = 0; q < SEG; ++q) {
+            const int j = y0 + y_0 + q;
+            const bool ok = gi < L.nx && j < L.ny;
+            const long long e = p * P + L.at(gi, j);
+            u0v[q] = (STAGE >= 2 && ok) ? gu0[e] : make_float2(0.f, 0.f);
+            dv[q] = (STAGE >= 3 && ok) ? gacc[e] : make_float2(0.f, 0.f);
+        }
+        float2 u[SEG + 6];   // rows y_0-3 .. y_0+SEG+2 (region row = cell row + 3)
+#pragma unroll
+        for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][y_0 + q][col + 4];
         float2 hy[SEG];
-#pragma unroll
-        for (int q = 0; q < SEG; ++q) hy[q] = make_float2(0.f, 0.f);
         if constexpr (HD) {
-            float2 d1[SEG + 3], d3[SEG + 3];
+            float2 s2[SEG + 2];   // rows y_0-1 .. y_0+SEG (shock row = cell row + 1)
 #pragma unroll
-            for (int q = 0; q < SEG + 3; ++q) {
-                d1[q] = sub2(u[q + 2], u[q + 1]);
-                d3[q] = fma2(m3, d1[q], sub2(u[q + 3], u[q]));
-            }
+            for (int q = 0; q < SEG + 2; ++q) s2[q] = S.s[y_0 + q][col + 1];
             float2 G[SEG + 1];
-#pragma unroll
-            for (int q = 1; q <= SEG + 1; ++q) {
-                float m1x = fmaxf(max3abs(d1[q - 1].x, d1[q].x, d1[q + 1].x), 1e-30f);
-                float m1y = fmaxf(max3abs(d1[q - 1].y, d1[q].y, d1[q + 1].y), 1e-30f);
-                float m3x = max3abs(d3[q - 1].x, d3[q].x, d3[q + 1].x);
-                float m3y = max3abs(d3[q - 1].y, d3[q].y, d3[q + 1].y);
-                float2 R = mul2(make_float2(m3x, m3y), make_float2(rcp_approx(m1x), rcp_approx(m1y)));
-                const int f = y_0 - 2 + q;   // face between rows f and f+1 (tile coordinates)
-                float2 sf = add2(S.s[f + 1][col + 1], S.s[f + 2][col + 1]);
-                float2 nu = fma2(ay[p], R, mul2(bh, sf));
-                G[q - 1] = mul2(nu, d1[q]);
-            }
+            face_fluxes(u, s2, S.ay[p], bh, G);
 #pragma unroll
             for (int q = 0; q < SEG; ++q) hy[q] = sub2(G[q + 1], G[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < SEG; ++q) hy[q] = make_float2(0.f, 0.f);
         }
-        float2 F[SEG + 4];
+        float2 F[SEG + 4];   // rows y_0-2 .. y_0+SEG+1 (fy row = cell row + 2)
 #pragma unroll
         for (int q = 0; q < SEG + 4; ++q) F[q] = S.fy[p][y_0 + q][col];
 #pragma unroll
         for (int q = 0; q < SEG; ++q) {
             const int j = y0 + y_0 + q;
-            float2 d = fma2(eight, sub2(F[q + 3], F[q + 1]), sub2(F[q], F[q + 4]));
-            float2 k = add2(fma2(m12y, d, hy[q]), KX[p][y_0 + q][col]);
+            const float2 d = fma2(eight, sub2(F[q + 3], F[q + 1]), sub2(F[q], F[q + 4]));
+            const float2 k = add2(fma2(m12y, d, hy[q]), KX[p][y_0 + q][col]);
             const float2 ucen = u[q + 3];
-            float2 o;
+            float2 o = make_float2(0.f, 0.f);
             if (gi < L.nx && j < L.ny) {
                 const long long e = p * P + L.at(gi, j);
                 if (STAGE == 1) {
                     o = fma2(h2, k, ucen);
                 } else if (STAGE == 2) {
-                    const float2 u0 = gu0[e];
-                    gacc[e] = fma2(d3t, k, mul2(third, sub2(ucen, u0)));
-                    o = fma2(h2, k, u0);
+                    gacc[e] = fma2(d3t, k, mul2(third, sub2(ucen, u0v[q])));
+                    o = fma2(h2, k, u0v[q]);
                 } else if (STAGE == 3) {
-                    const float2 u0 = gu0[e];
-                    gacc[e] = fma2(d3t, k, gacc[e]);
-                    o = fma2(dt2, k, u0);
+                    gacc[e] = fma2(d3t, k, dv[q]);
+                    o = fma2(dt2, k, u0v[q]);
                 } else {
-                    const float2 u0 = gu0[e];
-                    o = add2(u0, fma2(d6t, k, gacc[e]));
+                    o = add2(u0v[q], fma2(d6t, k, dv[q]));
                 }
                 if (!edge) {
                     gout[e] = o;
@@ -386,8 +416,6 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
                     for (int yy = 0; yy < nys; ++yy)
                         for (int xx = 0; xx < nxs; ++xx) gout[p * P + L.at(xs[xx], ys[yy])] = o;
                 }
-            } else {
-                o = make_float2(0.f, 0.f);
             }
             outv[q][p] = o;
         }
@@ -410,7 +438,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
                     signal_speeds<float, false>(o0.x, o1.x, o1.y, o0.y, o2.x, o2.y, 0.f, 0.f, 0.f, 0.f,
                                                 (float)a.gamma, sx, sy);
                 }
-                unsigned long long kx_ = speed_key(sx), ky_ = speed_key(sy);
+                const unsigned long long kx_ = speed_key(sx), ky_ = speed_key(sy);
                 m[0] = kx_ > m[0] ? kx_ : m[0];
                 m[1] = ky_ > m[1] ? ky_ : m[1];
             }
@@ -419,7 +447,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         for (int d = 0; d < 2; ++d) {
             unsigned long long v = m[d];
             for (int o = 16; o > 0; o >>= 1) {
-                unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+                const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
                 v = w > v ? w : v;
             }
             if (lane == 0) red[d][warp] = v;
@@ -427,7 +455,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         __syncthreads();
         if (tid < 2) {
             unsigned long long v = 0ull;
-            for (int w = 0; w < NT / 32; ++w) v = red[tid][w] > v ? red[tid][w] : v;
+            for (int w = 0; w < NW; ++w) v = red[tid][w] > v ? red[tid][w] : v;
             atomicMax(&a.sc->cmax_bits[tid], v);
         }
     }
@@ -438,7 +466,7 @@ __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a)
 {
     if (a.sc->skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ unsigned long long red[2][NT / 32];
+    __shared__ unsigned long long red[2][NW];
     tile_body<STAGE, BG, HD>(a, blockIdx.x * TX, blockIdx.y * TY, *reinterpret_cast<Smem*>(smem_raw), red);
 }
 
