@@ -168,6 +168,50 @@ int sac_profile_stages(sac_ctx *c, int nsteps, double ms[5]);
 /* Wait for the context's stream and report a pending device error. */
 int sac_sync(sac_ctx *c);
 
+/* ---------------------------------------------------------------------------
+ * Batched runs: many independent runs of uneven grid size advanced together.
+ * Each RK stage of all runs is ONE kernel launch over a shared queue of
+ * 32x32 tiles (persistent CTAs pulling tiles from an atomic counter, or one
+ * CTA per tile), each run keeps its own CFL step, time and error status, and
+ * each RK step of the whole batch is replayed from a CUDA graph.  Every run
+ * must be SAC_FP32, on the same device and stream, with the same
+ * hyperdiffusion and has_background flags.  The per-run arithmetic is that of
+ * the single-run FP32 path (same tile code), so a batched run reproduces the
+ * single-run result.
+ * ------------------------------------------------------------------------- */
+typedef struct sac_batch sac_batch;
+
+/* Create a batch of n >= 1 runs from runs[0..n-1] (validated as for
+ * sac_init).  Errors: SAC_ERR_ARG, SAC_ERR_OOM, SAC_ERR_CUDA. */
+int sac_batch_init(const sac_params *runs, int n, sac_batch **out);
+void sac_batch_free(sac_batch *b);
+const char *sac_batch_last_error(const sac_batch *b);
+
+/* State of run `run` (0-based), host FP64 arrays as sac_set_state /
+ * sac_get_state.  Synchronous. */
+int sac_batch_set_state(sac_batch *b, int run, const double *w, const double *bg, double t);
+int sac_batch_get_state(sac_batch *b, int run, double *w, double *t);
+
+/* nsteps CFL steps of every run (each with its own dt).  ASYNC. */
+int sac_batch_steps(sac_batch *b, long nsteps);
+
+/* Wait for the batch's stream; report the first run in error. */
+int sac_batch_sync(sac_batch *b);
+
+/* Time and steps taken of one run.  Synchronous. */
+int sac_batch_time(sac_batch *b, int run, double *t, long *steps);
+
+/* Autotuner: times every candidate launch configuration (persistent or one
+ * CTA per tile, 1 or 2 resident CTAs per SM, three tile orders) on `trials`
+ * RK steps of the current states, keeps the fastest and restores the states
+ * it advanced (every run must have a state).  config[3] (may be NULL)
+ * receives (persistent, ctas_per_sm, order); ms (may be NULL) the mean time
+ * of one batch RK step with that configuration.  Synchronous. */
+int sac_batch_tune(sac_batch *b, int trials, int config[3], double *ms);
+
+/* Set the launch configuration directly (values as sac_batch_tune reports). */
+int sac_batch_set_config(sac_batch *b, int persistent, int ctas_per_sm, int order);
+
 #ifdef __cplusplus
 }
 #endif

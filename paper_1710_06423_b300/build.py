@@ -27,6 +27,7 @@ UNITS = [
     ("sac_engine.cu", ["--fmad=false"]),
     ("kernels_fp64.cu", ["--fmad=false"]),
     ("kernels_fp32.cu", []),
+    ("batch.cu", []),
 ]
 
 

@@ -27,6 +27,9 @@ EXPORTS = (
     "sac_set_state", "sac_get_state", "sac_set_state_dev", "sac_get_state_dev",
     "sac_step", "sac_steps", "sac_run_to", "sac_dt", "sac_time", "sac_cmax", "sac_sums",
     "sac_profile_stages", "sac_sync",
+    "sac_batch_init", "sac_batch_free", "sac_batch_last_error", "sac_batch_set_state",
+    "sac_batch_get_state", "sac_batch_steps", "sac_batch_sync", "sac_batch_time", "sac_batch_tune",
+    "sac_batch_set_config",
 )
 
 
@@ -86,6 +89,16 @@ def load() -> ctypes.CDLL:
         "sac_sums": (i, [vp, dp]),
         "sac_profile_stages": (i, [vp, i, dp]),
         "sac_sync": (i, [vp]),
+        "sac_batch_init": (i, [P, i, ctypes.POINTER(vp)]),
+        "sac_batch_free": (None, [vp]),
+        "sac_batch_last_error": (ctypes.c_char_p, [vp]),
+        "sac_batch_set_state": (i, [vp, i, dp, dp, d]),
+        "sac_batch_get_state": (i, [vp, i, dp, dp]),
+        "sac_batch_steps": (i, [vp, L]),
+        "sac_batch_sync": (i, [vp]),
+        "sac_batch_time": (i, [vp, i, dp, ctypes.POINTER(L)]),
+        "sac_batch_tune": (i, [vp, i, ctypes.POINTER(ctypes.c_int), dp]),
+        "sac_batch_set_config": (i, [vp, i, i, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -235,3 +248,98 @@ class Solver:
 
     def sync(self):
         self._check(load().sac_sync(self._ctx), "sac_sync")
+
+
+class Batch:
+    """Many independent FP32 runs advanced together (one launch per RK stage).
+
+    ``Batch([dict(nx=..., ny=..., gamma=...), ...])``: each dict holds the
+    ``sac_params`` fields of one run (precision is FP32 for every run).
+    """
+
+    def __init__(self, runs, stream="current", device=0):
+        lib = load()
+        n = len(runs)
+        arr = (SacParams * n)()
+        if stream == "current":
+            import torch
+            stream = torch.cuda.current_stream(device)
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        for k, kw in enumerate(runs):
+            p = default_params()
+            for key, v in kw.items():
+                if key == "c2":
+                    for j, x in enumerate(v):
+                        p.c2[j] = x
+                else:
+                    setattr(p, key, v)
+            p.precision = FP32
+            p.device = device
+            p.stream = stream or None
+            arr[k] = p
+        self.params = arr
+        self.n = n
+        self._b = ctypes.c_void_p()
+        rc = lib.sac_batch_init(arr, n, ctypes.byref(self._b))
+        if rc != SAC_OK:
+            raise SacError(rc, f"sac_batch_init failed: {lib.sac_status_string(rc).decode()}")
+
+    def _check(self, rc, what):
+        if rc != SAC_OK:
+            lib = load()
+            raise SacError(rc, f"{what}: {lib.sac_status_string(rc).decode()}: "
+                               f"{lib.sac_batch_last_error(self._b).decode()}")
+
+    def close(self):
+        if self._b:
+            load().sac_batch_free(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, run, w, bg=None, t=0.0):
+        p = self.params[run]
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != (NF, p.ny, p.nx):
+            raise ValueError(f"state shape {w.shape} != {(NF, p.ny, p.nx)}")
+        bg = None if bg is None else np.ascontiguousarray(bg, dtype=np.float64)
+        self._check(load().sac_batch_set_state(self._b, run, _dp(w), _dp(bg), float(t)), "sac_batch_set_state")
+
+    def get_state(self, run):
+        p = self.params[run]
+        w = np.empty((NF, p.ny, p.nx), dtype=np.float64)
+        t = ctypes.c_double()
+        self._check(load().sac_batch_get_state(self._b, run, _dp(w), ctypes.byref(t)), "sac_batch_get_state")
+        return w, t.value
+
+    def steps(self, n):
+        self._check(load().sac_batch_steps(self._b, int(n)), "sac_batch_steps")
+
+    def sync(self):
+        self._check(load().sac_batch_sync(self._b), "sac_batch_sync")
+
+    def time(self, run):
+        t, n = ctypes.c_double(), ctypes.c_long()
+        self._check(load().sac_batch_time(self._b, run, ctypes.byref(t), ctypes.byref(n)), "sac_batch_time")
+        return t.value, n.value
+
+    def tune(self, trials=3):
+        cfg = (ctypes.c_int * 3)()
+        ms = ctypes.c_double()
+        self._check(load().sac_batch_tune(self._b, int(trials), cfg, ctypes.byref(ms)), "sac_batch_tune")
+        return tuple(cfg), ms.value
+
+    def set_config(self, persistent, ctas_per_sm, order):
+        self._check(load().sac_batch_set_config(self._b, persistent, ctas_per_sm, order), "sac_batch_set_config")
+
