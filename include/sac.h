@@ -145,6 +145,12 @@ int sac_steps(sac_ctx *c, long nsteps);
  */
 int sac_run_to(sac_ctx *c, double t_end, long max_steps, long *steps_taken);
 
+/* Fixed step size for every later CFL step of this context (sac_steps,
+ * sac_run_to, sac_step with dt <= 0): dt > 0 replaces the CFL step (the signal
+ * speeds still scale the hyper-diffusion); dt <= 0 restores the CFL step.
+ * ASYNC; stays in force until changed or until the next set_state. */
+int sac_set_fixed_dt(sac_ctx *c, double dt);
+
 /* CFL step the next sac_step(c, 0, ...) would take.  Synchronous. */
 int sac_dt(sac_ctx *c, double *dt);
 
@@ -211,6 +217,54 @@ int sac_batch_tune(sac_batch *b, int trials, int config[3], double *ms);
 
 /* Set the launch configuration directly (values as sac_batch_tune reports). */
 int sac_batch_set_config(sac_batch *b, int persistent, int ctas_per_sm, int order);
+
+/* ---------------------------------------------------------------------------
+ * Learned coarse-grid correction (not in the paper; a form built on the
+ * section 2 method): a 4-layer periodic 3x3 convolutional network
+ * f = conv(32->6) . ReLU . conv(32->32) . ReLU . conv(32->32) . ReLU . conv(8->32)
+ * on 8 normalised features of the state (the six conserved fields, the kinetic
+ * pressure p_k and the current j_z = D_x B_y - D_y B_x with the section 2
+ * fourth-order difference, each divided by in_scale[c]).  After a coarse RK4
+ * step the state is corrected by u_f <- u_f + out_scale[f] * f_f(features(u)).
+ * Forward and backward run on BF16 tensor cores (weights and activations in
+ * BF16, FP32 accumulation, FP32 master weights updated with Adam).
+ * Parameters are FP32, flat, per layer W[cout][cin][3][3] then b[cout], layers
+ * in order (sac_cnn_param_count() of them).  Device arrays are packed FP32
+ * [6][ny][nx] conserved states (field order rho, m_x, m_y, e, B_x, B_y) on a
+ * periodic nx x ny grid; pred is FP32 [ny*nx][8] (channels 6, 7 unused).
+ * ------------------------------------------------------------------------- */
+typedef struct sac_cnn sac_cnn;
+
+long sac_cnn_param_count(void);
+/* Network workspace for an nx x ny periodic grid (8 <= nx, ny <= 16384) on
+ * `device`, enqueuing on `stream`.  Weights start at zero, scales at one. */
+int sac_cnn_init(int nx, int ny, int device, void *stream, sac_cnn **out);
+void sac_cnn_free(sac_cnn *c);
+const char *sac_cnn_last_error(const sac_cnn *c);
+/* Host FP32 parameters in/out (n must equal sac_cnn_param_count()); setting
+ * them also resets the optimiser state.  Synchronous. */
+int sac_cnn_set_params(sac_cnn *c, const float *params, long n);
+int sac_cnn_get_params(sac_cnn *c, float *params, long n);
+/* Host feature scales [8] and output scales [6].  Synchronous. */
+int sac_cnn_set_scales(sac_cnn *c, const float in_scale[8], const float out_scale[6]);
+/* pred_dev <- f(features(w_dev)).  ASYNC. */
+int sac_cnn_forward(sac_cnn *c, const float *w_dev, double gamma, double dx, double dy, float *pred_dev);
+/* Loss 0.5 * mean over 6 channels and all pixels of (f - target)^2 and its
+ * gradient with respect to every parameter (host FP32 grads may be NULL; loss
+ * may be NULL).  Synchronous when either output is non-NULL. */
+int sac_cnn_grads(sac_cnn *c, const float *w_dev, const float *target_dev, double gamma, double dx, double dy,
+                  float *grads, double *loss);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) at learning rate lr on that loss.
+ * *loss (may be NULL) receives the loss before the update. */
+int sac_cnn_train_step(sac_cnn *c, const float *w_dev, const float *target_dev, double gamma, double dx, double dy,
+                       double lr, double *loss);
+/* Correct the current state of a periodic SAC_FP32 context of the network's
+ * size in place: u += out_scale * f(features(u)); ghosts and the signal speed
+ * of the corrected state are refreshed so the next CFL step uses them.  ASYNC. */
+int sac_cnn_apply(sac_ctx *ctx, sac_cnn *c);
+/* r x r block average of a packed FP32 device array [nfields][nyf][nxf] into
+ * [nfields][nyf/r][nxf/r] (nxf, nyf multiples of r).  ASYNC on `stream`. */
+int sac_block_average(const float *fine_dev, int nfields, int nxf, int nyf, int r, float *coarse_dev, void *stream);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@ UNITS = [
     ("kernels_fp64.cu", ["--fmad=false"]),
     ("kernels_fp32.cu", []),
     ("batch.cu", []),
+    ("cnn.cu", []),
 ]
 
 

@@ -1,0 +1,786 @@
+// cnn.cu -- the learned coarse-grid correction: a 4-layer periodic 3x3 CNN
+// (8 -> 32 -> 32 -> 32 -> 6 channels, ReLU) whose output, scaled per field, is
+// added to the coarse state after each RK4 step.  Forward and backward run on
+// BF16 tensor cores (mma.sync m16n8k16, FP32 accumulation) in implicit-GEMM
+// kernels written here; the FP32 master weights are updated with Adam.
+//
+// Activations are NHWC bf16 ([pixel][channel], channels padded to 16 or 32).
+// Layer k weights for the forward pass are bf16 [cout][tap][cin] (tap = 3a+e,
+// a the row offset, e the column offset, cin contiguous); for the input
+// gradient they are bf16 [cin][tap'][cout] with tap' = 8 - tap (flipped).
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "sac_ctx.h"
+#include "speed.cuh"
+
+using namespace sac;
+
+namespace {
+
+constexpr int NLAYER = 4;
+constexpr int CIN_REAL[NLAYER] = {8, 32, 32, 32};
+constexpr int COUT_REAL[NLAYER] = {32, 32, 32, 6};
+constexpr int CIN_PAD[NLAYER] = {16, 32, 32, 32};
+constexpr int COUT_PAD[NLAYER] = {32, 32, 32, 8};
+constexpr int TH = 8, TW = 16;               // pixel tile: 8 rows x 16 columns
+constexpr int HH = TH + 2, HW = TW + 2;      // halo tile
+constexpr int NTHR = 128;
+
+long long param_offset(int layer)            // flat FP32 order: W[cout][cin][3][3], then b[cout], per layer
+{
+    long long o = 0;
+    for (int k = 0; k < layer; ++k) o += (long long)COUT_REAL[k] * CIN_REAL[k] * 9 + COUT_REAL[k];
+    return o;
+}
+constexpr long long kParams = 32 * 8 * 9 + 32 + 2 * (32 * 32 * 9 + 32) + 6 * 32 * 9 + 6;   // 22566
+
+// ---- ldmatrix / mma helpers (inline PTX) ---------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(unsigned addr, unsigned& r0, unsigned& r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2_t(unsigned addr, unsigned& r0, unsigned& r1)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void cp16(void* s, const void* g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory"); }
+
+// XOR swizzle of the 16-byte chunks of one pixel row: 8 consecutive rows of an
+// ldmatrix land in 8 different bank groups for 2 or 4 chunks per row.
+template <int CPP>
+__device__ __forceinline__ int swz(int row, int chunk) { return row * CPP + (chunk ^ ((row / (8 / CPP)) % CPP)); }
+
+__device__ __forceinline__ int wrapm(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+
+// Load the (TH+2) x (TW+2) periodic halo tile of an NHWC bf16 image with C
+// channels into shared memory (swizzled 16-byte chunks).
+template <int C>
+__device__ __forceinline__ void load_halo(const __nv_bfloat16* __restrict__ img, int H, int W, int y0, int x0,
+                                          __nv_bfloat16* tile)
+{
+    constexpr int CPP = C / 8;
+    for (int v = threadIdx.x; v < HH * HW * CPP; v += NTHR) {
+        const int p = v / CPP, ch = v - p * CPP;
+        const int ty = p / HW, tx = p - ty * HW;
+        const int gy = wrapm(y0 - 1 + ty, H), gx = wrapm(x0 - 1 + tx, W);
+        cp16(tile + swz<CPP>(p, ch) * 8, img + ((long long)gy * W + gx) * C + ch * 8);
+    }
+}
+
+// ---- implicit-GEMM periodic 3x3 convolution ------------------------------------
+enum { MODE_RELU = 0, MODE_LINEAR_F32 = 1, MODE_MASK = 2 };
+
+struct ConvArgs {
+    const __nv_bfloat16* in;    // [H*W][CIN]
+    const __nv_bfloat16* w;     // [COUT][9][CIN]
+    const float* bias;          // [COUT] or null
+    void* out;                  // bf16 [H*W][COUT] (RELU, MASK) or float [H*W][COUT] (LINEAR_F32)
+    const __nv_bfloat16* mask;  // MASK: [H*W][COUT], output kept where mask > 0
+    int H, W;
+};
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(NTHR) conv3x3_kernel(const ConvArgs a)
+{
+    constexpr int CPP = CIN / 8;                 // 16-byte chunks per pixel
+    constexpr int WROW = 9 * CIN + 8;            // weight row (elements), padded to an odd number of chunks
+    constexpr int NT = COUT / 8;                 // n-tiles
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(smem);                 // [COUT][WROW]
+    __nv_bfloat16* st = sw + COUT * WROW;                                       // [HH*HW][CIN] swizzled
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (int v = threadIdx.x; v < COUT * 9 * CPP; v += NTHR) {
+        const int o = v / (9 * CPP), ch = v - o * 9 * CPP;
+        cp16(sw + o * WROW + ch * 8, a.w + (long long)o * 9 * CIN + ch * 8);
+    }
+    const int tiles_x = (a.W + TW - 1) / TW, tiles_y = (a.H + TH - 1) / TH;
+    for (int tile = blockIdx.x; tile < tiles_x * tiles_y; tile += gridDim.x) {
+        const int y0 = (tile / tiles_x) * TH, x0 = (tile % tiles_x) * TW;
+        __syncthreads();                               // previous tile's readers are done
+        load_halo<CIN>(a.in, a.H, a.W, y0, x0, st);
+        cp_wait();
+        __syncthreads();
+        float acc[2][NT][4];
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.f;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+            for (int kk = 0; kk < CIN / 16; ++kk) {
+                unsigned af[2][4];
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int py = warp * 2 + m;
+                    const int p = (py + dy) * HW + dx + (lane & 15);
+                    ldsm_x4(smem_u32(st + swz<CPP>(p, kk * 2 + (lane >> 4)) * 8), af[m][0], af[m][1], af[m][2], af[m][3]);
+                }
+#pragma unroll
+                for (int n = 0; n < NT; ++n) {
+                    unsigned b0, b1;
+                    const int o = n * 8 + (lane & 7);
+                    ldsm_x2(smem_u32(sw + o * WROW + tap * CIN + kk * 16 + ((lane >> 3) & 1) * 8), b0, b1);
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) mma_bf16(acc[m][n], af[m][0], af[m][1], af[m][2], af[m][3], b0, b1);
+                }
+            }
+        }
+        // epilogue: C fragment rows = pixels g and g+8 of the m-tile, cols = 2 channels
+        const int g = lane >> 2, t2 = (lane & 3) * 2;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int gy = y0 + warp * 2 + m;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int gx = x0 + g + half * 8;
+                if (gy >= a.H || gx >= a.W) continue;
+                const long long pix = (long long)gy * a.W + gx;
+#pragma unroll
+                for (int n = 0; n < NT; ++n) {
+                    const int o = n * 8 + t2;
+                    float v0 = acc[m][n][half * 2 + 0], v1 = acc[m][n][half * 2 + 1];
+                    if (MODE != MODE_MASK && a.bias) { v0 += a.bias[o]; v1 += a.bias[o + 1]; }
+                    if (MODE == MODE_RELU) { v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); }
+                    if (MODE == MODE_MASK) {
+                        const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + pix * COUT + o);
+                        if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                        if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                    }
+                    if (MODE == MODE_LINEAR_F32) {
+                        *reinterpret_cast<float2*>(reinterpret_cast<float*>(a.out) + pix * COUT + o) = make_float2(v0, v1);
+                    } else {
+                        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(a.out) + pix * COUT + o) =
+                            __floats2bfloat162_rn(v0, v1);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---- weight gradient: dW[o][tap][c] = sum_p dY[p][o] X[p + tap][c] ---------------
+struct DwArgs {
+    const __nv_bfloat16* dy;   // [H*W][MO]
+    const __nv_bfloat16* x;    // [H*W][CIN]
+    float* part;               // [gridDim.x][MO][9*CIN]
+    float* dbpart;             // [gridDim.x][MO]
+    int H, W;
+};
+
+template <int CIN, int MO>
+__global__ void __launch_bounds__(NTHR) conv3x3_dw_kernel(const DwArgs a)
+{
+    constexpr int CPPX = CIN / 8, CPPY = MO / 8;
+    constexpr int NTOT = 9 * CIN / 8;                  // n-tiles of 8 over (tap, c)
+    constexpr int NPW = (NTOT + 3) / 4;                // n-tiles per warp
+    constexpr int MT = MO / 16;                        // m-tiles of 16 over o
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16* sx = reinterpret_cast<__nv_bfloat16*>(smem);                 // halo tile [HH*HW][CIN]
+    __nv_bfloat16* sd = sx + HH * HW * CIN;                                     // dY tile [TH*TW][MO]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float acc[MT][NPW][4];
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int n = 0; n < NPW; ++n)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.f;
+    float db = 0.f;
+
+    const int tiles_x = (a.W + TW - 1) / TW, tiles_y = (a.H + TH - 1) / TH;
+    for (int tile = blockIdx.x; tile < tiles_x * tiles_y; tile += gridDim.x) {
+        const int y0 = (tile / tiles_x) * TH, x0 = (tile % tiles_x) * TW;
+        __syncthreads();
+        load_halo<CIN>(a.x, a.H, a.W, y0, x0, sx);
+        for (int v = threadIdx.x; v < TH * TW * CPPY; v += NTHR) {
+            const int p = v / CPPY, ch = v - p * CPPY;
+            const int gy = y0 + p / TW, gx = x0 + p % TW;
+            __nv_bfloat16* dst = sd + swz<CPPY>(p, ch) * 8;
+            if (gy < a.H && gx < a.W) cp16(dst, a.dy + ((long long)gy * a.W + gx) * MO + ch * 8);
+            else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);   // pixels outside the image add nothing
+        }
+        cp_wait();
+        __syncthreads();
+        if (threadIdx.x < MO) {
+            const int o = threadIdx.x;
+            for (int p = 0; p < TH * TW; ++p)
+                db += __bfloat162float(sd[swz<CPPY>(p, o >> 3) * 8 + (o & 7)]);
+        }
+#pragma unroll
+        for (int ks = 0; ks < TH; ++ks) {              // k-step: the 16 pixels of tile row ks
+            unsigned af[MT][4];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                // A[o][p] = dY[p][o]: stored rows p, transposed load; matrix j = lane>>3
+                const int j = lane >> 3;
+                const int p = ks * TW + (j >> 1) * 8 + (lane & 7);
+                const int ch = m * 2 + (j & 1);
+                ldsm_x4_t(smem_u32(sd + swz<CPPY>(p, ch) * 8), af[m][0], af[m][1], af[m][2], af[m][3]);
+            }
+#pragma unroll
+            for (int nn = 0; nn < NPW; ++nn) {
+                const int nt = warp + nn * 4;
+                if (nt >= NTOT) break;
+                const int tap = (nt * 8) / CIN, c0 = (nt * 8) % CIN;
+                const int dyy = tap / 3, dxx = tap % 3;
+                // B[p][(tap,c)] = X[p + tap][c]: stored rows p (halo pixels), transposed load
+                const int hp = (ks + dyy) * HW + dxx + ((lane >> 3) & 1) * 8 + (lane & 7);
+                unsigned b0, b1;
+                ldsm_x2_t(smem_u32(sx + swz<CPPX>(hp, c0 / 8) * 8), b0, b1);
+#pragma unroll
+                for (int m = 0; m < MT; ++m) mma_bf16(acc[m][nn], af[m][0], af[m][1], af[m][2], af[m][3], b0, b1);
+            }
+        }
+    }
+    // partials of this CTA: C rows = o (g, g+8), cols = n (2 per lane)
+    const int g = lane >> 2, t2 = (lane & 3) * 2;
+    float* out = a.part + (long long)blockIdx.x * MO * 9 * CIN;
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int nn = 0; nn < NPW; ++nn) {
+            const int nt = warp + nn * 4;
+            if (nt >= NTOT) break;
+            const int n = nt * 8 + t2;
+            out[(m * 16 + g) * 9 * CIN + n] = acc[m][nn][0];
+            out[(m * 16 + g) * 9 * CIN + n + 1] = acc[m][nn][1];
+            out[(m * 16 + g + 8) * 9 * CIN + n] = acc[m][nn][2];
+            out[(m * 16 + g + 8) * 9 * CIN + n + 1] = acc[m][nn][3];
+        }
+    if (threadIdx.x < MO) a.dbpart[(long long)blockIdx.x * MO + threadIdx.x] = db;
+}
+
+// Sum the per-CTA partials in a fixed order into the flat FP32 gradient of one layer.
+__global__ void dw_reduce_kernel(const float* __restrict__ part, const float* __restrict__ dbpart, int nblk,
+                                 int cin_pad, int mo_pad, int cin, int cout, float* __restrict__ gw,
+                                 float* __restrict__ gb)
+{
+    const int nw = cout * cin * 9;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nw + cout; v += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        if (v < nw) {
+            const int o = v / (cin * 9), rem = v - o * cin * 9, c = rem / 9, tap = rem % 9;
+            const long long idx = (long long)o * 9 * cin_pad + tap * cin_pad + c;
+            for (int b = 0; b < nblk; ++b) s += part[(long long)b * mo_pad * 9 * cin_pad + idx];
+            gw[v] = s;
+        } else {
+            const int o = v - nw;
+            for (int b = 0; b < nblk; ++b) s += dbpart[(long long)b * mo_pad + o];
+            gb[o] = s;
+        }
+    }
+}
+
+// FP32 master parameters -> bf16 forward weights [COUTP][9][CINP] and flipped,
+// transposed input-gradient weights [CINP][9][COUTP] (padding zero), FP32 bias.
+__global__ void pack_weights_kernel(const float* __restrict__ params, int cin, int cout, int cinp, int coutp,
+                                    int coutp_t, __nv_bfloat16* __restrict__ wf, __nv_bfloat16* __restrict__ wt,
+                                    float* __restrict__ bias)
+{
+    const int n = coutp * 9 * cinp;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int o = v / (9 * cinp), rem = v - o * 9 * cinp, tap = rem / cinp, c = rem % cinp;
+        const float w = (o < cout && c < cin) ? params[(o * cin + c) * 9 + tap] : 0.f;
+        const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+        wf[v] = wb;
+        if (wt) wt[((long long)c * 9 + (8 - tap)) * coutp_t + o] = wb;   // padding rows o >= coutp stay zero
+    }
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < coutp; v += gridDim.x * blockDim.x)
+        bias[v] = v < cout ? params[(long long)cout * cin * 9 + v] : 0.f;
+}
+
+// 8 input features (normalised) from a packed FP32 conserved state [6][H][W],
+// periodic: rho, m_x, m_y, e, B_x, B_y, p_k, j_z = D_x B_y - D_y B_x (section 2
+// fourth-order differences); channels 8..15 are zero padding.
+__global__ void features_kernel(const float* __restrict__ w, int H, int W, float gm1, float inv12dx, float inv12dy,
+                                const float* __restrict__ scale, __nv_bfloat16* __restrict__ out)
+{
+    const long long n = (long long)H * W;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(p / W), i = (int)(p % W);
+        const float rho = w[p], mx = w[n + p], my = w[2 * n + p], e = w[3 * n + p], bx = w[4 * n + p], by = w[5 * n + p];
+        const float pk = gm1 * (e - 0.5f * (mx * mx + my * my) / rho - 0.5f * (bx * bx + by * by));
+        const float* BY = w + 5 * n + (long long)j * W;
+        const float dby = (8.f * (BY[wrapm(i + 1, W)] - BY[wrapm(i - 1, W)]) - (BY[wrapm(i + 2, W)] - BY[wrapm(i - 2, W)])) * inv12dx;
+        const float* BX = w + 4 * n + i;
+        const float dbx = (8.f * (BX[(long long)wrapm(j + 1, H) * W] - BX[(long long)wrapm(j - 1, H) * W]) -
+                           (BX[(long long)wrapm(j + 2, H) * W] - BX[(long long)wrapm(j - 2, H) * W])) * inv12dy;
+        const float f[8] = {rho, mx, my, e, bx, by, pk, dby - dbx};
+        __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) o[c] = __float2bfloat16_rn(f[c] / scale[c]);
+#pragma unroll
+        for (int c = 8; c < 16; ++c) o[c] = __float2bfloat16_rn(0.f);
+        uint4* dst = reinterpret_cast<uint4*>(out + p * 16);
+        dst[0] = reinterpret_cast<const uint4*>(o)[0];
+        dst[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+}
+
+// loss 0.5 mean (pred - target)^2 over 6 channels; dY = (pred - target) / (6 n) as bf16 [p][16]
+__global__ void loss_kernel(const float* __restrict__ pred, const float* __restrict__ target, long long n,
+                            __nv_bfloat16* __restrict__ dy, float* __restrict__ loss_part)
+{
+    __shared__ float red[NTHR / 32];
+    float s = 0.f;
+    const float inv = 1.f / (6.f * (float)n);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float r = pred[p * 8 + c] - target[c * n + p];
+            s += r * r;
+            o[c] = __float2bfloat16_rn(r * inv);
+        }
+#pragma unroll
+        for (int c = 6; c < 16; ++c) o[c] = __float2bfloat16_rn(0.f);
+        uint4* d = reinterpret_cast<uint4*>(dy + p * 16);
+        d[0] = reinterpret_cast<const uint4*>(o)[0];
+        d[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int k = 0; k < NTHR / 32; ++k) t += red[k];
+        loss_part[blockIdx.x] = t;
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps,
+                            float c1, float c2)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const float gk = g[k];
+        const float mk = b1 * m[k] + (1.f - b1) * gk;
+        const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+        m[k] = mk; v[k] = vk;
+        p[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+    }
+}
+
+__global__ void block_average_kernel(const float* __restrict__ fine, int nf, int hf, int wf, int r,
+                                     float* __restrict__ coarse)
+{
+    const int hc = hf / r, wc = wf / r;
+    const long long nc = (long long)hc * wc, total = nc * nf;
+    const float inv = 1.f / (float)(r * r);
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total; v += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(v / nc);
+        const long long q = v - (long long)f * nc;
+        const int J = (int)(q / wc), I = (int)(q % wc);
+        const float* src = fine + (long long)f * hf * wf + (long long)J * r * wf + (long long)I * r;
+        float s = 0.f;
+        for (int a = 0; a < r; ++a)
+            for (int b = 0; b < r; ++b) s += src[(long long)a * wf + b];
+        coarse[v] = s * inv;
+    }
+}
+
+// ---- correction of a solver context ---------------------------------------------
+__global__ void export_paired_kernel(const float* __restrict__ u0, Layout L, float* __restrict__ dst)
+{
+    const long long n = (long long)L.nx * L.ny;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n * NF; v += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(v / n);
+        const long long r = v - (long long)f * n;
+        dst[v] = u0[L.idx(f, (int)(r % L.nx), (int)(r / L.nx), false)];
+    }
+}
+
+// u += out_scale * pred on the interior and on every periodic ghost copy
+__global__ void add_correction_kernel(float* __restrict__ u0, Layout L, const float* __restrict__ pred,
+                                      const float* __restrict__ out_scale, DevScalars* sc)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) { sc->cmax_bits[0] = 0ull; sc->cmax_bits[1] = 0ull; }
+    const long long ex = L.nx + 2 * GY, ey = L.ny + 2 * GY, total = (long long)NF * ex * ey;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total; v += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(v / (ex * ey));
+        const long long r = v - (long long)f * ex * ey;
+        const int j = (int)(r / ex) - GY, i = (int)(r % ex) - GY;
+        const int si = wrapm(i, L.nx), sj = wrapm(j, L.ny);
+        u0[L.idx(f, i, j, false)] += out_scale[f] * pred[((long long)sj * L.nx + si) * 8 + f];
+    }
+}
+
+__global__ void cmax_paired_kernel(const float* __restrict__ w, Layout L, float gamma, DevScalars* sc)
+{
+    __shared__ unsigned long long red[2][NTHR / 32];
+    unsigned long long m[2] = {0ull, 0ull};
+    const long long n = (long long)L.nx * L.ny;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(v / L.nx), i = (int)(v % L.nx);
+        float q[NF];
+        for (int f = 0; f < NF; ++f) q[f] = w[L.idx(f, i, j, false)];
+        float sx, sy;
+        signal_speeds<float, false>(q[0], q[1], q[2], q[3], q[4], q[5], 0.f, 0.f, 0.f, 0.f, gamma, sx, sy);
+        const unsigned long long a = speed_key(sx), b = speed_key(sy);
+        m[0] = a > m[0] ? a : m[0];
+        m[1] = b > m[1] ? b : m[1];
+    }
+    for (int d = 0; d < 2; ++d) {
+        unsigned long long x = m[d];
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = y > x ? y : x;
+        }
+        if ((threadIdx.x & 31) == 0) red[d][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        unsigned long long x = 0ull;
+        for (int k = 0; k < NTHR / 32; ++k) x = red[threadIdx.x][k] > x ? red[threadIdx.x][k] : x;
+        atomicMax(&sc->cmax_bits[threadIdx.x], x);
+    }
+}
+
+template <int CIN, int COUT>
+constexpr size_t conv_smem() { return (size_t)(COUT * (9 * CIN + 8) + HH * HW * CIN) * 2; }
+template <int CIN, int MO>
+constexpr size_t dw_smem() { return (size_t)(HH * HW * CIN + TH * TW * MO) * 2; }
+
+int grid_n(long long n, int cap) { long long g = (n + 255) / 256; return (int)(g < 1 ? 1 : (g > cap ? cap : g)); }
+
+}  // namespace
+
+struct sac_cnn {
+    int H = 0, W = 0, device = 0, nsm = 148, conv_grid = 0;
+    cudaStream_t stream = nullptr;
+    float* params = nullptr;      // FP32 master [kParams]
+    float* grads = nullptr;       // [kParams]
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    long long adam_t = 0;
+    __nv_bfloat16* wf[NLAYER] = {nullptr};
+    __nv_bfloat16* wt[NLAYER] = {nullptr};
+    float* bias[NLAYER] = {nullptr};
+    __nv_bfloat16* feat = nullptr;      // [P][16]
+    __nv_bfloat16* act[3] = {nullptr};  // [P][32]
+    float* pred = nullptr;              // [P][8]
+    __nv_bfloat16* dy3 = nullptr;       // [P][16]
+    __nv_bfloat16* dact[3] = {nullptr}; // [P][32] gradients of act[0..2]
+    float* part = nullptr;              // dW partials
+    float* dbpart = nullptr;
+    float* loss_part = nullptr;
+    float* state = nullptr;             // packed FP32 [6][P] (for sac_cnn_apply)
+    float* in_scale = nullptr;          // [8]
+    float* out_scale = nullptr;         // [6]
+    float h_loss_part[1024];
+    char err[512] = {0};
+};
+
+static int cfail(sac_cnn* c, int code, const char* fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+#define CC(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return cfail(c, e_ == cudaErrorMemoryAllocation ? SAC_ERR_OOM : SAC_ERR_CUDA, \
+                         "%s failed: %s", #call, cudaGetErrorString(e_));                 \
+    } while (0)
+
+template <int CIN, int COUT, int MODE>
+static cudaError_t run_conv(sac_cnn* c, const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, void* out,
+                            const __nv_bfloat16* mask)
+{
+    ConvArgs a;
+    a.in = in; a.w = w; a.bias = bias; a.out = out; a.mask = mask; a.H = c->H; a.W = c->W;
+    conv3x3_kernel<CIN, COUT, MODE><<<c->conv_grid, NTHR, conv_smem<CIN, COUT>(), c->stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int CIN, int MO>
+static cudaError_t run_dw(sac_cnn* c, const __nv_bfloat16* dy, const __nv_bfloat16* x, int layer)
+{
+    DwArgs a;
+    a.dy = dy; a.x = x; a.part = c->part; a.dbpart = c->dbpart; a.H = c->H; a.W = c->W;
+    conv3x3_dw_kernel<CIN, MO><<<c->conv_grid, NTHR, dw_smem<CIN, MO>(), c->stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long off = param_offset(layer);
+    const int cin = CIN_REAL[layer], cout = COUT_REAL[layer];
+    dw_reduce_kernel<<<grid_n(cout * cin * 9 + cout, 1024), 256, 0, c->stream>>>(
+        c->part, c->dbpart, c->conv_grid, CIN, MO, cin, cout, c->grads + off, c->grads + off + (long long)cout * cin * 9);
+    return cudaGetLastError();
+}
+
+static cudaError_t pack_all(sac_cnn* c)
+{
+    for (int k = 0; k < NLAYER; ++k) {
+        pack_weights_kernel<<<64, 256, 0, c->stream>>>(c->params + param_offset(k), CIN_REAL[k], COUT_REAL[k],
+                                                       CIN_PAD[k], COUT_PAD[k], COUT_PAD[k] < 16 ? 16 : COUT_PAD[k],
+                                                       c->wf[k], c->wt[k], c->bias[k]);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// features of the packed state -> forward through the 4 layers -> pred [P][8]
+static cudaError_t forward_all(sac_cnn* c, const float* w, double gamma, double dx, double dy)
+{
+    const long long P = (long long)c->H * c->W;
+    features_kernel<<<grid_n(P, 4096), 256, 0, c->stream>>>(w, c->H, c->W, (float)(gamma - 1.0),
+                                                            (float)(1.0 / (12.0 * dx)), (float)(1.0 / (12.0 * dy)),
+                                                            c->in_scale, c->feat);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = run_conv<16, 32, MODE_RELU>(c, c->feat, c->wf[0], c->bias[0], c->act[0], nullptr);
+    if (e == cudaSuccess) e = run_conv<32, 32, MODE_RELU>(c, c->act[0], c->wf[1], c->bias[1], c->act[1], nullptr);
+    if (e == cudaSuccess) e = run_conv<32, 32, MODE_RELU>(c, c->act[1], c->wf[2], c->bias[2], c->act[2], nullptr);
+    if (e == cudaSuccess) e = run_conv<32, 8, MODE_LINEAR_F32>(c, c->act[2], c->wf[3], c->bias[3], c->pred, nullptr);
+    return e;
+}
+
+// loss and gradients of every parameter into c->grads; *loss (host) if non-null
+static int backward_all(sac_cnn* c, const float* target, double* loss)
+{
+    const long long P = (long long)c->H * c->W;
+    const int lg = 296;
+    loss_kernel<<<lg, NTHR, 0, c->stream>>>(c->pred, target, P, c->dy3, c->loss_part);
+    CC(cudaGetLastError());
+    CC((run_dw<32, 16>(c, c->dy3, c->act[2], 3)));
+    CC((run_conv<16, 32, MODE_MASK>(c, c->dy3, c->wt[3], nullptr, c->dact[2], c->act[2])));
+    CC((run_dw<32, 32>(c, c->dact[2], c->act[1], 2)));
+    CC((run_conv<32, 32, MODE_MASK>(c, c->dact[2], c->wt[2], nullptr, c->dact[1], c->act[1])));
+    CC((run_dw<32, 32>(c, c->dact[1], c->act[0], 1)));
+    CC((run_conv<32, 32, MODE_MASK>(c, c->dact[1], c->wt[1], nullptr, c->dact[0], c->act[0])));
+    CC((run_dw<16, 32>(c, c->dact[0], c->feat, 0)));
+    if (loss) {
+        CC(cudaMemcpyAsync(c->h_loss_part, c->loss_part, lg * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CC(cudaStreamSynchronize(c->stream));
+        double s = 0.0;
+        for (int k = 0; k < lg; ++k) s += c->h_loss_part[k];
+        *loss = 0.5 * s / (6.0 * (double)P);
+    }
+    return SAC_OK;
+}
+
+template <int CIN, int COUT, int MODE>
+static cudaError_t conv_attr()
+{
+    return cudaFuncSetAttribute(conv3x3_kernel<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)conv_smem<CIN, COUT>());
+}
+template <int CIN, int MO>
+static cudaError_t dw_attr()
+{
+    return cudaFuncSetAttribute(conv3x3_dw_kernel<CIN, MO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dw_smem<CIN, MO>());
+}
+
+extern "C" {
+
+long sac_cnn_param_count(void) { return (long)kParams; }
+
+const char* sac_cnn_last_error(const sac_cnn* c) { return c ? c->err : "no network"; }
+
+void sac_cnn_free(sac_cnn* c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->params); cudaFree(c->grads); cudaFree(c->adam_m); cudaFree(c->adam_v);
+    for (int k = 0; k < NLAYER; ++k) { cudaFree(c->wf[k]); cudaFree(c->wt[k]); cudaFree(c->bias[k]); }
+    cudaFree(c->feat); for (int k = 0; k < 3; ++k) { cudaFree(c->act[k]); cudaFree(c->dact[k]); }
+    cudaFree(c->pred); cudaFree(c->dy3); cudaFree(c->part); cudaFree(c->dbpart); cudaFree(c->loss_part);
+    cudaFree(c->state); cudaFree(c->in_scale); cudaFree(c->out_scale);
+    delete c;
+}
+
+int sac_cnn_init(int nx, int ny, int device, void* stream, sac_cnn** out)
+{
+    if (out) *out = nullptr;
+    if (!out || nx < 8 || ny < 8 || nx > 16384 || ny > 16384) return SAC_ERR_ARG;
+    sac_cnn* c = new sac_cnn();
+    c->H = ny; c->W = nx; c->device = device; c->stream = (cudaStream_t)stream;
+    int rc = SAC_OK;
+    do {
+        if (cudaSetDevice(device) != cudaSuccess) { rc = cfail(c, SAC_ERR_ARG, "device %d", device); break; }
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
+        c->conv_grid = 4 * c->nsm;
+        const long long P = (long long)nx * ny;
+        bool ok = true;
+        auto A = [&](void** p, size_t bytes) { if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false; if (ok) cudaMemset(*p, 0, bytes); };
+        A((void**)&c->params, kParams * 4); A((void**)&c->grads, kParams * 4);
+        A((void**)&c->adam_m, kParams * 4); A((void**)&c->adam_v, kParams * 4);
+        for (int k = 0; k < NLAYER; ++k) {
+            const size_t nwp = (size_t)COUT_PAD[k] * 9 * CIN_PAD[k];
+            A((void**)&c->wf[k], nwp * 2);
+            A((void**)&c->wt[k], (size_t)CIN_PAD[k] * 9 * (COUT_PAD[k] < 16 ? 16 : COUT_PAD[k]) * 2);
+            A((void**)&c->bias[k], COUT_PAD[k] * 4);
+        }
+        A((void**)&c->feat, P * 16 * 2);
+        for (int k = 0; k < 3; ++k) { A((void**)&c->act[k], P * 32 * 2); A((void**)&c->dact[k], P * 32 * 2); }
+        A((void**)&c->pred, P * 8 * 4); A((void**)&c->dy3, P * 16 * 2);
+        A((void**)&c->part, (size_t)c->conv_grid * 32 * 9 * 32 * 4); A((void**)&c->dbpart, (size_t)c->conv_grid * 32 * 4);
+        A((void**)&c->loss_part, 1024 * 4);
+        A((void**)&c->state, P * NF * 4);
+        A((void**)&c->in_scale, 8 * 4); A((void**)&c->out_scale, 6 * 4);
+        if (!ok) { rc = cfail(c, SAC_ERR_OOM, "network buffers"); break; }
+        cudaError_t e = conv_attr<16, 32, MODE_RELU>();
+        if (e == cudaSuccess) e = conv_attr<32, 32, MODE_RELU>();
+        if (e == cudaSuccess) e = conv_attr<32, 8, MODE_LINEAR_F32>();
+        if (e == cudaSuccess) e = conv_attr<16, 32, MODE_MASK>();
+        if (e == cudaSuccess) e = conv_attr<32, 32, MODE_MASK>();
+        if (e == cudaSuccess) e = dw_attr<32, 16>();
+        if (e == cudaSuccess) e = dw_attr<32, 32>();
+        if (e == cudaSuccess) e = dw_attr<16, 32>();
+        if (e != cudaSuccess) { rc = cfail(c, SAC_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e)); break; }
+        const float ones[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+        if (cudaMemcpy(c->in_scale, ones, 32, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(c->out_scale, ones, 24, cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = cfail(c, SAC_ERR_CUDA, "scales"); break;
+        }
+    } while (0);
+    if (rc != SAC_OK) { sac_cnn_free(c); return rc; }
+    *out = c;
+    return SAC_OK;
+}
+
+int sac_cnn_set_params(sac_cnn* c, const float* params, long n)
+{
+    if (!c || !params || n != (long)kParams) return cfail(c, SAC_ERR_ARG, "expected %lld parameters", kParams);
+    CC(cudaSetDevice(c->device));
+    CC(cudaMemcpyAsync(c->params, params, kParams * 4, cudaMemcpyHostToDevice, c->stream));
+    CC(cudaMemsetAsync(c->adam_m, 0, kParams * 4, c->stream));
+    CC(cudaMemsetAsync(c->adam_v, 0, kParams * 4, c->stream));
+    c->adam_t = 0;
+    CC(pack_all(c));
+    CC(cudaStreamSynchronize(c->stream));
+    return SAC_OK;
+}
+
+int sac_cnn_get_params(sac_cnn* c, float* params, long n)
+{
+    if (!c || !params || n != (long)kParams) return cfail(c, SAC_ERR_ARG, "expected %lld parameters", kParams);
+    CC(cudaSetDevice(c->device));
+    CC(cudaMemcpyAsync(params, c->params, kParams * 4, cudaMemcpyDeviceToHost, c->stream));
+    CC(cudaStreamSynchronize(c->stream));
+    return SAC_OK;
+}
+
+int sac_cnn_set_scales(sac_cnn* c, const float in_scale[8], const float out_scale[6])
+{
+    if (!c || !in_scale || !out_scale) return SAC_ERR_ARG;
+    CC(cudaSetDevice(c->device));
+    CC(cudaMemcpyAsync(c->in_scale, in_scale, 32, cudaMemcpyHostToDevice, c->stream));
+    CC(cudaMemcpyAsync(c->out_scale, out_scale, 24, cudaMemcpyHostToDevice, c->stream));
+    CC(cudaStreamSynchronize(c->stream));
+    return SAC_OK;
+}
+
+int sac_cnn_forward(sac_cnn* c, const float* w, double gamma, double dx, double dy, float* pred)
+{
+    if (!c || !w || !pred) return SAC_ERR_ARG;
+    CC(cudaSetDevice(c->device));
+    CC(forward_all(c, w, gamma, dx, dy));
+    CC(cudaMemcpyAsync(pred, c->pred, (size_t)c->H * c->W * 8 * 4, cudaMemcpyDeviceToDevice, c->stream));
+    return SAC_OK;
+}
+
+int sac_cnn_grads(sac_cnn* c, const float* w, const float* target, double gamma, double dx, double dy,
+                  float* grads, double* loss)
+{
+    if (!c || !w || !target) return SAC_ERR_ARG;
+    CC(cudaSetDevice(c->device));
+    CC(forward_all(c, w, gamma, dx, dy));
+    int rc = backward_all(c, target, loss);
+    if (rc != SAC_OK) return rc;
+    if (grads) {
+        CC(cudaMemcpyAsync(grads, c->grads, kParams * 4, cudaMemcpyDeviceToHost, c->stream));
+        CC(cudaStreamSynchronize(c->stream));
+    }
+    return SAC_OK;
+}
+
+int sac_cnn_train_step(sac_cnn* c, const float* w, const float* target, double gamma, double dx, double dy,
+                       double lr, double* loss)
+{
+    if (!c || !w || !target || !(lr > 0.0)) return SAC_ERR_ARG;
+    CC(cudaSetDevice(c->device));
+    CC(forward_all(c, w, gamma, dx, dy));
+    int rc = backward_all(c, target, loss);
+    if (rc != SAC_OK) return rc;
+    c->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)c->adam_t)), c2 = (float)(1.0 - std::pow(0.999, (double)c->adam_t));
+    adam_kernel<<<grid_n(kParams, 256), 256, 0, c->stream>>>(c->params, c->grads, c->adam_m, c->adam_v, kParams,
+                                                             (float)lr, b1, b2, 1e-8f, c1, c2);
+    CC(cudaGetLastError());
+    CC(pack_all(c));
+    return SAC_OK;
+}
+
+int sac_cnn_apply(sac_ctx* ctx, sac_cnn* c)
+{
+    if (!ctx || !c) return SAC_ERR_ARG;
+    if (!ctx->fp32 || ctx->p.has_background || ctx->p.bc_x != SAC_BC_PERIODIC || ctx->p.bc_y != SAC_BC_PERIODIC ||
+        ctx->p.nx != c->W || ctx->p.ny != c->H)
+        return cfail(c, SAC_ERR_ARG, "the correction needs a periodic FP32 run of the network's size");
+    if (!ctx->have_state) return cfail(c, SAC_ERR_STATE, "no state");
+    CC(cudaSetDevice(c->device));
+    const long long P = (long long)c->H * c->W;
+    float* u0 = (float*)ctx->u0;
+    export_paired_kernel<<<grid_n(P * NF, 4096), 256, 0, c->stream>>>(u0, ctx->L, c->state);
+    CC(cudaGetLastError());
+    CC(forward_all(c, c->state, ctx->p.gamma, (ctx->p.x1 - ctx->p.x0) / ctx->p.nx, (ctx->p.y1 - ctx->p.y0) / ctx->p.ny));
+    const long long ng = (long long)NF * (ctx->p.nx + 2 * GY) * (ctx->p.ny + 2 * GY);
+    add_correction_kernel<<<grid_n(ng, 4096), 256, 0, c->stream>>>(u0, ctx->L, c->pred, c->out_scale, ctx->sc);
+    CC(cudaGetLastError());
+    cmax_paired_kernel<<<grid_n(P, 2048), NTHR, 0, c->stream>>>(u0, ctx->L, (float)ctx->p.gamma, ctx->sc);
+    CC(cudaGetLastError());
+    return SAC_OK;
+}
+
+int sac_block_average(const float* fine, int nfields, int nxf, int nyf, int r, float* coarse, void* stream)
+{
+    if (!fine || !coarse || nfields < 1 || r < 1 || nxf % r || nyf % r) return SAC_ERR_ARG;
+    const long long n = (long long)nfields * (nxf / r) * (nyf / r);
+    block_average_kernel<<<grid_n(n, 4096), 256, 0, (cudaStream_t)stream>>>(fine, nfields, nyf, nxf, r, coarse);
+    return cudaGetLastError() == cudaSuccess ? SAC_OK : SAC_ERR_CUDA;
+}
+
+}  // extern "C"

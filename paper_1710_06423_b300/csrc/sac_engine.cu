@@ -113,6 +113,8 @@ __global__ void reset_kernel(DevScalars* sc, double t)
     sc->steps = 0; sc->skip = 0; sc->done = 0; sc->status = ST_OK;
 }
 
+__global__ void fixed_dt_kernel(DevScalars* sc, double dt) { sc->fixed_dt = dt > 0.0 ? dt : 0.0; }
+
 __global__ void control_kernel(DevScalars* sc, double t_end)
 {
     sc->t_end = t_end;
@@ -602,6 +604,16 @@ int sac_run_to(sac_ctx* c, double t_end, long max_steps, long* steps_taken)
     }
     if (steps_taken) *steps_taken = (long)(c->hsc->steps - s0);
     return rc;
+}
+
+int sac_set_fixed_dt(sac_ctx* c, double dt)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (!(dt <= 0.0) && !std::isfinite(dt)) return fail(c, SAC_ERR_ARG, "dt must be finite");
+    CK(cudaSetDevice(c->p.device));
+    fixed_dt_kernel<<<1, 1, 0, c->stream>>>(c->sc, dt);
+    CK(cudaGetLastError());
+    return SAC_OK;
 }
 
 int sac_dt(sac_ctx* c, double* dt)

@@ -25,11 +25,14 @@ NF, NB = 6, 4
 EXPORTS = (
     "sac_default_params", "sac_init", "sac_free", "sac_last_error", "sac_status_string",
     "sac_set_state", "sac_get_state", "sac_set_state_dev", "sac_get_state_dev",
-    "sac_step", "sac_steps", "sac_run_to", "sac_dt", "sac_time", "sac_cmax", "sac_sums",
+    "sac_step", "sac_steps", "sac_run_to", "sac_set_fixed_dt", "sac_dt", "sac_time", "sac_cmax", "sac_sums",
     "sac_profile_stages", "sac_sync",
     "sac_batch_init", "sac_batch_free", "sac_batch_last_error", "sac_batch_set_state",
     "sac_batch_get_state", "sac_batch_steps", "sac_batch_sync", "sac_batch_time", "sac_batch_tune",
     "sac_batch_set_config",
+    "sac_cnn_param_count", "sac_cnn_init", "sac_cnn_free", "sac_cnn_last_error", "sac_cnn_set_params",
+    "sac_cnn_get_params", "sac_cnn_set_scales", "sac_cnn_forward", "sac_cnn_grads", "sac_cnn_train_step",
+    "sac_cnn_apply", "sac_block_average",
 )
 
 
@@ -83,6 +86,7 @@ def load() -> ctypes.CDLL:
         "sac_step": (i, [vp, d, dp]),
         "sac_steps": (i, [vp, L]),
         "sac_run_to": (i, [vp, d, L, ctypes.POINTER(L)]),
+        "sac_set_fixed_dt": (i, [vp, d]),
         "sac_dt": (i, [vp, dp]),
         "sac_time": (i, [vp, dp, ctypes.POINTER(L)]),
         "sac_cmax": (i, [vp, dp, dp]),
@@ -99,6 +103,18 @@ def load() -> ctypes.CDLL:
         "sac_batch_time": (i, [vp, i, dp, ctypes.POINTER(L)]),
         "sac_batch_tune": (i, [vp, i, ctypes.POINTER(ctypes.c_int), dp]),
         "sac_batch_set_config": (i, [vp, i, i, i]),
+        "sac_cnn_param_count": (L, []),
+        "sac_cnn_init": (i, [i, i, i, vp, ctypes.POINTER(vp)]),
+        "sac_cnn_free": (None, [vp]),
+        "sac_cnn_last_error": (ctypes.c_char_p, [vp]),
+        "sac_cnn_set_params": (i, [vp, ctypes.POINTER(ctypes.c_float), L]),
+        "sac_cnn_get_params": (i, [vp, ctypes.POINTER(ctypes.c_float), L]),
+        "sac_cnn_set_scales": (i, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+        "sac_cnn_forward": (i, [vp, vp, d, d, d, vp]),
+        "sac_cnn_grads": (i, [vp, vp, vp, d, d, d, ctypes.POINTER(ctypes.c_float), dp]),
+        "sac_cnn_train_step": (i, [vp, vp, vp, d, d, d, d, dp]),
+        "sac_cnn_apply": (i, [vp, vp]),
+        "sac_block_average": (i, [vp, i, i, i, i, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -219,6 +235,10 @@ class Solver:
         n = ctypes.c_long()
         self._check(load().sac_run_to(self._ctx, float(t_end), int(max_steps), ctypes.byref(n)), "sac_run_to")
         return n.value
+
+    def set_fixed_dt(self, dt: float):
+        """dt > 0: every later CFL step takes dt; dt <= 0: back to the CFL step."""
+        self._check(load().sac_set_fixed_dt(self._ctx, float(dt)), "sac_set_fixed_dt")
 
     def dt(self) -> float:
         out = ctypes.c_double()
@@ -342,4 +362,90 @@ class Batch:
 
     def set_config(self, persistent, ctas_per_sm, order):
         self._check(load().sac_batch_set_config(self._b, persistent, ctas_per_sm, order), "sac_batch_set_config")
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _stream_handle(stream, device=0):
+    if stream == "current":
+        import torch
+        stream = torch.cuda.current_stream(device)
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    return stream or None
+
+
+class CNN:
+    """The learned coarse-grid correction network of an nx x ny periodic grid."""
+
+    def __init__(self, nx, ny, device=0, stream="current"):
+        lib = load()
+        self.nx, self.ny, self.device = nx, ny, device
+        self.stream = _stream_handle(stream, device)
+        self._c = ctypes.c_void_p()
+        rc = lib.sac_cnn_init(nx, ny, device, self.stream, ctypes.byref(self._c))
+        if rc != SAC_OK:
+            raise SacError(rc, f"sac_cnn_init: {lib.sac_status_string(rc).decode()}")
+        self.nparams = int(lib.sac_cnn_param_count())
+
+    def _check(self, rc, what):
+        if rc != SAC_OK:
+            lib = load()
+            raise SacError(rc, f"{what}: {lib.sac_status_string(rc).decode()}: {lib.sac_cnn_last_error(self._c).decode()}")
+
+    def close(self):
+        if self._c:
+            load().sac_cnn_free(self._c)
+            self._c = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(load().sac_cnn_set_params(self._c, _fp(flat), flat.size), "sac_cnn_set_params")
+
+    def get_params(self):
+        out = np.zeros(self.nparams, dtype=np.float32)
+        self._check(load().sac_cnn_get_params(self._c, _fp(out), out.size), "sac_cnn_get_params")
+        return out
+
+    def set_scales(self, in_scale, out_scale):
+        a = np.ascontiguousarray(in_scale, dtype=np.float32)
+        b = np.ascontiguousarray(out_scale, dtype=np.float32)
+        self._check(load().sac_cnn_set_scales(self._c, _fp(a), _fp(b)), "sac_cnn_set_scales")
+
+    def forward(self, w_dev, gamma, dx, dy, pred_dev):
+        self._check(load().sac_cnn_forward(self._c, ctypes.c_void_p(w_dev.data_ptr()), gamma, dx, dy,
+                                           ctypes.c_void_p(pred_dev.data_ptr())), "sac_cnn_forward")
+
+    def grads(self, w_dev, target_dev, gamma, dx, dy):
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(load().sac_cnn_grads(self._c, ctypes.c_void_p(w_dev.data_ptr()),
+                                         ctypes.c_void_p(target_dev.data_ptr()), gamma, dx, dy, _fp(g),
+                                         ctypes.byref(loss)), "sac_cnn_grads")
+        return loss.value, g
+
+    def train_step(self, w_dev, target_dev, gamma, dx, dy, lr, want_loss=True):
+        loss = ctypes.c_double()
+        self._check(load().sac_cnn_train_step(self._c, ctypes.c_void_p(w_dev.data_ptr()),
+                                              ctypes.c_void_p(target_dev.data_ptr()), gamma, dx, dy, lr,
+                                              ctypes.byref(loss) if want_loss else None), "sac_cnn_train_step")
+        return loss.value
+
+    def apply(self, solver):
+        self._check(load().sac_cnn_apply(solver._ctx, self._c), "sac_cnn_apply")
+
+
+def block_average(fine_dev, nfields, nxf, nyf, r, coarse_dev, stream="current"):
+    rc = load().sac_block_average(ctypes.c_void_p(fine_dev.data_ptr()), nfields, nxf, nyf, r,
+                                  ctypes.c_void_p(coarse_dev.data_ptr()), _stream_handle(stream))
+    if rc != SAC_OK:
+        raise SacError(rc, "sac_block_average")
 
