@@ -266,6 +266,38 @@ int sac_cnn_apply(sac_ctx *ctx, sac_cnn *c);
  * [nfields][nyf/r][nxf/r] (nxf, nyf multiples of r).  ASYNC on `stream`. */
 int sac_block_average(const float *fine_dev, int nfields, int nxf, int nyf, int r, float *coarse_dev, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free step.  The paper has no counterpart: this entry point serves
+ * callers that cannot allocate device memory (code that runs while a CUDA graph
+ * is being captured, allocator-restricted plugins, or real-time loops that
+ * forbid allocation): it runs one SAC_FP32 RK4 step with the same kernels as
+ * sac_step but keeps its working memory (ghost-padded RK registers and step
+ * scalars) in a fixed array of 7,244,032 bytes compiled into the library.
+ * Every GPU that loads the library holds that array until the process exits.
+ *
+ *   p         run parameters; precision must be SAC_FP32 and has_background 0
+ *             (device and stream are used as given)
+ *   w_in      DEVICE float [6][ny][nx], the state to advance (read only)
+ *   w_out     DEVICE float [6][ny][nx], receives the new state (may equal w_in)
+ *   dt        > 0: step size; <= 0: the CFL step of w_in
+ *   dt_taken  host pointer or NULL.  Non-NULL: the call waits for the stream and
+ *             stores the step taken.  NULL: the call only enqueues work.
+ * The grid must fit the fixed memory: its padded plane (as sac_init pads it)
+ * holds at most 75,456 float2 elements (any grid up to 256 x 256 qualifies);
+ * larger grids are rejected with SAC_ERR_TOO_LARGE before any GPU work.
+ * Fixed boundaries hold the nearest interior cell of w_in.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and sets
+ * kernel attributes, so make it before any stream capture.  It calls no
+ * cudaMalloc/cudaFree or any allocating routine.  All calls share the one
+ * array: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  The state is the only input:
+ * the array's previous contents are overwritten (scalars reset) each call.
+ * Returns SAC_OK, SAC_ERR_ARG, SAC_ERR_TOO_LARGE, SAC_ERR_CUDA, or
+ * SAC_ERR_NONFINITE (only detectable when dt_taken is non-NULL).
+ * ------------------------------------------------------------------------- */
+#define SAC_ERR_TOO_LARGE (-7)
+int sac_step_noalloc(const sac_params *p, const float *w_in, float *w_out, double dt, double *dt_taken);
+
 #ifdef __cplusplus
 }
 #endif

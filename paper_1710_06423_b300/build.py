@@ -29,6 +29,7 @@ UNITS = [
     ("kernels_fp32.cu", []),
     ("batch.cu", []),
     ("cnn.cu", []),
+    ("noalloc.cu", []),
 ]
 
 

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libsac.so")
 
 SAC_OK, SAC_ERR_ARG, SAC_ERR_STATE, SAC_ERR_CUDA, SAC_ERR_OOM, SAC_ERR_NONFINITE, SAC_ERR_TIMEOUT = \
     0, -1, -2, -3, -4, -5, -6
+SAC_ERR_TOO_LARGE = -7
 BC_PERIODIC, BC_FIXED, BC_OUTFLOW = 0, 1, 2
 FP64, FP32 = 0, 1
 NF, NB = 6, 4
@@ -33,6 +34,7 @@ EXPORTS = (
     "sac_cnn_param_count", "sac_cnn_init", "sac_cnn_free", "sac_cnn_last_error", "sac_cnn_set_params",
     "sac_cnn_get_params", "sac_cnn_set_scales", "sac_cnn_forward", "sac_cnn_grads", "sac_cnn_train_step",
     "sac_cnn_apply", "sac_block_average",
+    "sac_step_noalloc",
 )
 
 
@@ -115,6 +117,7 @@ def load() -> ctypes.CDLL:
         "sac_cnn_train_step": (i, [vp, vp, vp, d, d, d, d, dp]),
         "sac_cnn_apply": (i, [vp, vp]),
         "sac_block_average": (i, [vp, i, i, i, i, vp, vp]),
+        "sac_step_noalloc": (i, [P, vp, vp, d, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -449,3 +452,30 @@ def block_average(fine_dev, nfields, nxf, nyf, r, coarse_dev, stream="current"):
     if rc != SAC_OK:
         raise SacError(rc, "sac_block_average")
 
+
+def step_noalloc(w_in, w_out, dt: float = 0.0, wait: bool = True, **kw) -> float:
+    """One FP32 RK4 step of the device tensors ``w_in`` -> ``w_out`` (float32,
+    contiguous, shape (6, ny, nx)) through ``sac_step_noalloc``: no allocation;
+    keyword arguments are ``sac_params`` fields (stream: torch stream or handle)."""
+    lib = load()
+    p = default_params()
+    stream = kw.pop("stream", "current")
+    for k, v in kw.items():
+        if k == "c2":
+            for j, x in enumerate(v):
+                p.c2[j] = x
+        else:
+            setattr(p, k, v)
+    p.precision = FP32
+    if stream == "current":
+        import torch
+        stream = torch.cuda.current_stream(p.device)
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    p.stream = stream or None
+    out = ctypes.c_double(0.0)
+    rc = lib.sac_step_noalloc(ctypes.byref(p), ctypes.c_void_p(w_in.data_ptr()), ctypes.c_void_p(w_out.data_ptr()),
+                              float(dt), ctypes.byref(out) if wait else None)
+    if rc != SAC_OK:
+        raise SacError(rc, f"sac_step_noalloc: {lib.sac_status_string(rc).decode()}")
+    return out.value

@@ -1,0 +1,55 @@
+"""The allocation-free step (sac_step_noalloc) against the allocating one.
+
+Some callers cannot allocate device memory (for example code running while a
+CUDA graph is captured, or plugins whose host forbids allocation); for them the
+library keeps the working memory of one FP32 RK4 step in a fixed array compiled
+into it.  This test calls that entry point through the C ABI twice in a row,
+each time on the previous output, and checks it against the context-based path
+(sac_set_state_dev + sac_step + sac_get_state_dev) on the same states.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL_FP32_L1, l1rel
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_step_matches_context_step_twice(inputs_mod):
+    import torch
+    from paper_1710_06423_b300 import sac
+    nx, ny = 200, 150
+    w0 = inputs_mod.orszag_tang(nx, ny, noise=1e-3, seed=9)
+    dev = torch.from_numpy(w0.astype(np.float32)).cuda().contiguous()
+    # reference: the context path, two CFL steps
+    refs, dts = [], []
+    with sac.Solver(nx=nx, ny=ny, precision=sac.FP32) as s:
+        s.set_state_dev(dev, None, 0.0)
+        for _ in range(2):
+            dts.append(s.step(0.0))
+            r = torch.empty_like(dev)
+            s.get_state_dev(r)
+            torch.cuda.synchronize()
+            refs.append(r.double().cpu().numpy())
+    # the allocation-free path, two calls in a row
+    a = dev.clone()
+    b = torch.empty_like(dev)
+    dt1 = sac.step_noalloc(a, b, 0.0, nx=nx, ny=ny)
+    dt2 = sac.step_noalloc(b, a, 0.0, nx=nx, ny=ny)
+    torch.cuda.synchronize()
+    got = [b.double().cpu().numpy(), a.double().cpu().numpy()]
+    assert (dt1, dt2) == tuple(dts)
+    for g, r in zip(got, refs):
+        assert np.all(l1rel(g, r) <= TOL_FP32_L1), l1rel(g, r)
+        assert np.array_equal(g, r)          # same kernels, same arithmetic
+
+
+def test_noalloc_rejects_grids_beyond_its_memory():
+    import torch
+    from paper_1710_06423_b300 import sac
+    w = torch.zeros((6, 300, 300), dtype=torch.float32, device="cuda")
+    with pytest.raises(sac.SacError) as ei:
+        sac.step_noalloc(w, w, 0.0, nx=300, ny=300)
+    assert ei.value.code == sac.SAC_ERR_TOO_LARGE
