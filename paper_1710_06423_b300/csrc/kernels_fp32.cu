@@ -19,11 +19,14 @@ cudaError_t set_attr()
     return e;
 }
 
+int g_resident = 296;   // persistent grid: resident CTAs on the device (2 per SM)
+
 template <int S, bool BG, bool HD>
 cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
 {
-    dim3 grid((a.L.nx + TX - 1) / TX, (a.L.ny + TY - 1) / TY);
-    f32k::stage_fp32<S, BG, HD><<<grid, NT, sizeof(f32k::Smem), s>>>(a);
+    const int ntx = (a.L.nx + TX - 1) / TX, nty = (a.L.ny + TY - 1) / TY, ntiles = ntx * nty;
+    const int grid = ntiles < g_resident ? ntiles : g_resident;
+    f32k::stage_fp32<S, BG, HD><<<grid, NT, sizeof(f32k::Smem), s>>>(a, ntx, ntiles);
     return cudaGetLastError();
 }
 
@@ -51,7 +54,12 @@ cudaError_t attr_all()
 
 cudaError_t prepare_stage_fp32()
 {
-    cudaError_t e = attr_all<false, false>();
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_resident = 2 * nsm;
+    e = attr_all<false, false>();
     if (e == cudaSuccess) e = attr_all<false, true>();
     if (e == cudaSuccess) e = attr_all<true, false>();
     if (e == cudaSuccess) e = attr_all<true, true>();

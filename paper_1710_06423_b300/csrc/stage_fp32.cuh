@@ -183,6 +183,33 @@ __device__ __forceinline__ void face_fluxes(const float2 (&u)[SEG + 6], const fl
     }
 }
 
+// Warm L2 with what the tile at (x0, y0) will read: its staged region of the
+// stencil input and (stages 2-4) its rows of the pointwise registers U0 and D.
+// One prefetch per 128-byte line; issued while the previous tile computes.
+template <int STAGE>
+__device__ __forceinline__ void prefetch_tile(const StageArgs<float>& a, const int x0, const int y0)
+{
+    const Layout L = a.L;
+    const long long P = L.fstride;
+    const float2* gin = reinterpret_cast<const float2*>(a.sin);
+    const long long rbase = (long long)y0 * L.pitch + x0;
+    constexpr int LPR = (RX * 8 + 127) / 128;                  // lines per staged row (3)
+    for (int v = threadIdx.x; v < 3 * RY * LPR; v += NT) {
+        const int p = v / (RY * LPR), rem = v - p * (RY * LPR), r = rem / LPR, l = rem - r * LPR;
+        prefetch_l2(gin + p * P + rbase + (long long)r * L.pitch + l * 16);
+    }
+    if (STAGE >= 2) {
+        const float2* u0 = reinterpret_cast<const float2*>(a.u0);
+        const float2* dd = reinterpret_cast<const float2*>(a.acc);
+        for (int v = threadIdx.x; v < 3 * TY * 2; v += NT) {   // 2 lines of 128 B per tile row
+            const int p = v / (TY * 2), rem = v - p * TY * 2, r = rem >> 1, h = rem & 1;
+            const long long e = p * P + L.at(x0 + 16 * h, y0 + r);
+            prefetch_l2(u0 + e);
+            if (STAGE >= 3) prefetch_l2(dd + e);
+        }
+    }
+}
+
 // One tile (x0, y0) of one run; every thread of the CTA calls it (it holds
 // barriers).  `red` is a block-shared scratch for the stage-4 reduction.
 template <int STAGE, bool BG, bool HD>
@@ -221,10 +248,9 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     const float gm1 = (float)(a.gamma - 1.0);
 
     // ---- 1. primitives and fluxes on the staged box [x0-3, x0+TX+3) x [y0-3, y0+TY+3)
+    // (cells v and v + NT per iteration: two independent dependency chains)
     {
-        int r = tid / PW, c = 1 + tid - (tid / PW) * PW;
-#pragma unroll 1
-        for (int v = tid; v < RY * PW; v += NT) {
+        auto prim_cell = [&](const int r, const int c) {
             const float2 P0 = S.u[0][r][c], P1 = S.u[1][r][c], P2 = S.u[2][r][c];
             const float mx = P1.x, my = P1.y, btx = P2.x, bty = P2.y, et = P0.y;
             float ux, uy, pt, etot, bx, by;
@@ -277,8 +303,18 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
                 S.fy[1][r - 1][c - 4] = f1;
                 S.fy[2][r - 1][c - 4] = make_float2(uy * bx - by * ux, 0.f);
             }
-            c += NT % PW; r += NT / PW;
+        };
+        constexpr int NCELL = RY * PW;
+        int r = tid / PW, c = 1 + tid - (tid / PW) * PW;
+        int r2 = (tid + NT) / PW, c2 = 1 + (tid + NT) - ((tid + NT) / PW) * PW;
+#pragma unroll 1
+        for (int v = tid; v < NCELL; v += 2 * NT) {
+            prim_cell(r, c);
+            if (v + NT < NCELL) prim_cell(r2, c2);
+            c += (2 * NT) % PW; r += (2 * NT) / PW;
             if (c >= 1 + PW) { c -= PW; ++r; }
+            c2 += (2 * NT) % PW; r2 += (2 * NT) / PW;
+            if (c2 >= 1 + PW) { c2 -= PW; ++r2; }
         }
     }
     __syncthreads();
@@ -287,16 +323,24 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 
     // ---- 2. shock indicator on [x0-1, x0+TX] x [y0-1, y0+TY] ---------------------
     if constexpr (HD) {
-        int sr = tid / SW, scn = tid - (tid / SW) * SW;
-#pragma unroll 1
-        for (int v = tid; v < SH * SW; v += NT) {
+        auto shock_cell = [&](const int sr, const int scn) {
             const int r = sr + 2, c = scn + 3;
             const float dvx = (8.f * (S.vx[r][c + 1] - S.vx[r][c - 1]) - (S.vx[r][c + 2] - S.vx[r][c - 2])) * inv12dx;
             const float dvy = (8.f * (S.vy[r + 1][c] - S.vy[r - 1][c]) - (S.vy[r + 2][c] - S.vy[r - 2][c])) * inv12dy;
             const float sv = fmaxf(0.f, -(dvx + dvy));
             S.s[sr][scn] = make_float2(sv, sv);
-            scn += NT % SW; sr += NT / SW;
+        };
+        constexpr int NS = SH * SW;
+        int sr = tid / SW, scn = tid - (tid / SW) * SW;
+        int sr2 = (tid + NT) / SW, scn2 = (tid + NT) - ((tid + NT) / SW) * SW;
+#pragma unroll 1
+        for (int v = tid; v < NS; v += 2 * NT) {
+            shock_cell(sr, scn);
+            if (v + NT < NS) shock_cell(sr2, scn2);
+            scn += (2 * NT) % SW; sr += (2 * NT) / SW;
             if (scn >= SW) { scn -= SW; ++sr; }
+            scn2 += (2 * NT) % SW; sr2 += (2 * NT) / SW;
+            if (scn2 >= SW) { scn2 -= SW; ++sr2; }
         }
         __syncthreads();
     }
@@ -461,13 +505,21 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     }
 }
 
+// Persistent: each CTA walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (row-major), prefetching the next tile into L2 before computing the current.
 template <int STAGE, bool BG, bool HD>
-__global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a)
+__global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, const int ntx, const int ntiles)
 {
     if (a.sc->skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long red[2][NW];
-    tile_body<STAGE, BG, HD>(a, blockIdx.x * TX, blockIdx.y * TY, *reinterpret_cast<Smem*>(smem_raw), red);
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        if (tn < ntiles) prefetch_tile<STAGE>(a, (tn % ntx) * TX, (tn / ntx) * TY);
+        tile_body<STAGE, BG, HD>(a, (t % ntx) * TX, (t / ntx) * TY, S, red);
+        __syncthreads();   // shared memory is reused by the next tile
+    }
 }
 
 }  // namespace f32k
