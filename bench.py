@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the other sizes and the HD-off line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--batch-steps", type=int, default=500, help="steps of the 64-run batched workload")
+    ap.add_argument("--learned", action="store_true",
+                    help="run the learned coarse-grid correction experiment instead (several minutes)")
+    ap.add_argument("--t-end", type=float, default=0.5, help="horizon of the learned experiment")
     return ap.parse_args()
 
 
@@ -64,6 +67,17 @@ def dist_setup(args):
         dist.init_process_group(backend=backend)
         pg = dist
     return ws, rank, local, pg
+
+
+def reduce_max(value: float, pg, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (identity without a process group).
+    `device` "cuda" for NCCL groups; CPU tensors otherwise (gloo)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device or "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
 
 
 def measured_peaks():
@@ -149,6 +163,15 @@ def cpu_oracle_rate(side: int, steps: int, budget_s: float = 20.0):
     return side * side * done / el, threads, done, el
 
 
+def workload_config(args, ws):
+    n = args.size
+    return {"workload": f"orszag-tang {n}x{n} periodic, HD on, 1e-3 noise on rho and p, FP32 perturbations",
+            "nx": n, "ny": n, "rk": "classical RK4, graph-replayed steps",
+            "l2": f"inputs larger than L2 ({n * n * 24 / 1e9:.2f} GB per RK register)",
+            "parallelism": "replicas" if ws > 1 else "single",
+            "vs_baseline_basis": "paper Table 1, 8000^2 with HD, 100 iterations on 100 K20c: 3.91e7 cell-steps/s"}
+
+
 def run_reference(args, ws, rank):
     """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -176,8 +199,7 @@ def run_reference(args, ws, rank):
         "ms_per_step": 1e3 * el / max(n, 1) * (args.size * args.size) / (side * side),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_8000_HD,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"orszag-tang {args.size}x{args.size} periodic, HD on, 1e-3 noise",
-                   "nx": args.size, "ny": args.size, "sample": sample},
+        "config": workload_config(args, ws),
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -202,12 +224,7 @@ def time_device_steps(solver, steps, warmup, pg, torch):
     solver.sync()
     if pg:
         pg.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms
+    return reduce_max(ev0.elapsed_time(ev1), pg, "cuda")
 
 
 def run_batched(args, ws, local, pg, torch):
@@ -236,11 +253,7 @@ def run_batched(args, ws, local, pg, torch):
     ev1.record(stream)
     ev1.synchronize()
     b.sync()
-    ms = ev0.elapsed_time(ev1)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ev0.elapsed_time(ev1), pg, "cuda")
     cells = sum(n * n for n in sizes)
     counts = {str(n): sizes.count(n) for n in sorted(set(sizes))}
     b.close()
@@ -249,6 +262,77 @@ def run_batched(args, ws, local, pg, torch):
             "steps": args.batch_steps, "runs": len(sizes), "sizes": counts, "cells": cells,
             "tuned_config": {"persistent": cfg[0], "ctas_per_sm": cfg[1], "order": cfg[2]},
             "gb_per_s": value * 4 * 90 / 1e9, "gpu_launches": 5 * args.batch_steps}
+
+
+def run_learned(args, local):
+    """Learned 1000^2 coarse run vs plain FP32 runs at equal L1 error against the
+    block-averaged 4000^2 plain run (Orszag-Tang family, horizon t_end)."""
+    import torch
+    from paper_1710_06423_b300 import learned
+    from paper_1710_06423_b300.sac import CNN, FP32, Solver, block_average
+    torch.cuda.set_device(local)
+    nc, ratio = 1000, 4
+    nf = nc * ratio
+    dx = 1.0 / nc
+    dt_c = 0.25 * dx / 3.0                      # fixed coarse step: Courant 0.25 at a signal speed of 3
+    steps = int(round(args.t_end / dt_c))
+    every = max(1, steps // 200)
+    # shock viscosity 2 (default 0.5): with 0.5 the family's 2000^2-4000^2 runs turn
+    # non-finite before t = 0.5; every run of this experiment uses the same value
+    kw = dict(c_shk=2.0)
+    t0 = time.perf_counter()
+    pairs = learned.Pairs()
+    train_members = (0, 1, 2)
+    completed = {}
+    for k in train_members:
+        completed[k] = learned.generate_pairs(pairs, 2024, k, nc, ratio, dt_c, steps, every, torch, solver_kw=kw)
+    t_data = time.perf_counter() - t0
+    osc = learned.out_scales(pairs, torch)
+    net = CNN(nc, nc)
+    net.set_params(learned.init_params(1))
+    net.set_scales(learned.FEATURE_SCALES, osc)
+    t0 = time.perf_counter()
+    losses = learned.train(net, pairs, osc, dx, iters=3000, lr=1e-3, torch=torch, log_every=500)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del pairs
+    torch.cuda.empty_cache()
+
+    held = 20                                    # held-out family member
+    w0f, gamma = learned.family_state(2024, held, nf)
+    fine_out = torch.empty((6, nf, nf), dtype=torch.float32, device="cuda")
+    with Solver(nx=nf, ny=nf, precision=FP32, gamma=gamma, **kw) as fine:
+        fine.set_state(w0f, None, 0.0)
+        fine.set_fixed_dt(dt_c / ratio)
+        fine.steps(steps * ratio)
+        fine.get_state_dev(fine_out)
+    truth = learned.downsample(fine_out, nc, torch)
+    del fine_out
+    wf_dev = torch.from_numpy(w0f.astype(np.float32)).cuda().contiguous()
+    curve, plain = [], {}
+    for n in (1000, 2000, 3000):
+        w0n = learned.downsample(wf_dev, n, torch) if nf % n == 0 else None
+        if w0n is None:
+            w0n_np, _ = learned.family_state(2024, held, n)
+        else:
+            w0n_np = w0n.double().cpu().numpy()
+        out, sec = learned.run_plain(w0n_np, gamma, n, dt_c * nc / n, steps * n // nc, torch, solver_kw=kw)
+        err = learned.l1_error(learned.downsample(out, nc, torch), truth)   # n is a multiple of nc
+        plain[n] = {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec}
+        curve.append((sec, float(err.mean())))
+    w0c = learned.downsample(wf_dev, nc, torch).double().cpu().numpy()
+    out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, net=net, solver_kw=kw)
+    err = learned.l1_error(out, truth)
+    t_eq = learned.equal_error_time(curve, float(err.mean()))
+    res = {"metric": "learned-vs-plain time at equal L1 error", "t_end": args.t_end, "coarse": nc, "fine": nf,
+           "dt_coarse": dt_c, "steps_coarse": steps, "train_members": list(train_members), "held_out_member": held,
+           "c_shk": kw["c_shk"], "member_steps_completed": completed,
+           "pairs": int(sum(len(range(0, completed[k], every)) for k in train_members)), "data_seconds": t_data,
+           "train_seconds": t_train, "losses": losses,
+           "learned": {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec},
+           "plain": plain, "plain_time_at_learned_error": t_eq,
+           "speedup_at_equal_error": (t_eq / sec) if t_eq else None}
+    print(json.dumps(res), flush=True)
 
 
 def run_ours(args, ws, rank, local, pg):
@@ -300,11 +384,7 @@ def run_ours(args, ws, rank, local, pg):
     for _ in range(args.steps):
         s2.step(0.0)
     s2.get_state_into(out_pinned.numpy())
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(time.perf_counter() - t0, pg, "cuda")
     scal = 96   # device scalar record read back by every synchronous step
     e2e = {"value": ws * cells * args.steps / e2e_s, "unit": "cell-updates/s",
            "h2d_bytes_per_step": state_bytes / args.steps,
@@ -342,11 +422,7 @@ def run_ours(args, ws, rank, local, pg):
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_8000_HD,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"orszag-tang {n}x{n} periodic, HD on, 1e-3 noise on rho and p, FP32 perturbations",
-                   "nx": n, "ny": n, "rk": "classical RK4, graph-replayed steps",
-                   "l2": "inputs larger than L2 (1.5 GB per RK register at 8000^2)",
-                   "parallelism": "replicas" if ws > 1 else "single",
-                   "vs_baseline_basis": "paper Table 1, 8000^2 with HD, 100 iterations on 100 K20c: 3.91e7 cell-steps/s"},
+        "config": workload_config(args, ws),
         "cell_stage_rate": 4 * value,
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -365,6 +441,9 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, ws, rank)
+        elif args.learned:
+            if rank == 0:
+                run_learned(args, local)
         else:
             run_ours(args, ws, rank, local, pg)
     finally:

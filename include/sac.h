@@ -249,19 +249,28 @@ int sac_cnn_get_params(sac_cnn *c, float *params, long n);
 int sac_cnn_set_scales(sac_cnn *c, const float in_scale[8], const float out_scale[6]);
 /* pred_dev <- f(features(w_dev)).  ASYNC. */
 int sac_cnn_forward(sac_cnn *c, const float *w_dev, double gamma, double dx, double dy, float *pred_dev);
-/* Loss 0.5 * mean over 6 channels and all pixels of (f - target)^2 and its
- * gradient with respect to every parameter (host FP32 grads may be NULL; loss
- * may be NULL).  Synchronous when either output is non-NULL. */
-int sac_cnn_grads(sac_cnn *c, const float *w_dev, const float *target_dev, double gamma, double dx, double dy,
+/* Training target: next_dev is the state the corrected step should reach (the
+ * block-averaged fine run at the same time); the network's target is
+ * t = (next - w) / out_scale per field.  Loss 0.5 * mean over 6 channels and all
+ * pixels of (f(features(w)) - t)^2 and its gradient with respect to every
+ * parameter (host FP32 grads may be NULL; loss may be NULL).  Synchronous when
+ * either output is non-NULL. */
+int sac_cnn_grads(sac_cnn *c, const float *w_dev, const float *next_dev, double gamma, double dx, double dy,
                   float *grads, double *loss);
 /* One Adam step (beta 0.9, 0.999, eps 1e-8) at learning rate lr on that loss.
  * *loss (may be NULL) receives the loss before the update. */
-int sac_cnn_train_step(sac_cnn *c, const float *w_dev, const float *target_dev, double gamma, double dx, double dy,
+int sac_cnn_train_step(sac_cnn *c, const float *w_dev, const float *next_dev, double gamma, double dx, double dy,
                        double lr, double *loss);
 /* Correct the current state of a periodic SAC_FP32 context of the network's
- * size in place: u += out_scale * f(features(u)); ghosts and the signal speed
- * of the corrected state are refreshed so the next CFL step uses them.  ASYNC. */
+ * size in place: u += out_scale * (f(features(u)) - mean f), the per-field mean
+ * taken over the grid so the correction conserves every periodic sum; ghosts
+ * and the signal speed of the corrected state are refreshed so the next CFL
+ * step uses them.  ASYNC. */
 int sac_cnn_apply(sac_ctx *ctx, sac_cnn *c);
+/* Training-input augmentation: out = w + amp[f] * xi with xi ~ U[-1, 1) from
+ * SplitMix64 counters (seed, element index); w, out device [6][ny][nx] of the
+ * network's grid (out may equal w).  Synchronous. */
+int sac_cnn_perturb(sac_cnn *c, const float *w_dev, float *out_dev, const float amp[6], unsigned long long seed);
 /* r x r block average of a packed FP32 device array [nfields][nyf][nxf] into
  * [nfields][nyf/r][nxf/r] (nxf, nyf multiples of r).  ASYNC on `stream`. */
 int sac_block_average(const float *fine_dev, int nfields, int nxf, int nyf, int r, float *coarse_dev, void *stream);

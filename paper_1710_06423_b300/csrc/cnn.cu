@@ -351,18 +351,24 @@ __global__ void features_kernel(const float* __restrict__ w, int H, int W, float
     }
 }
 
-// loss 0.5 mean (pred - target)^2 over 6 channels; dY = (pred - target) / (6 n) as bf16 [p][16]
-__global__ void loss_kernel(const float* __restrict__ pred, const float* __restrict__ target, long long n,
+// Target t_c = (next_c - w_c) / out_scale_c (the residual the coarse step left);
+// loss 0.5 mean (pred - t)^2 over 6 channels; dY = (pred - t) / (6 n) as bf16 [p][16]
+__global__ void loss_kernel(const float* __restrict__ pred, const float* __restrict__ w,
+                            const float* __restrict__ next, const float* __restrict__ out_scale, long long n,
                             __nv_bfloat16* __restrict__ dy, float* __restrict__ loss_part)
 {
     __shared__ float red[NTHR / 32];
     float s = 0.f;
     const float inv = 1.f / (6.f * (float)n);
+    float iscale[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) iscale[c] = 1.f / out_scale[c];
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
         __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const float r = pred[p * 8 + c] - target[c * n + p];
+            const float t = (next[c * n + p] - w[c * n + p]) * iscale[c];
+            const float r = pred[p * 8 + c] - t;
             s += r * r;
             o[c] = __float2bfloat16_rn(r * inv);
         }
@@ -395,6 +401,21 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     }
 }
 
+// out = w + amp_f * xi, xi ~ U[-1,1) from SplitMix64 of (seed, element index)
+__global__ void perturb_kernel(const float* __restrict__ w, float* __restrict__ out, long long n_per_field,
+                               const float* __restrict__ amp, unsigned long long seed)
+{
+    const long long total = n_per_field * NF;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total; v += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (unsigned long long)(v + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const float xi = 2.f * (float)((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.f;
+        out[v] = w[v] + amp[v / n_per_field] * xi;
+    }
+}
+
 __global__ void block_average_kernel(const float* __restrict__ fine, int nf, int hf, int wf, int r,
                                      float* __restrict__ coarse)
 {
@@ -424,10 +445,43 @@ __global__ void export_paired_kernel(const float* __restrict__ u0, Layout L, flo
     }
 }
 
-// u += out_scale * pred on the interior and on every periodic ghost copy
-__global__ void add_correction_kernel(float* __restrict__ u0, Layout L, const float* __restrict__ pred,
-                                      const float* __restrict__ out_scale, DevScalars* sc)
+// Per-block partial sums of the 6 output channels (fixed order; the final sum is
+// taken in add_correction_kernel's prologue by every block, in the same order).
+__global__ void pred_sum_kernel(const float* __restrict__ pred, long long n, float* __restrict__ part)
 {
+    __shared__ float red[6][NTHR / 32];
+    float s[6] = {0, 0, 0, 0, 0, 0};
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s[c] += pred[p * 8 + c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        float x = s[c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float x = 0.f;
+        for (int k = 0; k < NTHR / 32; ++k) x += red[threadIdx.x][k];
+        part[blockIdx.x * 6 + threadIdx.x] = x;
+    }
+}
+
+// u += out_scale * (pred - mean(pred)) on the interior and on every periodic ghost
+// copy: the correction is conservative (it moves no mass, momentum, energy or flux
+// in or out of the periodic domain, as the fine and coarse runs conserve them).
+__global__ void add_correction_kernel(float* __restrict__ u0, Layout L, const float* __restrict__ pred,
+                                      const float* __restrict__ out_scale, const float* __restrict__ part,
+                                      int nblk, DevScalars* sc)
+{
+    __shared__ float mean[6];
+    if (threadIdx.x < 6) {
+        float x = 0.f;
+        for (int b = 0; b < nblk; ++b) x += part[b * 6 + threadIdx.x];
+        mean[threadIdx.x] = x / (float)((long long)L.nx * L.ny);
+    }
+    __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) { sc->cmax_bits[0] = 0ull; sc->cmax_bits[1] = 0ull; }
     const long long ex = L.nx + 2 * GY, ey = L.ny + 2 * GY, total = (long long)NF * ex * ey;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total; v += (long long)gridDim.x * blockDim.x) {
@@ -435,7 +489,7 @@ __global__ void add_correction_kernel(float* __restrict__ u0, Layout L, const fl
         const long long r = v - (long long)f * ex * ey;
         const int j = (int)(r / ex) - GY, i = (int)(r % ex) - GY;
         const int si = wrapm(i, L.nx), sj = wrapm(j, L.ny);
-        u0[L.idx(f, i, j, false)] += out_scale[f] * pred[((long long)sj * L.nx + si) * 8 + f];
+        u0[L.idx(f, i, j, false)] += out_scale[f] * (pred[((long long)sj * L.nx + si) * 8 + f] - mean[f]);
     }
 }
 
@@ -576,11 +630,11 @@ static cudaError_t forward_all(sac_cnn* c, const float* w, double gamma, double 
 }
 
 // loss and gradients of every parameter into c->grads; *loss (host) if non-null
-static int backward_all(sac_cnn* c, const float* target, double* loss)
+static int backward_all(sac_cnn* c, const float* w, const float* next, double* loss)
 {
     const long long P = (long long)c->H * c->W;
     const int lg = 296;
-    loss_kernel<<<lg, NTHR, 0, c->stream>>>(c->pred, target, P, c->dy3, c->loss_part);
+    loss_kernel<<<lg, NTHR, 0, c->stream>>>(c->pred, w, next, c->out_scale, P, c->dy3, c->loss_part);
     CC(cudaGetLastError());
     CC((run_dw<32, 16>(c, c->dy3, c->act[2], 3)));
     CC((run_conv<16, 32, MODE_MASK>(c, c->dy3, c->wt[3], nullptr, c->dact[2], c->act[2])));
@@ -721,13 +775,13 @@ int sac_cnn_forward(sac_cnn* c, const float* w, double gamma, double dx, double 
     return SAC_OK;
 }
 
-int sac_cnn_grads(sac_cnn* c, const float* w, const float* target, double gamma, double dx, double dy,
+int sac_cnn_grads(sac_cnn* c, const float* w, const float* next, double gamma, double dx, double dy,
                   float* grads, double* loss)
 {
-    if (!c || !w || !target) return SAC_ERR_ARG;
+    if (!c || !w || !next) return SAC_ERR_ARG;
     CC(cudaSetDevice(c->device));
     CC(forward_all(c, w, gamma, dx, dy));
-    int rc = backward_all(c, target, loss);
+    int rc = backward_all(c, w, next, loss);
     if (rc != SAC_OK) return rc;
     if (grads) {
         CC(cudaMemcpyAsync(grads, c->grads, kParams * 4, cudaMemcpyDeviceToHost, c->stream));
@@ -736,13 +790,13 @@ int sac_cnn_grads(sac_cnn* c, const float* w, const float* target, double gamma,
     return SAC_OK;
 }
 
-int sac_cnn_train_step(sac_cnn* c, const float* w, const float* target, double gamma, double dx, double dy,
+int sac_cnn_train_step(sac_cnn* c, const float* w, const float* next, double gamma, double dx, double dy,
                        double lr, double* loss)
 {
-    if (!c || !w || !target || !(lr > 0.0)) return SAC_ERR_ARG;
+    if (!c || !w || !next || !(lr > 0.0)) return SAC_ERR_ARG;
     CC(cudaSetDevice(c->device));
     CC(forward_all(c, w, gamma, dx, dy));
-    int rc = backward_all(c, target, loss);
+    int rc = backward_all(c, w, next, loss);
     if (rc != SAC_OK) return rc;
     c->adam_t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
@@ -767,11 +821,27 @@ int sac_cnn_apply(sac_ctx* ctx, sac_cnn* c)
     export_paired_kernel<<<grid_n(P * NF, 4096), 256, 0, c->stream>>>(u0, ctx->L, c->state);
     CC(cudaGetLastError());
     CC(forward_all(c, c->state, ctx->p.gamma, (ctx->p.x1 - ctx->p.x0) / ctx->p.nx, (ctx->p.y1 - ctx->p.y0) / ctx->p.ny));
+    const int nsum = 148;
+    pred_sum_kernel<<<nsum, NTHR, 0, c->stream>>>(c->pred, P, c->loss_part);
+    CC(cudaGetLastError());
     const long long ng = (long long)NF * (ctx->p.nx + 2 * GY) * (ctx->p.ny + 2 * GY);
-    add_correction_kernel<<<grid_n(ng, 4096), 256, 0, c->stream>>>(u0, ctx->L, c->pred, c->out_scale, ctx->sc);
+    add_correction_kernel<<<grid_n(ng, 4096), 256, 0, c->stream>>>(u0, ctx->L, c->pred, c->out_scale, c->loss_part,
+                                                                   nsum, ctx->sc);
     CC(cudaGetLastError());
     cmax_paired_kernel<<<grid_n(P, 2048), NTHR, 0, c->stream>>>(u0, ctx->L, (float)ctx->p.gamma, ctx->sc);
     CC(cudaGetLastError());
+    return SAC_OK;
+}
+
+int sac_cnn_perturb(sac_cnn* c, const float* w, float* out, const float amp[6], unsigned long long seed)
+{
+    if (!c || !w || !out || !amp) return SAC_ERR_ARG;
+    CC(cudaSetDevice(c->device));
+    CC(cudaMemcpyAsync(c->loss_part + 1000, amp, 6 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    const long long n = (long long)c->H * c->W;
+    perturb_kernel<<<grid_n(n * NF, 4096), 256, 0, c->stream>>>(w, out, n, c->loss_part + 1000, seed);
+    CC(cudaGetLastError());
+    CC(cudaStreamSynchronize(c->stream));
     return SAC_OK;
 }
 

@@ -73,10 +73,10 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
     return r;
 }
 __device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float max3abs(float a, float b, float c)
+__device__ __forceinline__ float max3(float a, float b, float c)
 {
     float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(fabsf(a)), "f"(fabsf(b)), "f"(fabsf(c)));
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
 }
 __device__ __forceinline__ float rcp_approx(float v)
@@ -164,18 +164,21 @@ __device__ __forceinline__ void face_fluxes(const float2 (&u)[SEG + 6], const fl
                                             float2 a, float2 bh, float2 (&G)[SEG + 1])
 {
     const float2 m3 = splat(-3.f);
-    float2 d1[SEG + 3], d3[SEG + 3];
+    float2 d1[SEG + 3];
+    float a1x[SEG + 3], a1y[SEG + 3], a3x[SEG + 3], a3y[SEG + 3];   // |d1|, |d3| per face and lane
 #pragma unroll
     for (int q = 0; q < SEG + 3; ++q) {   // face f = q - 2 relative to the first cell
         d1[q] = sub2(u[q + 2], u[q + 1]);
-        d3[q] = fma2(m3, d1[q], sub2(u[q + 3], u[q]));
+        const float2 d3 = fma2(m3, d1[q], sub2(u[q + 3], u[q]));
+        a1x[q] = fabsf(d1[q].x); a1y[q] = fabsf(d1[q].y);
+        a3x[q] = fabsf(d3.x); a3y[q] = fabsf(d3.y);
     }
 #pragma unroll
     for (int q = 1; q <= SEG + 1; ++q) {
-        const float m1x = fmaxf(max3abs(d1[q - 1].x, d1[q].x, d1[q + 1].x), 1e-30f);
-        const float m1y = fmaxf(max3abs(d1[q - 1].y, d1[q].y, d1[q + 1].y), 1e-30f);
-        const float m3x = max3abs(d3[q - 1].x, d3[q].x, d3[q + 1].x);
-        const float m3y = max3abs(d3[q - 1].y, d3[q].y, d3[q + 1].y);
+        const float m1x = fmaxf(max3(a1x[q - 1], a1x[q], a1x[q + 1]), 1e-30f);
+        const float m1y = fmaxf(max3(a1y[q - 1], a1y[q], a1y[q + 1]), 1e-30f);
+        const float m3x = max3(a3x[q - 1], a3x[q], a3x[q + 1]);
+        const float m3y = max3(a3y[q - 1], a3y[q], a3y[q + 1]);
         const float2 R = make_float2(fdiv(m3x, m1x), fdiv(m3y, m1y));
         const float2 sf = add2(s2[q - 1], s2[q]);
         const float2 nu = fma2(a, R, mul2(bh, sf));
@@ -224,16 +227,17 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     // region (r, c) <-> interior (x0 - 4 + c, y0 - 3 + r) <-> padded element (y0 + r) * pitch + x0 + c
     const long long rbase = (long long)y0 * L.pitch + x0;
 
-    // ---- 0. stage the three planes (8-byte cp.async; incremental indices) ------
+    // ---- 0. stage the three planes: one warp per row, lanes across columns --------
+    {
+        const float2* src = gin + rbase + lane;
+        float2* dst = &S.u[0][0][0] + lane;
 #pragma unroll 1
-    for (int p = 0; p < 3; ++p) {
-        const float2* src = gin + p * P + rbase;
-        int r = tid / RX, c = tid - (tid / RX) * RX;
-#pragma unroll 1
-        for (int v = tid; v < RY * RX; v += NT) {
-            cp_async8(&S.u[p][r][c], src + (long long)r * L.pitch + c);
-            c += NT % RX; r += NT / RX;
-            if (c >= RX) { c -= RX; ++r; }
+        for (int row = warp; row < 3 * RY; row += NW) {           // row = plane * RY + r
+            const int p = row / RY, r = row - p * RY;
+            const float2* g = src + p * P + (long long)r * L.pitch;
+            float2* d = dst + row * RXP;
+            cp_async8(d, g);
+            if (lane < RX - 32) cp_async8(d + 32, g + 32);
         }
     }
     if (tid < 3) {
@@ -401,17 +405,18 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     float2* __restrict__ gacc = reinterpret_cast<float2*>(a.acc);
     float2 outv[SEG][3];
 
+    const long long e_first = L.at(gi, y0 + y_0);   // this thread's first cell; the next q is + q * pitch
+    const bool col_ok = gi < L.nx;
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
         // pointwise registers of this pair first, so their latency hides behind the sweep
+        const long long ep = p * P + e_first;
         float2 u0v[SEG], dv[SEG];
 #pragma unroll
         for (int q = 0; q < SEG; ++q) {
-            const int j = y0 + y_0 + q;
-            const bool ok = gi < L.nx && j < L.ny;
-            const long long e = p * P + L.at(gi, j);
-            u0v[q] = (STAGE >= 2 && ok) ? gu0[e] : make_float2(0.f, 0.f);
-            dv[q] = (STAGE >= 3 && ok) ? gacc[e] : make_float2(0.f, 0.f);
+            const bool ok = col_ok && (y0 + y_0 + q) < L.ny;
+            u0v[q] = (STAGE >= 2 && ok) ? gu0[ep + q * L.pitch] : make_float2(0.f, 0.f);
+            dv[q] = (STAGE >= 3 && ok) ? gacc[ep + q * L.pitch] : make_float2(0.f, 0.f);
         }
         float2 u[SEG + 6];   // rows y_0-3 .. y_0+SEG+2 (region row = cell row + 3)
 #pragma unroll
@@ -439,8 +444,8 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             const float2 k = add2(fma2(m12y, d, hy[q]), KX[p][y_0 + q][col]);
             const float2 ucen = u[q + 3];
             float2 o = make_float2(0.f, 0.f);
-            if (gi < L.nx && j < L.ny) {
-                const long long e = p * P + L.at(gi, j);
+            if (col_ok && j < L.ny) {
+                const long long e = ep + q * L.pitch;
                 if (STAGE == 1) {
                     o = fma2(h2, k, ucen);
                 } else if (STAGE == 2) {

@@ -22,7 +22,7 @@ import time
 import numpy as np
 
 from . import inputs
-from .sac import CNN, FP32, Solver, block_average
+from .sac import CNN, FP32, SacError, Solver, block_average
 
 #: fixed feature scales: rho, m_x, m_y, e, B_x, B_y, p_k, j_z (Orszag-Tang magnitudes)
 FEATURE_SCALES = np.array([0.25, 0.25, 0.25, 0.5, 0.3, 0.3, 0.15, 10.0], dtype=np.float32)
@@ -52,97 +52,122 @@ def family_state(seed: int, k: int, n: int):
 
 
 class Pairs:
-    """Training pairs on the device: inputs x' (coarse state after one coarse step)
-    and raw residuals r = avg(fine(t + dt_c)) - x'."""
+    """Training pairs on the device: x' (the coarse state after one coarse step
+    from avg(fine(t))) and next = avg(fine(t + dt_c)), the state the corrected
+    step should reach; the network's target (next - x') / out_scale is formed
+    inside the loss kernel."""
 
     def __init__(self):
-        self.x, self.r, self.gamma = [], [], []
+        self.x, self.next, self.gamma = [], [], []
 
     def __len__(self):
         return len(self.x)
 
 
 def generate_pairs(pairs: Pairs, seed: int, k: int, n_coarse: int, ratio: int, dt_c: float, n_steps: int,
-                   every: int, torch):
+                   every: int, torch, solver_kw=None):
     """Run the fine solver of family member (seed, k) for n_steps coarse steps and
-    collect a pair every `every` coarse steps."""
+    collect a pair every `every` coarse steps (solver_kw: extra sac_params fields,
+    e.g. the diffusion coefficients, used by both grids).  If the fine run turns
+    non-finite, the pairs collected before stay and the member ends there;
+    returns the number of coarse steps the member completed."""
+    kw = dict(solver_kw or {})
     nf = n_coarse * ratio
     w0, gamma = family_state(seed, k, nf)
     fine_buf = torch.empty((6, nf, nf), dtype=torch.float32, device="cuda")
     a0 = torch.empty((6, n_coarse, n_coarse), dtype=torch.float32, device="cuda")
-    with Solver(nx=nf, ny=nf, precision=FP32, gamma=gamma) as fine, \
-            Solver(nx=n_coarse, ny=n_coarse, precision=FP32, gamma=gamma) as coarse:
+    with Solver(nx=nf, ny=nf, precision=FP32, gamma=gamma, **kw) as fine, \
+            Solver(nx=n_coarse, ny=n_coarse, precision=FP32, gamma=gamma, **kw) as coarse:
         fine.set_state(w0, None, 0.0)
         fine.set_fixed_dt(dt_c / ratio)
         coarse_steps = 0
-        while coarse_steps + 1 <= n_steps:
-            fine.get_state_dev(fine_buf)
-            block_average(fine_buf, 6, nf, nf, ratio, a0)
-            fine.steps(ratio)
-            fine.get_state_dev(fine_buf)
-            a1 = torch.empty_like(a0)
-            block_average(fine_buf, 6, nf, nf, ratio, a1)
-            coarse.set_state_dev(a0, None, 0.0)
-            coarse.step(dt_c)
-            xp = torch.empty_like(a0)
-            coarse.get_state_dev(xp)
-            pairs.x.append(xp)
-            pairs.r.append(a1 - xp)
-            pairs.gamma.append(gamma)
-            coarse_steps += 1
-            skip = min(every - 1, n_steps - coarse_steps)
-            if skip > 0:
-                fine.steps(ratio * skip)
-                coarse_steps += skip
-        fine.sync()
-    return pairs
+        try:
+            while coarse_steps + 1 <= n_steps:
+                fine.get_state_dev(fine_buf)
+                block_average(fine_buf, 6, nf, nf, ratio, a0)
+                fine.steps(ratio)
+                fine.get_state_dev(fine_buf)
+                fine.sync()                      # a non-finite fine state stops here
+                a1 = torch.empty_like(a0)
+                block_average(fine_buf, 6, nf, nf, ratio, a1)
+                coarse.set_state_dev(a0, None, 0.0)
+                coarse.step(dt_c)
+                xp = torch.empty_like(a0)
+                coarse.get_state_dev(xp)
+                pairs.x.append(xp)
+                pairs.next.append(a1)
+                pairs.gamma.append(gamma)
+                coarse_steps += 1
+                skip = min(every - 1, n_steps - coarse_steps)
+                if skip > 0:
+                    fine.steps(ratio * skip)
+                    coarse_steps += skip
+        except SacError:
+            pass
+    return coarse_steps
 
 
-def out_scales(pairs: Pairs, torch) -> np.ndarray:
-    """Per-field RMS of the residuals (the network predicts residual / scale)."""
-    acc = torch.zeros(6, dtype=torch.float64, device="cuda")
-    for r in pairs.r:
-        acc += (r.double() ** 2).mean(dim=(1, 2))
-    rms = torch.sqrt(acc / len(pairs)).cpu().numpy()
-    return np.maximum(rms, 1e-30).astype(np.float32)
+def _host(x):
+    return x.double().cpu().numpy()
+
+
+def out_scales(pairs: Pairs, torch, samples: int = 16) -> np.ndarray:
+    """Per-field RMS of the residuals next - x' over evenly spaced pairs (host);
+    the network predicts residual / scale."""
+    idx = np.linspace(0, len(pairs) - 1, min(samples, len(pairs))).astype(int)
+    acc = np.zeros(6)
+    for j in idx:
+        r = _host(pairs.next[j]) - _host(pairs.x[j])
+        acc += (r * r).mean(axis=(1, 2))
+    return np.maximum(np.sqrt(acc / len(idx)), 1e-30).astype(np.float32)
 
 
 def train(net: CNN, pairs: Pairs, osc: np.ndarray, dx: float, iters: int, lr: float, torch, seed: int = 0,
-          log_every: int = 0):
-    """Adam on randomly drawn pairs; lr decays by 10x over the run (cosine)."""
+          log_every: int = 0, noise: float = 0.0):
+    """Adam on randomly drawn pairs; lr decays by 10x over the run (cosine).
+
+    noise > 0: on every other iteration the input x' is perturbed by
+    noise * out_scale * U[-1,1) per field (sac_cnn_perturb) while the target state
+    stays the fine one, so the network also learns to pull perturbed states back
+    (its own errors, in a rollout) toward the fine solution."""
     rng = np.random.default_rng(seed)
-    inv = torch.from_numpy(1.0 / osc).cuda().view(6, 1, 1)
-    targets = [(r * inv).contiguous() for r in pairs.r]
     losses = []
+    scratch = torch.empty_like(pairs.x[0]) if noise > 0 else None
+    amp = (noise * osc).astype(np.float32)
     for it in range(iters):
         j = int(rng.integers(len(pairs)))
         lr_t = lr * (0.1 + 0.9 * 0.5 * (1 + math.cos(math.pi * it / max(1, iters))))
         want = log_every > 0 and (it % log_every == 0 or it == iters - 1)
-        loss = net.train_step(pairs.x[j], targets[j], pairs.gamma[j], dx, dx, lr_t, want_loss=want)
+        x = pairs.x[j]
+        if noise > 0 and it % 2 == 1:
+            net.perturb(x, scratch, amp, seed * 1000003 + it)
+            x = scratch
+        loss = net.train_step(x, pairs.next[j], pairs.gamma[j], dx, dx, lr_t, want_loss=want)
         if want:
             losses.append((it, loss))
     return losses
 
 
 def residual_gain(net: CNN, pairs: Pairs, osc: np.ndarray, dx: float, torch) -> float:
-    """mean |r - out_scale f(x')| / mean |r| over pairs (1 = no gain)."""
+    """mean |r - out_scale f(x')| / mean |r| over pairs, r = next - x' (1 = no gain); host norms."""
     n = pairs.x[0].shape[1]
     pred = torch.empty((n * n, 8), dtype=torch.float32, device="cuda")
     num = den = 0.0
-    sc = torch.from_numpy(osc).cuda().view(6, 1, 1)
-    for x, r, g in zip(pairs.x, pairs.r, pairs.gamma):
+    for x, nx_, g in zip(pairs.x, pairs.next, pairs.gamma):
         net.forward(x, g, dx, dx, pred)
-        corr = pred[:, :6].t().reshape(6, n, n) * sc
-        num += float((r - corr).abs().sum())
-        den += float(r.abs().sum())
+        torch.cuda.synchronize()
+        corr = pred.double().cpu().numpy()[:, :6].T.reshape(6, n, n) * osc.astype(np.float64)[:, None, None]
+        r = _host(nx_) - _host(x)
+        num += float(np.abs(r - corr).sum())
+        den += float(np.abs(r).sum())
     return num / den
 
 
-def run_plain(w0, gamma, n, dt, steps, torch, net=None):
+def run_plain(w0, gamma, n, dt, steps, torch, net=None, solver_kw=None):
     """Coarse (or plain) run of `steps` fixed steps; with `net`, the correction after
     every step.  Returns the final state (device) and the device time in seconds."""
     out = torch.empty((6, n, n), dtype=torch.float32, device="cuda")
-    with Solver(nx=n, ny=n, precision=FP32, gamma=gamma) as s:
+    with Solver(nx=n, ny=n, precision=FP32, gamma=gamma, **(solver_kw or {})) as s:
         s.set_state(w0, None, 0.0)
         s.set_fixed_dt(dt)
         stream = torch.cuda.current_stream()
@@ -167,8 +192,9 @@ def run_plain(w0, gamma, n, dt, steps, torch, net=None):
 
 
 def l1_error(a, b) -> np.ndarray:
-    """Relative L1 error per field of a against b (device tensors [6, n, n])."""
-    return ((a - b).abs().sum(dim=(1, 2)) / b.abs().sum(dim=(1, 2))).double().cpu().numpy()
+    """Relative L1 error per field of a against b (device tensors [6, n, n]; host norms)."""
+    ah, bh = _host(a), _host(b)
+    return np.abs(ah - bh).reshape(6, -1).sum(axis=1) / np.abs(bh).reshape(6, -1).sum(axis=1)
 
 
 def downsample(x, n_to, torch):

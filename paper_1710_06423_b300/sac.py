@@ -33,7 +33,7 @@ EXPORTS = (
     "sac_batch_set_config",
     "sac_cnn_param_count", "sac_cnn_init", "sac_cnn_free", "sac_cnn_last_error", "sac_cnn_set_params",
     "sac_cnn_get_params", "sac_cnn_set_scales", "sac_cnn_forward", "sac_cnn_grads", "sac_cnn_train_step",
-    "sac_cnn_apply", "sac_block_average",
+    "sac_cnn_apply", "sac_cnn_perturb", "sac_block_average",
     "sac_step_noalloc",
 )
 
@@ -116,6 +116,7 @@ def load() -> ctypes.CDLL:
         "sac_cnn_grads": (i, [vp, vp, vp, d, d, d, ctypes.POINTER(ctypes.c_float), dp]),
         "sac_cnn_train_step": (i, [vp, vp, vp, d, d, d, d, dp]),
         "sac_cnn_apply": (i, [vp, vp]),
+        "sac_cnn_perturb": (i, [vp, vp, vp, ctypes.POINTER(ctypes.c_float), ctypes.c_ulonglong]),
         "sac_block_average": (i, [vp, i, i, i, i, vp, vp]),
         "sac_step_noalloc": (i, [P, vp, vp, d, dp]),
     }
@@ -427,20 +428,25 @@ class CNN:
         self._check(load().sac_cnn_forward(self._c, ctypes.c_void_p(w_dev.data_ptr()), gamma, dx, dy,
                                            ctypes.c_void_p(pred_dev.data_ptr())), "sac_cnn_forward")
 
-    def grads(self, w_dev, target_dev, gamma, dx, dy):
+    def grads(self, w_dev, next_dev, gamma, dx, dy):
         g = np.zeros(self.nparams, dtype=np.float32)
         loss = ctypes.c_double()
         self._check(load().sac_cnn_grads(self._c, ctypes.c_void_p(w_dev.data_ptr()),
-                                         ctypes.c_void_p(target_dev.data_ptr()), gamma, dx, dy, _fp(g),
+                                         ctypes.c_void_p(next_dev.data_ptr()), gamma, dx, dy, _fp(g),
                                          ctypes.byref(loss)), "sac_cnn_grads")
         return loss.value, g
 
-    def train_step(self, w_dev, target_dev, gamma, dx, dy, lr, want_loss=True):
+    def train_step(self, w_dev, next_dev, gamma, dx, dy, lr, want_loss=True):
         loss = ctypes.c_double()
         self._check(load().sac_cnn_train_step(self._c, ctypes.c_void_p(w_dev.data_ptr()),
-                                              ctypes.c_void_p(target_dev.data_ptr()), gamma, dx, dy, lr,
+                                              ctypes.c_void_p(next_dev.data_ptr()), gamma, dx, dy, lr,
                                               ctypes.byref(loss) if want_loss else None), "sac_cnn_train_step")
         return loss.value
+
+    def perturb(self, w_dev, out_dev, amp, seed: int):
+        a = np.ascontiguousarray(amp, dtype=np.float32)
+        self._check(load().sac_cnn_perturb(self._c, ctypes.c_void_p(w_dev.data_ptr()),
+                                           ctypes.c_void_p(out_dev.data_ptr()), _fp(a), int(seed)), "sac_cnn_perturb")
 
     def apply(self, solver):
         self._check(load().sac_cnn_apply(solver._ctx, self._c), "sac_cnn_apply")
