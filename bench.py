@@ -269,7 +269,7 @@ def run_learned(args, local):
     block-averaged 4000^2 plain run (Orszag-Tang family, horizon t_end)."""
     import torch
     from paper_1710_06423_b300 import learned
-    from paper_1710_06423_b300.sac import CNN, FP32, Solver, block_average
+    from paper_1710_06423_b300.sac import CNN, FP32, SacError, Solver
     torch.cuda.set_device(local)
     nc, ratio = 1000, 4
     nf = nc * ratio
@@ -292,11 +292,19 @@ def run_learned(args, local):
     net.set_params(learned.init_params(1))
     net.set_scales(learned.FEATURE_SCALES, osc)
     t0 = time.perf_counter()
-    losses = learned.train(net, pairs, osc, dx, iters=3000, lr=1e-3, torch=torch, log_every=500)
+    # noise-injected training (inputs perturbed by out_scale * U[-1,1) every other step)
+    losses = learned.train(net, pairs, osc, dx, iters=3000, lr=1e-3, torch=torch, log_every=500, noise=1.0)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del pairs
     torch.cuda.empty_cache()
+    held_pairs = learned.Pairs()                # one-step gain on the held-out member (first fifth of the horizon)
+    learned.generate_pairs(held_pairs, 2024, 20, nc, ratio, dt_c, steps // 5, max(1, steps // 100), torch,
+                           solver_kw=kw)
+    held_gain = learned.residual_gain(net, held_pairs, osc, dx, torch)
+    del held_pairs
+    alpha = 0.5                                  # relaxation of the applied correction
+    net.set_scales(learned.FEATURE_SCALES, osc * alpha)
 
     held = 20                                    # held-out family member
     w0f, gamma = learned.family_state(2024, held, nf)
@@ -321,15 +329,22 @@ def run_learned(args, local):
         plain[n] = {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec}
         curve.append((sec, float(err.mean())))
     w0c = learned.downsample(wf_dev, nc, torch).double().cpu().numpy()
-    out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, net=net, solver_kw=kw)
+    fell_back = False
+    try:
+        out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, net=net, solver_kw=kw)
+    except SacError:
+        # the plain coarse solver is the fallback of the learned run
+        fell_back = True
+        out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, solver_kw=kw)
     err = learned.l1_error(out, truth)
     t_eq = learned.equal_error_time(curve, float(err.mean()))
     res = {"metric": "learned-vs-plain time at equal L1 error", "t_end": args.t_end, "coarse": nc, "fine": nf,
            "dt_coarse": dt_c, "steps_coarse": steps, "train_members": list(train_members), "held_out_member": held,
            "c_shk": kw["c_shk"], "member_steps_completed": completed,
            "pairs": int(sum(len(range(0, completed[k], every)) for k in train_members)), "data_seconds": t_data,
-           "train_seconds": t_train, "losses": losses,
-           "learned": {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec},
+           "train_seconds": t_train, "losses": losses, "noise": 1.0, "alpha": alpha,
+           "held_out_one_step_residual_ratio": held_gain,
+           "learned": {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec, "fell_back_to_plain": fell_back},
            "plain": plain, "plain_time_at_learned_error": t_eq,
            "speedup_at_equal_error": (t_eq / sec) if t_eq else None}
     print(json.dumps(res), flush=True)
