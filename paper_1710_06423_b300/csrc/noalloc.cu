@@ -164,6 +164,7 @@ extern "C" int sac_step_noalloc(const sac_params* p, const float* w_in, float* w
     a.dx = dx; a.dy = dy; a.gamma = p->gamma;
     for (int f = 0; f < NF; ++f) a.c2[f] = p->c2[f];
     a.c_shk = p->c_shk; a.bc_x = p->bc_x; a.bc_y = p->bc_y;
+    a.derive_f32();
     for (int stage = 1; stage <= 4; ++stage) {
         a.sin = stage == 1 ? u0 : (stage == 2 ? sa : (stage == 3 ? sb : sa));
         a.sout = stage == 1 ? sa : (stage == 2 ? sb : (stage == 3 ? sa : u0));

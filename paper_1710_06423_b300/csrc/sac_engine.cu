@@ -214,6 +214,7 @@ static void fill_stage_args(const sac_ctx* c, int stage, StageArgs<T>* a)
     a->gamma = c->p.gamma;
     for (int f = 0; f < NF; ++f) a->c2[f] = c->p.c2[f];
     a->c_shk = c->p.c_shk; a->bc_x = c->p.bc_x; a->bc_y = c->p.bc_y;
+    a->derive_f32();
 }
 
 void sac_fp32_stage_args(const sac_ctx* c, int stage, StageArgs<float>* out) { fill_stage_args<float>(c, stage, out); }

@@ -61,6 +61,8 @@ struct DevScalars {
     int done;                 // t reached t_end
     int status;               // ST_OK or an error code
     int pad;
+    float fdt[4];             // FP32 kernels: dt/2, dt, dt/3, dt/6 of the current step (rounded once)
+    float fcmax[2];           // FP32 kernels: cmax_step rounded to float
 };
 
 __device__ __forceinline__ double decode_speed(unsigned long long b, int fp32)
@@ -89,6 +91,9 @@ __device__ __forceinline__ void step_begin(DevScalars* sc, double dx, double dy,
     if (sc->t + dt >= sc->t_end) { dt = sc->t_end - sc->t; last = 1; }
     sc->dt = dt;
     sc->cmax_step[0] = cx; sc->cmax_step[1] = cy;
+    sc->fdt[0] = (float)(0.5 * dt); sc->fdt[1] = (float)dt;
+    sc->fdt[2] = (float)(dt / 3.0); sc->fdt[3] = (float)(dt / 6.0);
+    sc->fcmax[0] = (float)cx; sc->fcmax[1] = (float)cy;
     sc->t = last ? sc->t_end : sc->t + dt;
     sc->steps += 1;
     if (last) sc->done = 1;
@@ -109,6 +114,17 @@ struct StageArgs {
     double c2[NF];
     double c_shk;
     int bc_x, bc_y;
+    // FP32 kernels: the parameters above rounded once on the host, so a tile
+    // does no double arithmetic (FP64 issues at 1/64 of the FP32 rate here)
+    float f_gm1, f_gamma, f_bh;          // gamma - 1, gamma, c_shk / 2
+    float f_inv12dx, f_inv12dy;          // 1 / (12 dx), 1 / (12 dy)
+    float f_c2dx[NF], f_c2dy[NF];        // c2_f / dx, c2_f / dy
+    __host__ void derive_f32()
+    {
+        f_gm1 = (float)(gamma - 1.0); f_gamma = (float)gamma; f_bh = (float)(0.5 * c_shk);
+        f_inv12dx = (float)(1.0 / (12.0 * dx)); f_inv12dy = (float)(1.0 / (12.0 * dy));
+        for (int f = 0; f < NF; ++f) { f_c2dx[f] = (float)(c2[f] / dx); f_c2dy[f] = (float)(c2[f] / dy); }
+    }
 };
 
 // ---- launchers implemented in the kernel translation units --------------

@@ -8,7 +8,8 @@
 // one packed f32x2 instruction (fma/add/sub/mul.rn.f32x2) advances two
 // variables at once and every stencil offset stays an aligned 8-byte access.
 //
-// One CTA (128 threads) owns a 32 x 32 tile:
+// One CTA (256 threads, two per SM) owns a 32 x 32 tile at a time and walks
+// the tiles of the grid persistently:
 //   0. stage the tile + 3-cell halo of the three planes into shared memory
 //      with 8-byte cp.async (odd row strides keep row-mapped phases free of
 //      bank conflicts);
@@ -22,8 +23,8 @@
 //      memory over the dead x-flux buffer);
 //   4. Y sweep: each thread walks 8 cells of one column the same way, adds
 //      k_x, applies the RK stage update (D scheme, see below), stores the
-//      stage output with its ghost copies and, in stage 4, reduces the
-//      maximum signal speed of the new state.
+//      stage output with its ghost copies and, in stage 4, folds the signal
+//      speed of the new state into a per-thread maximum (reduced once per CTA).
 //
 // RK registers (D scheme, 22.5 values moved per cell-stage):
 //   s1: S1 = U0 + dt/2 k1
@@ -94,10 +95,6 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-}
-__device__ __forceinline__ void prefetch_l2(const void* p)
-{
-    asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
 }
 
 // Division flavours (compile-time): the fast path uses rcp.approx for 1/rho and
@@ -186,38 +183,60 @@ __device__ __forceinline__ void face_fluxes(const float2 (&u)[SEG + 6], const fl
     }
 }
 
-// Warm L2 with what the tile at (x0, y0) will read: its staged region of the
-// stencil input and (stages 2-4) its rows of the pointwise registers U0 and D.
-// One prefetch per 128-byte line; issued while the previous tile computes.
-template <int STAGE>
-__device__ __forceinline__ void prefetch_tile(const StageArgs<float>& a, const int x0, const int y0)
+// Per-step constants of one run: the RK stage weights (from the device-side
+// step scalars) and, in shared memory, the per-pair hyper-diffusion
+// coefficients c2 cmax / d.  Loaded once per launch by the single-run kernel,
+// once per tile by the batch kernel (whose tiles belong to different runs).
+struct StepConsts {
+    float2 h2, dt2, d3t, d6t;
+};
+__device__ __forceinline__ StepConsts load_step_consts(const DevScalars* sc)
 {
-    const Layout L = a.L;
-    const long long P = L.fstride;
-    const float2* gin = reinterpret_cast<const float2*>(a.sin);
-    const long long rbase = (long long)y0 * L.pitch + x0;
-    constexpr int LPR = (RX * 8 + 127) / 128;                  // lines per staged row (3)
-    for (int v = threadIdx.x; v < 3 * RY * LPR; v += NT) {
-        const int p = v / (RY * LPR), rem = v - p * (RY * LPR), r = rem / LPR, l = rem - r * LPR;
-        prefetch_l2(gin + p * P + rbase + (long long)r * L.pitch + l * 16);
+    StepConsts k;
+    k.h2 = splat(sc->fdt[0]); k.dt2 = splat(sc->fdt[1]); k.d3t = splat(sc->fdt[2]); k.d6t = splat(sc->fdt[3]);
+    return k;
+}
+// threads 0..2 (one pair each); visible to the CTA after its next barrier
+__device__ __forceinline__ void store_hd_coeffs(const StageArgs<float>& a, Smem& S, const int tid)
+{
+    if (tid < 3) {
+        const float cmx = a.sc->fcmax[0], cmy = a.sc->fcmax[1];
+        const int f0 = tid == 0 ? 0 : (tid == 1 ? 1 : 4), f1 = tid == 0 ? 3 : (tid == 1 ? 2 : 5);
+        S.ax[tid] = make_float2(a.f_c2dx[f0] * cmx, a.f_c2dx[f1] * cmx);
+        S.ay[tid] = make_float2(a.f_c2dy[f0] * cmy, a.f_c2dy[f1] * cmy);
     }
-    if (STAGE >= 2) {
-        const float2* u0 = reinterpret_cast<const float2*>(a.u0);
-        const float2* dd = reinterpret_cast<const float2*>(a.acc);
-        for (int v = threadIdx.x; v < 3 * TY * 2; v += NT) {   // 2 lines of 128 B per tile row
-            const int p = v / (TY * 2), rem = v - p * TY * 2, r = rem >> 1, h = rem & 1;
-            const long long e = p * P + L.at(x0 + 16 * h, y0 + r);
-            prefetch_l2(u0 + e);
-            if (STAGE >= 3) prefetch_l2(dd + e);
+}
+
+// Block maximum of the per-thread running signal-speed keys m[0] (x), m[1] (y)
+// folded into the run's cmax_bits with one atomicMax per direction.  Every
+// thread of the CTA calls it (it holds a barrier).
+__device__ __forceinline__ void block_speed_max(const unsigned long long (&m)[2], unsigned long long (*red)[NW],
+                                                DevScalars* sc)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+        unsigned long long v = m[d];
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = w > v ? w : v;
         }
+        if (lane == 0) red[d][warp] = v;
+    }
+    __syncthreads();
+    if (tid < 2) {
+        unsigned long long v = 0ull;
+        for (int w = 0; w < NW; ++w) v = red[tid][w] > v ? red[tid][w] : v;
+        atomicMax(&sc->cmax_bits[tid], v);
     }
 }
 
 // One tile (x0, y0) of one run; every thread of the CTA calls it (it holds
-// barriers).  `red` is a block-shared scratch for the stage-4 reduction.
+// barriers).  S.ax/S.ay must hold the run's coefficients (store_hd_coeffs).
+// Stage 4 folds the signal speeds of the tile's new state into m.
 template <int STAGE, bool BG, bool HD>
 __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x0, const int y0, Smem& S,
-                                          unsigned long long (*red)[NW])
+                                          const StepConsts& K, unsigned long long (&m)[2])
 {
     const Layout L = a.L;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -240,16 +259,10 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             if (lane < RX - 32) cp_async8(d + 32, g + 32);
         }
     }
-    if (tid < 3) {
-        const float cmx = (float)a.sc->cmax_step[0], cmy = (float)a.sc->cmax_step[1];
-        const int f0 = tid == 0 ? 0 : (tid == 1 ? 1 : 4), f1 = tid == 0 ? 3 : (tid == 1 ? 2 : 5);
-        S.ax[tid] = make_float2((float)(a.c2[f0] / a.dx) * cmx, (float)(a.c2[f1] / a.dx) * cmx);
-        S.ay[tid] = make_float2((float)(a.c2[f0] / a.dy) * cmy, (float)(a.c2[f1] / a.dy) * cmy);
-    }
     cp_async_wait_all();
     __syncthreads();
 
-    const float gm1 = (float)(a.gamma - 1.0);
+    const float gm1 = a.f_gm1;
 
     // ---- 1. primitives and fluxes on the staged box [x0-3, x0+TX+3) x [y0-3, y0+TY+3)
     // (cells v and v + NT per iteration: two independent dependency chains)
@@ -323,7 +336,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     }
     __syncthreads();
 
-    const float inv12dx = (float)(1.0 / (12.0 * a.dx)), inv12dy = (float)(1.0 / (12.0 * a.dy));
+    const float inv12dx = a.f_inv12dx, inv12dy = a.f_inv12dy;
 
     // ---- 2. shock indicator on [x0-1, x0+TX] x [y0-1, y0+TY] ---------------------
     if constexpr (HD) {
@@ -349,7 +362,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         __syncthreads();
     }
 
-    const float2 bh = splat((float)(0.5 * a.c_shk));
+    const float2 bh = splat(a.f_bh);
     const float2 m12x = splat(-inv12dx), m12y = splat(-inv12dy), eight = splat(8.f);
 
     // ---- 3. X sweep: thread = (row lane, SEG-cell segment per warp) ---------------
@@ -396,9 +409,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     const float2 (*KX)[TY][KXP] = reinterpret_cast<const float2 (*)[TY][KXP]>(&S.fx[0][0][0]);
     const int col = lane, y_0 = warp * SEG;
     const int gi = x0 + col;
-    const double dtd = a.sc->dt;
-    const float2 h2 = splat((float)(0.5 * dtd)), dt2 = splat((float)dtd), d3t = splat((float)(dtd / 3.0)),
-                 d6t = splat((float)(dtd / 6.0)), third = splat((float)(1.0 / 3.0));
+    const float2 h2 = K.h2, dt2 = K.dt2, d3t = K.d3t, d6t = K.d6t, third = splat((float)(1.0 / 3.0));
     const bool edge = (x0 < GY) || (x0 + TX > L.nx - GY) || (y0 < GY) || (y0 + TY > L.ny - GY);
     float2* __restrict__ gout = reinterpret_cast<float2*>(a.sout);
     const float2* __restrict__ gu0 = reinterpret_cast<const float2*>(a.u0);
@@ -471,7 +482,6 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     }
 
     if (STAGE == 4) {
-        unsigned long long m[2] = {0ull, 0ull};
 #pragma unroll
         for (int q = 0; q < SEG; ++q) {
             const int j = y0 + y_0 + q;
@@ -482,36 +492,24 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
                     const long long e = L.at(gi, j);
                     const float2 B0 = __ldg(gbg + e), B1 = __ldg(gbg + P + e);
                     signal_speeds<float, true>(o0.x, o1.x, o1.y, o0.y, o2.x, o2.y, B0.x, B0.y, B1.x, B1.y,
-                                               (float)a.gamma, sx, sy);
+                                               a.f_gamma, sx, sy);
                 } else {
                     signal_speeds<float, false>(o0.x, o1.x, o1.y, o0.y, o2.x, o2.y, 0.f, 0.f, 0.f, 0.f,
-                                                (float)a.gamma, sx, sy);
+                                                a.f_gamma, sx, sy);
                 }
                 const unsigned long long kx_ = speed_key(sx), ky_ = speed_key(sy);
                 m[0] = kx_ > m[0] ? kx_ : m[0];
                 m[1] = ky_ > m[1] ? ky_ : m[1];
             }
         }
-#pragma unroll
-        for (int d = 0; d < 2; ++d) {
-            unsigned long long v = m[d];
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-                v = w > v ? w : v;
-            }
-            if (lane == 0) red[d][warp] = v;
-        }
-        __syncthreads();
-        if (tid < 2) {
-            unsigned long long v = 0ull;
-            for (int w = 0; w < NW; ++w) v = red[tid][w] > v ? red[tid][w] : v;
-            atomicMax(&a.sc->cmax_bits[tid], v);
-        }
     }
 }
 
 // Persistent: each CTA walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// (row-major), prefetching the next tile into L2 before computing the current.
+// (row-major; the CTAs of one wave cover neighbouring tiles, so halo rows come
+// from L2).  An explicit L2 prefetch of the next tile measured slightly slower.
+// The step constants are read once; stage 4 keeps the signal-speed maximum of
+// all its tiles in registers and reduces it once at the end.
 template <int STAGE, bool BG, bool HD>
 __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, const int ntx, const int ntiles)
 {
@@ -519,12 +517,14 @@ __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, co
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long red[2][NW];
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    store_hd_coeffs(a, S, threadIdx.x);   // no later phase writes S.ax/S.ay
+    const StepConsts K = load_step_consts(a.sc);
+    unsigned long long m[2] = {0ull, 0ull};
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int tn = t + gridDim.x;
-        if (tn < ntiles) prefetch_tile<STAGE>(a, (tn % ntx) * TX, (tn / ntx) * TY);
-        tile_body<STAGE, BG, HD>(a, (t % ntx) * TX, (t / ntx) * TY, S, red);
+        tile_body<STAGE, BG, HD>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m);
         __syncthreads();   // shared memory is reused by the next tile
     }
+    if (STAGE == 4) block_speed_max(m, red, a.sc);
 }
 
 }  // namespace f32k
