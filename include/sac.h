@@ -187,8 +187,8 @@ int sac_sync(sac_ctx *c);
  * ------------------------------------------------------------------------- */
 typedef struct sac_batch sac_batch;
 
-/* Create a batch of n >= 1 runs from runs[0..n-1] (validated as for
- * sac_init).  Errors: SAC_ERR_ARG, SAC_ERR_OOM, SAC_ERR_CUDA. */
+/* Create a batch of 1 <= n <= 65535 runs from runs[0..n-1] (validated as
+ * for sac_init).  Errors: SAC_ERR_ARG, SAC_ERR_OOM, SAC_ERR_CUDA. */
 int sac_batch_init(const sac_params *runs, int n, sac_batch **out);
 void sac_batch_free(sac_batch *b);
 const char *sac_batch_last_error(const sac_batch *b);

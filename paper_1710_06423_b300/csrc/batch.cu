@@ -74,6 +74,17 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
     }
 }
 
+// Ghost frames of every run's stage output (one grid row per run).
+__global__ void halo_fp32_batch(const StageArgs<float>* __restrict__ args, int stage)
+{
+    const StageArgs<float>& a = args[blockIdx.y * 4 + (stage - 1)];
+    if (a.sc->skip || (a.bc_x == BC_FIXED && a.bc_y == BC_FIXED)) return;
+    const long long n = f32k::halo_count(a.L);
+    float2* w = reinterpret_cast<float2*>(a.sout);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        f32k::halo_cell(w, a.L, a.bc_x, a.bc_y, t);
+}
+
 template <int S, bool BG, bool HD>
 cudaError_t set_attr()
 {
@@ -113,6 +124,8 @@ struct sac_batch {
     cudaStream_t cap = nullptr;
     bool hd = true, bg = false;
     int nsm = 148;
+    long long max_halo = 0;         // largest ghost frame over the runs (cells)
+    bool any_halo = false;          // some run has a periodic or outflow boundary
     StageArgs<float>* d_args = nullptr;
     RunCtl* d_ctl = nullptr;
     int4* d_tiles = nullptr;
@@ -182,9 +195,14 @@ static cudaError_t enqueue_batch_step(sac_batch* b, cudaStream_t s)
     a.args = b->d_args; a.tiles = b->d_tiles; a.ntiles = b->ntiles; a.counters = b->d_counters;
     a.persistent = b->persistent;
     const int grid = b->persistent ? std::min(b->ntiles, b->ctas_per_sm * b->nsm) : b->ntiles;
+    const int hgrid = (int)std::min<long long>((b->max_halo + 255) / 256, 2 * b->nsm);
     for (int stage = 1; stage <= 4 && e == cudaSuccess; ++stage) {
         if (b->bg) e = b->hd ? launch<true, true>(a, stage, grid, s) : launch<true, false>(a, stage, grid, s);
         else e = b->hd ? launch<false, true>(a, stage, grid, s) : launch<false, false>(a, stage, grid, s);
+        if (e == cudaSuccess && b->any_halo) {
+            halo_fp32_batch<<<dim3(hgrid, b->n), 256, 0, s>>>(b->d_args, stage);
+            e = cudaGetLastError();
+        }
     }
     return e;
 }
@@ -239,7 +257,7 @@ void sac_batch_free(sac_batch* b)
 int sac_batch_init(const sac_params* runs, int n, sac_batch** out)
 {
     if (out) *out = nullptr;
-    if (!runs || !out || n < 1) return SAC_ERR_ARG;
+    if (!runs || !out || n < 1 || n > 65535) return SAC_ERR_ARG;   // one halo grid row per run
     for (int i = 0; i < n; ++i) {
         if (runs[i].precision != SAC_FP32 || runs[i].device != runs[0].device || runs[i].stream != runs[0].stream ||
             runs[i].hyperdiffusion != runs[0].hyperdiffusion || runs[i].has_background != runs[0].has_background)
@@ -275,6 +293,10 @@ int sac_batch_init(const sac_params* runs, int n, sac_batch** out)
         for (int i = 0; i < n; ++i) {
             const sac_ctx* c = b->runs[i];
             for (int s = 1; s <= 4; ++s) sac_fp32_stage_args(c, s, &args[4 * i + s - 1]);
+            if (c->p.bc_x != BC_FIXED || c->p.bc_y != BC_FIXED) {
+                b->any_halo = true;
+                b->max_halo = std::max(b->max_halo, f32k::halo_count(c->L));
+            }
             ctl[i].sc = c->sc;
             ctl[i].dx = (c->p.x1 - c->p.x0) / c->p.nx;
             ctl[i].dy = (c->p.y1 - c->p.y0) / c->p.ny;

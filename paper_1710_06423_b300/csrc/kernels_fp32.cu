@@ -1,5 +1,7 @@
 // kernels_fp32.cu -- launchers of the FP32 fused RK stage kernel (field-pair
 // layout, packed f32x2 arithmetic, D-scheme RK registers).
+#include <algorithm>
+
 #include "stage_fp32.cuh"
 
 namespace sac {
@@ -21,12 +23,25 @@ cudaError_t set_attr()
 
 int g_resident = 296;   // persistent grid: resident CTAs on the device (2 per SM)
 
+__global__ void halo_fp32(const StageArgs<float> a, long long n)
+{
+    if (a.sc->skip) return;
+    float2* w = reinterpret_cast<float2*>(a.sout);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        f32k::halo_cell(w, a.L, a.bc_x, a.bc_y, t);
+}
+
 template <int S, bool BG, bool HD>
 cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
 {
     const int ntx = (a.L.nx + TX - 1) / TX, nty = (a.L.ny + TY - 1) / TY, ntiles = ntx * nty;
     const int grid = ntiles < g_resident ? ntiles : g_resident;
     f32k::stage_fp32<S, BG, HD><<<grid, NT, sizeof(f32k::Smem), s>>>(a, ntx, ntiles);
+    if (a.bc_x != BC_FIXED || a.bc_y != BC_FIXED) {
+        const long long n = f32k::halo_count(a.L);
+        const int hb = (int)std::min<long long>((n + 255) / 256, g_resident * 2);
+        halo_fp32<<<hb, 256, 0, s>>>(a, n);
+    }
     return cudaGetLastError();
 }
 

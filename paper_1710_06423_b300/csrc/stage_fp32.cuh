@@ -23,8 +23,10 @@
 //      memory over the dead x-flux buffer);
 //   4. Y sweep: each thread walks 8 cells of one column the same way, adds
 //      k_x, applies the RK stage update (D scheme, see below), stores the
-//      stage output with its ghost copies and, in stage 4, folds the signal
-//      speed of the new state into a per-thread maximum (reduced once per CTA).
+//      stage output and, in stage 4, folds the signal speed of the new state
+//      into a per-thread maximum (reduced once per CTA).
+// A small kernel after each stage fills the ghost frame of the output
+// (periodic/outflow copies), so the tile code has no boundary cases.
 //
 // RK registers (D scheme, 22.5 values moved per cell-stage):
 //   s1: S1 = U0 + dt/2 k1
@@ -92,6 +94,12 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(s), "l"(gmem) : "memory");
 }
+// predicated form: no copy (and no read of gmem) when pred is false, without a branch
+__device__ __forceinline__ void cp_async8_if(unsigned sdst, const void* gmem, bool pred)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q cp.async.ca.shared.global [%0], [%1], 8;\n}"
+                 :: "r"(sdst), "l"(gmem), "r"((int)pred) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
@@ -133,19 +141,44 @@ struct Smem {
 };
 static_assert(sizeof(float2) * 3 * TY * KXP <= sizeof(float2) * 3 * TY * FXP, "kx must fit in fx");
 
-__device__ __forceinline__ int wrap_i(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
-__device__ __forceinline__ int ghost_list(int i, int n, int bc, int* list)
+// ---- ghost frame of a stage output ----------------------------------------------
+// Periodic and outflow boundaries: ghost cell (gx, gy) (either coordinate
+// outside the interior, up to GY cells out) holds interior cell
+// (map(gx), map(gy)) in all three planes, map = wrap (periodic) or clamp to
+// the edge (outflow); a ghost outside a fixed boundary keeps its value.
+// Ghost t of the frame: t < GY*fw bottom rows, < 2*GY*fw top rows, then the
+// left/right GY cells of each interior row (fw = nx + 2 GY).
+__host__ __device__ inline long long halo_count(const Layout& L)
 {
-    int cnt = 0;
-    list[cnt++] = i;
-    if (bc == BC_PERIODIC) {
-        for (int g = -GY; g < 0; ++g) if (wrap_i(g, n) == i) list[cnt++] = g;
-        for (int g = n; g < n + GY; ++g) if (wrap_i(g, n) == i) list[cnt++] = g;
-    } else if (bc == BC_OUTFLOW) {
-        if (i == 0) { list[cnt++] = -1; list[cnt++] = -2; list[cnt++] = -3; }
-        if (i == n - 1) { list[cnt++] = n; list[cnt++] = n + 1; list[cnt++] = n + 2; }
+    return (long long)(L.nx + 2 * GY) * (L.ny + 2 * GY) - (long long)L.nx * L.ny;
+}
+__device__ __forceinline__ int halo_map(int g, int n, int bc)
+{
+    if (bc == BC_PERIODIC) { const int r = g % n; return r < 0 ? r + n : r; }
+    return g < 0 ? 0 : n - 1;
+}
+__device__ __forceinline__ void halo_cell(float2* __restrict__ w, const Layout& L, int bc_x, int bc_y, long long t)
+{
+    const int fw = L.nx + 2 * GY;
+    const long long band = (long long)GY * fw;
+    int gx, gy;
+    if (t < 2 * band) {
+        const long long u = t < band ? t : t - band;
+        const int r = (int)(u / fw);
+        gx = (int)(u - (long long)r * fw) - GY;
+        gy = t < band ? r - GY : L.ny + r;
+    } else {
+        const long long u = t - 2 * band;
+        gy = (int)(u / (2 * GY));
+        const int c = (int)(u - (long long)gy * (2 * GY));
+        gx = c < GY ? c - GY : L.nx + (c - GY);
     }
-    return cnt;
+    const bool ox = gx < 0 || gx >= L.nx, oy = gy < 0 || gy >= L.ny;
+    if ((ox && bc_x == BC_FIXED) || (oy && bc_y == BC_FIXED)) return;
+    const int sx = ox ? halo_map(gx, L.nx, bc_x) : gx, sy = oy ? halo_map(gy, L.ny, bc_y) : gy;
+    const long long src = L.at(sx, sy), dst = L.at(gx, gy);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) w[p * L.fstride + dst] = w[p * L.fstride + src];
 }
 
 // Face hyper-diffusion fluxes G (already divided by d^2) on the SEG+1 faces
@@ -246,17 +279,24 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     // region (r, c) <-> interior (x0 - 4 + c, y0 - 3 + r) <-> padded element (y0 + r) * pitch + x0 + c
     const long long rbase = (long long)y0 * L.pitch + x0;
 
-    // ---- 0. stage the three planes: one warp per row, lanes across columns --------
+    // ---- 0. stage the three planes: warp w copies rows w, w + NW, ... of each
+    // plane, lanes across columns (lanes 0 .. RX-33 also the last RX-32 columns)
     {
-        const float2* src = gin + rbase + lane;
-        float2* dst = &S.u[0][0][0] + lane;
-#pragma unroll 1
-        for (int row = warp; row < 3 * RY; row += NW) {           // row = plane * RY + r
-            const int p = row / RY, r = row - p * RY;
-            const float2* g = src + p * P + (long long)r * L.pitch;
-            float2* d = dst + row * RXP;
-            cp_async8(d, g);
-            if (lane < RX - 32) cp_async8(d + 32, g + 32);
+        const unsigned sbase = (unsigned)__cvta_generic_to_shared(&S.u[0][warp][lane]);
+        const bool tail = lane < RX - 32;
+        const long long rstep = (long long)NW * L.pitch;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const float2* g = gin + p * P + rbase + (long long)warp * L.pitch + lane;
+#pragma unroll
+            for (int k = 0; k < (RY + NW - 1) / NW; ++k) {
+                if (k * NW + warp < RY) {   // warp-uniform
+                    const unsigned d = sbase + (unsigned)(((p * RY + k * NW) * RXP) * sizeof(float2));
+                    cp_async8_if(d, g, true);
+                    cp_async8_if(d + 32 * sizeof(float2), g + 32, tail);
+                }
+                g += rstep;
+            }
         }
     }
     cp_async_wait_all();
@@ -347,17 +387,13 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             const float sv = fmaxf(0.f, -(dvx + dvy));
             S.s[sr][scn] = make_float2(sv, sv);
         };
-        constexpr int NS = SH * SW;
-        int sr = tid / SW, scn = tid - (tid / SW) * SW;
-        int sr2 = (tid + NT) / SW, scn2 = (tid + NT) - ((tid + NT) / SW) * SW;
-#pragma unroll 1
-        for (int v = tid; v < NS; v += 2 * NT) {
-            shock_cell(sr, scn);
-            if (v + NT < NS) shock_cell(sr2, scn2);
-            scn += (2 * NT) % SW; sr += (2 * NT) / SW;
-            if (scn >= SW) { scn -= SW; ++sr; }
-            scn2 += (2 * NT) % SW; sr2 += (2 * NT) / SW;
-            if (scn2 >= SW) { scn2 -= SW; ++sr2; }
+        // thread -> (column, row group): rows g, g + SG, ... (SW * SG <= NT threads busy)
+        constexpr int SG = NT / SW;
+        const int scn = tid % SW, sg = tid / SW;
+        if (sg < SG) {
+#pragma unroll
+            for (int i = 0; i < (SH + SG - 1) / SG; ++i)
+                if (i * SG + sg < SH) shock_cell(i * SG + sg, scn);
         }
         __syncthreads();
     }
@@ -410,14 +446,14 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     const int col = lane, y_0 = warp * SEG;
     const int gi = x0 + col;
     const float2 h2 = K.h2, dt2 = K.dt2, d3t = K.d3t, d6t = K.d6t, third = splat((float)(1.0 / 3.0));
-    const bool edge = (x0 < GY) || (x0 + TX > L.nx - GY) || (y0 < GY) || (y0 + TY > L.ny - GY);
     float2* __restrict__ gout = reinterpret_cast<float2*>(a.sout);
     const float2* __restrict__ gu0 = reinterpret_cast<const float2*>(a.u0);
     float2* __restrict__ gacc = reinterpret_cast<float2*>(a.acc);
     float2 outv[SEG][3];
 
     const long long e_first = L.at(gi, y0 + y_0);   // this thread's first cell; the next q is + q * pitch
-    const bool col_ok = gi < L.nx;
+    // cells q < nq of this thread's segment lie inside the grid (ragged last tiles)
+    const int nq = gi < L.nx ? L.ny - (y0 + y_0) : 0;
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
         // pointwise registers of this pair first, so their latency hides behind the sweep
@@ -425,7 +461,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         float2 u0v[SEG], dv[SEG];
 #pragma unroll
         for (int q = 0; q < SEG; ++q) {
-            const bool ok = col_ok && (y0 + y_0 + q) < L.ny;
+            const bool ok = q < nq;
             u0v[q] = (STAGE >= 2 && ok) ? gu0[ep + q * L.pitch] : make_float2(0.f, 0.f);
             dv[q] = (STAGE >= 3 && ok) ? gacc[ep + q * L.pitch] : make_float2(0.f, 0.f);
         }
@@ -450,12 +486,11 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         for (int q = 0; q < SEG + 4; ++q) F[q] = S.fy[p][y_0 + q][col];
 #pragma unroll
         for (int q = 0; q < SEG; ++q) {
-            const int j = y0 + y_0 + q;
             const float2 d = fma2(eight, sub2(F[q + 3], F[q + 1]), sub2(F[q], F[q + 4]));
             const float2 k = add2(fma2(m12y, d, hy[q]), KX[p][y_0 + q][col]);
             const float2 ucen = u[q + 3];
             float2 o = make_float2(0.f, 0.f);
-            if (col_ok && j < L.ny) {
+            if (q < nq) {
                 const long long e = ep + q * L.pitch;
                 if (STAGE == 1) {
                     o = fma2(h2, k, ucen);
@@ -468,14 +503,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
                 } else {
                     o = add2(u0v[q], fma2(d6t, k, dv[q]));
                 }
-                if (!edge) {
-                    gout[e] = o;
-                } else {
-                    int xs[7], ys[7];
-                    const int nxs = ghost_list(gi, L.nx, a.bc_x, xs), nys = ghost_list(j, L.ny, a.bc_y, ys);
-                    for (int yy = 0; yy < nys; ++yy)
-                        for (int xx = 0; xx < nxs; ++xx) gout[p * P + L.at(xs[xx], ys[yy])] = o;
-                }
+                gout[e] = o;
             }
             outv[q][p] = o;
         }
@@ -484,12 +512,11 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     if (STAGE == 4) {
 #pragma unroll
         for (int q = 0; q < SEG; ++q) {
-            const int j = y0 + y_0 + q;
-            if (gi < L.nx && j < L.ny) {
+            if (q < nq) {
                 float sx, sy;
                 const float2 o0 = outv[q][0], o1 = outv[q][1], o2 = outv[q][2];
                 if constexpr (BG) {
-                    const long long e = L.at(gi, j);
+                    const long long e = L.at(gi, y0 + y_0 + q);
                     const float2 B0 = __ldg(gbg + e), B1 = __ldg(gbg + P + e);
                     signal_speeds<float, true>(o0.x, o1.x, o1.y, o0.y, o2.x, o2.y, B0.x, B0.y, B1.x, B1.y,
                                                a.f_gamma, sx, sy);
