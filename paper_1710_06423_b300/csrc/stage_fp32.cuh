@@ -105,6 +105,14 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
+// Scalar arithmetic of the element phases with every product/sum pairing
+// spelled out (fma_/mul_ are the round-to-nearest intrinsics): the compiler
+// may not contract them on its own, so the FP32 result depends only on this
+// source, not on how the surrounding code is shaped or inlined (the single-run
+// and batch kernels share the tile code and must agree bit for bit).
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+
 // Division flavours (compile-time): the fast path uses rcp.approx for 1/rho and
 // for the hyper-diffusion ratio; SAC_FP32_IEEE_DIV=1 selects correctly rounded
 // division for both (accuracy studies).
@@ -116,7 +124,7 @@ __device__ __forceinline__ float fdiv(float a, float b)
 #if SAC_FP32_IEEE_DIV
     return __fdiv_rn(a, b);
 #else
-    return a * rcp_approx(b);
+    return mul_(a, rcp_approx(b));
 #endif
 }
 
@@ -305,9 +313,9 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     const float gm1 = a.f_gm1;
 
     // ---- 1. primitives and fluxes on the staged box [x0-3, x0+TX+3) x [y0-3, y0+TY+3)
-    // (cells v and v + NT per iteration: two independent dependency chains)
     {
-        auto prim_cell = [&](const int r, const int c) {
+        // region cell (r, c); fx_ok / fy_ok: the cell's x / y fluxes are needed
+        auto prim_cell = [&](const int r, const int c, const bool fx_ok, const bool fy_ok) {
             const float2 P0 = S.u[0][r][c], P1 = S.u[1][r][c], P2 = S.u[2][r][c];
             const float mx = P1.x, my = P1.y, btx = P2.x, bty = P2.y, et = P0.y;
             float ux, uy, pt, etot, bx, by;
@@ -317,14 +325,14 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
                 const float2 B0 = __ldg(gbg + e), B1 = __ldg(gbg + P + e);   // (rho_b, e_b), (B_bx, B_by)
                 bb2 = B1;
                 const float rinv = fdiv(1.f, B0.x + P0.x);
-                ux = mx * rinv; uy = my * rinv;
-                const float ekin = 0.5f * (mx * ux + my * uy);
-                const float bb = B1.x * btx + B1.y * bty;
-                const float b2p = 0.5f * (btx * btx + bty * bty);
-                const float pk = gm1 * (((et - ekin) - bb) - b2p);
+                ux = mul_(mx, rinv); uy = mul_(my, rinv);
+                const float ekin = mul_(0.5f, fma_(mx, ux, mul_(my, uy)));
+                const float bb = fma_(B1.x, btx, mul_(B1.y, bty));
+                const float b2p = mul_(0.5f, fma_(btx, btx, mul_(bty, bty)));
+                const float pk = mul_(gm1, ((et - ekin) - bb) - b2p);
                 pt = (pk + bb) + b2p;
-                const float b2b = 0.5f * (B1.x * B1.x + B1.y * B1.y);
-                const float ptb = gm1 * (B0.y - b2b) + b2b;
+                const float b2b = mul_(0.5f, fma_(B1.x, B1.x, mul_(B1.y, B1.y)));
+                const float ptb = fma_(gm1, B0.y - b2b, b2b);
                 etot = ((et + B0.y) + pt) + ptb;
                 bx = B1.x + btx; by = B1.y + bty;
             } else {
@@ -332,46 +340,64 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
                 ux = __fdiv_rn(mx, P0.x); uy = __fdiv_rn(my, P0.x);
 #else
                 const float rinv = rcp_approx(P0.x);
-                ux = mx * rinv; uy = my * rinv;
+                ux = mul_(mx, rinv); uy = mul_(my, rinv);
 #endif
-                const float ekin = 0.5f * (mx * ux + my * uy);
-                const float b2p = 0.5f * (btx * btx + bty * bty);
-                pt = gm1 * ((et - ekin) - b2p) + b2p;
+                const float ekin = mul_(0.5f, fma_(mx, ux, mul_(my, uy)));
+                const float b2p = mul_(0.5f, fma_(btx, btx, mul_(bty, bty)));
+                pt = fma_(gm1, (et - ekin) - b2p, b2p);
                 etot = et + pt;
                 bx = btx; by = bty;
             }
             S.vx[r][c] = ux; S.vy[r][c] = uy;
-            const float bv = bx * ux + by * uy;
-            if (r >= 3 && r < 3 + TY && c >= 2 && c < 2 + FXW) {
-                // x fluxes: (m_x, F_e), (F_mx, F_my), (0, F_By)
-                float2 f1 = fma2(splat(ux), P1, make_float2(pt, 0.f));
-                f1 = fma2(splat(-btx), P2, f1);
-                if constexpr (BG) { f1 = fma2(splat(-btx), bb2, f1); f1 = fma2(splat(-bb2.x), P2, f1); }
-                S.fx[0][r - 3][c - 2] = make_float2(mx, ux * etot - bx * bv);
-                S.fx[1][r - 3][c - 2] = f1;
-                S.fx[2][r - 3][c - 2] = make_float2(0.f, ux * by - bx * uy);
-            }
-            if (c >= 4 && c < 4 + TX && r >= 1 && r < 1 + FYH) {
-                // y fluxes: (m_y, F_e), (F_mx, F_my), (F_Bx, 0)
-                float2 f1 = fma2(splat(uy), P1, make_float2(0.f, pt));
-                f1 = fma2(splat(-bty), P2, f1);
-                if constexpr (BG) { f1 = fma2(splat(-bty), bb2, f1); f1 = fma2(splat(-bb2.y), P2, f1); }
-                S.fy[0][r - 1][c - 4] = make_float2(my, uy * etot - by * bv);
-                S.fy[1][r - 1][c - 4] = f1;
-                S.fy[2][r - 1][c - 4] = make_float2(uy * bx - by * ux, 0.f);
-            }
+            const float bv = fma_(bx, ux, mul_(by, uy));
+            // both flux sets for every cell (straight-line code); only the stores are conditional
+            // x fluxes: (m_x, F_e), (F_mx, F_my), (0, F_By)
+            float2 f1x = fma2(splat(ux), P1, make_float2(pt, 0.f));
+            f1x = fma2(splat(-btx), P2, f1x);
+            if constexpr (BG) { f1x = fma2(splat(-btx), bb2, f1x); f1x = fma2(splat(-bb2.x), P2, f1x); }
+            const float2 f0x = make_float2(mx, fma_(ux, etot, -mul_(bx, bv)));
+            const float2 f2x = make_float2(0.f, fma_(ux, by, -mul_(bx, uy)));
+            // y fluxes: (m_y, F_e), (F_mx, F_my), (F_Bx, 0)
+            float2 f1y = fma2(splat(uy), P1, make_float2(0.f, pt));
+            f1y = fma2(splat(-bty), P2, f1y);
+            if constexpr (BG) { f1y = fma2(splat(-bty), bb2, f1y); f1y = fma2(splat(-bb2.y), P2, f1y); }
+            const float2 f0y = make_float2(my, fma_(uy, etot, -mul_(by, bv)));
+            const float2 f2y = make_float2(fma_(uy, bx, -mul_(by, ux)), 0.f);
+            if (fx_ok) { S.fx[0][r - 3][c - 2] = f0x; S.fx[1][r - 3][c - 2] = f1x; S.fx[2][r - 3][c - 2] = f2x; }
+            if (fy_ok) { S.fy[0][r - 1][c - 4] = f0y; S.fy[1][r - 1][c - 4] = f1y; S.fy[2][r - 1][c - 4] = f2y; }
         };
-        constexpr int NCELL = RY * PW;
-        int r = tid / PW, c = 1 + tid - (tid / PW) * PW;
-        int r2 = (tid + NT) / PW, c2 = 1 + (tid + NT) - ((tid + NT) / PW) * PW;
-#pragma unroll 1
-        for (int v = tid; v < NCELL; v += 2 * NT) {
-            prim_cell(r, c);
-            if (v + NT < NCELL) prim_cell(r2, c2);
-            c += (2 * NT) % PW; r += (2 * NT) / PW;
-            if (c >= 1 + PW) { c -= PW; ++r; }
-            c2 += (2 * NT) % PW; r2 += (2 * NT) / PW;
-            if (c2 >= 1 + PW) { c2 -= PW; ++r2; }
+        auto flux_ok = [](const int r, const int c, bool& fx_ok, bool& fy_ok) {
+            fx_ok = (unsigned)(r - 3) < (unsigned)TY && (unsigned)(c - 2) < (unsigned)FXW;
+            fy_ok = (unsigned)(r - 1) < (unsigned)FYH && (unsigned)(c - 4) < (unsigned)TX;
+        };
+        // thread -> (column c = 1 + cc, row group g): rows g, g + PG, ..., so the
+        // shared-memory offsets of a thread's cells differ by compile-time
+        // constants.  The last group is partial (PLAST columns); the cells of
+        // its rows beyond those columns go to threads of the groups with one row
+        // less, so no thread takes more than ceil(RY / PG) cells.
+        constexpr int PG = (NT + PW - 1) / PW;                  // 7 row groups
+        constexpr int PLAST = NT - (PG - 1) * PW;               // 28 columns in the last group
+        constexpr int NROW = (RY + PG - 1) / PG;                // 6 rows in groups g < RY % PG, else 5
+        constexpr int NLEFT = (RY / PG) * (PW - PLAST);         // 5 rows x 10 columns left over
+        constexpr int LEFT0 = (RY % PG) * PW;                   // first thread of the 5-row groups
+        static_assert(PG == 7 && PLAST == 28 && NROW == 6 && NLEFT == 50 && LEFT0 + NLEFT <= (PG - 1) * PW,
+                      "primitive-phase thread mapping");
+        const int g = tid / PW, c = 1 + (tid - g * PW);
+#pragma unroll 2
+        for (int i = 0; i < NROW; ++i) {
+            const int r = g + PG * i;
+            if (i < NROW - 1 || g < RY % PG) {
+                bool fx_ok, fy_ok;
+                flux_ok(r, c, fx_ok, fy_ok);
+                prim_cell(r, c, fx_ok, fy_ok);
+            }
+        }
+        if (tid >= LEFT0 && tid < LEFT0 + NLEFT) {
+            const int l = tid - LEFT0, lq = l / (PW - PLAST);
+            const int r = (PG - 1) + PG * lq, c2 = 1 + PLAST + (l - lq * (PW - PLAST));
+            bool fx_ok, fy_ok;
+            flux_ok(r, c2, fx_ok, fy_ok);
+            prim_cell(r, c2, fx_ok, fy_ok);
         }
     }
     __syncthreads();
@@ -382,8 +408,8 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     if constexpr (HD) {
         auto shock_cell = [&](const int sr, const int scn) {
             const int r = sr + 2, c = scn + 3;
-            const float dvx = (8.f * (S.vx[r][c + 1] - S.vx[r][c - 1]) - (S.vx[r][c + 2] - S.vx[r][c - 2])) * inv12dx;
-            const float dvy = (8.f * (S.vy[r + 1][c] - S.vy[r - 1][c]) - (S.vy[r + 2][c] - S.vy[r - 2][c])) * inv12dy;
+            const float dvx = mul_(fma_(8.f, S.vx[r][c + 1] - S.vx[r][c - 1], -(S.vx[r][c + 2] - S.vx[r][c - 2])), inv12dx);
+            const float dvy = mul_(fma_(8.f, S.vy[r + 1][c] - S.vy[r - 1][c], -(S.vy[r + 2][c] - S.vy[r - 2][c])), inv12dy);
             const float sv = fmaxf(0.f, -(dvx + dvy));
             S.s[sr][scn] = make_float2(sv, sv);
         };
@@ -454,16 +480,28 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     const long long e_first = L.at(gi, y0 + y_0);   // this thread's first cell; the next q is + q * pitch
     // cells q < nq of this thread's segment lie inside the grid (ragged last tiles)
     const int nq = gi < L.nx ? L.ny - (y0 + y_0) : 0;
+    // pointwise registers U0, D of the cells of this thread, one pair ahead of
+    // the sweep so that their load latency hides behind the previous pair
+    float2 nu0[SEG], ndv[SEG];
+#pragma unroll
+    for (int q = 0; q < SEG; ++q) {
+        const bool ok = q < nq;
+        nu0[q] = (STAGE >= 2 && ok) ? gu0[e_first + q * L.pitch] : make_float2(0.f, 0.f);
+        ndv[q] = (STAGE >= 3 && ok) ? gacc[e_first + q * L.pitch] : make_float2(0.f, 0.f);
+    }
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
-        // pointwise registers of this pair first, so their latency hides behind the sweep
         const long long ep = p * P + e_first;
         float2 u0v[SEG], dv[SEG];
 #pragma unroll
-        for (int q = 0; q < SEG; ++q) {
-            const bool ok = q < nq;
-            u0v[q] = (STAGE >= 2 && ok) ? gu0[ep + q * L.pitch] : make_float2(0.f, 0.f);
-            dv[q] = (STAGE >= 3 && ok) ? gacc[ep + q * L.pitch] : make_float2(0.f, 0.f);
+        for (int q = 0; q < SEG; ++q) { u0v[q] = nu0[q]; dv[q] = ndv[q]; }
+        if (p < 2) {
+#pragma unroll
+            for (int q = 0; q < SEG; ++q) {
+                const bool ok = q < nq;
+                nu0[q] = (STAGE >= 2 && ok) ? gu0[ep + P + q * L.pitch] : make_float2(0.f, 0.f);
+                ndv[q] = (STAGE >= 3 && ok) ? gacc[ep + P + q * L.pitch] : make_float2(0.f, 0.f);
+            }
         }
         float2 u[SEG + 6];   // rows y_0-3 .. y_0+SEG+2 (region row = cell row + 3)
 #pragma unroll
