@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
             f32k::store_hd_coeffs(sa, S, threadIdx.x);   // visible after the tile's staging barrier
             const f32k::StepConsts K = f32k::load_step_consts(sa.sc);
             unsigned long long m[2] = {0ull, 0ull};
-            f32k::tile_body<STAGE, BG, HD>(sa, d.y * f32k::TX, d.z * f32k::TY, S, K, m);
+            f32k::tile_body<STAGE, BG, HD, false>(sa, d.y * f32k::TX, d.z * f32k::TY, S, K, m);
             if (STAGE == 4) f32k::block_speed_max(m, red, sa.sc);
         }
         __syncthreads();   // shared memory and `sa` are reused by the next tile

@@ -272,40 +272,50 @@ __device__ __forceinline__ void block_speed_max(const unsigned long long (&m)[2]
     }
 }
 
+// Issue the cp.async copies of plane p of the staged region of tile (x0, y0):
+// warp w copies rows w, w + NW, ..., lanes across columns (lanes 0 .. RX-33
+// also the last RX-32 columns).  Completion: cp_async_wait_all.
+__device__ __forceinline__ void stage_plane(const StageArgs<float>& a, Smem& S, const int x0, const int y0, const int p)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const Layout L = a.L;
+    const float2* gin = reinterpret_cast<const float2*>(a.sin);
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(&S.u[p][warp][lane]);
+    const bool tail = lane < RX - 32;
+    const long long rstep = (long long)NW * L.pitch;
+    const float2* g = gin + p * L.fstride + (long long)(y0 + warp) * L.pitch + x0 + lane;
+#pragma unroll
+    for (int k = 0; k < (RY + NW - 1) / NW; ++k) {
+        if (k * NW + warp < RY) {   // warp-uniform
+            const unsigned d = sbase + (unsigned)((k * NW * RXP) * sizeof(float2));
+            cp_async8_if(d, g, true);
+            cp_async8_if(d + 32 * sizeof(float2), g + 32, tail);
+        }
+        g += rstep;
+    }
+}
+
 // One tile (x0, y0) of one run; every thread of the CTA calls it (it holds
-// barriers).  S.ax/S.ay must hold the run's coefficients (store_hd_coeffs).
+// barriers).  OVERLAP: the caller has issued the copies of this tile's staged
+// region, and the Y sweep issues those of the next tile (xn, yn; has_next)
+// plane by plane as soon as the CTA has read the plane it replaces.  S.ax/S.ay must hold the run's coefficients (store_hd_coeffs).
 // Stage 4 folds the signal speeds of the tile's new state into m.
-template <int STAGE, bool BG, bool HD>
+template <int STAGE, bool BG, bool HD, bool OVERLAP>
 __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x0, const int y0, Smem& S,
-                                          const StepConsts& K, unsigned long long (&m)[2])
+                                          const StepConsts& K, unsigned long long (&m)[2],
+                                          const bool has_next = false, const int xn = 0, const int yn = 0)
 {
     const Layout L = a.L;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float2* __restrict__ gin = reinterpret_cast<const float2*>(a.sin);
     const float2* __restrict__ gbg = reinterpret_cast<const float2*>(a.bg);
     const long long P = L.fstride;              // plane stride in float2 elements
     // region (r, c) <-> interior (x0 - 4 + c, y0 - 3 + r) <-> padded element (y0 + r) * pitch + x0 + c
     const long long rbase = (long long)y0 * L.pitch + x0;
 
-    // ---- 0. stage the three planes: warp w copies rows w, w + NW, ... of each
-    // plane, lanes across columns (lanes 0 .. RX-33 also the last RX-32 columns)
-    {
-        const unsigned sbase = (unsigned)__cvta_generic_to_shared(&S.u[0][warp][lane]);
-        const bool tail = lane < RX - 32;
-        const long long rstep = (long long)NW * L.pitch;
+    // ---- 0. the staged region of the three planes in shared memory -----------------
+    if (!OVERLAP) {
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
-            const float2* g = gin + p * P + rbase + (long long)warp * L.pitch + lane;
-#pragma unroll
-            for (int k = 0; k < (RY + NW - 1) / NW; ++k) {
-                if (k * NW + warp < RY) {   // warp-uniform
-                    const unsigned d = sbase + (unsigned)(((p * RY + k * NW) * RXP) * sizeof(float2));
-                    cp_async8_if(d, g, true);
-                    cp_async8_if(d + 32 * sizeof(float2), g + 32, tail);
-                }
-                g += rstep;
-            }
-        }
+        for (int p = 0; p < 3; ++p) stage_plane(a, S, x0, y0, p);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -506,6 +516,10 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         float2 u[SEG + 6];   // rows y_0-3 .. y_0+SEG+2 (region row = cell row + 3)
 #pragma unroll
         for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][y_0 + q][col + 4];
+        if (OVERLAP) {
+            __syncthreads();   // plane p of this tile is read for good
+            if (has_next) stage_plane(a, S, xn, yn, p);
+        }
         float2 hy[SEG];
         if constexpr (HD) {
             float2 s2[SEG + 2];   // rows y_0-1 .. y_0+SEG (shock row = cell row + 1)
@@ -572,7 +586,8 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 
 // Persistent: each CTA walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
 // (row-major; the CTAs of one wave cover neighbouring tiles, so halo rows come
-// from L2).  An explicit L2 prefetch of the next tile measured slightly slower.
+// from L2), copying the next tile's region into shared memory while it
+// finishes the current one.
 // The step constants are read once; stage 4 keeps the signal-speed maximum of
 // all its tiles in registers and reduces it once at the end.
 template <int STAGE, bool BG, bool HD>
@@ -585,9 +600,17 @@ __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, co
     store_hd_coeffs(a, S, threadIdx.x);   // no later phase writes S.ax/S.ay
     const StepConsts K = load_step_consts(a.sc);
     unsigned long long m[2] = {0ull, 0ull};
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        tile_body<STAGE, BG, HD>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m);
-        __syncthreads();   // shared memory is reused by the next tile
+    int t = blockIdx.x;
+    if (t < ntiles) {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) stage_plane(a, S, (t % ntx) * TX, (t / ntx) * TY, p);
+    }
+    for (; t < ntiles; t += gridDim.x) {
+        // the next tile's region streams into shared memory during this tile's Y sweep;
+        // the next tile_body starts with the barrier that makes it (and all else) visible
+        const int tn = t + gridDim.x;
+        tile_body<STAGE, BG, HD, true>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m, tn < ntiles,
+                                       (tn % ntx) * TX, (tn / ntx) * TY);
     }
     if (STAGE == 4) block_speed_max(m, red, a.sc);
 }
