@@ -132,22 +132,31 @@ __device__ __forceinline__ float fdiv(float a, float b)
 constexpr int TX = 32, TY = 32, NT = 256, NW = NT / 32, SEG = 4;
 static_assert(TX / SEG == NW && TY / SEG == NW, "one segment per warp in both sweeps");
 constexpr int RX = TX + 8, RY = TY + 6, RXP = RX + 1;      // staged region (cols x0-4.., rows y0-3..)
+constexpr int VXP = RX + 1;                                // row pitch of the velocity arrays (odd)
 constexpr int FXW = TX + 4, FXP = FXW + 1;                 // x fluxes: cols x0-2 .. x0+TX+1
-constexpr int FYH = TY + 4;                                // y fluxes: rows y0-2 .. y0+TY+1
+constexpr int FYH = TY + 4, FYP = TX + 1;                 // y fluxes: rows y0-2 .. y0+TY+1 (odd pitch)
 constexpr int SW = TX + 2, SH = TY + 2, SP = SW + 1;       // shock indicator: x0-1.., y0-1..
 constexpr int KXP = TX + 1;                                // k_x rows (aliases the x fluxes)
 constexpr int PW = RX - 2;                                 // primitive columns 1 .. RX-2
 
+// The flux of the third pair has an exactly zero component in each direction,
+// (0, F_By) along x and (F_Bx, 0) along y: only the nonzero one is stored.
 struct Smem {
     float2 u[3][RY][RXP];
-    float2 fx[3][TY][FXP];     // reused as kx[3][TY][KXP] after the X sweep
-    float2 fy[3][FYH][TX];
-    float2 s[SH][SP];          // (s, s): the shock indicator duplicated for packed use
-    float vx[RY][RX];
-    float vy[RY][RX];
-    float2 ax[3], ay[3];       // per-pair hyper-diffusion coefficients c2 cmax / d
+    union {
+        struct {
+            float2 fx[2][TY][FXP];   // x fluxes of pairs 0, 1
+            float fx2[TY][FXP];      // F_By along x
+        };
+        float2 kx[3][TY][KXP];       // k_x, after the X sweep
+    };
+    float2 fy[2][FYH][FYP];          // y fluxes of pairs 0, 1
+    float fy2[FYH][FYP];             // F_Bx along y
+    float s[SH][SP];                 // shock indicator
+    float vx[RY][VXP];
+    float vy[RY][VXP];
+    float2 ax[3], ay[3];             // per-pair hyper-diffusion coefficients c2 cmax / d
 };
-static_assert(sizeof(float2) * 3 * TY * KXP <= sizeof(float2) * 3 * TY * FXP, "kx must fit in fx");
 
 // ---- ghost frame of a stage output ----------------------------------------------
 // Periodic and outflow boundaries: ghost cell (gx, gy) (either coordinate
@@ -373,41 +382,34 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             if constexpr (BG) { f1y = fma2(splat(-bty), bb2, f1y); f1y = fma2(splat(-bb2.y), P2, f1y); }
             const float2 f0y = make_float2(my, fma_(uy, etot, -mul_(by, bv)));
             const float2 f2y = make_float2(fma_(uy, bx, -mul_(by, ux)), 0.f);
-            if (fx_ok) { S.fx[0][r - 3][c - 2] = f0x; S.fx[1][r - 3][c - 2] = f1x; S.fx[2][r - 3][c - 2] = f2x; }
-            if (fy_ok) { S.fy[0][r - 1][c - 4] = f0y; S.fy[1][r - 1][c - 4] = f1y; S.fy[2][r - 1][c - 4] = f2y; }
+            if (fx_ok) { S.fx[0][r - 3][c - 2] = f0x; S.fx[1][r - 3][c - 2] = f1x; S.fx2[r - 3][c - 2] = f2x.y; }
+            if (fy_ok) { S.fy[0][r - 1][c - 4] = f0y; S.fy[1][r - 1][c - 4] = f1y; S.fy2[r - 1][c - 4] = f2y.x; }
         };
         auto flux_ok = [](const int r, const int c, bool& fx_ok, bool& fy_ok) {
             fx_ok = (unsigned)(r - 3) < (unsigned)TY && (unsigned)(c - 2) < (unsigned)FXW;
             fy_ok = (unsigned)(r - 1) < (unsigned)FYH && (unsigned)(c - 4) < (unsigned)TX;
         };
-        // thread -> (column c = 1 + cc, row group g): rows g, g + PG, ..., so the
-        // shared-memory offsets of a thread's cells differ by compile-time
-        // constants.  The last group is partial (PLAST columns); the cells of
-        // its rows beyond those columns go to threads of the groups with one row
-        // less, so no thread takes more than ceil(RY / PG) cells.
-        constexpr int PG = (NT + PW - 1) / PW;                  // 7 row groups
-        constexpr int PLAST = NT - (PG - 1) * PW;               // 28 columns in the last group
-        constexpr int NROW = (RY + PG - 1) / PG;                // 6 rows in groups g < RY % PG, else 5
-        constexpr int NLEFT = (RY / PG) * (PW - PLAST);         // 5 rows x 10 columns left over
-        constexpr int LEFT0 = (RY % PG) * PW;                   // first thread of the 5-row groups
-        static_assert(PG == 7 && PLAST == 28 && NROW == 6 && NLEFT == 50 && LEFT0 + NLEFT <= (PG - 1) * PW,
-                      "primitive-phase thread mapping");
-        const int g = tid / PW, c = 1 + (tid - g * PW);
-#pragma unroll 2
-        for (int i = 0; i < NROW; ++i) {
-            const int r = g + PG * i;
-            if (i < NROW - 1 || g < RY % PG) {
+        // Main pass: warp w, lane l -> column 1 + l of rows w, w + NW, ... (one
+        // row per warp-instruction: conflict-free); tail: the last PW - 32
+        // columns walked down the rows, one cell per thread (a warp covers
+        // consecutive rows of a column; the odd pitches keep that conflict-free).
+        // At most ceil(RY / NW) + 1 = 6 cells per thread.
+        constexpr int NTAIL = (PW - 32) * RY;
+        static_assert(PW > 32 && NTAIL <= NT, "primitive-phase mapping");
+#pragma unroll 1
+        for (int k = 0; k < (RY + NW - 1) / NW; ++k) {
+            const int r = warp + NW * k;
+            if (r < RY) {
                 bool fx_ok, fy_ok;
-                flux_ok(r, c, fx_ok, fy_ok);
-                prim_cell(r, c, fx_ok, fy_ok);
+                flux_ok(r, 1 + lane, fx_ok, fy_ok);
+                prim_cell(r, 1 + lane, fx_ok, fy_ok);
             }
         }
-        if (tid >= LEFT0 && tid < LEFT0 + NLEFT) {
-            const int l = tid - LEFT0, lq = l / (PW - PLAST);
-            const int r = (PG - 1) + PG * lq, c2 = 1 + PLAST + (l - lq * (PW - PLAST));
+        if (tid < NTAIL) {
+            const int cc = tid / RY, r = tid - cc * RY;
             bool fx_ok, fy_ok;
-            flux_ok(r, c2, fx_ok, fy_ok);
-            prim_cell(r, c2, fx_ok, fy_ok);
+            flux_ok(r, 33 + cc, fx_ok, fy_ok);
+            prim_cell(r, 33 + cc, fx_ok, fy_ok);
         }
     }
     __syncthreads();
@@ -421,15 +423,19 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             const float dvx = mul_(fma_(8.f, S.vx[r][c + 1] - S.vx[r][c - 1], -(S.vx[r][c + 2] - S.vx[r][c - 2])), inv12dx);
             const float dvy = mul_(fma_(8.f, S.vy[r + 1][c] - S.vy[r - 1][c], -(S.vy[r + 2][c] - S.vy[r - 2][c])), inv12dy);
             const float sv = fmaxf(0.f, -(dvx + dvy));
-            S.s[sr][scn] = make_float2(sv, sv);
+            S.s[sr][scn] = sv;
         };
-        // thread -> (column, row group): rows g, g + SG, ... (SW * SG <= NT threads busy)
-        constexpr int SG = NT / SW;
-        const int scn = tid % SW, sg = tid / SW;
-        if (sg < SG) {
-#pragma unroll
-            for (int i = 0; i < (SH + SG - 1) / SG; ++i)
-                if (i * SG + sg < SH) shock_cell(i * SG + sg, scn);
+        // main pass: warp w, lane l -> column l of rows w, w + NW, ...; tail: the
+        // last SW - 32 columns walked down the rows, on the threads of the warps
+        // with one main row less (at most ceil(SH / NW) = 5 cells per thread)
+        constexpr int STAIL = (SW - 32) * SH, S0 = (SH % NW) * 32;
+        static_assert(SW > 32 && S0 + STAIL <= NT, "shock-phase mapping");
+#pragma unroll 2
+        for (int k = 0; k < (SH + NW - 1) / NW; ++k)
+            if (warp + NW * k < SH) shock_cell(warp + NW * k, lane);
+        if (tid >= S0 && tid < S0 + STAIL) {
+            const int t = tid - S0, cc = t / SH;
+            shock_cell(t - cc * SH, 32 + cc);
         }
         __syncthreads();
     }
@@ -450,7 +456,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             if constexpr (HD) {
                 float2 s2[SEG + 2];   // cells x_0-1 .. x_0+SEG (shock col = cell + 1)
 #pragma unroll
-                for (int q = 0; q < SEG + 2; ++q) s2[q] = S.s[row + 1][x_0 + q];
+                for (int q = 0; q < SEG + 2; ++q) s2[q] = splat(S.s[row + 1][x_0 + q]);
                 float2 G[SEG + 1];
                 face_fluxes(u, s2, S.ax[p], bh, G);
 #pragma unroll
@@ -461,7 +467,8 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             }
             float2 F[SEG + 4];   // cells x_0-2 .. x_0+SEG+1 (fx col = cell + 2)
 #pragma unroll
-            for (int q = 0; q < SEG + 4; ++q) F[q] = S.fx[p][row][x_0 + q];
+            for (int q = 0; q < SEG + 4; ++q)
+                F[q] = p < 2 ? S.fx[p][row][x_0 + q] : make_float2(0.f, S.fx2[row][x_0 + q]);
 #pragma unroll
             for (int q = 0; q < SEG; ++q) {
                 const float2 d = fma2(eight, sub2(F[q + 3], F[q + 1]), sub2(F[q], F[q + 4]));
@@ -469,7 +476,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             }
         }
         __syncthreads();   // every thread is done with the x fluxes
-        float2 (*KX)[TY][KXP] = reinterpret_cast<float2 (*)[TY][KXP]>(&S.fx[0][0][0]);
+        float2 (*KX)[TY][KXP] = S.kx;
 #pragma unroll
         for (int p = 0; p < 3; ++p)
 #pragma unroll
@@ -478,7 +485,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     __syncthreads();
 
     // ---- 4. Y sweep, RK update, stores ---------------------------------------------
-    const float2 (*KX)[TY][KXP] = reinterpret_cast<const float2 (*)[TY][KXP]>(&S.fx[0][0][0]);
+    const float2 (*KX)[TY][KXP] = S.kx;
     const int col = lane, y_0 = warp * SEG;
     const int gi = x0 + col;
     const float2 h2 = K.h2, dt2 = K.dt2, d3t = K.d3t, d6t = K.d6t, third = splat((float)(1.0 / 3.0));
@@ -524,7 +531,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         if constexpr (HD) {
             float2 s2[SEG + 2];   // rows y_0-1 .. y_0+SEG (shock row = cell row + 1)
 #pragma unroll
-            for (int q = 0; q < SEG + 2; ++q) s2[q] = S.s[y_0 + q][col + 1];
+            for (int q = 0; q < SEG + 2; ++q) s2[q] = splat(S.s[y_0 + q][col + 1]);
             float2 G[SEG + 1];
             face_fluxes(u, s2, S.ay[p], bh, G);
 #pragma unroll
@@ -535,7 +542,8 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         }
         float2 F[SEG + 4];   // rows y_0-2 .. y_0+SEG+1 (fy row = cell row + 2)
 #pragma unroll
-        for (int q = 0; q < SEG + 4; ++q) F[q] = S.fy[p][y_0 + q][col];
+        for (int q = 0; q < SEG + 4; ++q)
+            F[q] = p < 2 ? S.fy[p][y_0 + q][col] : make_float2(S.fy2[y_0 + q][col], 0.f);
 #pragma unroll
         for (int q = 0; q < SEG; ++q) {
             const float2 d = fma2(eight, sub2(F[q + 3], F[q + 1]), sub2(F[q], F[q + 4]));
