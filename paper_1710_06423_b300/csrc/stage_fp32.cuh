@@ -304,6 +304,22 @@ __device__ __forceinline__ void stage_plane(const StageArgs<float>& a, Smem& S, 
     }
 }
 
+// Pointwise RK registers U0 (stages 2-4) and D (stages 3-4) of plane p at the
+// cells e_first + q * pitch, q < SEG (zero where q >= nq: outside the grid).
+template <int STAGE>
+__device__ __forceinline__ void load_pointwise(const StageArgs<float>& a, const long long e, const int nq,
+                                               float2 (&u0v)[SEG], float2 (&dv)[SEG])
+{
+    const float2* __restrict__ gu0 = reinterpret_cast<const float2*>(a.u0);
+    const float2* __restrict__ gacc = reinterpret_cast<const float2*>(a.acc);
+#pragma unroll
+    for (int q = 0; q < SEG; ++q) {
+        const bool ok = q < nq;
+        u0v[q] = (STAGE >= 2 && ok) ? gu0[e + q * a.L.pitch] : make_float2(0.f, 0.f);
+        dv[q] = (STAGE >= 3 && ok) ? gacc[e + q * a.L.pitch] : make_float2(0.f, 0.f);
+    }
+}
+
 // One tile (x0, y0) of one run; every thread of the CTA calls it (it holds
 // barriers).  OVERLAP: the caller has issued the copies of this tile's staged
 // region, and the Y sweep issues those of the next tile (xn, yn; has_next)
@@ -320,6 +336,16 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     const long long P = L.fstride;              // plane stride in float2 elements
     // region (r, c) <-> interior (x0 - 4 + c, y0 - 3 + r) <-> padded element (y0 + r) * pitch + x0 + c
     const long long rbase = (long long)y0 * L.pitch + x0;
+
+    // this thread's cells in the Y sweep and RK update: column x0 + col, rows
+    // y0 + y_0 + q (q < nq inside the grid; ragged last tiles)
+    const int col = lane, y_0 = warp * SEG, gi = x0 + col;
+    const long long e_first = L.at(gi, y0 + y_0);
+    const int nq = gi < L.nx ? L.ny - (y0 + y_0) : 0;
+    // pointwise registers of the first pair, issued before the staging wait so
+    // that their latency overlaps the tile's phases up to the Y sweep
+    float2 nu0[SEG], ndv[SEG];
+    load_pointwise<STAGE>(a, e_first, nq, nu0, ndv);
 
     // ---- 0. the staged region of the three planes in shared memory -----------------
     if (!OVERLAP) {
@@ -443,6 +469,10 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     const float2 bh = splat(a.f_bh);
     const float2 m12x = splat(-inv12dx), m12y = splat(-inv12dy), eight = splat(8.f);
 
+    // pointwise registers of the second pair, issued before the X sweep
+    float2 mu0[SEG], mdv[SEG];
+    load_pointwise<STAGE>(a, P + e_first, nq, mu0, mdv);
+
     // ---- 3. X sweep: thread = (row lane, SEG-cell segment per warp) ---------------
     {
         const int row = lane, x_0 = warp * SEG;
@@ -486,40 +516,23 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 
     // ---- 4. Y sweep, RK update, stores ---------------------------------------------
     const float2 (*KX)[TY][KXP] = S.kx;
-    const int col = lane, y_0 = warp * SEG;
-    const int gi = x0 + col;
     const float2 h2 = K.h2, dt2 = K.dt2, d3t = K.d3t, d6t = K.d6t, third = splat((float)(1.0 / 3.0));
     float2* __restrict__ gout = reinterpret_cast<float2*>(a.sout);
-    const float2* __restrict__ gu0 = reinterpret_cast<const float2*>(a.u0);
     float2* __restrict__ gacc = reinterpret_cast<float2*>(a.acc);
     float2 outv[SEG][3];
 
-    const long long e_first = L.at(gi, y0 + y_0);   // this thread's first cell; the next q is + q * pitch
-    // cells q < nq of this thread's segment lie inside the grid (ragged last tiles)
-    const int nq = gi < L.nx ? L.ny - (y0 + y_0) : 0;
-    // pointwise registers U0, D of the cells of this thread, one pair ahead of
-    // the sweep so that their load latency hides behind the previous pair
-    float2 nu0[SEG], ndv[SEG];
-#pragma unroll
-    for (int q = 0; q < SEG; ++q) {
-        const bool ok = q < nq;
-        nu0[q] = (STAGE >= 2 && ok) ? gu0[e_first + q * L.pitch] : make_float2(0.f, 0.f);
-        ndv[q] = (STAGE >= 3 && ok) ? gacc[e_first + q * L.pitch] : make_float2(0.f, 0.f);
-    }
+    // (those of the third pair are loaded while the second is swept)
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
         const long long ep = p * P + e_first;
         float2 u0v[SEG], dv[SEG];
 #pragma unroll
         for (int q = 0; q < SEG; ++q) { u0v[q] = nu0[q]; dv[q] = ndv[q]; }
-        if (p < 2) {
+        if (p == 0) {
 #pragma unroll
-            for (int q = 0; q < SEG; ++q) {
-                const bool ok = q < nq;
-                nu0[q] = (STAGE >= 2 && ok) ? gu0[ep + P + q * L.pitch] : make_float2(0.f, 0.f);
-                ndv[q] = (STAGE >= 3 && ok) ? gacc[ep + P + q * L.pitch] : make_float2(0.f, 0.f);
-            }
+            for (int q = 0; q < SEG; ++q) { nu0[q] = mu0[q]; ndv[q] = mdv[q]; }
         }
+        if (p == 1) load_pointwise<STAGE>(a, ep + P, nq, nu0, ndv);
         float2 u[SEG + 6];   // rows y_0-3 .. y_0+SEG+2 (region row = cell row + 3)
 #pragma unroll
         for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][y_0 + q][col + 4];
