@@ -35,6 +35,11 @@ PAPER_8000_HD = 8000 * 8000 * 100 / 163.60   # Table 1: 8000^2, 100 iterations w
 #   s3: read S2, U0, D / write S3, D;         s4: read S3, U0, D / write U0
 # halo re-reads of the stencil input are served by L2 and are not algorithmic bytes
 STAGE_VALUES_FP32 = (12, 24, 30, 24)
+# DRAM bytes per cell of each stage_fp32 launch (stages 1..4) measured by ncu as
+# dram__bytes_read.sum + dram__bytes_write.sum on the 4000^2 workload (three times L2 per
+# RK register; profiles/stage_fp32_dram_ot4000.md).  Traffic scales with the cells
+# processed; the figures hold for the stage kernel as of that capture.
+STAGE_TRAFFIC_B_PER_CELL_FP32 = (47.6, 96.5, 120.8, 97.4)
 
 
 def parse():
@@ -378,8 +383,11 @@ def run_ours(args, ws, rank, local, pg):
     stage_bytes = [v * 4 * cells for v in STAGE_VALUES_FP32]
     peak, peak_kind = measured_peaks()
     achieved = sum(stage_bytes) / (sum(stage_ms) * 1e-3) / 1e9
+    # per average stage launch, like `achieved` (measured bytes per cell x cells of one launch)
+    traffic = sum(STAGE_TRAFFIC_B_PER_CELL_FP32) / 4 * cells
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per stage launch (ncu, 4000^2 per-cell figures x cells)",
                 "kernel": "stage_fp32 (all four RK stages)",
                 "bytes_per_cell_stage": 4 * sum(STAGE_VALUES_FP32) / 4,
                 "stage_ms": stage_ms, "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
