@@ -37,11 +37,51 @@ template <> struct Rn<double> : RnD {};
 
 // Conserved perturbations (rt, mx, my, et, btx, bty), background (rb, eb, bbx,
 // bby; ignored when !BG) -> signal speeds along x and y.
+// FP32: one reciprocal of rho and a square root, both the fixed approximate
+// PTX instructions (relative error ~1e-7, far below what a CFL step needs),
+// every other operation round-to-nearest.  Deterministic like the FP64 form,
+// so every FP32 reduction (fused or stand-alone) gives the same bits.
+template <bool BG>
+__device__ __forceinline__ void signal_speeds_f32(float rt, float mx, float my, float et, float btx, float bty,
+                                                  float rb, float eb, float bbx, float bby, float gamma,
+                                                  float& sx, float& sy)
+{
+    using R = RnF;
+    const float gm1 = R::sub(gamma, 1.f), half = 0.5f;
+    float rho, pkt, bx, by;
+    if constexpr (BG) rho = R::add(rb, rt); else rho = rt;
+    float rinv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rinv) : "f"(rho));
+    const float ux = R::mul(mx, rinv), uy = R::mul(my, rinv);
+    const float ekin = R::mul(half, R::add(R::mul(mx, ux), R::mul(my, uy)));
+    const float b2p = R::mul(half, R::add(R::mul(btx, btx), R::mul(bty, bty)));
+    if constexpr (BG) {
+        const float bb = R::add(R::mul(bbx, btx), R::mul(bby, bty));
+        const float pk = R::mul(gm1, R::sub(R::sub(R::sub(et, ekin), bb), b2p));
+        const float b2b = R::mul(half, R::add(R::mul(bbx, bbx), R::mul(bby, bby)));
+        pkt = R::add(R::mul(gm1, R::sub(eb, b2b)), pk);
+        bx = R::add(bbx, btx); by = R::add(bby, bty);
+    } else {
+        pkt = R::mul(gm1, R::sub(R::sub(et, ekin), b2p));
+        bx = btx; by = bty;
+        (void)eb;
+    }
+    const float c2 = R::mul(R::add(R::mul(gamma, pkt), R::add(R::mul(bx, bx), R::mul(by, by))), rinv);
+    float cf;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(cf) : "f"(c2));
+    sx = R::add(fabsf(ux), cf);
+    sy = R::add(fabsf(uy), cf);
+}
+
 template <typename T, bool BG>
 __device__ __forceinline__ void signal_speeds(T rt, T mx, T my, T et, T btx, T bty,
                                               T rb, T eb, T bbx, T bby, T gamma,
                                               T& sx, T& sy)
 {
+    if constexpr (sizeof(T) == sizeof(float)) {
+        signal_speeds_f32<BG>(rt, mx, my, et, btx, bty, rb, eb, bbx, bby, gamma, sx, sy);
+        return;
+    } else {
     using R = Rn<T>;
     const T gm1 = R::sub(gamma, (T)1), half = (T)0.5;
     T rho, ux, uy, pkt, bx, by;
@@ -68,6 +108,7 @@ __device__ __forceinline__ void signal_speeds(T rt, T mx, T my, T et, T btx, T b
     T cf = R::sqrt_(R::div(R::add(R::mul(gamma, pkt), R::add(R::mul(bx, bx), R::mul(by, by))), rho));
     sx = R::add(R::abs_(ux), cf);
     sy = R::add(R::abs_(uy), cf);
+    }
 }
 
 __device__ __forceinline__ unsigned long long speed_key(double v) { return (unsigned long long)__double_as_longlong(v); }
