@@ -94,6 +94,11 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(s), "l"(gmem) : "memory");
 }
+// Bring 256 bytes at p (16-byte aligned, inside an allocation) into L2.
+__device__ __forceinline__ void prefetch_l2_bulk256(const void* p)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" :: "l"(p) : "memory");
+}
 // predicated form: no copy (and no read of gmem) when pred is false, without a branch
 __device__ __forceinline__ void cp_async8_if(unsigned sdst, const void* gmem, bool pred)
 {
@@ -346,6 +351,17 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     // that their latency overlaps the tile's phases up to the Y sweep
     float2 nu0[SEG], ndv[SEG];
     load_pointwise<STAGE>(a, e_first, nq, nu0, ndv);
+    // ... and those of the second and third pairs brought into L2 now (one bulk
+    // prefetch per 256-byte row segment: lane l of the warp takes pair 1 + l/8,
+    // array U0 or D by (l/4)%2, row l%4 of the warp's 4 x 32 cells), so their
+    // register loads later in the tile hit L2.  Prefetching a whole tile ahead
+    // measured slower.
+    if (STAGE >= 2 && lane < 16) {
+        const int pp = 1 + (lane >> 3), arr = (lane >> 2) & 1, qq = lane & 3;
+        if (STAGE >= 3 || arr == 0)
+            prefetch_l2_bulk256(reinterpret_cast<const float2*>(arr ? a.acc : a.u0) + pp * P
+                                + L.at(x0, y0 + y_0 + qq));
+    }
 
     // ---- 0. the staged region of the three planes in shared memory -----------------
     if (!OVERLAP) {
