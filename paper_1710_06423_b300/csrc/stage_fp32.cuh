@@ -347,17 +347,13 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     const int col = lane, y_0 = warp * SEG, gi = x0 + col;
     const long long e_first = L.at(gi, y0 + y_0);
     const int nq = gi < L.nx ? L.ny - (y0 + y_0) : 0;
-    // pointwise registers of the first pair, issued before the staging wait so
-    // that their latency overlaps the tile's phases up to the Y sweep
-    float2 nu0[SEG], ndv[SEG];
-    load_pointwise<STAGE>(a, e_first, nq, nu0, ndv);
-    // ... and those of the second and third pairs brought into L2 now (one bulk
-    // prefetch per 256-byte row segment: lane l of the warp takes pair 1 + l/8,
-    // array U0 or D by (l/4)%2, row l%4 of the warp's 4 x 32 cells), so their
-    // register loads later in the tile hit L2.  Prefetching a whole tile ahead
-    // measured slower.
-    if (STAGE >= 2 && lane < 16) {
-        const int pp = 1 + (lane >> 3), arr = (lane >> 2) & 1, qq = lane & 3;
+    // The pointwise RK registers U0/D of these cells are brought into L2 when the
+    // tile starts (one bulk prefetch per 256-byte row segment: lane l of the warp
+    // takes pair l/8, array U0 or D by (l/4)%2, row l%4 of the warp's 4 x 32
+    // cells), so the register loads later in the tile hit L2.  Prefetching a
+    // whole tile ahead measured slower.
+    if (STAGE >= 2 && lane < 24) {
+        const int pp = lane >> 3, arr = (lane >> 2) & 1, qq = lane & 3;
         if (STAGE >= 3 || arr == 0)
             prefetch_l2_bulk256(reinterpret_cast<const float2*>(arr ? a.acc : a.u0) + pp * P
                                 + L.at(x0, y0 + y_0 + qq));
@@ -458,6 +454,10 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 
     const float inv12dx = a.f_inv12dx, inv12dy = a.f_inv12dy;
 
+    // register loads of the first pair's pointwise values (from L2), issued before the shock phase
+    float2 nu0[SEG], ndv[SEG];
+    load_pointwise<STAGE>(a, e_first, nq, nu0, ndv);
+
     // ---- 2. shock indicator on [x0-1, x0+TX] x [y0-1, y0+TY] ---------------------
     if constexpr (HD) {
         auto shock_cell = [&](const int sr, const int scn) {
@@ -485,7 +485,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     const float2 bh = splat(a.f_bh);
     const float2 m12x = splat(-inv12dx), m12y = splat(-inv12dy), eight = splat(8.f);
 
-    // pointwise registers of the second pair, issued before the X sweep
+    // ... and of the second pair, issued before the X sweep
     float2 mu0[SEG], mdv[SEG];
     load_pointwise<STAGE>(a, P + e_first, nq, mu0, mdv);
 
@@ -584,15 +584,15 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
                 if (STAGE == 1) {
                     o = fma2(h2, k, ucen);
                 } else if (STAGE == 2) {
-                    gacc[e] = fma2(d3t, k, mul2(third, sub2(ucen, u0v[q])));
+                    __stcs(gacc + e, fma2(d3t, k, mul2(third, sub2(ucen, u0v[q]))));
                     o = fma2(h2, k, u0v[q]);
                 } else if (STAGE == 3) {
-                    gacc[e] = fma2(d3t, k, dv[q]);
+                    __stcs(gacc + e, fma2(d3t, k, dv[q]));
                     o = fma2(dt2, k, u0v[q]);
                 } else {
                     o = add2(u0v[q], fma2(d6t, k, dv[q]));
                 }
-                gout[e] = o;
+                __stcs(gout + e, o);   // evict-first: L2 cannot keep it for the next stage
             }
             outv[q][p] = o;
         }
