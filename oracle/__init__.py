@@ -57,6 +57,7 @@ class _Params(ctypes.Structure):
         ("c2", ctypes.c_double * NF),
         ("c_shk", ctypes.c_double),
         ("nthreads", ctypes.c_int),
+        ("grav", ctypes.c_double * 2),
     ]
 
 
@@ -101,6 +102,7 @@ class Problem:
     c2: tuple = DEFAULT_C2
     c_shk: float = DEFAULT_CSHK
     nthreads: int = field(default_factory=lambda: int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1)))
+    gravity: tuple = (0.0, 0.0)   # (g_x, g_y): sources rt g in momentum, m.g in energy (section 2)
 
     @property
     def dx(self) -> float:
@@ -121,6 +123,7 @@ class Problem:
             p.c2[i] = v
         p.c_shk = self.c_shk
         p.nthreads = self.nthreads
+        p.grav[0], p.grav[1] = float(self.gravity[0]), float(self.gravity[1])
         return p
 
 

@@ -38,6 +38,13 @@
  *       nu_f = (c2_u dx cmax_d) R_f + (c_shk dx dx) s_f,
  *       H_i = (nu_{i+1/2} d1_{i+1/2} - nu_{i-1/2} d1_{i-1/2}) / (dx dx).
  *   * k_u = (H_x + H_y) - (D_x F_x + D_y F_y).
+ *   * gravity g (section 2: the rho g source of the momentum equation and its
+ *     work term in the energy equation), with the background read as being in
+ *     magnetohydrostatic balance, -grad p_tb + div(B_b B_b) + rho_b g = 0, so
+ *     that its own force cancels: the perturbation sources are
+ *       S_mk = rt g_k,  S_e = m.g = m_x g_x + m_y g_y  (m the total momentum),
+ *     added last: k = ((H_x + H_y) - (D_x F_x + D_y F_y)) + S, and only when
+ *     g is nonzero.
  *   * c_fast^2 = (gamma p_k + |B|^2)/rho with total p_k; cmax_d = max(|v_d| + c_fast)
  *     over interior cells, taken once per step from the step-start state and
  *     used by all four stages; dt = C min(dx/cmax_x, dy/cmax_y).
@@ -71,6 +78,7 @@ typedef struct {
     double c2[NF];        /* hyper-diffusion coefficient per conserved variable */
     double c_shk;         /* shock-viscosity coefficient */
     int nthreads;         /* OpenMP threads (<= 0: 1) */
+    double grav[2];       /* gravitational acceleration (g_x, g_y); zero: no source */
 } orc_params;
 
 /* ghost-extended index: i in [-GH, nx+GH), j in [-GH, ny+GH) */
@@ -263,6 +271,7 @@ void orc_rhs(const orc_params *p, const double *w, const double *bg,
     }
 
     const double cm[2] = {cmax_x, cmax_y};
+    const int grav = p->grav[0] != 0.0 || p->grav[1] != 0.0;
     const double dd[2] = {p->dx, p->dy};
     const size_t st[2] = {sx, sy};
 
@@ -304,7 +313,13 @@ void orc_rhs(const orc_params *p, const double *w, const double *bg,
                 }
                 double dfx = dcen(fx + f * ne, c, sx, d12x);
                 double dfy = dcen(fy + f * ne, c, sy, d12y);
-                k[f * n + (size_t)j * nx + i] = hsum - (dfx + dfy);
+                double kf = hsum - (dfx + dfy);
+                if (grav) {
+                    if (f == 1) kf = kf + rt[c] * p->grav[0];
+                    else if (f == 2) kf = kf + rt[c] * p->grav[1];
+                    else if (f == 3) kf = kf + (mx[c] * p->grav[0] + my[c] * p->grav[1]);
+                }
+                k[f * n + (size_t)j * nx + i] = kf;
             }
         }
     }

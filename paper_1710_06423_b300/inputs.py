@@ -138,3 +138,24 @@ def alfven_wave(nx: int, ny: int = 1, amp: float = 1e-6, gamma: float = 5.0 / 3.
     one = np.ones((ny, nx))
     z = np.zeros((ny, nx))
     return conserved(one, z, amp * s, one, one, -amp * s, gamma)
+
+
+def stratified_background(nx: int, ny: int, *, g: float, scale_height: float, bx: float = 0.0,
+                          rho0: float = 1.0, gamma: float = 5.0 / 3.0) -> np.ndarray:
+    """Isothermal magnetohydrostatic background on [0,1]^2 under gravity (0, -g):
+    rho_b = rho0 exp(-y/H), p_b = rho_b g H (dp_b/dy = -rho_b g), a uniform
+    horizontal field B_b = (bx, 0) (no magnetic force).  Returns the four
+    background fields (rho_b, e_b, B_bx, B_by), shape (4, ny, nx)."""
+    y = cell_centres(ny)[:, None] * np.ones((1, nx))
+    rho = rho0 * np.exp(-y / scale_height)
+    p = rho * g * scale_height
+    e = p / (gamma - 1.0) + 0.5 * bx * bx
+    return np.ascontiguousarray(np.stack([rho, e, bx * np.ones_like(y), np.zeros_like(y)]).astype(np.float64))
+
+
+def gaussian_blob(nx: int, ny: int, *, amp: float, centre=(0.5, 0.5), width: float = 0.1) -> np.ndarray:
+    """amp exp(-r^2 / width^2) about `centre` on the cell centres of [0,1]^2, shape (ny, nx)."""
+    x = cell_centres(nx)[None, :]
+    y = cell_centres(ny)[:, None]
+    r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2
+    return np.ascontiguousarray(amp * np.exp(-r2 / (width * width)))
