@@ -355,6 +355,28 @@ def run_learned(args, local):
     print(json.dumps(res), flush=True)
 
 
+def run_stratified(args, ws, local, pg, torch, n=4000):
+    """Gravity about an isothermal magnetohydrostatic background (section 2's rho g
+    source): 4000^2 FP32, periodic in x, fixed in y, a heavy Gaussian blob and a
+    shear flow as the perturbation.  The background adds 4 values per cell-stage."""
+    from paper_1710_06423_b300 import inputs
+    from paper_1710_06423_b300.sac import FP32, Solver
+    g = 2.0
+    bg = inputs.stratified_background(n, n, g=g, scale_height=0.4, bx=0.3)
+    w = np.zeros((6, n, n))
+    w[0] = inputs.gaussian_blob(n, n, amp=0.05, centre=(0.5, 0.45), width=0.12)
+    rho = bg[0] + w[0]
+    w[1] = rho * 0.02 * np.sin(2 * np.pi * inputs.cell_centres(n))[None, :]
+    w[3] = 0.5 * w[1] ** 2 / rho + 0.02 * np.exp(-inputs.cell_centres(n)[:, None] / 0.4)
+    s = Solver(nx=n, ny=n, precision=FP32, device=local, bc_x=0, bc_y=1, has_background=1, gravity=(0.0, -g))
+    s.set_state(w, bg, 0.0)
+    ms = time_device_steps(s, args.steps, args.warmup, pg, torch)
+    del s
+    return {"value": ws * n * n * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            "workload": f"isothermal stratified background {n}x{n}, gravity (0,-{g}), blob + shear flow, FP32",
+            "bytes_per_cell_stage": 90.0 + 16.0}
+
+
 def run_ours(args, ws, rank, local, pg):
     import torch
     from paper_1710_06423_b300 import inputs
@@ -431,6 +453,7 @@ def run_ours(args, ws, rank, local, pg):
             msm = time_device_steps(sm_, args.steps, args.warmup, pg, torch)
             extra[f"ot{m}"] = {"value": ws * m * m * args.steps / (msm * 1e-3), "ms_per_step": msm / args.steps}
             del sm_
+        extra["stratified_gravity"] = run_stratified(args, ws, local, pg, torch)
         extra["batched"] = run_batched(args, ws, local, pg, torch)
 
     cpu = None

@@ -72,6 +72,13 @@ enum { SAC_FP64 = 0, SAC_FP32 = 1 };
  *   has_background    1: a static background (bg) is supplied to sac_set_state
  *   device            CUDA device ordinal
  *   stream            cudaStream_t the context enqueues on (NULL = default)
+ *   gravity[2]        gravitational acceleration (g_x, g_y) (section 2's rho g
+ *                     source).  The background is taken to be in
+ *                     magnetohydrostatic balance (its own weight cancels), so the
+ *                     perturbation gains rt g in the momentum equation and m.g in
+ *                     the energy equation.  Nonzero gravity requires
+ *                     has_background = 1 (a zero background array is allowed) and
+ *                     is not supported by sac_batch_* or sac_step_noalloc.
  */
 typedef struct {
     int nx, ny;
@@ -85,11 +92,12 @@ typedef struct {
     int has_background;
     int device;
     void *stream;
+    double gravity[2];
 } sac_params;
 
 /* Fill *p with defaults: 64x64 periodic on [0,1]^2, gamma 5/3, C 0.3, FP64,
  * HD on, c2 = (0.02, 0.1, 0.1, 0.02, 0.02, 0.02), c_shk = 0.5, no background,
- * device 0, default stream. */
+ * device 0, default stream, no gravity. */
 void sac_default_params(sac_params *p);
 
 /* Validate *p, allocate the device buffers of one run and return a context in

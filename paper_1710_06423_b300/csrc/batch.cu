@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
             f32k::store_hd_coeffs(sa, S, threadIdx.x);   // visible after the tile's staging barrier
             const f32k::StepConsts K = f32k::load_step_consts(sa.sc);
             unsigned long long m[2] = {0ull, 0ull};
-            f32k::tile_body<STAGE, BG, HD, false>(sa, d.y * f32k::TX, d.z * f32k::TY, S, K, m);
+            f32k::tile_body<STAGE, BG, HD, false, false>(sa, d.y * f32k::TX, d.z * f32k::TY, S, K, m);
             if (STAGE == 4) f32k::block_speed_max(m, red, sa.sc);
         }
         __syncthreads();   // shared memory and `sa` are reused by the next tile
@@ -260,7 +260,8 @@ int sac_batch_init(const sac_params* runs, int n, sac_batch** out)
     if (!runs || !out || n < 1 || n > 65535) return SAC_ERR_ARG;   // one halo grid row per run
     for (int i = 0; i < n; ++i) {
         if (runs[i].precision != SAC_FP32 || runs[i].device != runs[0].device || runs[i].stream != runs[0].stream ||
-            runs[i].hyperdiffusion != runs[0].hyperdiffusion || runs[i].has_background != runs[0].has_background)
+            runs[i].hyperdiffusion != runs[0].hyperdiffusion || runs[i].has_background != runs[0].has_background ||
+            runs[i].gravity[0] != 0.0 || runs[i].gravity[1] != 0.0)
             return SAC_ERR_ARG;
     }
     sac_batch* b = new sac_batch();

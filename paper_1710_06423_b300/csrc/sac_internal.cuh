@@ -114,16 +114,20 @@ struct StageArgs {
     double c2[NF];
     double c_shk;
     int bc_x, bc_y;
+    double grav[2];    // gravitational acceleration; sources rt g (momentum), m.g (energy)
+    __host__ __device__ bool has_grav() const { return grav[0] != 0.0 || grav[1] != 0.0; }
     // FP32 kernels: the parameters above rounded once on the host, so a tile
     // does no double arithmetic (FP64 issues at 1/64 of the FP32 rate here)
     float f_gm1, f_gamma, f_bh;          // gamma - 1, gamma, c_shk / 2
     float f_inv12dx, f_inv12dy;          // 1 / (12 dx), 1 / (12 dy)
     float f_c2dx[NF], f_c2dy[NF];        // c2_f / dx, c2_f / dy
+    float f_grav[2];                     // grav
     __host__ void derive_f32()
     {
         f_gm1 = (float)(gamma - 1.0); f_gamma = (float)gamma; f_bh = (float)(0.5 * c_shk);
         f_inv12dx = (float)(1.0 / (12.0 * dx)); f_inv12dy = (float)(1.0 / (12.0 * dy));
         for (int f = 0; f < NF; ++f) { f_c2dx[f] = (float)(c2[f] / dx); f_c2dy[f] = (float)(c2[f] / dy); }
+        f_grav[0] = (float)grav[0]; f_grav[1] = (float)grav[1];
     }
 };
 

@@ -330,7 +330,7 @@ __device__ __forceinline__ void load_pointwise(const StageArgs<float>& a, const 
 // region, and the Y sweep issues those of the next tile (xn, yn; has_next)
 // plane by plane as soon as the CTA has read the plane it replaces.  S.ax/S.ay must hold the run's coefficients (store_hd_coeffs).
 // Stage 4 folds the signal speeds of the tile's new state into m.
-template <int STAGE, bool BG, bool HD, bool OVERLAP>
+template <int STAGE, bool BG, bool HD, bool OVERLAP, bool GRAV = false>
 __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x0, const int y0, Smem& S,
                                           const StepConsts& K, unsigned long long (&m)[2],
                                           const bool has_next = false, const int xn = 0, const int yn = 0)
@@ -536,6 +536,8 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     float2* __restrict__ gout = reinterpret_cast<float2*>(a.sout);
     float2* __restrict__ gacc = reinterpret_cast<float2*>(a.acc);
     float2 outv[SEG][3];
+    float rcen[SEG];   // GRAV: rt at this thread's cells (pair 0), for the momentum source
+    const float gxv = a.f_grav[0], gyv = a.f_grav[1];
 
     // (those of the third pair are loaded while the second is swept)
 #pragma unroll
@@ -576,8 +578,20 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 #pragma unroll
         for (int q = 0; q < SEG; ++q) {
             const float2 d = fma2(eight, sub2(F[q + 3], F[q + 1]), sub2(F[q], F[q + 4]));
-            const float2 k = add2(fma2(m12y, d, hy[q]), KX[p][y_0 + q][col]);
+            float2 k = add2(fma2(m12y, d, hy[q]), KX[p][y_0 + q][col]);
             const float2 ucen = u[q + 3];
+            if constexpr (GRAV) {
+                // gravity (section 2), after the flux and diffusion terms: m.g on e~
+                // (m from pair 1, still in shared memory while pair 0 is swept) and
+                // rt g on m (rt kept from pair 0)
+                if (p == 0) {
+                    const float2 m = S.u[1][y_0 + q + 3][col + 4];
+                    k.y = __fadd_rn(k.y, fma_(m.x, gxv, mul_(m.y, gyv)));
+                    rcen[q] = ucen.x;
+                } else if (p == 1) {
+                    k = add2(k, make_float2(mul_(rcen[q], gxv), mul_(rcen[q], gyv)));
+                }
+            }
             float2 o = make_float2(0.f, 0.f);
             if (q < nq) {
                 const long long e = ep + q * L.pitch;
@@ -627,7 +641,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 // finishes the current one.
 // The step constants are read once; stage 4 keeps the signal-speed maximum of
 // all its tiles in registers and reduces it once at the end.
-template <int STAGE, bool BG, bool HD>
+template <int STAGE, bool BG, bool HD, bool GRAV>
 __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, const int ntx, const int ntiles)
 {
     if (a.sc->skip) return;
@@ -646,8 +660,8 @@ __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, co
         // the next tile's region streams into shared memory during this tile's Y sweep;
         // the next tile_body starts with the barrier that makes it (and all else) visible
         const int tn = t + gridDim.x;
-        tile_body<STAGE, BG, HD, true>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m, tn < ntiles,
-                                       (tn % ntx) * TX, (tn / ntx) * TY);
+        tile_body<STAGE, BG, HD, true, GRAV>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m, tn < ntiles,
+                                             (tn % ntx) * TX, (tn / ntx) * TY);
     }
     if (STAGE == 4) block_speed_max(m, red, a.sc);
 }

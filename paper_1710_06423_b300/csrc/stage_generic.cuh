@@ -330,6 +330,8 @@ stage_generic(const StageArgs<T> a)
     const T third = (T)(1.0 / 3.0);
     const bool edge = (x0 < GY) || (x0 + TX > L.nx - GY) || (y0 < GY) || (y0 + TY > L.ny - GY);
     unsigned long long smax[2] = {0ull, 0ull};
+    const bool grav = a.has_grav();
+    const T gxv = (T)a.grav[0], gyv = (T)a.grav[1];
 
 #pragma unroll
     for (int cI = 0; cI < CPT; ++cI) {
@@ -339,10 +341,17 @@ stage_generic(const StageArgs<T> a)
         const int c = (cy + 3) * RX + (cx + 4);
         const long long g = L.at(i, j);
         T out[NF];
+        // gravity (section 2): rt g in the momentum and m.g in the energy
+        // equation, added after the flux and diffusion terms
+        T src[NF] = {(T)0, (T)0, (T)0, (T)0, (T)0, (T)0};
+        if (grav) {
+            const T rt = sU[0 * RN + c], mxc = sU[1 * RN + c], myc = sU[2 * RN + c];
+            src[1] = rt * gxv; src[2] = rt * gyv; src[3] = mxc * gxv + myc * gyv;
+        }
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             const long long gf = (long long)f * L.fstride + g;
-            const T kf = k[f][cI];
+            const T kf = grav && (f >= 1 && f <= 3) ? k[f][cI] + src[f] : k[f][cI];
             constexpr int RK = RkScheme<T>::value;
             if constexpr (RK == RK_K) {
                 if (STAGE == 1) {

@@ -59,6 +59,7 @@ class SacParams(ctypes.Structure):
         ("has_background", ctypes.c_int),
         ("device", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("gravity", ctypes.c_double * 2),
     ]
 
 
@@ -150,9 +151,10 @@ class Solver:
         p = default_params()
         stream = kw.pop("stream", "current")
         for k, v in kw.items():
-            if k == "c2":
+            if k in ("c2", "gravity"):
+                fld = getattr(p, k)
                 for j, x in enumerate(v):
-                    p.c2[j] = x
+                    fld[j] = x
             else:
                 setattr(p, k, v)
         if stream == "current":
@@ -293,9 +295,10 @@ class Batch:
         for k, kw in enumerate(runs):
             p = default_params()
             for key, v in kw.items():
-                if key == "c2":
+                if key in ("c2", "gravity"):
+                    fld = getattr(p, key)
                     for j, x in enumerate(v):
-                        p.c2[j] = x
+                        fld[j] = x
                 else:
                     setattr(p, key, v)
             p.precision = FP32
@@ -467,9 +470,10 @@ def step_noalloc(w_in, w_out, dt: float = 0.0, wait: bool = True, **kw) -> float
     p = default_params()
     stream = kw.pop("stream", "current")
     for k, v in kw.items():
-        if k == "c2":
+        if k in ("c2", "gravity"):
+            fld = getattr(p, k)
             for j, x in enumerate(v):
-                p.c2[j] = x
+                fld[j] = x
         else:
             setattr(p, k, v)
     p.precision = FP32
