@@ -11,7 +11,8 @@
 // One CTA (256 threads, two per SM) owns a 32 x 32 tile at a time and walks
 // the tiles of the grid persistently:
 //   0. stage the tile + 3-cell halo of the three planes into shared memory
-//      with 16-byte cp.async.cg (rows 16-byte aligned);
+//      (rows 16-byte aligned): TMA bulk row copies on an mbarrier in the
+//      persistent kernel, 16-byte cp.async.cg in the batch kernel;
 //   1. per staged cell: v = m/rho, total pressure, energy-flux factor, B.v,
 //      the x fluxes (cells x0-2..x0+TX+1 of the tile rows) and y fluxes
 //      (rows y0-2..y0+TY+1 of the tile columns) of all three pairs;
@@ -100,6 +101,29 @@ __device__ __forceinline__ void cp_async16_cg_if(unsigned sdst, const void* gmem
     asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q cp.async.cg.shared.global [%0], [%1], 16;\n}"
                  :: "r"(sdst), "l"(gmem), "r"((int)pred) : "memory");
 }
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_row_g2s(unsigned sdst, const void* gsrc, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(sdst), "l"(gsrc), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
@@ -132,10 +156,10 @@ __device__ __forceinline__ float fdiv(float a, float b)
 constexpr int TX = 32, TY = 32, NT = 256, NW = NT / 32, SEG = 4;
 static_assert(TX / SEG == NW && TY / SEG == NW, "one segment per warp in both sweeps");
 // staged region (cols x0-4.., rows y0-3..); its rows start 16-byte aligned
-// (pitch 42 float2) so that 16-byte cp.async.cg copies (L2 only, half the
-// instructions of 8-byte copies) can fill it.  The price is a 2-way bank
-// conflict in the X sweep's column-wise window loads; measured 8% faster
-// overall than an odd (conflict-free) pitch filled by 8-byte copies.
+// (pitch 42 float2) so that TMA bulk copies or 16-byte cp.async.cg copies can
+// fill it.  The price is a 2-way bank conflict in the X sweep's column-wise
+// window loads; measured 8% faster overall than an odd (conflict-free) pitch
+// filled by 8-byte cp.async, and the bulk copies another 2%.
 constexpr int RX = TX + 8, RY = TY + 6, RXP = RX + 2;
 constexpr int VXP = RX + 1;                                // row pitch of the velocity arrays (odd)
 constexpr int FXW = TX + 4, FXP = FXW + 1;                 // x fluxes: cols x0-2 .. x0+TX+1
@@ -324,15 +348,35 @@ __device__ __forceinline__ void load_pointwise(const StageArgs<float>& a, const 
     }
 }
 
+// Persistent kernel: plane p of the staged region of tile (x0, y0) by TMA bulk
+// copies, one 320-byte row per copy (lane k of warp w copies row w + NW k),
+// completing on the CTA's mbarrier; kTileBytes per tile (three planes).
+constexpr unsigned kTileBytes = 3u * RY * RX * sizeof(float2);
+__device__ __forceinline__ void stage_plane_bulk(const StageArgs<float>& a, Smem& S, const int x0, const int y0,
+                                                 const int p, unsigned long long* bar)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = warp + NW * lane;
+    if (lane < (RY + NW - 1) / NW && r < RY) {
+        const float2* g = reinterpret_cast<const float2*>(a.sin) + p * a.L.fstride + (long long)(y0 + r) * a.L.pitch + x0;
+        bulk_row_g2s(smem_u32(&S.u[p][r][0]), g, RX * sizeof(float2), bar);
+    }
+}
+
 // One tile (x0, y0) of one run; every thread of the CTA calls it (it holds
-// barriers).  OVERLAP: the caller has issued the copies of this tile's staged
-// region, and the Y sweep issues those of the next tile (xn, yn; has_next)
-// plane by plane as soon as the CTA has read the plane it replaces.  S.ax/S.ay must hold the run's coefficients (store_hd_coeffs).
+// barriers).  OVERLAP: the caller has issued the bulk copies of this tile's
+// staged region on *bar (expected at parity *phase), and the Y sweep issues
+// those of the next tile (xn, yn; has_next) plane by plane as soon as the CTA
+// has read the plane it replaces.  The wait is bounded: if the copies do not
+// land, the run's status becomes ST_ERR_TIMEOUT, *failed is set and every
+// thread returns.  S.ax/S.ay must hold the run's coefficients (store_hd_coeffs).
 // Stage 4 folds the signal speeds of the tile's new state into m.
 template <int STAGE, bool BG, bool HD, bool OVERLAP, bool GRAV = false>
 __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x0, const int y0, Smem& S,
                                           const StepConsts& K, unsigned long long (&m)[2],
-                                          const bool has_next = false, const int xn = 0, const int yn = 0)
+                                          const bool has_next = false, const int xn = 0, const int yn = 0,
+                                          unsigned long long* bar = nullptr, unsigned* phase = nullptr,
+                                          bool* failed = nullptr)
 {
     const Layout L = a.L;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -363,8 +407,22 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 #pragma unroll
         for (int p = 0; p < 3; ++p) stage_plane(a, S, x0, y0, p);
     }
-    cp_async_wait_all();
-    __syncthreads();
+    if (OVERLAP) {
+        unsigned it = 0;
+        bool to = false;
+        while (!mbar_try_wait(bar, *phase)) {
+            if (++it > (1u << 20)) { to = true; break; }
+        }
+        if (__syncthreads_or(to)) {
+            if (threadIdx.x == 0) a.sc->status = ST_ERR_TIMEOUT;
+            *failed = true;
+            return;
+        }
+        *phase ^= 1u;
+    } else {
+        cp_async_wait_all();
+        __syncthreads();
+    }
 
     const float gm1 = a.f_gm1;
 
@@ -555,7 +613,10 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][y_0 + q][col + 4];
         if (OVERLAP) {
             __syncthreads();   // plane p of this tile is read for good
-            if (has_next) stage_plane(a, S, xn, yn, p);
+            if (has_next) {
+                if (p == 0 && threadIdx.x == 0) mbar_expect_tx(bar, kTileBytes);
+                stage_plane_bulk(a, S, xn, yn, p, bar);
+            }
         }
         float2 hy[SEG];
         if constexpr (HD) {
@@ -636,8 +697,8 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 
 // Persistent: each CTA walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
 // (row-major; the CTAs of one wave cover neighbouring tiles, so halo rows come
-// from L2), copying the next tile's region into shared memory while it
-// finishes the current one.
+// from L2), copying the next tile's region into shared memory by TMA bulk
+// copies while it finishes the current one.
 // The step constants are read once; stage 4 keeps the signal-speed maximum of
 // all its tiles in registers and reduces it once at the end.
 template <int STAGE, bool BG, bool HD, bool GRAV>
@@ -650,17 +711,22 @@ __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, co
     store_hd_coeffs(a, S, threadIdx.x);   // no later phase writes S.ax/S.ay
     const StepConsts K = load_step_consts(a.sc);
     unsigned long long m[2] = {0ull, 0ull};
+    __shared__ __align__(8) unsigned long long bar;   // staging completion (one arrival + bytes per tile)
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    unsigned phase = 0;
+    bool failed = false;
     int t = blockIdx.x;
     if (t < ntiles) {
+        if (threadIdx.x == 0) mbar_expect_tx(&bar, kTileBytes);
 #pragma unroll
-        for (int p = 0; p < 3; ++p) stage_plane(a, S, (t % ntx) * TX, (t / ntx) * TY, p);
+        for (int p = 0; p < 3; ++p) stage_plane_bulk(a, S, (t % ntx) * TX, (t / ntx) * TY, p, &bar);
     }
     for (; t < ntiles; t += gridDim.x) {
-        // the next tile's region streams into shared memory during this tile's Y sweep;
-        // the next tile_body starts with the barrier that makes it (and all else) visible
         const int tn = t + gridDim.x;
         tile_body<STAGE, BG, HD, true, GRAV>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m, tn < ntiles,
-                                             (tn % ntx) * TX, (tn / ntx) * TY);
+                                             (tn % ntx) * TX, (tn / ntx) * TY, &bar, &phase, &failed);
+        if (failed) return;
     }
     if (STAGE == 4) block_speed_max(m, red, a.sc);
 }
