@@ -58,6 +58,7 @@ class _Params(ctypes.Structure):
         ("c_shk", ctypes.c_double),
         ("nthreads", ctypes.c_int),
         ("grav", ctypes.c_double * 2),
+        ("hd_single_face", ctypes.c_int),
     ]
 
 
@@ -103,6 +104,7 @@ class Problem:
     c_shk: float = DEFAULT_CSHK
     nthreads: int = field(default_factory=lambda: int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1)))
     gravity: tuple = (0.0, 0.0)   # (g_x, g_y): sources rt g in momentum, m.g in energy (section 2)
+    hd_single_face: int = 0       # 1: hyper-diffusion ratio from the face itself (no max over 3 faces)
 
     @property
     def dx(self) -> float:
@@ -124,6 +126,7 @@ class Problem:
         p.c_shk = self.c_shk
         p.nthreads = self.nthreads
         p.grav[0], p.grav[1] = float(self.gravity[0]), float(self.gravity[1])
+        p.hd_single_face = int(self.hd_single_face)
         return p
 
 

@@ -37,6 +37,9 @@
  *       s_i = max(0, -(D_x v_x + D_y v_y)_i),  s_f = (s_i + s_{i+1}) / 2,
  *       nu_f = (c2_u dx cmax_d) R_f + (c_shk dx dx) s_f,
  *       H_i = (nu_{i+1/2} d1_{i+1/2} - nu_{i-1/2} d1_{i-1/2}) / (dx dx).
+ *     single-face variant (hd_single_face = 1, the minimal form of the same
+ *     section-2 description, stencil radius 2): R_f = |d3_f| / |d1_f| on the
+ *     face itself (0 if d1_f = 0).
  *   * k_u = (H_x + H_y) - (D_x F_x + D_y F_y).
  *   * gravity g (section 2: the rho g source of the momentum equation and its
  *     work term in the energy equation), with the background read as being in
@@ -79,6 +82,7 @@ typedef struct {
     double c_shk;         /* shock-viscosity coefficient */
     int nthreads;         /* OpenMP threads (<= 0: 1) */
     double grav[2];       /* gravitational acceleration (g_x, g_y); zero: no source */
+    int hd_single_face;   /* 1: hyper-diffusion ratio from the face itself, not the max over 3 faces */
 } orc_params;
 
 /* ghost-extended index: i in [-GH, nx+GH), j in [-GH, ny+GH) */
@@ -300,8 +304,8 @@ void orc_rhs(const orc_params *p, const double *w, const double *bg,
                                 a3[o + 1] = fabs(d3);
                                 if (o == 0) d1c = d1;
                             }
-                            double m1 = fmax(fmax(a1[0], a1[1]), a1[2]);
-                            double m3 = fmax(fmax(a3[0], a3[1]), a3[2]);
+                            double m1 = p->hd_single_face ? a1[1] : fmax(fmax(a1[0], a1[1]), a1[2]);
+                            double m3 = p->hd_single_face ? a3[1] : fmax(fmax(a3[0], a3[1]), a3[2]);
                             double r = (m1 > 0.0) ? m3 / m1 : 0.0;
                             double sf = 0.5 * (s[fc] + s[fc + S]);
                             double nu = a * r + bsh * sf;
