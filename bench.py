@@ -453,6 +453,12 @@ def run_ours(args, ws, rank, local, pg):
             msm = time_device_steps(sm_, args.steps, args.warmup, pg, torch)
             extra[f"ot{m}"] = {"value": ws * m * m * args.steps / (msm * 1e-3), "ms_per_step": msm / args.steps}
             del sm_
+        s4 = Solver(**kw, hd_single_face=1)
+        s4.set_state(pinned.numpy(), None, 0.0)
+        ms4 = time_device_steps(s4, args.steps, args.warmup, pg, torch)
+        extra["hd_single_face"] = {"value": ws * cells * args.steps / (ms4 * 1e-3), "ms_per_step": ms4 / args.steps,
+                                   "workload": "as the main line, hyper-diffusion ratio from the face itself"}
+        del s4
         extra["stratified_gravity"] = run_stratified(args, ws, local, pg, torch)
         extra["batched"] = run_batched(args, ws, local, pg, torch)
 

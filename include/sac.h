@@ -79,6 +79,12 @@ enum { SAC_FP64 = 0, SAC_FP32 = 1 };
  *                     the energy equation.  Nonzero gravity requires
  *                     has_background = 1 (a zero background array is allowed) and
  *                     is not supported by sac_batch_* or sac_step_noalloc.
+ *   hd_single_face    0: the hyper-diffusion ratio takes the maxima of |d3| and
+ *                     |d1| over the face and its two neighbours (default);
+ *                     1: it uses the face itself (stencil radius 2), the
+ *                     minimal form, for comparison.  FP32 supports 1 only
+ *                     without background and gravity; not in sac_batch_* or
+ *                     sac_step_noalloc.
  */
 typedef struct {
     int nx, ny;
@@ -93,6 +99,7 @@ typedef struct {
     int device;
     void *stream;
     double gravity[2];
+    int hd_single_face;
 } sac_params;
 
 /* Fill *p with defaults: 64x64 periodic on [0,1]^2, gamma 5/3, C 0.3, FP64,

@@ -261,7 +261,7 @@ int sac_batch_init(const sac_params* runs, int n, sac_batch** out)
     for (int i = 0; i < n; ++i) {
         if (runs[i].precision != SAC_FP32 || runs[i].device != runs[0].device || runs[i].stream != runs[0].stream ||
             runs[i].hyperdiffusion != runs[0].hyperdiffusion || runs[i].has_background != runs[0].has_background ||
-            runs[i].gravity[0] != 0.0 || runs[i].gravity[1] != 0.0)
+            runs[i].gravity[0] != 0.0 || runs[i].gravity[1] != 0.0 || runs[i].hd_single_face)
             return SAC_ERR_ARG;
     }
     sac_batch* b = new sac_batch();

@@ -10,13 +10,13 @@ using f32k::NT;
 using f32k::TX;
 using f32k::TY;
 
-template <int S, bool BG, bool HD, bool GR>
+template <int S, bool BG, bool HD, bool GR, bool SF>
 cudaError_t set_attr()
 {
-    cudaError_t e = cudaFuncSetAttribute(f32k::stage_fp32<S, BG, HD, GR>,
+    cudaError_t e = cudaFuncSetAttribute(f32k::stage_fp32<S, BG, HD, GR, SF>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(f32k::Smem));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(f32k::stage_fp32<S, BG, HD, GR>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(f32k::stage_fp32<S, BG, HD, GR, SF>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
     return e;
 }
@@ -31,12 +31,12 @@ __global__ void halo_fp32(const StageArgs<float> a, long long n)
         f32k::halo_cell(w, a.L, a.bc_x, a.bc_y, t);
 }
 
-template <int S, bool BG, bool HD, bool GR>
+template <int S, bool BG, bool HD, bool GR, bool SF>
 cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
 {
     const int ntx = (a.L.nx + TX - 1) / TX, nty = (a.L.ny + TY - 1) / TY, ntiles = ntx * nty;
     const int grid = ntiles < g_resident ? ntiles : g_resident;
-    f32k::stage_fp32<S, BG, HD, GR><<<grid, NT, sizeof(f32k::Smem), s>>>(a, ntx, ntiles);
+    f32k::stage_fp32<S, BG, HD, GR, SF><<<grid, NT, sizeof(f32k::Smem), s>>>(a, ntx, ntiles);
     if (a.bc_x != BC_FIXED || a.bc_y != BC_FIXED) {
         const long long n = f32k::halo_count(a.L);
         const int hb = (int)std::min<long long>((n + 255) / 256, g_resident * 2);
@@ -45,24 +45,24 @@ cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <bool BG, bool HD, bool GR = false>
+template <bool BG, bool HD, bool GR = false, bool SF = false>
 cudaError_t by_stage(const StageArgs<float>& a, int stage, cudaStream_t s)
 {
     switch (stage) {
-        case 1: return launch<1, BG, HD, GR>(a, s);
-        case 2: return launch<2, BG, HD, GR>(a, s);
-        case 3: return launch<3, BG, HD, GR>(a, s);
-        default: return launch<4, BG, HD, GR>(a, s);
+        case 1: return launch<1, BG, HD, GR, SF>(a, s);
+        case 2: return launch<2, BG, HD, GR, SF>(a, s);
+        case 3: return launch<3, BG, HD, GR, SF>(a, s);
+        default: return launch<4, BG, HD, GR, SF>(a, s);
     }
 }
 
-template <bool BG, bool HD, bool GR = false>
+template <bool BG, bool HD, bool GR = false, bool SF = false>
 cudaError_t attr_all()
 {
-    cudaError_t e = set_attr<1, BG, HD, GR>();
-    if (e == cudaSuccess) e = set_attr<2, BG, HD, GR>();
-    if (e == cudaSuccess) e = set_attr<3, BG, HD, GR>();
-    if (e == cudaSuccess) e = set_attr<4, BG, HD, GR>();
+    cudaError_t e = set_attr<1, BG, HD, GR, SF>();
+    if (e == cudaSuccess) e = set_attr<2, BG, HD, GR, SF>();
+    if (e == cudaSuccess) e = set_attr<3, BG, HD, GR, SF>();
+    if (e == cudaSuccess) e = set_attr<4, BG, HD, GR, SF>();
     return e;
 }
 }  // namespace
@@ -80,11 +80,14 @@ cudaError_t prepare_stage_fp32()
     if (e == cudaSuccess) e = attr_all<true, true>();
     if (e == cudaSuccess) e = attr_all<true, false, true>();
     if (e == cudaSuccess) e = attr_all<true, true, true>();
+    if (e == cudaSuccess) e = attr_all<false, true, false, true>();
     return e;
 }
 
 cudaError_t launch_stage_fp32(const StageArgs<float>& a, int stage, bool hd, bool bg, cudaStream_t s)
 {
+    // the single-face variant: no background, no gravity (checked by sac_init)
+    if (a.hd_single_face && hd) return by_stage<false, true, false, true>(a, stage, s);
     // gravity needs a background (checked by sac_init)
     if (bg && a.has_grav())
         return hd ? by_stage<true, true, true>(a, stage, s) : by_stage<true, false, true>(a, stage, s);

@@ -121,7 +121,7 @@ extern "C" int sac_step_noalloc(const sac_params* p, const float* w_in, float* w
 {
     if (!p || !w_in || !w_out) return SAC_ERR_ARG;
     if (p->precision != SAC_FP32 || p->has_background) return SAC_ERR_ARG;
-    if (p->gravity[0] != 0.0 || p->gravity[1] != 0.0) return SAC_ERR_ARG;
+    if (p->gravity[0] != 0.0 || p->gravity[1] != 0.0 || p->hd_single_face) return SAC_ERR_ARG;
     if (p->nx < 1 || p->ny < 1 || p->nx > 65536 || p->ny > 65536) return SAC_ERR_ARG;
     if (!(p->x1 > p->x0) || !(p->y1 > p->y0) || !(p->gamma > 1.0) || !(p->courant > 0.0)) return SAC_ERR_ARG;
     if (p->bc_x < 0 || p->bc_x > 2 || p->bc_y < 0 || p->bc_y > 2) return SAC_ERR_ARG;
@@ -166,6 +166,7 @@ extern "C" int sac_step_noalloc(const sac_params* p, const float* w_in, float* w
     for (int f = 0; f < NF; ++f) a.c2[f] = p->c2[f];
     a.c_shk = p->c_shk; a.bc_x = p->bc_x; a.bc_y = p->bc_y;
     a.grav[0] = a.grav[1] = 0.0;
+    a.hd_single_face = 0;
     a.derive_f32();
     for (int stage = 1; stage <= 4; ++stage) {
         a.sin = stage == 1 ? u0 : (stage == 2 ? sa : (stage == 3 ? sb : sa));

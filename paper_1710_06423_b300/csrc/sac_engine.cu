@@ -215,6 +215,7 @@ static void fill_stage_args(const sac_ctx* c, int stage, StageArgs<T>* a)
     for (int f = 0; f < NF; ++f) a->c2[f] = c->p.c2[f];
     a->c_shk = c->p.c_shk; a->bc_x = c->p.bc_x; a->bc_y = c->p.bc_y;
     a->grav[0] = c->p.gravity[0]; a->grav[1] = c->p.gravity[1];
+    a->hd_single_face = c->p.hd_single_face;
     a->derive_f32();
 }
 
@@ -396,6 +397,10 @@ int sac_init(const sac_params* p, sac_ctx** out)
     if (!(p->c_shk >= 0.0)) return SAC_ERR_ARG;
     if (!std::isfinite(p->gravity[0]) || !std::isfinite(p->gravity[1])) return SAC_ERR_ARG;
     if ((p->gravity[0] != 0.0 || p->gravity[1] != 0.0) && !p->has_background) return SAC_ERR_ARG;
+    if (p->hd_single_face != 0 && p->hd_single_face != 1) return SAC_ERR_ARG;
+    if (p->hd_single_face && p->precision == SAC_FP32 &&
+        (p->has_background || p->gravity[0] != 0.0 || p->gravity[1] != 0.0))
+        return SAC_ERR_ARG;
 
     c = new sac_ctx();
     c->p = *p;

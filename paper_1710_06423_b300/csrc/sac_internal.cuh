@@ -114,6 +114,7 @@ struct StageArgs {
     double c2[NF];
     double c_shk;
     int bc_x, bc_y;
+    int hd_single_face;   // 1: hyper-diffusion ratio from the face itself (no max over 3 faces)
     double grav[2];    // gravitational acceleration; sources rt g (momentum), m.g (energy)
     __host__ __device__ bool has_grav() const { return grav[0] != 0.0 || grav[1] != 0.0; }
     // FP32 kernels: the parameters above rounded once on the host, so a tile

@@ -236,6 +236,7 @@ __device__ __forceinline__ void halo_cell(float2* __restrict__ w, const Layout& 
 //   G_f  = (a R_f + (c_shk/2)(s_f + s_{f+1})) d1_f.
 // A zero denominator means d1 is zero on all three faces, so G is zero: the
 // denominator is clamped to 1e-30 and the product with d1 = 0 gives that 0.
+template <bool SF = false>
 __device__ __forceinline__ void face_fluxes(const float2 (&u)[SEG + 6], const float2 (&s2)[SEG + 2],
                                             float2 a, float2 bh, float2 (&G)[SEG + 1])
 {
@@ -251,10 +252,11 @@ __device__ __forceinline__ void face_fluxes(const float2 (&u)[SEG + 6], const fl
     }
 #pragma unroll
     for (int q = 1; q <= SEG + 1; ++q) {
-        const float m1x = fmaxf(max3(a1x[q - 1], a1x[q], a1x[q + 1]), 1e-30f);
-        const float m1y = fmaxf(max3(a1y[q - 1], a1y[q], a1y[q + 1]), 1e-30f);
-        const float m3x = max3(a3x[q - 1], a3x[q], a3x[q + 1]);
-        const float m3y = max3(a3y[q - 1], a3y[q], a3y[q + 1]);
+        // SF: the single-face variant takes the ratio from the face itself
+        const float m1x = fmaxf(SF ? a1x[q] : max3(a1x[q - 1], a1x[q], a1x[q + 1]), 1e-30f);
+        const float m1y = fmaxf(SF ? a1y[q] : max3(a1y[q - 1], a1y[q], a1y[q + 1]), 1e-30f);
+        const float m3x = SF ? a3x[q] : max3(a3x[q - 1], a3x[q], a3x[q + 1]);
+        const float m3y = SF ? a3y[q] : max3(a3y[q - 1], a3y[q], a3y[q + 1]);
         const float2 R = make_float2(fdiv(m3x, m1x), fdiv(m3y, m1y));
         const float2 sf = add2(s2[q - 1], s2[q]);
         const float2 nu = fma2(a, R, mul2(bh, sf));
@@ -371,7 +373,7 @@ __device__ __forceinline__ void stage_plane_bulk(const StageArgs<float>& a, Smem
 // land, the run's status becomes ST_ERR_TIMEOUT, *failed is set and every
 // thread returns.  S.ax/S.ay must hold the run's coefficients (store_hd_coeffs).
 // Stage 4 folds the signal speeds of the tile's new state into m.
-template <int STAGE, bool BG, bool HD, bool OVERLAP, bool GRAV = false>
+template <int STAGE, bool BG, bool HD, bool OVERLAP, bool GRAV = false, bool SF = false>
 __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x0, const int y0, Smem& S,
                                           const StepConsts& K, unsigned long long (&m)[2],
                                           const bool has_next = false, const int xn = 0, const int yn = 0,
@@ -561,7 +563,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 #pragma unroll
                 for (int q = 0; q < SEG + 2; ++q) s2[q] = splat(S.s[row + 1][x_0 + q]);
                 float2 G[SEG + 1];
-                face_fluxes(u, s2, S.ax[p], bh, G);
+                face_fluxes<SF>(u, s2, S.ax[p], bh, G);
 #pragma unroll
                 for (int q = 0; q < SEG; ++q) hx[q] = sub2(G[q + 1], G[q]);
             } else {
@@ -624,7 +626,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 #pragma unroll
             for (int q = 0; q < SEG + 2; ++q) s2[q] = splat(S.s[y_0 + q][col + 1]);
             float2 G[SEG + 1];
-            face_fluxes(u, s2, S.ay[p], bh, G);
+            face_fluxes<SF>(u, s2, S.ay[p], bh, G);
 #pragma unroll
             for (int q = 0; q < SEG; ++q) hy[q] = sub2(G[q + 1], G[q]);
         } else {
@@ -701,7 +703,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 // copies while it finishes the current one.
 // The step constants are read once; stage 4 keeps the signal-speed maximum of
 // all its tiles in registers and reduces it once at the end.
-template <int STAGE, bool BG, bool HD, bool GRAV>
+template <int STAGE, bool BG, bool HD, bool GRAV, bool SF = false>
 __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, const int ntx, const int ntiles)
 {
     if (a.sc->skip) return;
@@ -724,7 +726,7 @@ __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, co
     }
     for (; t < ntiles; t += gridDim.x) {
         const int tn = t + gridDim.x;
-        tile_body<STAGE, BG, HD, true, GRAV>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m, tn < ntiles,
+        tile_body<STAGE, BG, HD, true, GRAV, SF>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m, tn < ntiles,
                                              (tn % ntx) * TX, (tn / ntx) * TY, &bar, &phase, &failed);
         if (failed) return;
     }

@@ -256,6 +256,7 @@ stage_generic(const StageArgs<T> a)
             }
         }
         if constexpr (HD) {
+            const bool sface = a.hd_single_face != 0;   // ratio from the face itself (variant)
             const T ax = ((T)a.c2[f] * (T)a.dx) * cm[0], ay = ((T)a.c2[f] * (T)a.dy) * cm[1];
             const T bx_ = ((T)a.c_shk * (T)a.dx) * (T)a.dx, by_ = ((T)a.c_shk * (T)a.dy) * (T)a.dy;
             // x faces: face q sits between cells q and q+1, q in [x0-1, x0+TX)
@@ -271,8 +272,8 @@ stage_generic(const StageArgs<T> a)
                     a1[o + 1] = tabs(d1); a3[o + 1] = tabs(d3);
                     if (o == 0) d1c = d1;
                 }
-                T m1 = tmax(tmax(a1[0], a1[1]), a1[2]);
-                T m3 = tmax(tmax(a3[0], a3[1]), a3[2]);
+                T m1 = sface ? a1[1] : tmax(tmax(a1[0], a1[1]), a1[2]);
+                T m3 = sface ? a3[1] : tmax(tmax(a3[0], a3[1]), a3[2]);
                 T rr = (m1 > (T)0) ? m3 / m1 : (T)0;
                 int sidx = (r + 1) * (TX + 2) + q;   // s at cell q and q+1
                 T sf = half * (sS[sidx] + sS[sidx + 1]);
@@ -292,8 +293,8 @@ stage_generic(const StageArgs<T> a)
                     a1[o + 1] = tabs(d1); a3[o + 1] = tabs(d3);
                     if (o == 0) d1c = d1;
                 }
-                T m1 = tmax(tmax(a1[0], a1[1]), a1[2]);
-                T m3 = tmax(tmax(a3[0], a3[1]), a3[2]);
+                T m1 = sface ? a1[1] : tmax(tmax(a1[0], a1[1]), a1[2]);
+                T m3 = sface ? a3[1] : tmax(tmax(a3[0], a3[1]), a3[2]);
                 T rr = (m1 > (T)0) ? m3 / m1 : (T)0;
                 int sidx = q * (TX + 2) + (cc + 1);
                 T sf = half * (sS[sidx] + sS[sidx + TX + 2]);

@@ -60,6 +60,7 @@ class SacParams(ctypes.Structure):
         ("device", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("gravity", ctypes.c_double * 2),
+        ("hd_single_face", ctypes.c_int),
     ]
 
 
