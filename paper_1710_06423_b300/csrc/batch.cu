@@ -38,39 +38,95 @@ __global__ void batch_begin_kernel(const RunCtl* __restrict__ ctl, int n, unsign
     if (i < n) step_begin(ctl[i].sc, ctl[i].dx, ctl[i].dy, ctl[i].courant, 1, 0.0);
 }
 
+// Copy the arguments of run `run`, stage STAGE, into shared memory (all threads).
+template <int STAGE>
+__device__ __forceinline__ void load_args(const BatchArgs& b, int run, StageArgs<float>& dst)
+{
+    const int* src = reinterpret_cast<const int*>(&b.args[run * 4 + (STAGE - 1)]);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(StageArgs<float>) / sizeof(int)); k += blockDim.x) d[k] = src[k];
+}
+
 template <int STAGE, bool BG, bool HD>
 __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long red[2][f32k::NW];
-    __shared__ __align__(16) StageArgs<float> sa;
-    __shared__ int tile_s;
+    __shared__ __align__(16) StageArgs<float> sa[2];   // current / next tile's run
+    __shared__ int tile_s[2];
+    __shared__ __align__(8) unsigned long long bar;   // staging completion (persistent mode)
     f32k::Smem& S = *reinterpret_cast<f32k::Smem*>(smem_raw);
-    for (int it = 0;; ++it) {
-        if (threadIdx.x == 0) {
-            if (b.persistent) tile_s = (int)atomicAdd(&b.counters[STAGE - 1], 1u);
-            else tile_s = it == 0 ? (int)blockIdx.x : b.ntiles;
-        }
-        __syncthreads();
-        const int t = tile_s;
-        if (t >= b.ntiles) break;
+    if (!b.persistent) {
+        // one tile per CTA: stage inside the tile
+        const int t = blockIdx.x;
+        if (t >= b.ntiles) return;
         const int4 d = b.tiles[t];
-        {
-            // stage the run's arguments in shared memory (uniform reads from then on)
-            const int* src = reinterpret_cast<const int*>(&b.args[d.x * 4 + (STAGE - 1)]);
-            int* dst = reinterpret_cast<int*>(&sa);
-            for (int k = threadIdx.x; k < (int)(sizeof(StageArgs<float>) / sizeof(int)); k += blockDim.x)
-                dst[k] = src[k];
+        load_args<STAGE>(b, d.x, sa[0]);
+        __syncthreads();
+        if (!sa[0].sc->skip) {
+            f32k::store_hd_coeffs(sa[0], S, threadIdx.x);   // visible after the tile's staging barrier
+            const f32k::StepConsts K = f32k::load_step_consts(sa[0].sc);
+            unsigned long long m[2] = {0ull, 0ull};
+            f32k::tile_body<STAGE, BG, HD, false, false>(sa[0], d.y * f32k::TX, d.z * f32k::TY, S, K, m);
+            if (STAGE == 4) f32k::block_speed_max(m, red, sa[0].sc);
+        }
+        return;
+    }
+    // persistent: tiles from the queue; the next tile is fetched when a tile
+    // starts so that its region streams into shared memory (TMA bulk copies)
+    // during the current tile's Y sweep, with the next run's own layout
+    if (threadIdx.x == 0) {
+        f32k::mbar_init(&bar, 1);
+        tile_s[0] = (int)atomicAdd(&b.counters[STAGE - 1], 1u);
+    }
+    __syncthreads();
+    int cur = tile_s[0], buf = 0;
+    unsigned phase = 0;
+    bool failed = false;
+    if (cur >= b.ntiles) return;
+    int4 d = b.tiles[cur];
+    load_args<STAGE>(b, d.x, sa[0]);
+    __syncthreads();
+    bool staged = !sa[0].sc->skip;
+    if (staged) {
+        if (threadIdx.x == 0) f32k::mbar_expect_tx(&bar, f32k::kTileBytes);
+        const f32k::NextTile first = f32k::next_tile(sa[0], true, d.y * f32k::TX, d.z * f32k::TY);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) f32k::stage_plane_bulk(first, S, p, &bar);
+    }
+    while (true) {
+        if (threadIdx.x == 0) tile_s[buf ^ 1] = (int)atomicAdd(&b.counters[STAGE - 1], 1u);
+        __syncthreads();
+        const int nxt = tile_s[buf ^ 1];
+        int4 dn = make_int4(0, 0, 0, 0);
+        if (nxt < b.ntiles) {
+            dn = b.tiles[nxt];
+            load_args<STAGE>(b, dn.x, sa[buf ^ 1]);
         }
         __syncthreads();
-        if (!sa.sc->skip) {
-            f32k::store_hd_coeffs(sa, S, threadIdx.x);   // visible after the tile's staging barrier
-            const f32k::StepConsts K = f32k::load_step_consts(sa.sc);
+        const StageArgs<float>& A = sa[buf];
+        const bool nstage = nxt < b.ntiles && !sa[buf ^ 1].sc->skip;
+        const f32k::NextTile nt = f32k::next_tile(sa[buf ^ 1], nstage, dn.y * f32k::TX, dn.z * f32k::TY);
+        if (staged) {
+            f32k::store_hd_coeffs(A, S, threadIdx.x);
+            const f32k::StepConsts K = f32k::load_step_consts(A.sc);
             unsigned long long m[2] = {0ull, 0ull};
-            f32k::tile_body<STAGE, BG, HD, false, false>(sa, d.y * f32k::TX, d.z * f32k::TY, S, K, m);
-            if (STAGE == 4) f32k::block_speed_max(m, red, sa.sc);
+            f32k::tile_body<STAGE, BG, HD, true, false>(A, d.y * f32k::TX, d.z * f32k::TY, S, K, m, nt,
+                                                       &bar, &phase, &failed);
+            if (failed) return;
+            if (STAGE == 4) f32k::block_speed_max(m, red, A.sc);
+        } else if (nstage) {
+            // this tile's run is done or failed: nothing was staged for it, so
+            // the next tile's region is copied now
+            if (threadIdx.x == 0) f32k::mbar_expect_tx(&bar, f32k::kTileBytes);
+#pragma unroll
+            for (int p = 0; p < 3; ++p) f32k::stage_plane_bulk(nt, S, p, &bar);
         }
-        __syncthreads();   // shared memory and `sa` are reused by the next tile
+        if (nxt >= b.ntiles) break;
+        staged = nstage;
+        d = dn;
+        buf ^= 1;
+        __syncthreads();   // sa[buf ^ 1] is rewritten by the next iteration
     }
 }
 

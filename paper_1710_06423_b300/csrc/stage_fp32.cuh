@@ -354,13 +354,25 @@ __device__ __forceinline__ void load_pointwise(const StageArgs<float>& a, const 
 // copies, one 320-byte row per copy (lane k of warp w copies row w + NW k),
 // completing on the CTA's mbarrier; kTileBytes per tile (three planes).
 constexpr unsigned kTileBytes = 3u * RY * RX * sizeof(float2);
-__device__ __forceinline__ void stage_plane_bulk(const StageArgs<float>& a, Smem& S, const int x0, const int y0,
-                                                 const int p, unsigned long long* bar)
+// Where the next tile's staged region comes from: its tile origin and the
+// stencil input of its run (a batch's next tile may belong to another run).
+struct NextTile {
+    bool has;
+    int x0, y0;
+    const float* sin;
+    long long fstride;
+    int pitch;
+};
+__device__ __forceinline__ NextTile next_tile(const StageArgs<float>& a, bool has, int x0, int y0)
+{
+    return NextTile{has, x0, y0, a.sin, a.L.fstride, a.L.pitch};
+}
+__device__ __forceinline__ void stage_plane_bulk(const NextTile& n, Smem& S, const int p, unsigned long long* bar)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = warp + NW * lane;
     if (lane < (RY + NW - 1) / NW && r < RY) {
-        const float2* g = reinterpret_cast<const float2*>(a.sin) + p * a.L.fstride + (long long)(y0 + r) * a.L.pitch + x0;
+        const float2* g = reinterpret_cast<const float2*>(n.sin) + p * n.fstride + (long long)(n.y0 + r) * n.pitch + n.x0;
         bulk_row_g2s(smem_u32(&S.u[p][r][0]), g, RX * sizeof(float2), bar);
     }
 }
@@ -368,7 +380,7 @@ __device__ __forceinline__ void stage_plane_bulk(const StageArgs<float>& a, Smem
 // One tile (x0, y0) of one run; every thread of the CTA calls it (it holds
 // barriers).  OVERLAP: the caller has issued the bulk copies of this tile's
 // staged region on *bar (expected at parity *phase), and the Y sweep issues
-// those of the next tile (xn, yn; has_next) plane by plane as soon as the CTA
+// those of the next tile (nt, if nt.has) plane by plane as soon as the CTA
 // has read the plane it replaces.  The wait is bounded: if the copies do not
 // land, the run's status becomes ST_ERR_TIMEOUT, *failed is set and every
 // thread returns.  S.ax/S.ay must hold the run's coefficients (store_hd_coeffs).
@@ -376,7 +388,7 @@ __device__ __forceinline__ void stage_plane_bulk(const StageArgs<float>& a, Smem
 template <int STAGE, bool BG, bool HD, bool OVERLAP, bool GRAV = false, bool SF = false>
 __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x0, const int y0, Smem& S,
                                           const StepConsts& K, unsigned long long (&m)[2],
-                                          const bool has_next = false, const int xn = 0, const int yn = 0,
+                                          const NextTile& nt = NextTile{},
                                           unsigned long long* bar = nullptr, unsigned* phase = nullptr,
                                           bool* failed = nullptr)
 {
@@ -615,9 +627,9 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][y_0 + q][col + 4];
         if (OVERLAP) {
             __syncthreads();   // plane p of this tile is read for good
-            if (has_next) {
+            if (nt.has) {
                 if (p == 0 && threadIdx.x == 0) mbar_expect_tx(bar, kTileBytes);
-                stage_plane_bulk(a, S, xn, yn, p, bar);
+                stage_plane_bulk(nt, S, p, bar);
             }
         }
         float2 hy[SEG];
@@ -722,12 +734,13 @@ __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, co
     if (t < ntiles) {
         if (threadIdx.x == 0) mbar_expect_tx(&bar, kTileBytes);
 #pragma unroll
-        for (int p = 0; p < 3; ++p) stage_plane_bulk(a, S, (t % ntx) * TX, (t / ntx) * TY, p, &bar);
+        for (int p = 0; p < 3; ++p) stage_plane_bulk(next_tile(a, true, (t % ntx) * TX, (t / ntx) * TY), S, p, &bar);
     }
     for (; t < ntiles; t += gridDim.x) {
         const int tn = t + gridDim.x;
-        tile_body<STAGE, BG, HD, true, GRAV, SF>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m, tn < ntiles,
-                                             (tn % ntx) * TX, (tn / ntx) * TY, &bar, &phase, &failed);
+        tile_body<STAGE, BG, HD, true, GRAV, SF>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m,
+                                                 next_tile(a, tn < ntiles, (tn % ntx) * TX, (tn / ntx) * TY),
+                                                 &bar, &phase, &failed);
         if (failed) return;
     }
     if (STAGE == 4) block_speed_max(m, red, a.sc);
