@@ -227,18 +227,27 @@ __device__ __forceinline__ void halo_cell(float2* __restrict__ w, const Layout& 
     for (int p = 0; p < 3; ++p) w[p * L.fstride + dst] = w[p * L.fstride + src];
 }
 
+// The shock part of the face coefficients, bh (s_f + s_{f+1}) with
+// bh = c_shk / 2, on the SEG+1 faces of a segment, from the shock indicators
+// s2 of its SEG+2 cells; the same for all three pairs, so computed once.
+__device__ __forceinline__ void shock_faces(const float2 (&s2)[SEG + 2], float2 bh, float2 (&bsf)[SEG + 1])
+{
+#pragma unroll
+    for (int q = 1; q <= SEG + 1; ++q) bsf[q - 1] = mul2(bh, add2(s2[q - 1], s2[q]));
+}
+
 // Face hyper-diffusion fluxes G (already divided by d^2) on the SEG+1 faces
 // around a segment of SEG cells, from the SEG+6 values u of the segment plus
-// a 3-cell halo on each side, and the duplicated shock indicators s2 of the
-// SEG+2 cells around it:
+// a 3-cell halo on each side, and the shock parts bsf of the face
+// coefficients (shock_faces):
 //   d1_f = u_{f+1} - u_f,   d3_f = (u_{f+2} - u_{f-1}) - 3 d1_f,
 //   R_f  = max(|d3_{f-1}|,|d3_f|,|d3_{f+1}|) / max(|d1_{f-1}|,|d1_f|,|d1_{f+1}|)  (0 if 0/0),
 //   G_f  = (a R_f + (c_shk/2)(s_f + s_{f+1})) d1_f.
 // A zero denominator means d1 is zero on all three faces, so G is zero: the
 // denominator is clamped to 1e-30 and the product with d1 = 0 gives that 0.
 template <bool SF = false>
-__device__ __forceinline__ void face_fluxes(const float2 (&u)[SEG + 6], const float2 (&s2)[SEG + 2],
-                                            float2 a, float2 bh, float2 (&G)[SEG + 1])
+__device__ __forceinline__ void face_fluxes(const float2 (&u)[SEG + 6], const float2 (&bsf)[SEG + 1],
+                                            float2 a, float2 (&G)[SEG + 1])
 {
     const float2 m3 = splat(-3.f);
     float2 d1[SEG + 3];
@@ -258,8 +267,7 @@ __device__ __forceinline__ void face_fluxes(const float2 (&u)[SEG + 6], const fl
         const float m3x = SF ? a3x[q] : max3(a3x[q - 1], a3x[q], a3x[q + 1]);
         const float m3y = SF ? a3y[q] : max3(a3y[q - 1], a3y[q], a3y[q + 1]);
         const float2 R = make_float2(fdiv(m3x, m1x), fdiv(m3y, m1y));
-        const float2 sf = add2(s2[q - 1], s2[q]);
-        const float2 nu = fma2(a, R, mul2(bh, sf));
+        const float2 nu = fma2(a, R, bsf[q - 1]);
         G[q - 1] = mul2(nu, d1[q]);
     }
 }
@@ -564,6 +572,13 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     {
         const int row = lane, x_0 = warp * SEG;
         float2 kx[3][SEG];
+        float2 bsfx[SEG + 1];
+        if constexpr (HD) {
+            float2 s2[SEG + 2];   // cells x_0-1 .. x_0+SEG (shock col = cell + 1)
+#pragma unroll
+            for (int q = 0; q < SEG + 2; ++q) s2[q] = splat(S.s[row + 1][x_0 + q]);
+            shock_faces(s2, bh, bsfx);
+        }
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
             float2 u[SEG + 6];   // cells x_0-3 .. x_0+SEG+2 (region col = cell + 4)
@@ -571,11 +586,8 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][row + 3][x_0 + 1 + q];
             float2 hx[SEG];
             if constexpr (HD) {
-                float2 s2[SEG + 2];   // cells x_0-1 .. x_0+SEG (shock col = cell + 1)
-#pragma unroll
-                for (int q = 0; q < SEG + 2; ++q) s2[q] = splat(S.s[row + 1][x_0 + q]);
                 float2 G[SEG + 1];
-                face_fluxes<SF>(u, s2, S.ax[p], bh, G);
+                face_fluxes<SF>(u, bsfx, S.ax[p], G);
 #pragma unroll
                 for (int q = 0; q < SEG; ++q) hx[q] = sub2(G[q + 1], G[q]);
             } else {
@@ -610,6 +622,13 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     float rcen[SEG];   // GRAV: rt at this thread's cells (pair 0), for the momentum source
     const float gxv = a.f_grav[0], gyv = a.f_grav[1];
 
+    float2 bsfy[SEG + 1];
+    if constexpr (HD) {
+        float2 s2[SEG + 2];   // rows y_0-1 .. y_0+SEG (shock row = cell row + 1)
+#pragma unroll
+        for (int q = 0; q < SEG + 2; ++q) s2[q] = splat(S.s[y_0 + q][col + 1]);
+        shock_faces(s2, bh, bsfy);
+    }
     // (those of the third pair are loaded while the second is swept)
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
@@ -634,11 +653,8 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         }
         float2 hy[SEG];
         if constexpr (HD) {
-            float2 s2[SEG + 2];   // rows y_0-1 .. y_0+SEG (shock row = cell row + 1)
-#pragma unroll
-            for (int q = 0; q < SEG + 2; ++q) s2[q] = splat(S.s[y_0 + q][col + 1]);
             float2 G[SEG + 1];
-            face_fluxes<SF>(u, s2, S.ay[p], bh, G);
+            face_fluxes<SF>(u, bsfy, S.ay[p], G);
 #pragma unroll
             for (int q = 0; q < SEG; ++q) hy[q] = sub2(G[q + 1], G[q]);
         } else {
