@@ -17,14 +17,17 @@
 //      the x fluxes (cells x0-2..x0+TX+1 of the tile rows) and y fluxes
 //      (rows y0-2..y0+TY+1 of the tile columns) of all three pairs;
 //   2. shock indicator s = max(0, -div v) around the tile;
-//   3. X sweep: each thread walks 8 cells of one row with register windows:
-//      face differences d1, d3, the max over three faces, the face
+//   3. X sweep: each thread walks SEG = 4 cells of one row with register
+//      windows: face differences d1, d3, the max over three faces, the face
 //      hyper-diffusion flux and the x flux derivative -> k_x (kept in shared
 //      memory over the dead x-flux buffer);
-//   4. Y sweep: each thread walks 8 cells of one column the same way, adds
+//   4. Y sweep: each thread walks 4 cells of one column the same way, adds
 //      k_x, applies the RK stage update (D scheme, see below), stores the
 //      stage output and, in stage 4, folds the signal speed of the new state
-//      into a per-thread maximum (reduced once per CTA).
+//      into a per-thread maximum (reduced once per CTA).  Its plane loop
+//      issues the next tile's staging plane by plane.
+// The RK registers U0/D of a thread's Y-sweep cells are prefetched into L2
+// when the tile starts and loaded into registers ahead of their use.
 // A small kernel after each stage fills the ghost frame of the output
 // (periodic/outflow copies), so the tile code has no boundary cases.
 //
