@@ -218,3 +218,124 @@ def run(pr: Problem, w, t0: float = 0.0, t_end: float = float("inf"), max_steps:
     if rc != 0:
         raise FloatingPointError(f"oracle run stopped: non-finite step after {steps.value} steps")
     return w, t.value, steps.value
+
+
+# ---- 3D form (eight fields rho, m_x, m_y, m_z, e, B_x, B_y, B_z; periodic) -----
+_SRC3 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "sac_oracle3d.c")
+_LIB3 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsac_oracle3d.so")
+NF3 = 8
+DEFAULT_C2_3D = (0.02, 0.1, 0.1, 0.1, 0.02, 0.02, 0.02, 0.02)
+
+
+def build3(force: bool = False) -> str:
+    """Compile ``sac_oracle3d.c`` into ``libsac_oracle3d.so`` (same flags as the 2D oracle)."""
+    if force or not os.path.exists(_LIB3) or os.path.getmtime(_LIB3) < os.path.getmtime(_SRC3):
+        tmp = _LIB3 + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                        "-fPIC", "-shared", "-o", tmp, _SRC3, "-lm"], check=True)
+        os.replace(tmp, _LIB3)
+    return _LIB3
+
+
+class _Params3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("courant", ctypes.c_double),
+        ("hyperdiffusion", ctypes.c_int),
+        ("c2", ctypes.c_double * NF3),
+        ("c_shk", ctypes.c_double),
+        ("nthreads", ctypes.c_int),
+    ]
+
+
+_lib3 = None
+
+
+def _load3():
+    global _lib3
+    if _lib3 is None:
+        lib = ctypes.CDLL(build3())
+        P = ctypes.POINTER(_Params3)
+        dp = ctypes.POINTER(ctypes.c_double)
+        d = ctypes.c_double
+        lib.orc3_rhs.argtypes = [P, dp, d, d, d, dp]
+        lib.orc3_cmax.argtypes = [P, dp, dp, dp, dp]
+        lib.orc3_cfl_dt.argtypes = [P, d, d, d]
+        lib.orc3_cfl_dt.restype = d
+        lib.orc3_rk4_step.argtypes = [P, dp, d, d, d, d]
+        lib.orc3_run.argtypes = [P, dp, dp, ctypes.c_long, d, ctypes.POINTER(ctypes.c_long)]
+        lib.orc3_run.restype = ctypes.c_int
+        _lib3 = lib
+    return _lib3
+
+
+@dataclass
+class Problem3:
+    """Periodic 3D grid on [x0,x1] x [y0,y1] x [z0,z1] (cell-centred)."""
+    nx: int
+    ny: int
+    nz: int
+    x0: float = 0.0
+    x1: float = 1.0
+    y0: float = 0.0
+    y1: float = 1.0
+    z0: float = 0.0
+    z1: float = 1.0
+    gamma: float = 5.0 / 3.0
+    courant: float = 0.3
+    hyperdiffusion: int = 1
+    c2: tuple = DEFAULT_C2_3D
+    c_shk: float = DEFAULT_CSHK
+    nthreads: int = field(default_factory=lambda: int(os.environ.get("ORACLE_THREADS", os.cpu_count() or 1)))
+
+    def _c(self) -> _Params3:
+        p = _Params3()
+        p.nx, p.ny, p.nz = self.nx, self.ny, self.nz
+        p.dx, p.dy, p.dz = (self.x1 - self.x0) / self.nx, (self.y1 - self.y0) / self.ny, (self.z1 - self.z0) / self.nz
+        p.gamma, p.courant = self.gamma, self.courant
+        p.hyperdiffusion = self.hyperdiffusion
+        for i, v in enumerate(self.c2):
+            p.c2[i] = v
+        p.c_shk = self.c_shk
+        p.nthreads = self.nthreads
+        return p
+
+
+def _state3(w, pr: Problem3):
+    a = np.ascontiguousarray(w, dtype=np.float64)
+    if a.shape != (NF3, pr.nz, pr.ny, pr.nx):
+        raise ValueError(f"state must be ({NF3}, {pr.nz}, {pr.ny}, {pr.nx}), got {a.shape}")
+    return a
+
+
+def rhs3(pr: Problem3, w, cmax=(0.0, 0.0, 0.0)) -> np.ndarray:
+    lib = _load3()
+    w = _state3(w, pr)
+    k = np.empty_like(w)
+    lib.orc3_rhs(ctypes.byref(pr._c()), _dp(w), cmax[0], cmax[1], cmax[2], _dp(k))
+    return k
+
+
+def cmax3(pr: Problem3, w) -> tuple[float, float, float]:
+    lib = _load3()
+    w = _state3(w, pr)
+    c = [ctypes.c_double() for _ in range(3)]
+    lib.orc3_cmax(ctypes.byref(pr._c()), _dp(w), *[ctypes.byref(x) for x in c])
+    return tuple(x.value for x in c)
+
+
+def cfl_dt3(pr: Problem3, cx: float, cy: float, cz: float) -> float:
+    return _load3().orc3_cfl_dt(ctypes.byref(pr._c()), cx, cy, cz)
+
+
+def run3(pr: Problem3, w, max_steps: int, fixed_dt: float = 0.0, t0: float = 0.0):
+    """max_steps CFL steps (or fixed_dt > 0); returns (w, t, steps)."""
+    lib = _load3()
+    w = _state3(w, pr).copy()
+    t = ctypes.c_double(t0)
+    steps = ctypes.c_long(0)
+    rc = lib.orc3_run(ctypes.byref(pr._c()), _dp(w), ctypes.byref(t), max_steps, fixed_dt, ctypes.byref(steps))
+    if rc != 0:
+        raise FloatingPointError(f"oracle 3D run turned non-finite after {steps.value} steps")
+    return w, t.value, steps.value
