@@ -377,10 +377,32 @@ def run_stratified(args, ws, local, pg, torch, n=4000):
             "bytes_per_cell_stage": 90.0 + 16.0}
 
 
+def run_3d(args, ws, local, pg, torch, n=256):
+    """The 3D form (eight fields, periodic box): a 3D Orszag-Tang variant, n^3 FP32,
+    hyper-diffusion on.  Each step synchronises once for its signal speeds."""
+    from paper_1710_06423_b300 import inputs
+    from paper_1710_06423_b300.sac import FP32, Solver3
+    with Solver3(nx=n, ny=n, nz=n, precision=FP32, device=local) as s:
+        s.set_state(inputs.ot_3d(n, n, n), 0.0)
+        stream = torch.cuda.current_stream()
+        s.steps(args.warmup)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.steps(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = reduce_max(ev0.elapsed_time(ev1), pg, "cuda")
+    return {"value": ws * n ** 3 * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            "workload": f"3D orszag-tang variant {n}^3, periodic, FP32, hyper-diffusion on"}
+
+
 def run_ours(args, ws, rank, local, pg):
     import torch
     from paper_1710_06423_b300 import inputs
-    from paper_1710_06423_b300.sac import FP32, Solver
+    from paper_1710_06423_b300.sac import FP32, FP64, Solver
 
     torch.cuda.set_device(local)
     n = args.size
@@ -459,8 +481,17 @@ def run_ours(args, ws, rank, local, pg):
         extra["hd_single_face"] = {"value": ws * cells * args.steps / (ms4 * 1e-3), "ms_per_step": ms4 / args.steps,
                                    "workload": "as the main line, hyper-diffusion ratio from the face itself"}
         del s4
+        # C1: Orszag-Tang 1000^2, 200 steps, FP64 (the oracle-order correctness path) and FP32
+        for prec, name in ((FP64, "ot1000_fp64"), (FP32, "ot1000_fp32")):
+            s5 = Solver(nx=1000, ny=1000, precision=prec, device=local)
+            s5.set_state(inputs.orszag_tang(1000), None, 0.0)
+            ms5 = time_device_steps(s5, 200, args.warmup, pg, torch)
+            extra[name] = {"value": ws * 1000 * 1000 * 200 / (ms5 * 1e-3), "ms_per_step": ms5 / 200,
+                           "workload": "orszag-tang 1000x1000, 200 RK4 steps, no noise"}
+            del s5
         extra["stratified_gravity"] = run_stratified(args, ws, local, pg, torch)
         extra["batched"] = run_batched(args, ws, local, pg, torch)
+        extra["ot3d_256"] = run_3d(args, ws, local, pg, torch)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

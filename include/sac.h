@@ -322,6 +322,57 @@ int sac_block_average(const float *fine_dev, int nfields, int nxf, int nyf, int 
 #define SAC_ERR_TOO_LARGE (-7)
 int sac_step_noalloc(const sac_params *p, const float *w_in, float *w_out, double dt, double *dt_taken);
 
+/* -------------------------------------------------------------------------
+ * 3D form (the same method with three-component vectors; section 2 writes the
+ * equations for vector fields and the paper runs them in 2D): eight conserved
+ * fields rho, m_x, m_y, m_z, e, B_x, B_y, B_z on a periodic box, no background,
+ * hyper-diffusion with the maxima over three faces, classical RK4, CFL step
+ * dt = C min(min(dx/cmax_x, dy/cmax_y), dz/cmax_z).  FP64 agrees with the FP64
+ * 3D oracle to rounding order; FP32 stores and computes in single precision.
+ * All calls are synchronous.
+ * ------------------------------------------------------------------------- */
+typedef struct sac3_ctx sac3_ctx;
+
+/*
+ *   nx, ny, nz        interior cells, 1 .. 4096 each; periodic in every direction
+ *   x0..z1            box; cell-centred grid
+ *   gamma, courant    as in sac_params
+ *   precision         SAC_FP64 or SAC_FP32
+ *   hyperdiffusion    1: hyper-diffusion and shock viscosity on
+ *   c2[8]             hyper-diffusion coefficient per field (rho, m_x, m_y, m_z, e, B_x, B_y, B_z)
+ *   c_shk             shock-viscosity coefficient
+ *   device, stream    CUDA device and stream (NULL = default)
+ */
+typedef struct {
+    int nx, ny, nz;
+    double x0, x1, y0, y1, z0, z1;
+    double gamma, courant;
+    int precision;
+    int hyperdiffusion;
+    double c2[8];
+    double c_shk;
+    int device;
+    void *stream;
+} sac3_params;
+
+/* Defaults: 32^3 on [0,1]^3, gamma 5/3, C 0.3, FP64, HD on,
+ * c2 = (0.02, 0.1, 0.1, 0.1, 0.02, 0.02, 0.02, 0.02), c_shk 0.5, device 0. */
+void sac3_default_params(sac3_params *p);
+/* Validate *p and allocate one run.  Errors: SAC_ERR_ARG, SAC_ERR_OOM, SAC_ERR_CUDA. */
+int sac3_init(const sac3_params *p, sac3_ctx **out);
+void sac3_free(sac3_ctx *c);
+const char *sac3_last_error(const sac3_ctx *c);
+/* State w: host FP64 array [8][nz][ny][nx] (copied; caller keeps ownership). */
+int sac3_set_state(sac3_ctx *c, const double *w, double t);
+int sac3_get_state(sac3_ctx *c, double *w, double *t);
+/* One RK4 step: dt > 0 is used as given, dt <= 0 takes the CFL step;
+ * *dt_taken (may be NULL) receives it.  SAC_ERR_NONFINITE if the state's signal
+ * speeds or the step are not finite. */
+int sac3_step(sac3_ctx *c, double dt, double *dt_taken);
+/* n CFL steps. */
+int sac3_steps(sac3_ctx *c, long n);
+double sac3_time(const sac3_ctx *c);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ UNITS = [
     ("batch.cu", []),
     ("cnn.cu", []),
     ("noalloc.cu", []),
+    ("sac3d.cu", ["--fmad=false"]),
 ]
 
 

@@ -159,3 +159,26 @@ def gaussian_blob(nx: int, ny: int, *, amp: float, centre=(0.5, 0.5), width: flo
     y = cell_centres(ny)[:, None]
     r2 = (x - centre[0]) ** 2 + (y - centre[1]) ** 2
     return np.ascontiguousarray(amp * np.exp(-r2 / (width * width)))
+
+
+def ot_3d(nx: int, ny: int, nz: int, *, gamma: float = 5.0 / 3.0, b0: float = 1.0 / math.sqrt(4.0 * math.pi),
+          tilt: float = 0.2) -> np.ndarray:
+    """A three-dimensional variant of the Orszag-Tang vortex on [0,1]^3: the 2D
+    vortex plus z-dependent velocity and field components of relative size
+    `tilt` (smooth, periodic, divergence-free B).  Eight conserved fields
+    (rho, m_x, m_y, m_z, e, B_x, B_y, B_z), shape (8, nz, ny, nx)."""
+    x = cell_centres(nx)[None, None, :]
+    y = cell_centres(ny)[None, :, None]
+    z = cell_centres(nz)[:, None, None]
+    tp = 2.0 * math.pi
+    one = np.ones((nz, ny, nx))
+    rho = 25.0 / (36.0 * math.pi) * one
+    p = 5.0 / (12.0 * math.pi) * one
+    vx = -np.sin(tp * y) + tilt * np.sin(tp * z) * one
+    vy = np.sin(tp * x) + tilt * np.cos(tp * z) * one
+    vz = tilt * np.sin(tp * (x + y)) * one
+    bx = b0 * (-np.sin(tp * y) + tilt * np.cos(tp * z)) * one
+    by = b0 * (np.sin(2 * tp * x) + tilt * np.sin(tp * z)) * one
+    bz = b0 * tilt * np.cos(tp * (x - y)) * one
+    e = p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy + vz * vz) + 0.5 * (bx * bx + by * by + bz * bz)
+    return np.ascontiguousarray(np.stack([rho, rho * vx, rho * vy, rho * vz, e, bx, by, bz]).astype(np.float64))

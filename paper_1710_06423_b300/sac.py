@@ -35,6 +35,8 @@ EXPORTS = (
     "sac_cnn_get_params", "sac_cnn_set_scales", "sac_cnn_forward", "sac_cnn_grads", "sac_cnn_train_step",
     "sac_cnn_apply", "sac_cnn_perturb", "sac_block_average",
     "sac_step_noalloc",
+    "sac3_default_params", "sac3_init", "sac3_free", "sac3_last_error", "sac3_set_state", "sac3_get_state",
+    "sac3_step", "sac3_steps", "sac3_time",
 )
 
 
@@ -64,6 +66,23 @@ class SacParams(ctypes.Structure):
     ]
 
 
+class Sac3Params(ctypes.Structure):
+    """Mirror of ``sac3_params`` (include/sac.h)."""
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("z0", ctypes.c_double), ("z1", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("courant", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("hyperdiffusion", ctypes.c_int),
+        ("c2", ctypes.c_double * 8),
+        ("c_shk", ctypes.c_double),
+        ("device", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 _lib = None
 
 
@@ -77,6 +96,7 @@ def load() -> ctypes.CDLL:
     lib = ctypes.CDLL(LIB_PATH)
     vp, dp, i, d, L = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_long
     P = ctypes.POINTER(SacParams)
+    P3 = ctypes.POINTER(Sac3Params)
     sig = {
         "sac_default_params": (None, [P]),
         "sac_init": (i, [P, ctypes.POINTER(vp)]),
@@ -121,6 +141,15 @@ def load() -> ctypes.CDLL:
         "sac_cnn_perturb": (i, [vp, vp, vp, ctypes.POINTER(ctypes.c_float), ctypes.c_ulonglong]),
         "sac_block_average": (i, [vp, i, i, i, i, vp, vp]),
         "sac_step_noalloc": (i, [P, vp, vp, d, dp]),
+        "sac3_default_params": (None, [P3]),
+        "sac3_init": (i, [P3, ctypes.POINTER(vp)]),
+        "sac3_free": (None, [vp]),
+        "sac3_last_error": (ctypes.c_char_p, [vp]),
+        "sac3_set_state": (i, [vp, dp, d]),
+        "sac3_get_state": (i, [vp, dp, dp]),
+        "sac3_step": (i, [vp, d, dp]),
+        "sac3_steps": (i, [vp, L]),
+        "sac3_time": (d, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -490,3 +519,79 @@ def step_noalloc(w_in, w_out, dt: float = 0.0, wait: bool = True, **kw) -> float
     if rc != SAC_OK:
         raise SacError(rc, f"sac_step_noalloc: {lib.sac_status_string(rc).decode()}")
     return out.value
+
+
+class Solver3:
+    """One periodic 3D run (eight fields rho, m_x, m_y, m_z, e, B_x, B_y, B_z):
+    ``Solver3(nx=..., ny=..., nz=..., precision=FP32)``; states are FP64 host
+    arrays of shape (8, nz, ny, nx).  Calls are synchronous."""
+
+    def __init__(self, stream="current", **kw):
+        lib = load()
+        p = Sac3Params()
+        lib.sac3_default_params(ctypes.byref(p))
+        for k, v in kw.items():
+            if k == "c2":
+                for j, x in enumerate(v):
+                    p.c2[j] = x
+            else:
+                setattr(p, k, v)
+        if stream == "current":
+            import torch
+            stream = torch.cuda.current_stream(p.device)
+        if stream is not None and not isinstance(stream, int):
+            stream = stream.cuda_stream
+        p.stream = stream or None
+        self.params = p
+        self._ctx = ctypes.c_void_p()
+        rc = lib.sac3_init(ctypes.byref(p), ctypes.byref(self._ctx))
+        if rc != SAC_OK:
+            raise SacError(rc, f"sac3_init failed: {lib.sac_status_string(rc).decode()}")
+        self.shape = (8, p.nz, p.ny, p.nx)
+
+    def _check(self, rc: int, what: str):
+        if rc != SAC_OK:
+            lib = load()
+            raise SacError(rc, f"{what}: {lib.sac_status_string(rc).decode()}: {lib.sac3_last_error(self._ctx).decode()}")
+
+    def set_state(self, w, t: float = 0.0):
+        a = np.ascontiguousarray(w, dtype=np.float64)
+        if a.shape != self.shape:
+            raise ValueError(f"state must be {self.shape}, got {a.shape}")
+        self._check(load().sac3_set_state(self._ctx, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), t),
+                    "sac3_set_state")
+
+    def get_state(self):
+        w = np.empty(self.shape, dtype=np.float64)
+        t = ctypes.c_double()
+        self._check(load().sac3_get_state(self._ctx, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          ctypes.byref(t)), "sac3_get_state")
+        return w, t.value
+
+    def step(self, dt: float = 0.0) -> float:
+        out = ctypes.c_double()
+        self._check(load().sac3_step(self._ctx, dt, ctypes.byref(out)), "sac3_step")
+        return out.value
+
+    def steps(self, n: int):
+        self._check(load().sac3_steps(self._ctx, n), "sac3_steps")
+
+    def time(self) -> float:
+        return load().sac3_time(self._ctx)
+
+    def close(self):
+        if self._ctx:
+            load().sac3_free(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

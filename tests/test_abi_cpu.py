@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared(header):
     src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sac_[a-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(sac3?_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -59,3 +59,15 @@ def test_status_strings(lib):
     assert lib.sac_status_string(0) == b"SAC_OK"
     assert lib.sac_status_string(-5) == b"SAC_ERR_NONFINITE"
     assert lib.sac_status_string(3) == b"SAC_UNKNOWN"
+
+
+def test_params3_struct_layout_matches_header(lib):
+    """3D defaults round-trip through the C struct (catches a field-order mismatch)."""
+    from paper_1710_06423_b300 import sac
+    p = sac.Sac3Params()
+    lib.sac3_default_params(ctypes.byref(p))
+    assert (p.nx, p.ny, p.nz) == (32, 32, 32)
+    assert (p.x1, p.y1, p.z1) == (1.0, 1.0, 1.0)
+    assert abs(p.gamma - 5 / 3) < 1e-15 and p.courant == 0.3 and p.hyperdiffusion == 1
+    assert list(p.c2) == [0.02, 0.1, 0.1, 0.1, 0.02, 0.02, 0.02, 0.02] and p.c_shk == 0.5
+    assert p.precision == sac.FP64 and p.device == 0 and not p.stream

@@ -1,0 +1,74 @@
+"""The 3D form on the GPU against the FP64 3D oracle (and, for z-uniform
+states, against the 2D solver)."""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL_FP32_L1, TOL_FP64, l1rel, maxrel
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    n = a.shape[0]
+    return maxrel(a.reshape(n, -1), b.reshape(n, -1))
+
+
+@pytest.mark.parametrize("nx,ny,nz,steps", [(12, 10, 8, 3), (16, 16, 16, 2)])
+def test_fp64_matches_oracle(oracle_mod, inputs_mod, nx, ny, nz, steps):
+    from paper_1710_06423_b300.sac import FP64, Solver3
+    w = inputs_mod.ot_3d(nx, ny, nz)
+    pr = oracle_mod.Problem3(nx=nx, ny=ny, nz=nz)
+    ref, t_ref, _ = oracle_mod.run3(pr, w, max_steps=steps)
+    with Solver3(nx=nx, ny=ny, nz=nz, precision=FP64) as s:
+        s.set_state(w, 0.0)
+        s.steps(steps)
+        got, t = s.get_state()
+    assert t == t_ref
+    assert np.all(_rel(got, ref) <= TOL_FP64), _rel(got, ref)
+
+
+def test_fp32_matches_oracle(oracle_mod, inputs_mod):
+    from paper_1710_06423_b300.sac import FP32, Solver3
+    n, steps = 24, 10
+    w = inputs_mod.ot_3d(n, n, n)
+    pr = oracle_mod.Problem3(nx=n, ny=n, nz=n)
+    ref, t_ref, _ = oracle_mod.run3(pr, w, max_steps=steps)
+    with Solver3(nx=n, ny=n, nz=n, precision=FP32) as s:
+        s.set_state(w, 0.0)
+        s.steps(steps)
+        got, t = s.get_state()
+    assert t == pytest.approx(t_ref, rel=1e-6)
+    err = l1rel(got.reshape(8, -1), ref.reshape(8, -1))
+    assert np.all(err <= TOL_FP32_L1), err
+
+
+def test_z_uniform_matches_2d_solver(inputs_mod):
+    from paper_1710_06423_b300.sac import FP64, Solver, Solver3
+    nx, ny, nz = 40, 24, 2
+    w2 = inputs_mod.orszag_tang(nx, ny, noise=1e-3, seed=11)
+    r, mx, my, e, bx, by = w2
+    z = np.zeros_like(r)
+    w3 = np.ascontiguousarray(np.stack([np.broadcast_to(a, (nz, ny, nx)) for a in (r, mx, my, z, e, bx, by, z)]))
+    with Solver(nx=nx, ny=ny, precision=FP64, c2=(0.02, 0.1, 0.1, 0.02, 0.02, 0.02)) as s2:
+        s2.set_state(w2, None, 0.0)
+        s2.steps(3)
+        ref, t2 = s2.get_state()
+    with Solver3(nx=nx, ny=ny, nz=nz, z1=100.0, precision=FP64) as s3:
+        s3.set_state(w3, 0.0)
+        s3.steps(3)
+        got, t3 = s3.get_state()
+    assert t3 == t2
+    for kz in range(nz):
+        assert np.all(maxrel(got[[0, 1, 2, 4, 5, 6], kz], ref) <= TOL_FP64)
+
+
+def test_nonfinite_state_is_reported():
+    from paper_1710_06423_b300.sac import FP32, SacError, Solver3
+    n = 8
+    w = np.zeros((8, n, n, n))
+    w[0] = -1.0                                   # negative density: no real signal speed
+    w[4] = 1.0
+    with Solver3(nx=n, ny=n, nz=n, precision=FP32) as s:
+        s.set_state(w, 0.0)
+        with pytest.raises(SacError):
+            s.step()
