@@ -32,31 +32,40 @@
 namespace {
 
 constexpr int NF3 = 8;   // rho, m_x, m_y, m_z, e, B_x, B_y, B_z
-constexpr int G3 = 3;    // ghost width
+constexpr int G3 = 3;    // ghost width in y and z (and at least this in x)
+constexpr int GX = 4;    // left ghost width in x: with ex a multiple of 4 every row
+                         // segment starting at a multiple of 4 cells is 16-byte aligned
 
 struct Grid3 {
     int nx, ny, nz;
-    long long ex, ey, ez;   // ghost-extended extents
+    long long ex, ey, ez;   // ghost-extended extents: ex = round_up(nx + 8, 4), ey = ny + 6, ez = nz + 6
     long long ne;           // cells per extended field
     __host__ __device__ long long at(int i, int j, int k) const
     {
-        return ((long long)(k + G3) * ey + (j + G3)) * ex + (i + G3);
+        return ((long long)(k + G3) * ey + (j + G3)) * ex + (i + GX);
     }
 };
 
 __device__ __forceinline__ int wrapn(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
 
+// periodic ghost frame: one block per extended row (y, z); ghost rows are copied
+// whole from their wrapped interior row, interior rows get their x ghosts.  Only
+// interior cells are read, so the copies are independent of one another.
 template <typename T>
 __global__ void ghosts3(T* __restrict__ s, Grid3 g)
 {
-    const long long tot = g.ne * NF3;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-        const int f = (int)(t / g.ne);
-        const long long c = t - (long long)f * g.ne;
-        const int i = (int)(c % g.ex) - G3, j = (int)((c / g.ex) % g.ey) - G3, k = (int)(c / (g.ex * g.ey)) - G3;
-        if (i >= 0 && i < g.nx && j >= 0 && j < g.ny && k >= 0 && k < g.nz) continue;
+    const int row = blockIdx.x;                       // 0 .. ey*ez - 1
+    const int j = row % (int)g.ey - G3, k = row / (int)g.ey - G3;
+    const bool ghost_row = j < 0 || j >= g.ny || k < 0 || k >= g.nz;
+    const long long dst = (long long)row * g.ex;
+    const long long src = ((long long)(wrapn(k, g.nz) + G3) * g.ey + (wrapn(j, g.ny) + G3)) * g.ex;
+    const int nxg = (int)g.ex - g.nx;                 // GX on the left, the rest on the right
+    const int cnt = ghost_row ? (int)g.ex : nxg;
+    for (int t = threadIdx.x; t < cnt * NF3; t += blockDim.x) {
+        const int f = t / cnt, q = t - f * cnt;
+        const int xi = ghost_row ? q : (q < GX ? q : g.nx + q);
         T* u = s + (long long)f * g.ne;
-        u[c] = u[g.at(wrapn(i, g.nx), wrapn(j, g.ny), wrapn(k, g.nz))];
+        u[dst + xi] = u[src + wrapn(xi - GX, g.nx) + GX];
     }
 }
 
@@ -187,24 +196,29 @@ __global__ void update3(const T* __restrict__ s, const T* __restrict__ fl, const
     }
 }
 
+// signal speeds |v_d| + c_f, maximum over the interior; blocks stride over the
+// (y, z) rows, threads over x; one ordered-bit atomic per warp and direction
 template <typename T>
 __global__ void cmax3_kernel(const T* __restrict__ s, Grid3 g, T gamma, unsigned long long* __restrict__ keys)
 {
-    const long long n = (long long)g.nx * g.ny * g.nz, ne = g.ne;
+    const long long ne = g.ne;
+    const int rows = g.ny * g.nz;
     double mxs[3] = {0.0, 0.0, 0.0};
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
-        const long long c = g.at(i, j, k);
-        const T rho = s[c], mx = s[ne + c], my = s[2 * ne + c], mz = s[3 * ne + c], et = s[4 * ne + c];
-        const T bx = s[5 * ne + c], by = s[6 * ne + c], bz = s[7 * ne + c];
-        const T ux = mx / rho, uy = my / rho, uz = mz / rho;
-        const T ekin = (T)0.5 * ((mx * ux + my * uy) + mz * uz);
-        const T b2 = (T)0.5 * ((bx * bx + by * by) + bz * bz);
-        const T pk = (gamma - (T)1) * ((et - ekin) - b2);
-        const T cfst = sqrt((gamma * pk + ((bx * bx + by * by) + bz * bz)) / rho);
-        const double sp[3] = {(double)(fabs(ux) + cfst), (double)(fabs(uy) + cfst), (double)(fabs(uz) + cfst)};
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int j = r % g.ny, k = r / g.ny;
+        for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+            const long long c = g.at(i, j, k);
+            const T rho = s[c], mx = s[ne + c], my = s[2 * ne + c], mz = s[3 * ne + c], et = s[4 * ne + c];
+            const T bx = s[5 * ne + c], by = s[6 * ne + c], bz = s[7 * ne + c];
+            const T ux = mx / rho, uy = my / rho, uz = mz / rho;
+            const T ekin = (T)0.5 * ((mx * ux + my * uy) + mz * uz);
+            const T b2 = (T)0.5 * ((bx * bx + by * by) + bz * bz);
+            const T pk = (gamma - (T)1) * ((et - ekin) - b2);
+            const T cfst = sqrt((gamma * pk + ((bx * bx + by * by) + bz * bz)) / rho);
+            const double sp[3] = {(double)(fabs(ux) + cfst), (double)(fabs(uy) + cfst), (double)(fabs(uz) + cfst)};
 #pragma unroll
-        for (int d = 0; d < 3; ++d) if (!(sp[d] <= mxs[d])) mxs[d] = sp[d];   // NaN propagates
+            for (int d = 0; d < 3; ++d) if (!(sp[d] <= mxs[d])) mxs[d] = sp[d];   // NaN propagates
+        }
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -241,6 +255,349 @@ __global__ void export3(const T* __restrict__ u, double* __restrict__ w, Grid3 g
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 fused RK stage.  One CTA owns TX x TY columns and marches through KZ
+// planes along z.  Per plane k it stages plane k with its x/y halo (cp.async,
+// 16-byte row segments) and the own column of plane k+3, builds the x and y
+// fluxes of plane k and the z flux of plane k+2 in shared memory, and then
+// every thread forms k = H - div F for its cell and applies the RK register
+// update.  Along z the face quantities |d1|, |d3|, d1 and the hyper-diffusive
+// face flux roll in registers, and the z fluxes roll through a five-plane ring.
+// The shock indicator comes from shock3_f32 (global, ghost-extended layout) and
+// is staged beside the fields.  Arithmetic is single precision throughout
+// (reciprocals, not divisions), so results differ from the FP64 order at the
+// level of FP32 rounding.
+namespace f3 {
+constexpr int TX = 32, TY = 4, NT = TX * TY;   // one warp per y row of the tile
+constexpr int HXS = 4, RW = TX + 2 * HXS;      // staged x range i0-4 .. i0+TX+3
+constexpr int RH = TY + 2 * G3;                // staged rows j0-3 .. j0+TY+2
+constexpr int NS = NF3 + 1;                    // eight fields and the shock indicator
+constexpr int KZ = 32;                         // planes per CTA
+constexpr int FXW = TX + 4, FYH = TY + 4;      // flux extents: x i0-2 .. i0+TX+1, y j0-2 .. j0+TY+1
+constexpr int VPR = RW / 4;                    // 16-byte segments per staged row
+
+struct Smem {
+    float full[NS][RH][RW];   // plane k
+    float col[3][NS][NT];     // planes k+1 .. k+3, own column (ring by plane % 3)
+    float fz[5][NF3][NT];     // z fluxes of planes k-2 .. k+2, own column (ring by plane % 5)
+    float fx[NF3][TY][FXW];
+    float fy[NF3][FYH][TX];
+    float rk[2][NF3][NT];     // U0 and the RK accumulator of the own cell
+};
+
+struct Coef {
+    float a[NF3][3];   // c2_f d cmax_d
+    float bsh[3];      // c_shk d^2 / 2 (the face mean of the two shock values folds in the 1/2)
+    float i12[3];      // 1 / (12 d)
+    float idd[3];      // 1 / d^2
+    float gm1, gamma, dt, h, d6;
+    int hd;
+};
+
+__device__ __forceinline__ float rcpf(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+}
+
+struct P3 {
+    float v[3], pt, bv;
+};
+__device__ __forceinline__ P3 prim3(const float* u, float gm1)
+{
+    P3 p;
+    const float ri = rcpf(u[0]);
+    p.v[0] = u[1] * ri; p.v[1] = u[2] * ri; p.v[2] = u[3] * ri;
+    const float ekin = 0.5f * __fmaf_rn(u[3], p.v[2], __fmaf_rn(u[2], p.v[1], u[1] * p.v[0]));
+    const float b2 = 0.5f * __fmaf_rn(u[7], u[7], __fmaf_rn(u[6], u[6], u[5] * u[5]));
+    p.pt = __fmaf_rn(gm1, (u[4] - ekin) - b2, b2);
+    p.bv = __fmaf_rn(u[7], p.v[2], __fmaf_rn(u[6], p.v[1], u[5] * p.v[0]));
+    return p;
+}
+// the eight fluxes along direction D
+template <int D>
+__device__ __forceinline__ void flux_dir(const float* u, const P3& p, float* F)
+{
+    const float vd = p.v[D], bd = u[5 + D];
+    F[0] = u[1 + D];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float m = __fmaf_rn(vd, u[1 + q], -(bd * u[5 + q]));
+        F[1 + q] = q == D ? m + p.pt : m;
+        F[5 + q] = q == D ? 0.0f : __fmaf_rn(vd, u[5 + q], -(bd * p.v[q]));
+    }
+    F[4] = __fmaf_rn(vd, u[4] + p.pt, -(bd * p.bv));
+}
+// face q lies between cells q and q+1: d1 = u[q+1] - u[q], d3 = (u[q+2] - u[q-1]) - 3 d1
+__device__ __forceinline__ void face13(float um, float u0, float u1, float u2, float& d1, float& d3)
+{
+    d1 = u1 - u0;
+    d3 = __fmaf_rn(-3.0f, d1, u2 - um);
+}
+// (g_right - g_left) of one direction from the seven values u[-3..3] along it
+__device__ __forceinline__ float hd_line(const float* u, int s, float a, float bl, float br)
+{
+    const float um3 = u[-3 * s], um2 = u[-2 * s], um1 = u[-s], uc = u[0], up1 = u[s], up2 = u[2 * s], up3 = u[3 * s];
+    float d1a, d3a, d1b, d3b, d1c, d3c, d1d, d3d;
+    face13(um3, um2, um1, uc, d1a, d3a);   // face -2
+    face13(um2, um1, uc, up1, d1b, d3b);   // face -1
+    face13(um1, uc, up1, up2, d1c, d3c);   // face 0
+    face13(uc, up1, up2, up3, d1d, d3d);   // face +1
+    const float a1b = fabsf(d1b), a1c = fabsf(d1c), a3b = fabsf(d3b), a3c = fabsf(d3c);
+    const float m1bc = fmaxf(a1b, a1c), m3bc = fmaxf(a3b, a3c);
+    const float m1l = fmaxf(fabsf(d1a), m1bc), m3l = fmaxf(fabsf(d3a), m3bc);
+    const float m1r = fmaxf(m1bc, fabsf(d1d)), m3r = fmaxf(m3bc, fabsf(d3d));
+    const float rl = m1l > 0.0f ? m3l * rcpf(m1l) : 0.0f;
+    const float rr = m1r > 0.0f ? m3r * rcpf(m1r) : 0.0f;
+    return __fmaf_rn(a, rr, br) * d1c - __fmaf_rn(a, rl, bl) * d1b;
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(NT, 3)
+stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const float* u0, float* __restrict__ acc,
+           float* out, Grid3 g, Coef cf, int ntx, unsigned long long* __restrict__ keys)
+// out == u0 in stage 4; in == u0 in stage 1; stage 4 also reduces the signal
+// speeds of its output into keys (ordered bits of FP64 maxima, one per direction)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int i0 = (int)(blockIdx.x % ntx) * TX, j0 = (int)(blockIdx.x / ntx) * TY;
+    const int k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
+    const int x = i0 + lane, y = j0 + w;
+    const bool valid = x < g.nx && y < g.ny;
+    const long long P = g.ex * g.ey, ne = g.ne;
+    // own column (clamped into the interior for the threads past a ragged edge)
+    const long long colc = (long long)(min(y, g.ny - 1) + G3) * g.ex + (min(x, g.nx - 1) + GX);
+    const auto plane = [&](int k) { return (long long)(k + G3) * P; };
+    const auto src = [&](int f) { return f < NF3 ? in + (long long)f * ne : sh; };
+    // staging descriptor: threads below RH * VPR own one 16-byte segment of every
+    // staged row (row r, segment v) and copy it for all nine planes' fields
+    const bool stager = tid < RH * VPR;
+    const int sr_ = tid / VPR, sv_ = tid - (tid / VPR) * VPR;
+    const bool sok = stager && j0 + sr_ < g.ey && i0 + 4 * sv_ < g.ex;
+    const long long soff_g = (long long)(j0 + sr_) * g.ex + (i0 + 4 * sv_);
+    const int soff_s = sr_ * RW + 4 * sv_;
+    float sp_max[3] = {0.0f, 0.0f, 0.0f};
+
+    // prologue: own column of planes k0+1, k0+2; z fluxes of planes k0-2 .. k0+1;
+    // z face state of faces k0-1, k0 and the face flux at k0-1/2
+#pragma unroll 1
+    for (int q = k0 + 1; q <= k0 + 2; ++q)
+        for (int f = 0; f < NS; ++f) cp_async4(&S.col[q % 3][f][tid], src(f) + plane(q) + colc);
+#pragma unroll 1
+    for (int q = k0 - 2; q <= k0 + 1; ++q) {
+        float u[NF3], F[NF3];
+#pragma unroll
+        for (int f = 0; f < NF3; ++f) u[f] = in[f * ne + plane(q) + colc];
+        const P3 p = prim3(u, cf.gm1);
+        flux_dir<2>(u, p, F);
+#pragma unroll
+        for (int f = 0; f < NF3; ++f) S.fz[(q + 5) % 5][f][tid] = F[f];
+    }
+    float zd1[NF3], za3[NF3], za1m[NF3], za3m[NF3], zg[NF3];   // face k: d1, |d3|; face k-1: |d1|, |d3|; g(k-1/2)
+    if (cf.hd) {
+        const float bz = cf.bsh[2] * (sh[plane(k0 - 1) + colc] + sh[plane(k0) + colc]);
+#pragma unroll
+        for (int f = 0; f < NF3; ++f) {
+            const float* uf = in + f * ne + colc;
+            float u[6];
+#pragma unroll
+            for (int o = 0; o < 6; ++o) u[o] = uf[plane(k0 - 3 + o)];
+            float d1a, d3a, d1b, d3b, d1c, d3c;
+            face13(u[0], u[1], u[2], u[3], d1a, d3a);   // face k0-2
+            face13(u[1], u[2], u[3], u[4], d1b, d3b);   // face k0-1
+            face13(u[2], u[3], u[4], u[5], d1c, d3c);   // face k0
+            const float m1 = fmaxf(fmaxf(fabsf(d1a), fabsf(d1b)), fabsf(d1c));
+            const float m3 = fmaxf(fmaxf(fabsf(d3a), fabsf(d3b)), fabsf(d3c));
+            const float r = m1 > 0.0f ? m3 * rcpf(m1) : 0.0f;
+            zg[f] = __fmaf_rn(cf.a[f][2], r, bz) * d1b;
+            zd1[f] = d1c; za3[f] = fabsf(d3c); za1m[f] = fabsf(d1b); za3m[f] = fabsf(d3b);
+        }
+    }
+
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+        __syncthreads();   // the previous plane's readers are done
+        const long long pk = plane(k);
+        if (sok) {   // rows of y = j0-3 .. j0+TY+2, x = i0-4 .. i0+TX+3
+            const float* gp = in + pk + soff_g;
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) cp_async16(&S.full[f][0][0] + soff_s, gp + f * ne);
+            cp_async16(&S.full[NF3][0][0] + soff_s, sh + pk + soff_g);
+        }
+        {
+            const long long q = plane(k + 3) + colc;   // plane k+3 <= nz + 2: inside the ghost frame
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) cp_async4(&S.col[(k + 3) % 3][f][tid], in + f * ne + q);
+            cp_async4(&S.col[(k + 3) % 3][NF3][tid], sh + q);
+        }
+        if (STAGE != 1) {   // RK registers of the own cell
+            const long long e = pk + colc;
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) {
+                cp_async4(&S.rk[0][f][tid], u0 + f * ne + e);
+                cp_async4(&S.rk[1][f][tid], acc + f * ne + e);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+
+        {   // x and y fluxes of the own cell
+            float u[NF3], F[NF3];
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) u[f] = S.full[f][G3 + w][HXS + lane];
+            const P3 p = prim3(u, cf.gm1);
+            flux_dir<0>(u, p, F);
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) S.fx[f][w][lane + 2] = F[f];
+            flux_dir<1>(u, p, F);
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) S.fy[f][w + 2][lane] = F[f];
+        }
+        {   // y fluxes of the halo rows y = j0-2, j0-1, j0+TY, j0+TY+1 (one warp per row)
+            const int fyr = w < 2 ? w : w + TY, sr = fyr + 1;
+            float u[NF3], F[NF3];
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) u[f] = S.full[f][sr][HXS + lane];
+            const P3 p = prim3(u, cf.gm1);
+            flux_dir<1>(u, p, F);
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) S.fy[f][fyr][lane] = F[f];
+        }
+        if (tid < 4 * TY) {   // x fluxes of the halo columns x = i0-2, i0-1, i0+TX, i0+TX+1
+            const int r = tid >> 2, q = tid & 3;
+            const int fxc = q < 2 ? q : q + TX, sc = fxc + 2;
+            float u[NF3], F[NF3];
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) u[f] = S.full[f][G3 + r][sc];
+            const P3 p = prim3(u, cf.gm1);
+            flux_dir<0>(u, p, F);
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) S.fx[f][r][fxc] = F[f];
+        }
+        {   // z flux of plane k+2, own column
+            float u[NF3], F[NF3];
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) u[f] = S.col[(k + 2) % 3][f][tid];
+            const P3 p = prim3(u, cf.gm1);
+            flux_dir<2>(u, p, F);
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) S.fz[(k + 2) % 5][f][tid] = F[f];
+        }
+        __syncthreads();
+        if (!valid) continue;
+
+        const float* sc = &S.full[NF3][G3 + w][HXS + lane];
+        float bxl = 0.f, bxr = 0.f, byl = 0.f, byr = 0.f, bzr = 0.f;
+        if (cf.hd) {
+            bxl = cf.bsh[0] * (sc[-1] + sc[0]);
+            bxr = cf.bsh[0] * (sc[0] + sc[1]);
+            byl = cf.bsh[1] * (sc[-RW] + sc[0]);
+            byr = cf.bsh[1] * (sc[0] + sc[RW]);
+            bzr = cf.bsh[2] * (sc[0] + S.col[(k + 1) % 3][NF3][tid]);
+        }
+        const int s1 = (k + 1) % 3, s2 = (k + 2) % 3, s3 = (k + 3) % 3;
+        float wn[NF3];   // the stage output of the own cell
+        const int zp1 = (k + 1) % 5, zm1 = (k + 4) % 5, zp2 = (k + 2) % 5, zm2 = (k + 3) % 5;
+#pragma unroll
+        for (int f = 0; f < NF3; ++f) {
+            const float* uc = &S.full[f][G3 + w][HXS + lane];
+            float hsum = 0.0f;
+            if (cf.hd) {
+                const float hx = hd_line(uc, 1, cf.a[f][0], bxl, bxr) * cf.idd[0];
+                const float hy = hd_line(uc, RW, cf.a[f][1], byl, byr) * cf.idd[1];
+                // z: the new face k+1 from planes k .. k+3, then face k+1/2
+                float d1n, d3n;
+                face13(uc[0], S.col[s1][f][tid], S.col[s2][f][tid], S.col[s3][f][tid], d1n, d3n);
+                const float a1n = fabsf(d1n), a3n = fabsf(d3n), a1 = fabsf(zd1[f]);
+                const float m1 = fmaxf(fmaxf(za1m[f], a1), a1n), m3 = fmaxf(fmaxf(za3m[f], za3[f]), a3n);
+                const float r = m1 > 0.0f ? m3 * rcpf(m1) : 0.0f;
+                const float gz = __fmaf_rn(cf.a[f][2], r, bzr) * zd1[f];
+                const float hz = (gz - zg[f]) * cf.idd[2];
+                zg[f] = gz; za1m[f] = a1; za3m[f] = za3[f]; zd1[f] = d1n; za3[f] = a3n;
+                hsum = (hx + hy) + hz;
+            }
+            const float* fxr = &S.fx[f][w][lane + 2];
+            const float* fyr = &S.fy[f][w + 2][lane];
+            const float dfx = __fmaf_rn(8.0f, fxr[1] - fxr[-1], -(fxr[2] - fxr[-2])) * cf.i12[0];
+            const float dfy = __fmaf_rn(8.0f, fyr[TX] - fyr[-TX], -(fyr[2 * TX] - fyr[-2 * TX])) * cf.i12[1];
+            const float dfz = __fmaf_rn(8.0f, S.fz[zp1][f][tid] - S.fz[zm1][f][tid],
+                                        -(S.fz[zp2][f][tid] - S.fz[zm2][f][tid])) * cf.i12[2];
+            const float kf = hsum - ((dfx + dfy) + dfz);
+            const long long e = f * ne + pk + colc;
+            const float r0 = S.rk[0][f][tid], ra = S.rk[1][f][tid];
+            if (STAGE == 1) {
+                __stcs(&acc[e], kf);
+                __stcs(&out[e], __fmaf_rn(cf.h, kf, uc[0]));
+            } else if (STAGE == 2) {
+                __stcs(&acc[e], __fmaf_rn(2.0f, kf, ra));
+                __stcs(&out[e], __fmaf_rn(cf.h, kf, r0));
+            } else if (STAGE == 3) {
+                __stcs(&acc[e], __fmaf_rn(2.0f, kf, ra));
+                __stcs(&out[e], __fmaf_rn(cf.dt, kf, r0));
+            } else {
+                wn[f] = __fmaf_rn(cf.d6, ra + kf, r0);
+                out[e] = wn[f];
+            }
+        }
+        if (STAGE == 4) {   // signal speeds |v_d| + c_f of the new state
+            const float ri = rcpf(wn[0]);
+            const float vx = wn[1] * ri, vy = wn[2] * ri, vz = wn[3] * ri;
+            const float b2 = __fmaf_rn(wn[7], wn[7], __fmaf_rn(wn[6], wn[6], wn[5] * wn[5]));
+            const float ekin = 0.5f * __fmaf_rn(wn[3], vz, __fmaf_rn(wn[2], vy, wn[1] * vx));
+            const float pk_ = (cf.gamma - 1.0f) * ((wn[4] - ekin) - 0.5f * b2);
+            const float cfs = sqrtf(__fmaf_rn(cf.gamma, pk_, b2) * ri);
+            const float sp[3] = {fabsf(vx) + cfs, fabsf(vy) + cfs, fabsf(vz) + cfs};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) if (!(sp[d] <= sp_max[d])) sp_max[d] = sp[d];   // NaN propagates
+        }
+    }
+    if (STAGE == 4) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            unsigned long long key = (unsigned long long)__double_as_longlong((double)sp_max[d]);
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long w2 = __shfl_xor_sync(0xffffffffu, key, o);
+                key = w2 > key ? w2 : key;
+            }
+            if (lane == 0) atomicMax(&keys[d], key);
+        }
+    }
+}
+
+// shock indicator s = max(0, -div v) on [-1, n+1) in every direction, from the
+// stage input directly; block (128) over x, grid (x blocks, y, z)
+__global__ void shock3_f32(const float* __restrict__ s, float* __restrict__ sh, Grid3 g, float i12x, float i12y,
+                           float i12z)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x - 1, j = blockIdx.y - 1, k = blockIdx.z - 1;
+    if (i > g.nx) return;
+    const long long ne = g.ne, c = g.at(i, j, k), sy = g.ex, sz = g.ex * g.ey;
+    const auto vel = [&](long long q, int d) { return s[(1 + d) * ne + q] * rcpf(s[q]); };
+    const auto dcen = [&](int d, long long st) {
+        return __fmaf_rn(8.0f, vel(c + st, d) - vel(c - st, d), -(vel(c + 2 * st, d) - vel(c - 2 * st, d)));
+    };
+    const float div = (dcen(0, 1) * i12x + dcen(1, sy) * i12y) + dcen(2, sz) * i12z;
+    sh[c] = fmaxf(0.0f, -div);
+}
+}  // namespace f3
+
 int grid_for(long long n) { long long b = (n + 255) / 256; return (int)(b < 4096 ? (b < 1 ? 1 : b) : 4096); }
 
 }  // namespace
@@ -256,6 +613,7 @@ struct sac3_ctx {
     unsigned long long* keys = nullptr;     // signal-speed keys (3)
     double t = 0.0;
     bool have_state = false;
+    bool keys_valid = false;                // keys hold the maxima of the current state
     std::string err;
 };
 
@@ -278,6 +636,71 @@ static int fail3(sac3_ctx* c, int code, const char* fmt, ...)
         if (e_ != cudaSuccess) return fail3(c, SAC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+// FP32: ghost frame, shock indicator and one fused kernel per stage
+template <int S>
+static cudaError_t launch_f32(const float* in, const float* sh, const float* u0, float* acc, float* out,
+                              const Grid3& g, const f3::Coef& cf, unsigned long long* keys, cudaStream_t st)
+{
+    const int ntx = (g.nx + f3::TX - 1) / f3::TX, nty = (g.ny + f3::TY - 1) / f3::TY;
+    const dim3 grid((unsigned)(ntx * nty), (unsigned)((g.nz + f3::KZ - 1) / f3::KZ));
+    f3::stage3_f32<S><<<grid, f3::NT, sizeof(f3::Smem), st>>>(in, sh, u0, acc, out, g, cf, ntx, keys);
+    return cudaGetLastError();
+}
+
+static cudaError_t prepare_f32()
+{
+    const int b = (int)sizeof(f3::Smem);
+    cudaError_t e = cudaFuncSetAttribute(f3::stage3_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f3::stage3_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f3::stage3_f32<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f3::stage3_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return e;
+}
+
+static int fused_f32(sac3_ctx* c, double dt, const double cm[3], const double dd[3], double* dt_taken)
+{
+    const Grid3& g = c->g;
+    f3::Coef cf;
+    for (int f = 0; f < NF3; ++f)
+        for (int d = 0; d < 3; ++d) cf.a[f][d] = (float)(c->p.c2[f] * dd[d] * cm[d]);
+    for (int d = 0; d < 3; ++d) {
+        cf.bsh[d] = (float)(0.5 * c->p.c_shk * dd[d] * dd[d]);
+        cf.i12[d] = (float)(1.0 / (12.0 * dd[d]));
+        cf.idd[d] = (float)(1.0 / (dd[d] * dd[d]));
+    }
+    cf.gm1 = (float)(c->p.gamma - 1.0);
+    cf.gamma = (float)c->p.gamma;
+    cf.dt = (float)dt; cf.h = (float)(0.5 * dt); cf.d6 = (float)(dt / 6.0);
+    cf.hd = c->p.hyperdiffusion != 0;
+    float* u0 = (float*)c->u0;
+    float* sa = (float*)c->sa;
+    float* sb = (float*)c->sb;
+    float* sh = (float*)c->sh;
+    float* acc = (float*)c->acc;
+    const dim3 sgrid((unsigned)((g.nx + 2 + 127) / 128), (unsigned)(g.ny + 2), (unsigned)(g.nz + 2));
+    for (int stage = 1; stage <= 4; ++stage) {
+        float* in = stage == 1 ? u0 : (stage == 2 ? sa : (stage == 3 ? sb : sa));
+        float* out = stage == 1 ? sa : (stage == 2 ? sb : (stage == 3 ? sa : u0));
+        ghosts3<float><<<(int)(g.ey * g.ez), 128, 0, c->stream>>>(in, g);
+        if (cf.hd) f3::shock3_f32<<<sgrid, 128, 0, c->stream>>>(in, sh, g, cf.i12[0], cf.i12[1], cf.i12[2]);
+        // stage 4 reduces the signal speeds of the new state for the next step
+        if (stage == 4) CK3(cudaMemsetAsync(c->keys, 0, 3 * sizeof(unsigned long long), c->stream));
+        cudaError_t e;
+        switch (stage) {
+            case 1: e = launch_f32<1>(in, sh, u0, acc, out, g, cf, c->keys, c->stream); break;
+            case 2: e = launch_f32<2>(in, sh, u0, acc, out, g, cf, c->keys, c->stream); break;
+            case 3: e = launch_f32<3>(in, sh, u0, acc, out, g, cf, c->keys, c->stream); break;
+            default: e = launch_f32<4>(in, sh, u0, acc, out, g, cf, c->keys, c->stream); break;
+        }
+        CK3(e);
+    }
+    CK3(cudaStreamSynchronize(c->stream));
+    c->keys_valid = true;
+    c->t += dt;
+    if (dt_taken) *dt_taken = dt;
+    return SAC_OK;
+}
+
 template <typename T>
 static int step3(sac3_ctx* c, double dt_in, double* dt_taken)
 {
@@ -285,9 +708,14 @@ static int step3(sac3_ctx* c, double dt_in, double* dt_taken)
     const long long n = (long long)g.nx * g.ny * g.nz;
     const double dd[3] = {(c->p.x1 - c->p.x0) / g.nx, (c->p.y1 - c->p.y0) / g.ny, (c->p.z1 - c->p.z0) / g.nz};
     // signal speeds of the step-start state (all four stages use them)
-    CK3(cudaMemsetAsync(c->keys, 0, 3 * sizeof(unsigned long long), c->stream));
-    cmax3_kernel<T><<<grid_for(n), 256, 0, c->stream>>>((const T*)c->u0, g, (T)c->p.gamma, c->keys);
-    CK3(cudaGetLastError());
+    // (the FP32 stage 4 leaves the maxima of its output in keys)
+    if (!c->keys_valid) {
+        CK3(cudaMemsetAsync(c->keys, 0, 3 * sizeof(unsigned long long), c->stream));
+        const int crow = g.ny * g.nz < 148 * 8 ? g.ny * g.nz : 148 * 8;
+        cmax3_kernel<T><<<crow, 128, 0, c->stream>>>((const T*)c->u0, g, (T)c->p.gamma, c->keys);
+        CK3(cudaGetLastError());
+    }
+    c->keys_valid = false;
     unsigned long long hk[3];
     CK3(cudaMemcpyAsync(hk, c->keys, sizeof hk, cudaMemcpyDeviceToHost, c->stream));
     CK3(cudaStreamSynchronize(c->stream));
@@ -296,6 +724,7 @@ static int step3(sac3_ctx* c, double dt_in, double* dt_taken)
     double dt = dt_in > 0.0 ? dt_in : c->p.courant * fmin(fmin(dd[0] / cm[0], dd[1] / cm[1]), dd[2] / cm[2]);
     if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(cm[0]) || !std::isfinite(cm[1]) || !std::isfinite(cm[2]))
         return fail3(c, SAC_ERR_NONFINITE, "non-finite state or step at t = %g", c->t);
+    if (c->fp32) return fused_f32(c, dt, cm, dd, dt_taken);
     Coef3 cf;
     for (int f = 0; f < NF3; ++f) cf.c2[f] = c->p.c2[f];
     cf.c_shk = c->p.c_shk;
@@ -310,7 +739,7 @@ static int step3(sac3_ctx* c, double dt_in, double* dt_taken)
     for (int stage = 1; stage <= 4; ++stage) {
         T* in = stage == 1 ? u0 : (stage == 2 ? sa : (stage == 3 ? sb : sa));
         T* out = stage == 1 ? sa : (stage == 2 ? sb : (stage == 3 ? sa : u0));
-        ghosts3<T><<<grid_for(g.ne * NF3), 256, 0, c->stream>>>(in, g);
+        ghosts3<T><<<(int)(g.ey * g.ez), 128, 0, c->stream>>>(in, g);
         flux3<T><<<grid_for(g.ne), 256, 0, c->stream>>>(in, (T*)c->v, (T*)c->fl, g, gm1);
         if (cf.hd)
             shock3<T><<<grid_for((long long)(g.nx + 2) * (g.ny + 2) * (g.nz + 2)), 256, 0, c->stream>>>(
@@ -381,7 +810,7 @@ int sac3_init(const sac3_params* p, sac3_ctx** out)
     c->stream = (cudaStream_t)p->stream;
     Grid3& g = c->g;
     g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
-    g.ex = p->nx + 2 * G3; g.ey = p->ny + 2 * G3; g.ez = p->nz + 2 * G3;
+    g.ex = (p->nx + 2 * GX + 3) / 4 * 4; g.ey = p->ny + 2 * G3; g.ez = p->nz + 2 * G3;
     g.ne = g.ex * g.ey * g.ez;
     const long long n = (long long)p->nx * p->ny * p->nz;
     int rc = SAC_OK;
@@ -390,8 +819,9 @@ int sac3_init(const sac3_params* p, sac3_ctx** out)
     if (rc == SAC_OK &&
         (cudaMalloc(&c->u0, NF3 * fb) != cudaSuccess || cudaMalloc(&c->sa, NF3 * fb) != cudaSuccess ||
          cudaMalloc(&c->sb, NF3 * fb) != cudaSuccess ||
-         cudaMalloc(&c->acc, NF3 * fb) != cudaSuccess || cudaMalloc(&c->v, 3 * fb) != cudaSuccess ||
-         cudaMalloc(&c->fl, 3 * NF3 * fb) != cudaSuccess || cudaMalloc(&c->sh, fb) != cudaSuccess ||
+         cudaMalloc(&c->acc, NF3 * fb) != cudaSuccess || cudaMalloc(&c->sh, fb) != cudaSuccess ||
+         // velocity and flux scratch of the FP64 kernels
+         (!c->fp32 && (cudaMalloc(&c->v, 3 * fb) != cudaSuccess || cudaMalloc(&c->fl, 3 * NF3 * fb) != cudaSuccess)) ||
          cudaMalloc(&c->wbuf, (size_t)NF3 * n * sizeof(double)) != cudaSuccess ||
          cudaMalloc(&c->keys, 3 * sizeof(unsigned long long)) != cudaSuccess)) {
         cudaGetLastError();
@@ -400,6 +830,7 @@ int sac3_init(const sac3_params* p, sac3_ctx** out)
     if (rc == SAC_OK && (cudaMemset(c->u0, 0, NF3 * fb) != cudaSuccess || cudaMemset(c->sa, 0, NF3 * fb) != cudaSuccess ||
                          cudaMemset(c->sb, 0, NF3 * fb) != cudaSuccess || cudaMemset(c->sh, 0, fb) != cudaSuccess))
         rc = fail3(c, SAC_ERR_CUDA, "cudaMemset");
+    if (rc == SAC_OK && c->fp32 && prepare_f32() != cudaSuccess) rc = fail3(c, SAC_ERR_CUDA, "cudaFuncSetAttribute");
     if (rc != SAC_OK) { sac3_free(c); return rc; }
     *out = c;
     return SAC_OK;
@@ -417,6 +848,7 @@ int sac3_set_state(sac3_ctx* c, const double* w, double t)
     CK3(cudaStreamSynchronize(c->stream));
     c->t = t;
     c->have_state = true;
+    c->keys_valid = false;
     return SAC_OK;
 }
 

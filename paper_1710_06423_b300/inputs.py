@@ -162,11 +162,13 @@ def gaussian_blob(nx: int, ny: int, *, amp: float, centre=(0.5, 0.5), width: flo
 
 
 def ot_3d(nx: int, ny: int, nz: int, *, gamma: float = 5.0 / 3.0, b0: float = 1.0 / math.sqrt(4.0 * math.pi),
-          tilt: float = 0.2) -> np.ndarray:
+          tilt: float = 0.2, compress: float = 0.0) -> np.ndarray:
     """A three-dimensional variant of the Orszag-Tang vortex on [0,1]^3: the 2D
     vortex plus z-dependent velocity and field components of relative size
-    `tilt` (smooth, periodic, divergence-free B).  Eight conserved fields
-    (rho, m_x, m_y, m_z, e, B_x, B_y, B_z), shape (8, nz, ny, nx)."""
+    `tilt` (smooth, periodic, divergence-free B).  `compress` adds the
+    compressive flow compress * (sin 2 pi x, 0, cos 2 pi z), so that the shock
+    indicator max(0, -div v) is non-zero from the first step.  Eight conserved
+    fields (rho, m_x, m_y, m_z, e, B_x, B_y, B_z), shape (8, nz, ny, nx)."""
     x = cell_centres(nx)[None, None, :]
     y = cell_centres(ny)[None, :, None]
     z = cell_centres(nz)[:, None, None]
@@ -177,6 +179,8 @@ def ot_3d(nx: int, ny: int, nz: int, *, gamma: float = 5.0 / 3.0, b0: float = 1.
     vx = -np.sin(tp * y) + tilt * np.sin(tp * z) * one
     vy = np.sin(tp * x) + tilt * np.cos(tp * z) * one
     vz = tilt * np.sin(tp * (x + y)) * one
+    vx = vx + compress * np.sin(tp * x)
+    vz = vz + compress * np.cos(tp * z)
     bx = b0 * (-np.sin(tp * y) + tilt * np.cos(tp * z)) * one
     by = b0 * (np.sin(2 * tp * x) + tilt * np.sin(tp * z)) * one
     bz = b0 * tilt * np.cos(tp * (x - y)) * one

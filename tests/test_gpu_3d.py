@@ -27,19 +27,46 @@ def test_fp64_matches_oracle(oracle_mod, inputs_mod, nx, ny, nz, steps):
     assert np.all(_rel(got, ref) <= TOL_FP64), _rel(got, ref)
 
 
-def test_fp32_matches_oracle(oracle_mod, inputs_mod):
+# FP32 cases span several 32 x 4 column tiles and 32-plane z chunks of the fused
+# kernel with ragged tails, an anisotropic box, hyper-diffusion off, and a
+# compressive flow that switches the shock viscosity on.
+FP32_CASES = [
+    dict(n=(24, 24, 24), steps=10, kw={}, compress=0.0),
+    dict(n=(37, 11, 70), steps=4, kw=dict(x1=1.5, z1=2.0), compress=0.3),
+    dict(n=(33, 9, 40), steps=4, kw=dict(hyperdiffusion=0), compress=0.3),
+    dict(n=(64, 8, 33), steps=3, kw=dict(y1=0.5), compress=0.5),
+]
+
+
+@pytest.mark.parametrize("case", FP32_CASES, ids=lambda c: "x".join(map(str, c["n"])) + str(c["kw"]))
+def test_fp32_matches_oracle(oracle_mod, inputs_mod, case):
     from paper_1710_06423_b300.sac import FP32, Solver3
-    n, steps = 24, 10
-    w = inputs_mod.ot_3d(n, n, n)
-    pr = oracle_mod.Problem3(nx=n, ny=n, nz=n)
+    nx, ny, nz = case["n"]
+    steps = case["steps"]
+    w = inputs_mod.ot_3d(nx, ny, nz, compress=case["compress"])
+    pr = oracle_mod.Problem3(nx=nx, ny=ny, nz=nz, **case["kw"])
     ref, t_ref, _ = oracle_mod.run3(pr, w, max_steps=steps)
-    with Solver3(nx=n, ny=n, nz=n, precision=FP32) as s:
+    with Solver3(nx=nx, ny=ny, nz=nz, precision=FP32, **case["kw"]) as s:
         s.set_state(w, 0.0)
         s.steps(steps)
         got, t = s.get_state()
-    assert t == pytest.approx(t_ref, rel=1e-6)
+    assert t == pytest.approx(t_ref, rel=1e-5)
     err = l1rel(got.reshape(8, -1), ref.reshape(8, -1))
     assert np.all(err <= TOL_FP32_L1), err
+
+
+def test_fp64_compressive_matches_oracle(oracle_mod, inputs_mod):
+    from paper_1710_06423_b300.sac import FP64, Solver3
+    nx, ny, nz = 20, 9, 14
+    w = inputs_mod.ot_3d(nx, ny, nz, compress=0.5)
+    pr = oracle_mod.Problem3(nx=nx, ny=ny, nz=nz, y1=0.7)
+    ref, t_ref, _ = oracle_mod.run3(pr, w, max_steps=3)
+    with Solver3(nx=nx, ny=ny, nz=nz, y1=0.7, precision=FP64) as s:
+        s.set_state(w, 0.0)
+        s.steps(3)
+        got, t = s.get_state()
+    assert t == t_ref
+    assert np.all(_rel(got, ref) <= TOL_FP64), _rel(got, ref)
 
 
 def test_z_uniform_matches_2d_solver(inputs_mod):
