@@ -257,11 +257,11 @@ __global__ void export3(const T* __restrict__ u, double* __restrict__ w, Grid3 g
 
 // ---------------------------------------------------------------------------
 // FP32 fused RK stage.  One CTA owns TX x TY columns and marches through KZ
-// planes along z.  Per plane k it stages plane k with its x/y halo (cp.async,
-// 16-byte row segments) and the own column of plane k+3, builds the x and y
-// fluxes of plane k and the z flux of plane k+2 in shared memory, and then
-// every thread forms k = H - div F for its cell and applies the RK register
-// update.  Along z the face quantities |d1|, |d3|, d1 and the hyper-diffusive
+// planes along z.  While it works on plane k, cp.async copies plane k+1 with its
+// x/y halo (16-byte row segments), the RK registers of plane k+1 and the own
+// column of plane k+4 into shared memory (double buffer); per plane it builds
+// the x and y fluxes of plane k and the z flux of plane k+2, and then every
+// thread forms k = H - div F for its cell and applies the RK register update.  Along z the face quantities |d1|, |d3|, d1 and the hyper-diffusive
 // face flux roll in registers, and the z fluxes roll through a five-plane ring.
 // The shock indicator comes from shock3_f32 (global, ghost-extended layout) and
 // is staged beside the fields.  Arithmetic is single precision throughout
@@ -277,12 +277,12 @@ constexpr int FXW = TX + 4, FYH = TY + 4;      // flux extents: x i0-2 .. i0+TX+
 constexpr int VPR = RW / 4;                    // 16-byte segments per staged row
 
 struct Smem {
-    float full[NS][RH][RW];   // plane k
-    float col[3][NS][NT];     // planes k+1 .. k+3, own column (ring by plane % 3)
+    float full[2][NS][RH][RW];   // planes k and k+1 (the next one is copied in during plane k)
+    float col[4][NS][NT];        // planes k+1 .. k+4, own column (ring by plane % 4)
     float fz[5][NF3][NT];     // z fluxes of planes k-2 .. k+2, own column (ring by plane % 5)
     float fx[NF3][TY][FXW];
     float fy[NF3][FYH][TX];
-    float rk[2][NF3][NT];     // U0 and the RK accumulator of the own cell
+    float rk[2][2][NF3][NT];     // U0 and the RK accumulator of the own cell, planes k and k+1
 };
 
 struct Coef {
@@ -310,10 +310,9 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src)
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src));
 }
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most one committed group (the newest) is still in flight
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 struct P3 {
     float v[3], pt, bv;
@@ -368,7 +367,7 @@ __device__ __forceinline__ float hd_line(const float* u, int s, float a, float b
 }
 
 template <int STAGE>
-__global__ void __launch_bounds__(NT, 3)
+__global__ void __launch_bounds__(NT, 2)
 stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const float* u0, float* __restrict__ acc,
            float* out, Grid3 g, Coef cf, int ntx, unsigned long long* __restrict__ keys)
 // out == u0 in stage 4; in == u0 in stage 1; stage 4 also reduces the signal
@@ -394,12 +393,32 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
     const long long soff_g = (long long)(j0 + sr_) * g.ex + (i0 + 4 * sv_);
     const int soff_s = sr_ * RW + 4 * sv_;
     float sp_max[3] = {0.0f, 0.0f, 0.0f};
+    const auto issue = [&](int k) {
+        const long long pk = plane(k);
+        if (sok) {
+            const float* gp = in + pk + soff_g;
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) cp_async16(&S.full[k & 1][f][0][0] + soff_s, gp + f * ne);
+            cp_async16(&S.full[k & 1][NF3][0][0] + soff_s, sh + pk + soff_g);
+        }
+        if (STAGE != 1) {
+            const long long e = pk + colc;
+#pragma unroll
+            for (int f = 0; f < NF3; ++f) {
+                cp_async4(&S.rk[k & 1][0][f][tid], u0 + f * ne + e);
+                cp_async4(&S.rk[k & 1][1][f][tid], acc + f * ne + e);
+            }
+        }
+    };
 
-    // prologue: own column of planes k0+1, k0+2; z fluxes of planes k0-2 .. k0+1;
-    // z face state of faces k0-1, k0 and the face flux at k0-1/2
+    // prologue: copies of plane k0 and of the own column of planes k0+1 .. k0+3;
+    // z fluxes of planes k0-2 .. k0+1; z face state of faces k0-1, k0 and the face
+    // flux at k0-1/2
 #pragma unroll 1
-    for (int q = k0 + 1; q <= k0 + 2; ++q)
-        for (int f = 0; f < NS; ++f) cp_async4(&S.col[q % 3][f][tid], src(f) + plane(q) + colc);
+    for (int q = k0 + 1; q <= k0 + 3; ++q)
+        for (int f = 0; f < NS; ++f) cp_async4(&S.col[q % 4][f][tid], src(f) + plane(q) + colc);
+    issue(k0);
+    cp_async_commit();
 #pragma unroll 1
     for (int q = k0 - 2; q <= k0 + 1; ++q) {
         float u[NF3], F[NF3];
@@ -435,33 +454,22 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
     for (int k = k0; k < k1; ++k) {
         __syncthreads();   // the previous plane's readers are done
         const long long pk = plane(k);
-        if (sok) {   // rows of y = j0-3 .. j0+TY+2, x = i0-4 .. i0+TX+3
-            const float* gp = in + pk + soff_g;
+        if (k + 1 < k1) {
+            issue(k + 1);
+            const long long q = plane(k + 4) + colc;   // used at step k+1 as its plane +3 (<= nz + 2)
 #pragma unroll
-            for (int f = 0; f < NF3; ++f) cp_async16(&S.full[f][0][0] + soff_s, gp + f * ne);
-            cp_async16(&S.full[NF3][0][0] + soff_s, sh + pk + soff_g);
+            for (int f = 0; f < NF3; ++f) cp_async4(&S.col[(k + 4) % 4][f][tid], in + f * ne + q);
+            cp_async4(&S.col[(k + 4) % 4][NF3][tid], sh + q);
         }
-        {
-            const long long q = plane(k + 3) + colc;   // plane k+3 <= nz + 2: inside the ghost frame
-#pragma unroll
-            for (int f = 0; f < NF3; ++f) cp_async4(&S.col[(k + 3) % 3][f][tid], in + f * ne + q);
-            cp_async4(&S.col[(k + 3) % 3][NF3][tid], sh + q);
-        }
-        if (STAGE != 1) {   // RK registers of the own cell
-            const long long e = pk + colc;
-#pragma unroll
-            for (int f = 0; f < NF3; ++f) {
-                cp_async4(&S.rk[0][f][tid], u0 + f * ne + e);
-                cp_async4(&S.rk[1][f][tid], acc + f * ne + e);
-            }
-        }
-        cp_async_wait_all();
+        cp_async_commit();     // (possibly empty: the group count stays one per plane)
+        cp_async_wait_prev();  // plane k's group has landed
         __syncthreads();
+        const int kb = k & 1;
 
         {   // x and y fluxes of the own cell
             float u[NF3], F[NF3];
 #pragma unroll
-            for (int f = 0; f < NF3; ++f) u[f] = S.full[f][G3 + w][HXS + lane];
+            for (int f = 0; f < NF3; ++f) u[f] = S.full[kb][f][G3 + w][HXS + lane];
             const P3 p = prim3(u, cf.gm1);
             flux_dir<0>(u, p, F);
 #pragma unroll
@@ -474,7 +482,7 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
             const int fyr = w < 2 ? w : w + TY, sr = fyr + 1;
             float u[NF3], F[NF3];
 #pragma unroll
-            for (int f = 0; f < NF3; ++f) u[f] = S.full[f][sr][HXS + lane];
+            for (int f = 0; f < NF3; ++f) u[f] = S.full[kb][f][sr][HXS + lane];
             const P3 p = prim3(u, cf.gm1);
             flux_dir<1>(u, p, F);
 #pragma unroll
@@ -485,7 +493,7 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
             const int fxc = q < 2 ? q : q + TX, sc = fxc + 2;
             float u[NF3], F[NF3];
 #pragma unroll
-            for (int f = 0; f < NF3; ++f) u[f] = S.full[f][G3 + r][sc];
+            for (int f = 0; f < NF3; ++f) u[f] = S.full[kb][f][G3 + r][sc];
             const P3 p = prim3(u, cf.gm1);
             flux_dir<0>(u, p, F);
 #pragma unroll
@@ -494,7 +502,7 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
         {   // z flux of plane k+2, own column
             float u[NF3], F[NF3];
 #pragma unroll
-            for (int f = 0; f < NF3; ++f) u[f] = S.col[(k + 2) % 3][f][tid];
+            for (int f = 0; f < NF3; ++f) u[f] = S.col[(k + 2) % 4][f][tid];
             const P3 p = prim3(u, cf.gm1);
             flux_dir<2>(u, p, F);
 #pragma unroll
@@ -503,21 +511,21 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
         __syncthreads();
         if (!valid) continue;
 
-        const float* sc = &S.full[NF3][G3 + w][HXS + lane];
+        const float* sc = &S.full[kb][NF3][G3 + w][HXS + lane];
         float bxl = 0.f, bxr = 0.f, byl = 0.f, byr = 0.f, bzr = 0.f;
         if (cf.hd) {
             bxl = cf.bsh[0] * (sc[-1] + sc[0]);
             bxr = cf.bsh[0] * (sc[0] + sc[1]);
             byl = cf.bsh[1] * (sc[-RW] + sc[0]);
             byr = cf.bsh[1] * (sc[0] + sc[RW]);
-            bzr = cf.bsh[2] * (sc[0] + S.col[(k + 1) % 3][NF3][tid]);
+            bzr = cf.bsh[2] * (sc[0] + S.col[(k + 1) % 4][NF3][tid]);
         }
-        const int s1 = (k + 1) % 3, s2 = (k + 2) % 3, s3 = (k + 3) % 3;
+        const int s1 = (k + 1) % 4, s2 = (k + 2) % 4, s3 = (k + 3) % 4;
         float wn[NF3];   // the stage output of the own cell
         const int zp1 = (k + 1) % 5, zm1 = (k + 4) % 5, zp2 = (k + 2) % 5, zm2 = (k + 3) % 5;
 #pragma unroll
         for (int f = 0; f < NF3; ++f) {
-            const float* uc = &S.full[f][G3 + w][HXS + lane];
+            const float* uc = &S.full[kb][f][G3 + w][HXS + lane];
             float hsum = 0.0f;
             if (cf.hd) {
                 const float hx = hd_line(uc, 1, cf.a[f][0], bxl, bxr) * cf.idd[0];
@@ -541,7 +549,7 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
                                         -(S.fz[zp2][f][tid] - S.fz[zm2][f][tid])) * cf.i12[2];
             const float kf = hsum - ((dfx + dfy) + dfz);
             const long long e = f * ne + pk + colc;
-            const float r0 = S.rk[0][f][tid], ra = S.rk[1][f][tid];
+            const float r0 = S.rk[kb][0][f][tid], ra = S.rk[kb][1][f][tid];
             if (STAGE == 1) {
                 __stcs(&acc[e], kf);
                 __stcs(&out[e], __fmaf_rn(cf.h, kf, uc[0]));
