@@ -265,10 +265,34 @@ def run_batched(args, ws, local, pg, torch):
     counts = {str(n): sizes.count(n) for n in sorted(set(sizes))}
     b.close()
     value = ws * cells * args.batch_steps / (ms * 1e-3)
+    # per size class: the runs of one size as a batch of their own (autotuned, 100 steps)
+    per_size = {}
+    for n in sorted(set(sizes)):
+        ks = [k for k, m in enumerate(sizes) if m == n]
+        bs = Batch([runs[k] for k in ks], device=local)
+        for j, k in enumerate(ks):
+            b0, gamma, phases = inputs.ot_family_params(2024, k)
+            bs.set_state(j, inputs.orszag_tang(n, b0=b0, gamma=gamma, phases=phases), None, 0.0)
+        cfg_n, _ = bs.tune(trials=2)
+        bs.steps(args.warmup)
+        bs.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bs.steps(100)
+        e1.record(stream)
+        e1.synchronize()
+        bs.sync()
+        ms_n = reduce_max(e0.elapsed_time(e1), pg, "cuda")
+        bs.close()
+        per_size[str(n)] = {"runs": len(ks), "value": ws * len(ks) * n * n * 100 / (ms_n * 1e-3),
+                            "tuned_config": {"persistent": cfg_n[0], "ctas_per_sm": cfg_n[1], "order": cfg_n[2]}}
+    peak, peak_kind = measured_peaks()
+    gbs = value * 4 * 90 / 1e9
     return {"value": value, "unit": "cell-updates/s", "ms_per_step": ms / args.batch_steps,
             "steps": args.batch_steps, "runs": len(sizes), "sizes": counts, "cells": cells,
             "tuned_config": {"persistent": cfg[0], "ctas_per_sm": cfg[1], "order": cfg[2]},
-            "gb_per_s": value * 4 * 90 / 1e9, "gpu_launches": 5 * args.batch_steps}
+            "gb_per_s": gbs, "roofline_frac": gbs / peak, "peak_kind": f"of {peak_kind}",
+            "per_size": per_size, "gpu_launches": 5 * args.batch_steps}
 
 
 def run_learned(args, local):

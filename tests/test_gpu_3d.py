@@ -35,6 +35,8 @@ FP32_CASES = [
     dict(n=(37, 11, 70), steps=4, kw=dict(x1=1.5, z1=2.0), compress=0.3),
     dict(n=(33, 9, 40), steps=4, kw=dict(hyperdiffusion=0), compress=0.3),
     dict(n=(64, 8, 33), steps=3, kw=dict(y1=0.5), compress=0.5),
+    dict(n=(45, 13, 37), steps=5, kw=dict(z1=1.3), compress=0.4),
+    dict(n=(12, 12, 12), steps=6, kw={}, compress=0.3),
 ]
 
 
