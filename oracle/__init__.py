@@ -329,6 +329,15 @@ def cfl_dt3(pr: Problem3, cx: float, cy: float, cz: float) -> float:
     return _load3().orc3_cfl_dt(ctypes.byref(pr._c()), cx, cy, cz)
 
 
+def rk4_step3(pr: Problem3, w, dt: float, cmax_xyz) -> np.ndarray:
+    """One classical RK4 step of length dt with the given signal speeds (the
+    hyper-diffusion coefficients use them); returns the new state."""
+    lib = _load3()
+    w = _state3(w, pr).copy()
+    lib.orc3_rk4_step(ctypes.byref(pr._c()), _dp(w), float(dt), *(float(c) for c in cmax_xyz))
+    return w
+
+
 def run3(pr: Problem3, w, max_steps: int, fixed_dt: float = 0.0, t0: float = 0.0):
     """max_steps CFL steps (or fixed_dt > 0); returns (w, t, steps)."""
     lib = _load3()

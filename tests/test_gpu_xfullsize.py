@@ -95,3 +95,38 @@ def test_bench_config_one_step_windows(oracle_mod, inputs_mod, n):
         err = l1rel(g, ref)
         assert np.all(err <= TOL_FP32_L1), (j0, i0, err)
         assert np.all(maxrel(g, ref) <= 1e-4), (j0, i0, maxrel(g, ref))
+
+
+def _window3(w, k0, j0, i0, size, margin):
+    """Periodic window of a 3D state [8][nz][ny][nx], size + 2 margin cells per side."""
+    nz, ny, nx = w.shape[1:]
+    kk = np.arange(k0 - margin, k0 + size + margin) % nz
+    jj = np.arange(j0 - margin, j0 + size + margin) % ny
+    ii = np.arange(i0 - margin, i0 + size + margin) % nx
+    return np.ascontiguousarray(w[:, kk][:, :, jj][:, :, :, ii])
+
+
+def test_3d_bench_config_one_step_windows(oracle_mod, inputs_mod):
+    """The 3D form at the size the benchmark times (256^3 FP32, compressive
+    Orszag-Tang variant): one CFL step compared with the FP64 oracle on sampled
+    periodic windows (a cell depends only on cells within 12 of it), given the
+    GPU's step and the oracle's signal speeds of the full state."""
+    from paper_1710_06423_b300.sac import FP32 as P32, Solver3
+    n = 256
+    w0 = inputs_mod.ot_3d(n, n, n, compress=0.3)
+    with Solver3(nx=n, ny=n, nz=n, precision=P32) as s:
+        s.set_state(w0, 0.0)
+        s.step()
+        got, dt = s.get_state()
+    cm = oracle_mod.cmax3(oracle_mod.Problem3(nx=n, ny=n, nz=n), w0)
+    size, margin = 16, 12
+    m = size + 2 * margin
+    starts = [(0, 0, 0), (n - 10, n - 20, n - 5), (n // 2 + 3, n // 3 + 7, n // 5), (5, n - 1, 77)]
+    for k0, j0, i0 in starts:
+        win = _window3(w0, k0, j0, i0, size, margin)
+        pr = oracle_mod.Problem3(nx=m, ny=m, nz=m, x1=m / n, y1=m / n, z1=m / n)
+        ref = oracle_mod.rk4_step3(pr, win, dt, cm)[:, margin:-margin, margin:-margin, margin:-margin]
+        g = _window3(got, k0, j0, i0, size, 0)
+        err = l1rel(g.reshape(8, -1), ref.reshape(8, -1))
+        assert np.all(err <= TOL_FP32_L1), ((k0, j0, i0), err)
+        assert np.all(maxrel(g.reshape(8, -1), ref.reshape(8, -1)) <= 1e-4), (k0, j0, i0)

@@ -95,3 +95,28 @@ def test_periodic_sums_conserved(oracle_mod):
     out, _, _ = o.run3(pr, w, max_steps=3)
     s0, s1 = w.reshape(8, -1).sum(axis=1), out.reshape(8, -1).sum(axis=1)
     np.testing.assert_allclose(s1, s0, rtol=0, atol=1e-12 * np.abs(w).reshape(8, -1).sum(axis=1).max())
+
+
+def test_one_step_depends_only_on_cells_within_12(oracle_mod, inputs_mod):
+    """One RK4 step reads 3 cells per stage in every direction, so the step on a
+    periodically-wrapped window with a 12-cell margin equals the full-grid step
+    inside the margin (the basis of the full-size window parity test)."""
+    o = oracle_mod
+    n, size, margin = 48, 8, 12
+    m = size + 2 * margin
+    w = inputs_mod.ot_3d(n, n, n, compress=0.4)
+    pr = o.Problem3(nx=n, ny=n, nz=n)
+    cm = o.cmax3(pr, w)
+    dt = o.cfl_dt3(pr, *cm)
+    full = o.rk4_step3(pr, w, dt, cm)
+    ref_run, _, _ = o.run3(pr, w, max_steps=1)
+    np.testing.assert_array_equal(full, ref_run)
+    for k0, j0, i0 in [(0, 0, 0), (40, 3, 45), (20, 30, 10)]:
+        idx = [np.arange(q - margin, q + size + margin) % n for q in (k0, j0, i0)]
+        win = np.ascontiguousarray(w[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]])
+        # the window's grid spacing is exactly 1/n (m/n and (m/n)/m are exact here)
+        prw = o.Problem3(nx=m, ny=m, nz=m, x1=m / n, y1=m / n, z1=m / n)
+        got = o.rk4_step3(prw, win, dt, cm)[:, margin:-margin, margin:-margin, margin:-margin]
+        inner = [np.arange(q, q + size) % n for q in (k0, j0, i0)]
+        exp = full[:, inner[0]][:, :, inner[1]][:, :, :, inner[2]]
+        np.testing.assert_array_equal(got, exp)
