@@ -11,8 +11,9 @@
 // One CTA (256 threads, two per SM) owns a 32 x 32 tile at a time and walks
 // the tiles of the grid persistently:
 //   0. stage the tile + 3-cell halo of the three planes into shared memory
-//      (rows 16-byte aligned): TMA bulk row copies on an mbarrier in the
-//      persistent kernel, 16-byte cp.async.cg in the batch kernel;
+//      (rows 16-byte aligned): one 3D tensor copy (TMA, cp.async.bulk.tensor)
+//      per plane on an mbarrier in the persistent kernel; bulk row copies in
+//      the batch kernel's persistent mode, 16-byte cp.async.cg otherwise;
 //   1. per staged cell: v = m/rho, total pressure, energy-flux factor, B.v,
 //      the x fluxes (cells x0-2..x0+TX+1 of the tile rows) and y fluxes
 //      (rows y0-2..y0+TY+1 of the tile columns) of all three pairs;
@@ -39,6 +40,7 @@
 // (S1 - U0 is exact when both are within a factor of two, so the new state is
 // rounded once per step.)
 #pragma once
+#include <cuda.h>
 #include "sac_internal.cuh"
 #include "speed.cuh"
 
@@ -92,10 +94,15 @@ __device__ __forceinline__ float rcp_approx(float v)
     return r;
 }
 
-// Bring 256 bytes at p (16-byte aligned, inside an allocation) into L2.
-__device__ __forceinline__ void prefetch_l2_bulk256(const void* p)
+// Bring the 256 bytes at p (inside an allocation) into L2: three per-thread
+// line prefetches.  (A bulk prefetch takes a uniform operand, so lanes with
+// different addresses would be issued one after another.)
+__device__ __forceinline__ void prefetch_l2_256(const void* p)
 {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" :: "l"(p) : "memory");
+    const char* c = reinterpret_cast<const char*>(p);
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(c));
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(c + 128));
+    asm volatile("prefetch.global.L2 [%0];" :: "l"(c + 255));
 }
 // 16-byte copy through L2 only (no L1 allocation); predicated without a
 // branch: no copy and no read of gmem when pred is false
@@ -174,7 +181,7 @@ constexpr int PW = RX - 2;                                 // primitive columns 
 // The flux of the third pair has an exactly zero component in each direction,
 // (0, F_By) along x and (F_Bx, 0) along y: only the nonzero one is stored.
 struct Smem {
-    float2 u[3][RY][RXP];
+    float2 u[3][RY + 2][RXP];   // two spare rows: planes start 128-byte aligned (RY+2)*RXP*8 = 105*128
     union {
         struct {
             float2 fx[2][TY][FXP];   // x fluxes of pairs 0, 1
@@ -361,9 +368,13 @@ __device__ __forceinline__ void load_pointwise(const StageArgs<float>& a, const 
     }
 }
 
-// Persistent kernel: plane p of the staged region of tile (x0, y0) by TMA bulk
-// copies, one 320-byte row per copy (lane k of warp w copies row w + NW k),
-// completing on the CTA's mbarrier; kTileBytes per tile (three planes).
+// Persistent kernels: plane p of the staged region of tile (x0, y0), completing
+// on the CTA's mbarrier.  With a tensor map of the stage input (single-run
+// kernel): one 3D tensor copy of the plane's RXP x RY box (RXP float2 per row,
+// the region's own pitch; coordinates past the grid read zeros), issued by one
+// thread; kTileBytesTM per tile.  Without one (batch kernel, whose next tile
+// may belong to another run): one 320-byte bulk copy per row (lane k of warp w
+// copies row w + NW k); kTileBytes per tile.
 constexpr unsigned kTileBytes = 3u * RY * RX * sizeof(float2);
 // Where the next tile's staged region comes from: its tile origin and the
 // stencil input of its run (a batch's next tile may belong to another run).
@@ -373,13 +384,24 @@ struct NextTile {
     const float* sin;
     long long fstride;
     int pitch;
+    const CUtensorMap* tm = nullptr;   // the stage input as a 3D tensor (pitch, rows, 3 planes)
 };
+constexpr unsigned kTileBytesTM = 3u * RY * RXP * sizeof(float2);
+static_assert((RY + 2) * RXP * sizeof(float2) % 128 == 0, "tensor-copy destinations 128-byte aligned");
 __device__ __forceinline__ NextTile next_tile(const StageArgs<float>& a, bool has, int x0, int y0)
 {
     return NextTile{has, x0, y0, a.sin, a.L.fstride, a.L.pitch};
 }
 __device__ __forceinline__ void stage_plane_bulk(const NextTile& n, Smem& S, const int p, unsigned long long* bar)
 {
+    if (n.tm) {   // one tensor copy of the plane's RY x RXP box (rows of RXP float2, as the region's pitch)
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                         :: "r"(smem_u32(&S.u[p][0][0])), "l"(n.tm), "r"(n.x0), "r"(n.y0), "r"(p), "r"(smem_u32(bar)) : "memory");
+        }
+        return;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = warp + NW * lane;
     if (lane < (RY + NW - 1) / NW && r < RY) {
@@ -416,14 +438,14 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     const long long e_first = L.at(gi, y0 + y_0);
     const int nq = gi < L.nx ? L.ny - (y0 + y_0) : 0;
     // The pointwise RK registers U0/D of these cells are brought into L2 when the
-    // tile starts (one bulk prefetch per 256-byte row segment: lane l of the warp
+    // tile starts (one prefetch per 256-byte row segment: lane l of the warp
     // takes pair l/8, array U0 or D by (l/4)%2, row l%4 of the warp's 4 x 32
     // cells), so the register loads later in the tile hit L2.  Prefetching a
     // whole tile ahead measured slower.
     if (STAGE >= 2 && lane < 24) {
         const int pp = lane >> 3, arr = (lane >> 2) & 1, qq = lane & 3;
         if (STAGE >= 3 || arr == 0)
-            prefetch_l2_bulk256(reinterpret_cast<const float2*>(arr ? a.acc : a.u0) + pp * P
+            prefetch_l2_256(reinterpret_cast<const float2*>(arr ? a.acc : a.u0) + pp * P
                                 + L.at(x0, y0 + y_0 + qq));
     }
 
@@ -650,7 +672,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         if (OVERLAP) {
             __syncthreads();   // plane p of this tile is read for good
             if (nt.has) {
-                if (p == 0 && threadIdx.x == 0) mbar_expect_tx(bar, kTileBytes);
+                if (p == 0 && threadIdx.x == 0) mbar_expect_tx(bar, nt.tm ? kTileBytesTM : kTileBytes);
                 stage_plane_bulk(nt, S, p, bar);
             }
         }
@@ -735,13 +757,16 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 // The step constants are read once; stage 4 keeps the signal-speed maximum of
 // all its tiles in registers and reduces it once at the end.
 template <int STAGE, bool BG, bool HD, bool GRAV, bool SF = false>
-__global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, const int ntx, const int ntiles)
+__global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, const int ntx, const int ntiles,
+                                                    const __grid_constant__ CUtensorMap tm)
 {
     if (a.sc->skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ unsigned long long red[2][NW];
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
     store_hd_coeffs(a, S, threadIdx.x);   // no later phase writes S.ax/S.ay
+    // tensor copies need 128-byte aligned destinations; otherwise row copies
+    const CUtensorMap* tmp = (smem_u32(&S.u[0][0][0]) & 127u) == 0 ? &tm : nullptr;
     const StepConsts K = load_step_consts(a.sc);
     unsigned long long m[2] = {0ull, 0ull};
     __shared__ __align__(8) unsigned long long bar;   // staging completion (one arrival + bytes per tile)
@@ -751,15 +776,17 @@ __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, co
     bool failed = false;
     int t = blockIdx.x;
     if (t < ntiles) {
-        if (threadIdx.x == 0) mbar_expect_tx(&bar, kTileBytes);
+        NextTile f = next_tile(a, true, (t % ntx) * TX, (t / ntx) * TY);
+        f.tm = tmp;
+        if (threadIdx.x == 0) mbar_expect_tx(&bar, f.tm ? kTileBytesTM : kTileBytes);
 #pragma unroll
-        for (int p = 0; p < 3; ++p) stage_plane_bulk(next_tile(a, true, (t % ntx) * TX, (t / ntx) * TY), S, p, &bar);
+        for (int p = 0; p < 3; ++p) stage_plane_bulk(f, S, p, &bar);
     }
     for (; t < ntiles; t += gridDim.x) {
         const int tn = t + gridDim.x;
-        tile_body<STAGE, BG, HD, true, GRAV, SF>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m,
-                                                 next_tile(a, tn < ntiles, (tn % ntx) * TX, (tn / ntx) * TY),
-                                                 &bar, &phase, &failed);
+        NextTile nt = next_tile(a, tn < ntiles, (tn % ntx) * TX, (tn / ntx) * TY);
+        nt.tm = tmp;
+        tile_body<STAGE, BG, HD, true, GRAV, SF>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m, nt, &bar, &phase, &failed);
         if (failed) return;
     }
     if (STAGE == 4) block_speed_max(m, red, a.sc);
