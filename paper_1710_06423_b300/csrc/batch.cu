@@ -28,6 +28,7 @@ struct BatchArgs {
     int ntiles;
     unsigned* counters;             // [4] per-stage queue heads (persistent mode)
     int persistent;
+    const CUtensorMap* tmaps;       // [nruns][4]: tensor map of each run's stage input, or null
 };
 
 // Start one step of every run; also re-arms the four stage queues.
@@ -50,7 +51,7 @@ __device__ __forceinline__ void load_args(const BatchArgs& b, int run, StageArgs
 template <int STAGE, bool BG, bool HD>
 __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs b)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ unsigned long long red[2][f32k::NW];
     __shared__ __align__(16) StageArgs<float> sa[2];   // current / next tile's run
     __shared__ int tile_s[2];
@@ -73,8 +74,11 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
         return;
     }
     // persistent: tiles from the queue; the next tile is fetched when a tile
-    // starts so that its region streams into shared memory (TMA bulk copies)
-    // during the current tile's Y sweep, with the next run's own layout
+    // starts so that its region streams into shared memory (one TMA tensor copy
+    // per plane with the next run's tensor map, else bulk row copies) during the
+    // current tile's Y sweep
+    const bool tma = b.tmaps != nullptr && (f32k::smem_u32(&S.u[0][0][0]) & 127u) == 0;
+    const auto tmap = [&](int run) { return tma ? &b.tmaps[run * 4 + (STAGE - 1)] : nullptr; };
     if (threadIdx.x == 0) {
         f32k::mbar_init(&bar, 1);
         tile_s[0] = (int)atomicAdd(&b.counters[STAGE - 1], 1u);
@@ -89,8 +93,9 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
     __syncthreads();
     bool staged = !sa[0].sc->skip;
     if (staged) {
-        if (threadIdx.x == 0) f32k::mbar_expect_tx(&bar, f32k::kTileBytes);
-        const f32k::NextTile first = f32k::next_tile(sa[0], true, d.y * f32k::TX, d.z * f32k::TY);
+        f32k::NextTile first = f32k::next_tile(sa[0], true, d.y * f32k::TX, d.z * f32k::TY);
+        first.tm = tmap(d.x);
+        if (threadIdx.x == 0) f32k::mbar_expect_tx(&bar, first.tm ? f32k::kTileBytesTM : f32k::kTileBytes);
 #pragma unroll
         for (int p = 0; p < 3; ++p) f32k::stage_plane_bulk(first, S, p, &bar);
     }
@@ -106,7 +111,8 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
         __syncthreads();
         const StageArgs<float>& A = sa[buf];
         const bool nstage = nxt < b.ntiles && !sa[buf ^ 1].sc->skip;
-        const f32k::NextTile nt = f32k::next_tile(sa[buf ^ 1], nstage, dn.y * f32k::TX, dn.z * f32k::TY);
+        f32k::NextTile nt = f32k::next_tile(sa[buf ^ 1], nstage, dn.y * f32k::TX, dn.z * f32k::TY);
+        nt.tm = nstage ? tmap(dn.x) : nullptr;
         if (staged) {
             f32k::store_hd_coeffs(A, S, threadIdx.x);
             const f32k::StepConsts K = f32k::load_step_consts(A.sc);
@@ -118,7 +124,7 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
         } else if (nstage) {
             // this tile's run is done or failed: nothing was staged for it, so
             // the next tile's region is copied now
-            if (threadIdx.x == 0) f32k::mbar_expect_tx(&bar, f32k::kTileBytes);
+            if (threadIdx.x == 0) f32k::mbar_expect_tx(&bar, nt.tm ? f32k::kTileBytesTM : f32k::kTileBytes);
 #pragma unroll
             for (int p = 0; p < 3; ++p) f32k::stage_plane_bulk(nt, S, p, &bar);
         }
@@ -186,6 +192,7 @@ struct sac_batch {
     RunCtl* d_ctl = nullptr;
     int4* d_tiles = nullptr;
     unsigned* d_counters = nullptr;
+    CUtensorMap* d_tmaps = nullptr;   // [n][4], or null (row copies)
     int ntiles = 0;
     int persistent = 1, ctas_per_sm = 2, order = 1;
     cudaGraphExec_t g1 = nullptr, gN = nullptr;
@@ -249,6 +256,7 @@ static cudaError_t enqueue_batch_step(sac_batch* b, cudaStream_t s)
     if (e != cudaSuccess) return e;
     BatchArgs a;
     a.args = b->d_args; a.tiles = b->d_tiles; a.ntiles = b->ntiles; a.counters = b->d_counters;
+    a.tmaps = b->d_tmaps;
     a.persistent = b->persistent;
     const int grid = b->persistent ? std::min(b->ntiles, b->ctas_per_sm * b->nsm) : b->ntiles;
     const int hgrid = (int)std::min<long long>((b->max_halo + 255) / 256, 2 * b->nsm);
@@ -305,7 +313,7 @@ void sac_batch_free(sac_batch* b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graphs(b);
     for (sac_ctx* c : b->runs) sac_free(c);
-    cudaFree(b->d_args); cudaFree(b->d_ctl); cudaFree(b->d_tiles); cudaFree(b->d_counters);
+    cudaFree(b->d_args); cudaFree(b->d_ctl); cudaFree(b->d_tiles); cudaFree(b->d_counters); cudaFree(b->d_tmaps);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
 }
@@ -373,6 +381,20 @@ int sac_batch_init(const sac_params* runs, int n, sac_batch** out)
         if (e == cudaSuccess) e = cudaMemcpy(b->d_ctl, ctl.data(), n * sizeof(RunCtl), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, 4 * sizeof(unsigned));
         if (e != cudaSuccess) { rc = bfail(b, SAC_ERR_CUDA, "tables: %s", cudaGetErrorString(e)); break; }
+        {   // tensor maps of every run's stage inputs (without them the kernel copies rows)
+            std::vector<CUtensorMap> maps(args.size());
+            bool ok = true;
+            for (size_t k = 0; k < args.size() && ok; ++k) ok = encode_stage_tensor_map(args[k], &maps[k]) == cudaSuccess;
+            if (ok && cudaMalloc(&b->d_tmaps, maps.size() * sizeof(CUtensorMap)) == cudaSuccess) {
+                if (cudaMemcpy(b->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess) {
+                    cudaFree(b->d_tmaps);
+                    b->d_tmaps = nullptr;
+                }
+            } else {
+                cudaGetLastError();
+                b->d_tmaps = nullptr;
+            }
+        }
         rc = apply_config(b, 1, 2, 1);
     } while (0);
     if (rc != SAC_OK) {

@@ -28,7 +28,8 @@ cudaError_t set_attr()
 int g_resident = 296;   // persistent grid: resident CTAs on the device (2 per SM)
 
 // Tensor maps of the stage inputs (3D: pitch float2 x padded rows x 3 planes;
-// box RXP x RY x 1), encoded once per buffer and layout.
+// box RXP x RY x 1), encoded once per buffer and layout (the driver's encoder
+// is reached through the runtime's entry-point query: no link to libcuda).
 struct TmEntry {
     const void* p;
     int pitch, rows;
@@ -38,7 +39,9 @@ struct TmEntry {
 TmEntry g_tm[16];
 int g_ntm = 0, g_tm_next = 0;
 std::mutex g_tm_mu;
-cudaError_t stage_tensor_map(const StageArgs<float>& a, CUtensorMap* out)
+}  // namespace
+
+cudaError_t encode_stage_tensor_map(const StageArgs<float>& a, CUtensorMap* out)
 {
     std::lock_guard<std::mutex> lk(g_tm_mu);
     for (int i = 0; i < g_ntm; ++i)
@@ -68,6 +71,8 @@ cudaError_t stage_tensor_map(const StageArgs<float>& a, CUtensorMap* out)
     return cudaSuccess;
 }
 
+namespace {
+
 __global__ void halo_fp32(const StageArgs<float> a, long long n)
 {
     if (a.sc->skip) return;
@@ -82,7 +87,7 @@ cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
     const int ntx = (a.L.nx + TX - 1) / TX, nty = (a.L.ny + TY - 1) / TY, ntiles = ntx * nty;
     const int grid = ntiles < g_resident ? ntiles : g_resident;
     CUtensorMap tm;
-    const cudaError_t te = stage_tensor_map(a, &tm);
+    const cudaError_t te = encode_stage_tensor_map(a, &tm);
     if (te != cudaSuccess) return te;
     f32k::stage_fp32<S, BG, HD, GR, SF><<<grid, NT, sizeof(f32k::Smem), s>>>(a, ntx, ntiles, tm);
     if (a.bc_x != BC_FIXED || a.bc_y != BC_FIXED) {

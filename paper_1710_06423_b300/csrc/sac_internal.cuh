@@ -1,6 +1,7 @@
 // sac_internal.cuh -- device data layout, per-context scalars and kernel
 // arguments shared by the kernel translation units and the host engine.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -135,6 +136,9 @@ struct StageArgs {
 // ---- launchers implemented in the kernel translation units --------------
 cudaError_t launch_stage_fp64(const StageArgs<double>& a, int stage, bool hd, bool bg, cudaStream_t s);
 cudaError_t launch_stage_fp32(const StageArgs<float>& a, int stage, bool hd, bool bg, cudaStream_t s);
+// the tensor map of a FP32 stage input (3D: pitch float2 x padded rows x 3 planes,
+// box of one staged plane), cached per buffer and layout (kernels_fp32.cu)
+cudaError_t encode_stage_tensor_map(const StageArgs<float>& a, CUtensorMap* out);
 // one-time kernel attribute set-up (dynamic shared memory limits); idempotent
 cudaError_t prepare_stage_fp64();
 cudaError_t prepare_stage_fp32();

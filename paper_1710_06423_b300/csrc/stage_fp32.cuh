@@ -440,11 +440,11 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
     // The pointwise RK registers U0/D of these cells are brought into L2 when the
     // tile starts (one prefetch per 256-byte row segment: lane l of the warp
     // takes pair l/8, array U0 or D by (l/4)%2, row l%4 of the warp's 4 x 32
-    // cells), so the register loads later in the tile hit L2.  Prefetching a
-    // whole tile ahead measured slower.
+    // cells; rows inside the grid), so the register loads later in the tile hit
+    // L2.  Prefetching a whole tile ahead measured slower.
     if (STAGE >= 2 && lane < 24) {
         const int pp = lane >> 3, arr = (lane >> 2) & 1, qq = lane & 3;
-        if (STAGE >= 3 || arr == 0)
+        if ((STAGE >= 3 || arr == 0) && y0 + y_0 + qq < L.ny)
             prefetch_l2_256(reinterpret_cast<const float2*>(arr ? a.acc : a.u0) + pp * P
                                 + L.at(x0, y0 + y_0 + qq));
     }
