@@ -276,7 +276,12 @@ __device__ __forceinline__ void face_fluxes(const float2 (&u)[SEG + 6], const fl
         const float m1y = fmaxf(SF ? a1y[q] : max3(a1y[q - 1], a1y[q], a1y[q + 1]), 1e-30f);
         const float m3x = SF ? a3x[q] : max3(a3x[q - 1], a3x[q], a3x[q + 1]);
         const float m3y = SF ? a3y[q] : max3(a3y[q - 1], a3y[q], a3y[q + 1]);
+#if SAC_FP32_IEEE_DIV
         const float2 R = make_float2(fdiv(m3x, m1x), fdiv(m3y, m1y));
+#else
+        // one packed product of the two components' m3 * rcp(m1) (the same roundings as two scalar ones)
+        const float2 R = mul2(make_float2(m3x, m3y), make_float2(rcp_approx(m1x), rcp_approx(m1y)));
+#endif
         const float2 nu = fma2(a, R, bsf[q - 1]);
         G[q - 1] = mul2(nu, d1[q]);
     }
