@@ -422,9 +422,15 @@ def run_3d(args, ws, local, pg, torch, n=256):
         ev1.record(stream)
         ev1.synchronize()
         ms = reduce_max(ev0.elapsed_time(ev1), pg, "cuda")
-    return {"value": ws * n ** 3 * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+    value = ws * n ** 3 * args.steps / (ms * 1e-3)
+    # algorithmic bytes per cell and RK4 step: 136 B per stage in the stage kernel
+    # (8 fields: input, U0, accumulator read/write, output) + 20 B in the shock kernel
+    bpc = 4 * 136.0 + 4 * 20.0
+    peak, peak_kind = measured_peaks()
+    return {"value": value, "ms_per_step": ms / args.steps,
             "workload": f"3D orszag-tang variant {n}^3 with compressive flow 0.3, periodic, FP32, hyper-diffusion on",
-            "bytes_per_cell_step": 4 * 136.0 + 4 * 20.0}
+            "bytes_per_cell_step": bpc, "gb_per_s": value * bpc / 1e9 / ws,
+            "roofline_frac": value * bpc / 1e9 / ws / peak, "peak_kind": f"of {peak_kind}"}
 
 
 def run_ours(args, ws, rank, local, pg):
