@@ -18,11 +18,14 @@
 // bits, NaN propagates); dt = C min(min(dx/cx, dy/cy), dz/cz) is formed on
 // the host in FP64.  This first 3D path keeps the fluxes in global memory (a
 // correctness-first layout: about twice the bytes of a fused tile kernel).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <limits>
 #include <string>
@@ -257,11 +260,13 @@ __global__ void export3(const T* __restrict__ u, double* __restrict__ w, Grid3 g
 
 // ---------------------------------------------------------------------------
 // FP32 fused RK stage.  One CTA owns TX x TY columns and marches through KZ
-// planes along z.  While it works on plane k, cp.async copies plane k+1 with its
-// x/y halo (16-byte row segments), the RK registers of plane k+1 and the own
-// column of plane k+4 into shared memory (double buffer); per plane it builds
-// the x and y fluxes of plane k and the z flux of plane k+2, and then every
-// thread forms k = H - div F for its cell and applies the RK register update.  Along z the face quantities |d1|, |d3|, d1 and the hyper-diffusive
+// planes along z.  While it works on plane k, one thread's tensor-map TMA
+// copies bring plane k+1 with its x/y halo (all eight fields in one 4D box, the
+// shock indicator in one 3D box), the RK registers of plane k+1 and the column
+// tile of plane k+4 into shared memory (double buffer, one mbarrier per
+// buffer); per plane it builds the x and y fluxes of plane k and the z flux of
+// plane k+2, and then every thread forms k = H - div F for its cell and applies
+// the RK register update.  Along z the face quantities |d1|, |d3|, d1 and the hyper-diffusive
 // face flux roll in registers, and the z fluxes roll through a five-plane ring.
 // The shock indicator comes from shock3_f32 (global, ghost-extended layout) and
 // is staged beside the fields.  Arithmetic is single precision throughout
@@ -274,10 +279,9 @@ constexpr int RH = TY + 2 * G3;                // staged rows j0-3 .. j0+TY+2
 constexpr int NS = NF3 + 1;                    // eight fields and the shock indicator
 constexpr int KZ = 32;                         // planes per CTA
 constexpr int FXW = TX + 4, FYH = TY + 4;      // flux extents: x i0-2 .. i0+TX+1, y j0-2 .. j0+TY+1
-constexpr int VPR = RW / 4;                    // 16-byte segments per staged row
 
 struct Smem {
-    float full[2][NS][RH][RW];   // planes k and k+1 (the next one is copied in during plane k)
+    float full[2][NS + 1][RH][RW];   // planes k and k+1 (one spare field-plane: 128-byte aligned buffers)
     float col[4][NS][NT];        // planes k+1 .. k+4, own column (ring by plane % 4)
     float fz[5][NF3][NT];     // z fluxes of planes k-2 .. k+2, own column (ring by plane % 5)
     float fx[NF3][TY][FXW];
@@ -300,19 +304,47 @@ __device__ __forceinline__ float rcpf(float x)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+// tensor maps of one stage launch: the stage input (4D: x, y, z, field) and the
+// shock indicator (3D) as a staged plane box and as a column-tile box, U0 and
+// the RK accumulator as column-tile boxes
+struct Maps {
+    CUtensorMap in_full, in_col, sh_full, sh_col, u0_col, acc_col;
+};
+constexpr unsigned kFullBytes = (unsigned)(NF3 * RH * RW * sizeof(float)), kShFullBytes = (unsigned)(RH * RW * sizeof(float));
+constexpr unsigned kColBytes = (unsigned)(NS * NT * sizeof(float)), kRkBytes = (unsigned)(NF3 * NT * sizeof(float));
+// every tensor-copy destination starts on a 128-byte boundary of the Smem block
+static_assert(offsetof(Smem, col) % 128 == 0 && offsetof(Smem, rk) % 128 == 0, "Smem layout");
+static_assert(sizeof(Smem::full[0]) % 128 == 0 && (NF3 * RH * RW * sizeof(float)) % 128 == 0, "plane buffers");
+static_assert(sizeof(Smem::col[0]) % 128 == 0 && (NF3 * NT * sizeof(float)) % 128 == 0, "column ring");
+static_assert(sizeof(Smem::rk[0][0]) % 128 == 0, "RK registers");
+static_assert((RW * sizeof(float)) % 16 == 0 && (TX * sizeof(float)) % 16 == 0, "box rows");
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void tma4(const void* dst, const CUtensorMap* m, int x, int y, int z, int f, unsigned long long* bar)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src));
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                 :: "r"(su32(dst)), "l"(m), "r"(x), "r"(y), "r"(z), "r"(f), "r"(su32(bar)) : "memory");
 }
-__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+__device__ __forceinline__ void tma3(const void* dst, const CUtensorMap* m, int x, int y, int z, unsigned long long* bar)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src));
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 :: "r"(su32(dst)), "l"(m), "r"(x), "r"(y), "r"(z), "r"(su32(bar)) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// wait until at most one committed group (the newest) is still in flight
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(su32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(su32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
 
 struct P3 {
     float v[3], pt, bv;
@@ -369,11 +401,13 @@ __device__ __forceinline__ float hd_line(const float* u, int s, float a, float b
 template <int STAGE>
 __global__ void __launch_bounds__(NT, 2)
 stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const float* u0, float* __restrict__ acc,
-           float* out, Grid3 g, Coef cf, int ntx, unsigned long long* __restrict__ keys)
+           float* out, Grid3 g, Coef cf, int ntx, unsigned long long* __restrict__ keys, int* __restrict__ status,
+           const __grid_constant__ Maps tm)
 // out == u0 in stage 4; in == u0 in stage 1; stage 4 also reduces the signal
 // speeds of its output into keys (ordered bits of FP64 maxima, one per direction)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar[2];   // copies of planes with even / odd k
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int i0 = (int)(blockIdx.x % ntx) * TX, j0 = (int)(blockIdx.x / ntx) * TY;
@@ -384,41 +418,39 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
     // own column (clamped into the interior for the threads past a ragged edge)
     const long long colc = (long long)(min(y, g.ny - 1) + G3) * g.ex + (min(x, g.nx - 1) + GX);
     const auto plane = [&](int k) { return (long long)(k + G3) * P; };
-    const auto src = [&](int f) { return f < NF3 ? in + (long long)f * ne : sh; };
-    // staging descriptor: threads below RH * VPR own one 16-byte segment of every
-    // staged row (row r, segment v) and copy it for all nine planes' fields
-    const bool stager = tid < RH * VPR;
-    const int sr_ = tid / VPR, sv_ = tid - (tid / VPR) * VPR;
-    const bool sok = stager && j0 + sr_ < g.ey && i0 + 4 * sv_ < g.ex;
-    const long long soff_g = (long long)(j0 + sr_) * g.ex + (i0 + 4 * sv_);
-    const int soff_s = sr_ * RW + 4 * sv_;
     float sp_max[3] = {0.0f, 0.0f, 0.0f};
-    const auto issue = [&](int k) {
-        const long long pk = plane(k);
-        if (sok) {
-            const float* gp = in + pk + soff_g;
-#pragma unroll
-            for (int f = 0; f < NF3; ++f) cp_async16(&S.full[k & 1][f][0][0] + soff_s, gp + f * ne);
-            cp_async16(&S.full[k & 1][NF3][0][0] + soff_s, sh + pk + soff_g);
-        }
-        if (STAGE != 1) {
-            const long long e = pk + colc;
-#pragma unroll
-            for (int f = 0; f < NF3; ++f) {
-                cp_async4(&S.rk[k & 1][0][f][tid], u0 + f * ne + e);
-                cp_async4(&S.rk[k & 1][1][f][tid], acc + f * ne + e);
+    // one thread copies plane k (8 fields + shock indicator, with halo), its RK
+    // registers and the own-column tiles of planes q0 .. q1 on bar[k & 1]
+    const auto issue = [&](int k, int q0, int q1) {
+        if (tid == 0) {
+            unsigned long long* b = &bar[k & 1];
+            mbar_expect_tx(b, kFullBytes + kShFullBytes + (unsigned)(q1 - q0 + 1) * kColBytes + (STAGE != 1 ? 2u * kRkBytes : 0u));
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma4(&S.full[k & 1][0][0][0], &tm.in_full, i0, j0, k + G3, 0, b);        // x = i0-4, y = j0-3 (extended)
+            tma3(&S.full[k & 1][NF3][0][0], &tm.sh_full, i0, j0, k + G3, b);
+            for (int q = q0; q <= q1; ++q) {
+                tma4(&S.col[q & 3][0][0], &tm.in_col, i0 + GX, j0 + G3, q + G3, 0, b);
+                tma3(&S.col[q & 3][NF3][0], &tm.sh_col, i0 + GX, j0 + G3, q + G3, b);
+            }
+            if (STAGE != 1) {
+                tma4(&S.rk[k & 1][0][0][0], &tm.u0_col, i0 + GX, j0 + G3, k + G3, 0, b);
+                tma4(&S.rk[k & 1][1][0][0], &tm.acc_col, i0 + GX, j0 + G3, k + G3, 0, b);
             }
         }
     };
+    unsigned phase = 0;   // bit b: parity of bar[b]'s next completion
+    // tensor copies need 128-byte aligned destinations (all buffer offsets are multiples of 128)
+    if ((su32(&S) & 127u) != 0) {
+        if (tid == 0) atomicExch(status, 2);
+        return;
+    }
+    if (tid == 0) { mbar_init(&bar[0]); mbar_init(&bar[1]); }
+    __syncthreads();
 
     // prologue: copies of plane k0 and of the own column of planes k0+1 .. k0+3;
     // z fluxes of planes k0-2 .. k0+1; z face state of faces k0-1, k0 and the face
     // flux at k0-1/2
-#pragma unroll 1
-    for (int q = k0 + 1; q <= k0 + 3; ++q)
-        for (int f = 0; f < NS; ++f) cp_async4(&S.col[q % 4][f][tid], src(f) + plane(q) + colc);
-    issue(k0);
-    cp_async_commit();
+    issue(k0, k0 + 1, k0 + 3);
 #pragma unroll 1
     for (int q = k0 - 2; q <= k0 + 1; ++q) {
         float u[NF3], F[NF3];
@@ -454,16 +486,25 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
     for (int k = k0; k < k1; ++k) {
         __syncthreads();   // the previous plane's readers are done
         const long long pk = plane(k);
-        if (k + 1 < k1) {
-            issue(k + 1);
-            const long long q = plane(k + 4) + colc;   // used at step k+1 as its plane +3 (<= nz + 2)
-#pragma unroll
-            for (int f = 0; f < NF3; ++f) cp_async4(&S.col[(k + 4) % 4][f][tid], in + f * ne + q);
-            cp_async4(&S.col[(k + 4) % 4][NF3][tid], sh + q);
+        if (k + 1 < k1) issue(k + 1, k + 4, k + 4);   // plane k+4 <= nz + 2: inside the ghost frame
+        {   // plane k's copies (bounded wait; a timeout is reported and every thread leaves)
+            const int kb_ = k & 1;
+            unsigned it = 0;
+            bool to = false;
+            while (!mbar_try_wait(&bar[kb_], (phase >> kb_) & 1u)) {
+                if (++it > (1u << 22)) { to = true; break; }
+            }
+            if (__syncthreads_or(to)) {
+                if (tid == 0) {
+                    atomicExch(status, 1);
+                    // let plane k+1's copies (if issued) land before the CTA's memory is released
+                    if (k + 1 < k1)
+                        for (unsigned j = 0; j < (1u << 22) && !mbar_try_wait(&bar[kb_ ^ 1], (phase >> (kb_ ^ 1)) & 1u); ++j) {}
+                }
+                return;
+            }
+            phase ^= 1u << kb_;
         }
-        cp_async_commit();     // (possibly empty: the group count stays one per plane)
-        cp_async_wait_prev();  // plane k's group has landed
-        __syncthreads();
         const int kb = k & 1;
 
         {   // x and y fluxes of the own cell
@@ -619,6 +660,9 @@ struct sac3_ctx {
     void *u0 = nullptr, *sa = nullptr, *sb = nullptr, *acc = nullptr, *v = nullptr, *fl = nullptr, *sh = nullptr;
     double* wbuf = nullptr;                 // device FP64 staging of a host state
     unsigned long long* keys = nullptr;     // signal-speed keys (3)
+    int* status = nullptr;                  // FP32 stage kernels: 1 = a copy wait timed out
+    CUtensorMap m_full[3], m_col[3];        // FP32: stage inputs U0, SA, SB (plane box, column box)
+    CUtensorMap m_sh_full, m_sh_col, m_acc_col;
     double t = 0.0;
     bool have_state = false;
     bool keys_valid = false;                // keys hold the maxima of the current state
@@ -647,12 +691,43 @@ static int fail3(sac3_ctx* c, int code, const char* fmt, ...)
 // FP32: ghost frame, shock indicator and one fused kernel per stage
 template <int S>
 static cudaError_t launch_f32(const float* in, const float* sh, const float* u0, float* acc, float* out,
-                              const Grid3& g, const f3::Coef& cf, unsigned long long* keys, cudaStream_t st)
+                              const Grid3& g, const f3::Coef& cf, unsigned long long* keys, int* status,
+                              const f3::Maps& m, cudaStream_t st)
 {
     const int ntx = (g.nx + f3::TX - 1) / f3::TX, nty = (g.ny + f3::TY - 1) / f3::TY;
     const dim3 grid((unsigned)(ntx * nty), (unsigned)((g.nz + f3::KZ - 1) / f3::KZ));
-    f3::stage3_f32<S><<<grid, f3::NT, sizeof(f3::Smem), st>>>(in, sh, u0, acc, out, g, cf, ntx, keys);
+    f3::stage3_f32<S><<<grid, f3::NT, sizeof(f3::Smem), st>>>(in, sh, u0, acc, out, g, cf, ntx, keys, status, m);
     return cudaGetLastError();
+}
+
+// Tensor maps of the FP32 registers: 4D (x, y, z, field) for the eight-field
+// arrays, 3D for the shock indicator; box = a staged plane (40 x 10 x 1) or a
+// column tile (32 x 4 x 1), all fields at once.
+static bool encode_maps3(sac3_ctx* c)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !encode)
+            return false;
+    }
+    const Grid3& g = c->g;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.ex, (cuuint64_t)g.ey, (cuuint64_t)g.ez, (cuuint64_t)NF3};
+    const cuuint64_t str[3] = {(cuuint64_t)g.ex * 4, (cuuint64_t)(g.ex * g.ey) * 4, (cuuint64_t)g.ne * 4};
+    const cuuint32_t bfull[4] = {(cuuint32_t)f3::RW, (cuuint32_t)f3::RH, 1, (cuuint32_t)NF3};
+    const cuuint32_t bcol[4] = {(cuuint32_t)f3::TX, (cuuint32_t)f3::TY, 1, (cuuint32_t)NF3};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const auto enc = [&](CUtensorMap* m, void* base, int rank, const cuuint32_t* box) {
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    void* regs[3] = {c->u0, c->sa, c->sb};
+    bool ok = true;
+    for (int r = 0; r < 3 && ok; ++r) ok = enc(&c->m_full[r], regs[r], 4, bfull) && enc(&c->m_col[r], regs[r], 4, bcol);
+    ok = ok && enc(&c->m_sh_full, c->sh, 3, bfull) && enc(&c->m_sh_col, c->sh, 3, bcol) && enc(&c->m_acc_col, c->acc, 4, bcol);
+    return ok;
 }
 
 static cudaError_t prepare_f32()
@@ -693,16 +768,21 @@ static int fused_f32(sac3_ctx* c, double dt, const double cm[3], const double dd
         if (cf.hd) f3::shock3_f32<<<sgrid, 128, 0, c->stream>>>(in, sh, g, cf.i12[0], cf.i12[1], cf.i12[2]);
         // stage 4 reduces the signal speeds of the new state for the next step
         if (stage == 4) CK3(cudaMemsetAsync(c->keys, 0, 3 * sizeof(unsigned long long), c->stream));
+        const int ri = stage == 1 ? 0 : (stage == 3 ? 2 : 1);   // input register: U0, SA, SB, SA
+        const f3::Maps m{c->m_full[ri], c->m_col[ri], c->m_sh_full, c->m_sh_col, c->m_col[0], c->m_acc_col};
         cudaError_t e;
         switch (stage) {
-            case 1: e = launch_f32<1>(in, sh, u0, acc, out, g, cf, c->keys, c->stream); break;
-            case 2: e = launch_f32<2>(in, sh, u0, acc, out, g, cf, c->keys, c->stream); break;
-            case 3: e = launch_f32<3>(in, sh, u0, acc, out, g, cf, c->keys, c->stream); break;
-            default: e = launch_f32<4>(in, sh, u0, acc, out, g, cf, c->keys, c->stream); break;
+            case 1: e = launch_f32<1>(in, sh, u0, acc, out, g, cf, c->keys, c->status, m, c->stream); break;
+            case 2: e = launch_f32<2>(in, sh, u0, acc, out, g, cf, c->keys, c->status, m, c->stream); break;
+            case 3: e = launch_f32<3>(in, sh, u0, acc, out, g, cf, c->keys, c->status, m, c->stream); break;
+            default: e = launch_f32<4>(in, sh, u0, acc, out, g, cf, c->keys, c->status, m, c->stream); break;
         }
         CK3(e);
     }
+    int st = 0;
+    CK3(cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
     CK3(cudaStreamSynchronize(c->stream));
+    if (st != 0) return fail3(c, SAC_ERR_TIMEOUT, "a stage kernel's copy wait timed out");
     c->keys_valid = true;
     c->t += dt;
     if (dt_taken) *dt_taken = dt;
@@ -794,7 +874,7 @@ void sac3_free(sac3_ctx* c)
     cudaGetDevice(&prev);
     cudaSetDevice(c->p.device);
     cudaFree(c->u0); cudaFree(c->sa); cudaFree(c->sb); cudaFree(c->acc); cudaFree(c->v); cudaFree(c->fl); cudaFree(c->sh);
-    cudaFree(c->wbuf); cudaFree(c->keys);
+    cudaFree(c->wbuf); cudaFree(c->keys); cudaFree(c->status);
     cudaSetDevice(prev);
     delete c;
 }
@@ -831,7 +911,8 @@ int sac3_init(const sac3_params* p, sac3_ctx** out)
          // velocity and flux scratch of the FP64 kernels
          (!c->fp32 && (cudaMalloc(&c->v, 3 * fb) != cudaSuccess || cudaMalloc(&c->fl, 3 * NF3 * fb) != cudaSuccess)) ||
          cudaMalloc(&c->wbuf, (size_t)NF3 * n * sizeof(double)) != cudaSuccess ||
-         cudaMalloc(&c->keys, 3 * sizeof(unsigned long long)) != cudaSuccess)) {
+         cudaMalloc(&c->keys, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+         cudaMalloc(&c->status, sizeof(int)) != cudaSuccess)) {
         cudaGetLastError();
         rc = fail3(c, SAC_ERR_OOM, "device allocation failed");
     }
@@ -839,6 +920,8 @@ int sac3_init(const sac3_params* p, sac3_ctx** out)
                          cudaMemset(c->sb, 0, NF3 * fb) != cudaSuccess || cudaMemset(c->sh, 0, fb) != cudaSuccess))
         rc = fail3(c, SAC_ERR_CUDA, "cudaMemset");
     if (rc == SAC_OK && c->fp32 && prepare_f32() != cudaSuccess) rc = fail3(c, SAC_ERR_CUDA, "cudaFuncSetAttribute");
+    if (rc == SAC_OK && cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) rc = fail3(c, SAC_ERR_CUDA, "cudaMemset");
+    if (rc == SAC_OK && c->fp32 && !encode_maps3(c)) rc = fail3(c, SAC_ERR_CUDA, "tensor maps of the FP32 registers");
     if (rc != SAC_OK) { sac3_free(c); return rc; }
     *out = c;
     return SAC_OK;
