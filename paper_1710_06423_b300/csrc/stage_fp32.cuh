@@ -712,22 +712,25 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
                     k = add2(k, make_float2(mul_(rcen[q], gxv), mul_(rcen[q], gyv)));
                 }
             }
-            float2 o = make_float2(0.f, 0.f);
-            if (q < nq) {
-                const long long e = ep + q * L.pitch;
-                if (STAGE == 1) {
-                    o = fma2(h2, k, ucen);
-                } else if (STAGE == 2) {
-                    __stcs(gacc + e, fma2(d3t, k, mul2(third, sub2(ucen, u0v[q]))));
-                    o = fma2(h2, k, u0v[q]);
-                } else if (STAGE == 3) {
-                    __stcs(gacc + e, fma2(d3t, k, dv[q]));
-                    o = fma2(dt2, k, u0v[q]);
-                } else {
-                    o = add2(u0v[q], fma2(d6t, k, dv[q]));
-                }
-                __stcs(gout + e, o);   // evict-first: L2 cannot keep it for the next stage
+            // the update is formed for every q (cells past the grid hold zero RK
+            // registers); only the stores are predicated
+            const long long e = ep + q * L.pitch;
+            const bool in_grid = q < nq;
+            float2 o;
+            if (STAGE == 1) {
+                o = fma2(h2, k, ucen);
+            } else if (STAGE == 2) {
+                const float2 dn = fma2(d3t, k, mul2(third, sub2(ucen, u0v[q])));
+                if (in_grid) __stcs(gacc + e, dn);
+                o = fma2(h2, k, u0v[q]);
+            } else if (STAGE == 3) {
+                const float2 dn = fma2(d3t, k, dv[q]);
+                if (in_grid) __stcs(gacc + e, dn);
+                o = fma2(dt2, k, u0v[q]);
+            } else {
+                o = add2(u0v[q], fma2(d6t, k, dv[q]));
             }
+            if (in_grid) __stcs(gout + e, o);   // evict-first: L2 cannot keep it for the next stage
             outv[q][p] = o;
         }
     }
