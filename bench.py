@@ -39,7 +39,7 @@ STAGE_VALUES_FP32 = (12, 24, 30, 24)
 # dram__bytes_read.sum + dram__bytes_write.sum on the 4000^2 workload (three times L2 per
 # RK register; profiles/stage_fp32_dram_ot4000.md).  Traffic scales with the cells
 # processed; the figures hold for the stage kernel as of that capture.
-STAGE_TRAFFIC_B_PER_CELL_FP32 = (45.5, 95.3, 120.3, 97.4)
+STAGE_TRAFFIC_B_PER_CELL_FP32 = (45.6, 93.8, 120.2, 97.6)
 
 
 def parse():
