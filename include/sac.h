@@ -189,6 +189,16 @@ int sac_profile_stages(sac_ctx *c, int nsteps, double ms[5]);
 /* Wait for the context's stream and report a pending device error. */
 int sac_sync(sac_ctx *c);
 
+/* Test hook of the bounded device waits (FP32 contexts).  Each FP32 stage
+ * kernel waits on an mbarrier for its staging copies and gives up after about
+ * one second, recording SAC_ERR_TIMEOUT in the run's device status instead of
+ * hanging.  With on != 0 the stage kernels issue no copies for their first
+ * tile, so that wait runs out: the next step fails with SAC_ERR_TIMEOUT (the
+ * remaining stages of that step return at once, and later steps are skipped)
+ * until sac_set_state.  Call with on = 0 to clear it.  Nothing faults and no
+ * copy is left in flight.  Errors: SAC_ERR_ARG (FP64 context), SAC_ERR_CUDA. */
+int sac_debug_drop_copies(sac_ctx *c, int on);
+
 /* ---------------------------------------------------------------------------
  * Batched runs: many independent runs of uneven grid size advanced together.
  * Each RK stage of all runs is ONE kernel launch over a shared queue of
@@ -372,6 +382,11 @@ int sac3_step(sac3_ctx *c, double dt, double *dt_taken);
 /* n CFL steps. */
 int sac3_steps(sac3_ctx *c, long n);
 double sac3_time(const sac3_ctx *c);
+/* Test hook of the bounded copy waits of the FP32 3D stage kernel (as
+ * sac_debug_drop_copies): with on != 0 no copy is issued, each stage's wait
+ * gives up after about one second and sac3_step returns SAC_ERR_TIMEOUT with
+ * the state unchanged; on = 0 clears it.  Errors: SAC_ERR_ARG (FP64). */
+int sac3_debug_drop_copies(sac3_ctx *c, int on);
 
 #ifdef __cplusplus
 }

@@ -45,7 +45,7 @@ __global__ void na_import(const float* __restrict__ src, float* u0, float* sa, f
         sc->t = 0.0; sc->t_end = CUDART_INF; sc->dt = 0.0; sc->fixed_dt = 0.0;
         sc->cmax_step[0] = sc->cmax_step[1] = 0.0;
         sc->cmax_bits[0] = sc->cmax_bits[1] = 0ull;
-        sc->steps = 0; sc->skip = 0; sc->done = 0; sc->status = ST_OK;
+        sc->steps = 0; sc->skip = 0; sc->done = 0; sc->status = ST_OK; sc->drop_copies = 0;
     }
     const long long ex = L.nx + 2 * GY, ey = L.ny + 2 * GY, total = (long long)NF * ex * ey;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total;

@@ -296,6 +296,7 @@ struct Coef {
     float idd[3];      // 1 / d^2
     float gm1, gamma, dt, h, d6;
     int hd;
+    int drop;          // test hook (sac3_debug_drop_copies): issue no copies, so the first wait runs out
 };
 
 __device__ __forceinline__ float rcpf(float x)
@@ -338,12 +339,27 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(su32(bar)), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
 {
     unsigned ok;
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                  : "=r"(ok) : "r"(su32(bar)), "r"(parity) : "memory");
     return ok != 0;
+}
+// wait for the phase of *bar with the given parity; false after about one second
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
 }
 
 struct P3 {
@@ -426,6 +442,7 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
             unsigned long long* b = &bar[k & 1];
             mbar_expect_tx(b, kFullBytes + kShFullBytes + (unsigned)(q1 - q0 + 1) * kColBytes + (STAGE != 1 ? 2u * kRkBytes : 0u));
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (cf.drop) return;   // test hook: the expected bytes never arrive
             tma4(&S.full[k & 1][0][0][0], &tm.in_full, i0, j0, k + G3, 0, b);        // x = i0-4, y = j0-3 (extended)
             tma3(&S.full[k & 1][NF3][0][0], &tm.sh_full, i0, j0, k + G3, b);
             for (int q = q0; q <= q1; ++q) {
@@ -438,6 +455,7 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
             }
         }
     };
+    if (*status != 0) return;   // an earlier stage of this step gave up: nothing to do
     unsigned phase = 0;   // bit b: parity of bar[b]'s next completion
     // tensor copies need 128-byte aligned destinations (all buffer offsets are multiples of 128)
     if ((su32(&S) & 127u) != 0) {
@@ -489,17 +507,12 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
         if (k + 1 < k1) issue(k + 1, k + 4, k + 4);   // plane k+4 <= nz + 2: inside the ghost frame
         {   // plane k's copies (bounded wait; a timeout is reported and every thread leaves)
             const int kb_ = k & 1;
-            unsigned it = 0;
-            bool to = false;
-            while (!mbar_try_wait(&bar[kb_], (phase >> kb_) & 1u)) {
-                if (++it > (1u << 22)) { to = true; break; }
-            }
+            const bool to = !mbar_wait_bounded(&bar[kb_], (phase >> kb_) & 1u);
             if (__syncthreads_or(to)) {
                 if (tid == 0) {
                     atomicExch(status, 1);
                     // let plane k+1's copies (if issued) land before the CTA's memory is released
-                    if (k + 1 < k1)
-                        for (unsigned j = 0; j < (1u << 22) && !mbar_try_wait(&bar[kb_ ^ 1], (phase >> (kb_ ^ 1)) & 1u); ++j) {}
+                    if (k + 1 < k1 && !cf.drop) mbar_wait_bounded(&bar[kb_ ^ 1], (phase >> (kb_ ^ 1)) & 1u);
                 }
                 return;
             }
@@ -666,6 +679,7 @@ struct sac3_ctx {
     double t = 0.0;
     bool have_state = false;
     bool keys_valid = false;                // keys hold the maxima of the current state
+    int drop_copies = 0;                    // test hook of the bounded copy waits
     std::string err;
 };
 
@@ -755,6 +769,7 @@ static int fused_f32(sac3_ctx* c, double dt, const double cm[3], const double dd
     cf.gamma = (float)c->p.gamma;
     cf.dt = (float)dt; cf.h = (float)(0.5 * dt); cf.d6 = (float)(dt / 6.0);
     cf.hd = c->p.hyperdiffusion != 0;
+    cf.drop = c->drop_copies;
     float* u0 = (float*)c->u0;
     float* sa = (float*)c->sa;
     float* sb = (float*)c->sb;
@@ -782,7 +797,13 @@ static int fused_f32(sac3_ctx* c, double dt, const double cm[3], const double dd
     int st = 0;
     CK3(cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
     CK3(cudaStreamSynchronize(c->stream));
-    if (st != 0) return fail3(c, SAC_ERR_TIMEOUT, "a stage kernel's copy wait timed out");
+    if (st != 0) {
+        // the step is abandoned (U0 is written only by a completed stage 4); the next step retries
+        CK3(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+        CK3(cudaStreamSynchronize(c->stream));
+        c->keys_valid = false;
+        return fail3(c, SAC_ERR_TIMEOUT, "a stage kernel's copy wait timed out");
+    }
     c->keys_valid = true;
     c->t += dt;
     if (dt_taken) *dt_taken = dt;
@@ -978,5 +999,13 @@ int sac3_steps(sac3_ctx* c, long n)
 }
 
 double sac3_time(const sac3_ctx* c) { return c ? c->t : 0.0; }
+
+int sac3_debug_drop_copies(sac3_ctx* c, int on)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (!c->fp32) return fail3(c, SAC_ERR_ARG, "the copy-wait hook applies to FP32 contexts");
+    c->drop_copies = on ? 1 : 0;
+    return SAC_OK;
+}
 
 }  // extern "C"

@@ -447,6 +447,8 @@ int sac_init(const sac_params* p, sac_ctx** out)
         if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e)); break; }
         e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
         if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "stream: %s", cudaGetErrorString(e)); break; }
+        e = cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), c->stream);   // (drop_copies off)
+        if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "init: %s", cudaGetErrorString(e)); break; }
         reset_kernel<<<1, 1, 0, c->stream>>>(c->sc, 0.0);
         e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "init: %s", cudaGetErrorString(e)); break; }
@@ -722,6 +724,17 @@ int sac_sync(sac_ctx* c)
     if (!c) return SAC_ERR_ARG;
     CK(cudaSetDevice(c->p.device));
     return pull_scalars(c);
+}
+
+int sac_debug_drop_copies(sac_ctx* c, int on)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (c->p.precision != SAC_FP32) return fail(c, SAC_ERR_ARG, "the copy-wait hook applies to FP32 contexts");
+    CK(cudaSetDevice(c->p.device));
+    const int v = on ? 1 : 0;
+    CK(cudaMemcpyAsync(&c->sc->drop_copies, &v, sizeof v, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SAC_OK;
 }
 
 }  // extern "C"

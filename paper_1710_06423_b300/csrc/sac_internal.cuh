@@ -61,7 +61,7 @@ struct DevScalars {
     int skip;                 // 1: the stage kernels of this step return at once
     int done;                 // t reached t_end
     int status;               // ST_OK or an error code
-    int pad;
+    int drop_copies;          // test hook (sac_debug_drop_copies): FP32 stages issue no staging copies
     float fdt[4];             // FP32 kernels: dt/2, dt, dt/3, dt/6 of the current step (rounded once)
     float fcmax[2];           // FP32 kernels: cmax_step rounded to float
 };

@@ -27,7 +27,7 @@ EXPORTS = (
     "sac_default_params", "sac_init", "sac_free", "sac_last_error", "sac_status_string",
     "sac_set_state", "sac_get_state", "sac_set_state_dev", "sac_get_state_dev",
     "sac_step", "sac_steps", "sac_run_to", "sac_set_fixed_dt", "sac_dt", "sac_time", "sac_cmax", "sac_sums",
-    "sac_profile_stages", "sac_sync",
+    "sac_profile_stages", "sac_sync", "sac_debug_drop_copies",
     "sac_batch_init", "sac_batch_free", "sac_batch_last_error", "sac_batch_set_state",
     "sac_batch_get_state", "sac_batch_steps", "sac_batch_sync", "sac_batch_time", "sac_batch_tune",
     "sac_batch_set_config",
@@ -36,7 +36,7 @@ EXPORTS = (
     "sac_cnn_apply", "sac_cnn_perturb", "sac_block_average",
     "sac_step_noalloc",
     "sac3_default_params", "sac3_init", "sac3_free", "sac3_last_error", "sac3_set_state", "sac3_get_state",
-    "sac3_step", "sac3_steps", "sac3_time",
+    "sac3_step", "sac3_steps", "sac3_time", "sac3_debug_drop_copies",
 )
 
 
@@ -117,6 +117,7 @@ def load() -> ctypes.CDLL:
         "sac_sums": (i, [vp, dp]),
         "sac_profile_stages": (i, [vp, i, dp]),
         "sac_sync": (i, [vp]),
+        "sac_debug_drop_copies": (i, [vp, i]),
         "sac_batch_init": (i, [P, i, ctypes.POINTER(vp)]),
         "sac_batch_free": (None, [vp]),
         "sac_batch_last_error": (ctypes.c_char_p, [vp]),
@@ -150,6 +151,7 @@ def load() -> ctypes.CDLL:
         "sac3_step": (i, [vp, d, dp]),
         "sac3_steps": (i, [vp, L]),
         "sac3_time": (d, [vp]),
+        "sac3_debug_drop_copies": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -304,6 +306,10 @@ class Solver:
 
     def sync(self):
         self._check(load().sac_sync(self._ctx), "sac_sync")
+
+    def debug_drop_copies(self, on: bool):
+        """Test hook of the bounded copy waits (see sac_debug_drop_copies)."""
+        self._check(load().sac_debug_drop_copies(self._ctx, int(bool(on))), "sac_debug_drop_copies")
 
 
 class Batch:
@@ -578,6 +584,10 @@ class Solver3:
 
     def time(self) -> float:
         return load().sac3_time(self._ctx)
+
+    def debug_drop_copies(self, on: bool):
+        """Test hook of the bounded copy waits (see sac3_debug_drop_copies)."""
+        self._check(load().sac3_debug_drop_copies(self._ctx, int(bool(on))), "sac3_debug_drop_copies")
 
     def close(self):
         if self._ctx:
