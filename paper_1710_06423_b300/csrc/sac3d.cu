@@ -2,10 +2,10 @@
 // arXiv 1710.06423 written for three-component vectors): eight conserved
 // fields rho, m_x, m_y, m_z, e, B_x, B_y, B_z on a periodic box, no background.
 //
-// Each RK stage runs four kernels that follow the method's own order of
-// operations (FP64 agrees with the FP64 3D oracle to rounding order; the unit
-// is compiled without FMA contraction):
-//   ghosts3   periodic ghost frame (width 3) of the stage input;
+// FP64 (the oracle-order path; the unit is compiled without FMA contraction,
+// so FP64 agrees with the FP64 3D oracle to rounding order): each RK stage
+// runs four kernels in the method's own order of operations:
+//   ghosts3   periodic ghost frame (3 cells; 4 on the left in x) of the stage input;
 //   flux3     per ghost-extended cell: velocities and the fluxes of all eight
 //             fields along x, y and z (global scratch);
 //   shock3    s = max(0, -((D_x v_x + D_y v_y) + D_z v_z)) on the cells the
@@ -14,10 +14,12 @@
 //             + D_z F_z) (hyper-diffusion with the maxima over three faces,
 //             fourth-order flux differences) and the classical RK4 register
 //             update (K = k1 + 2 k2 + 2 k3, U = U0 + dt/6 (K + k4)).
+// FP32 (the performance path): ghosts3, shock3_f32 and one fused stage kernel
+// (f3::stage3_f32) that marches column tiles through z with tensor-map TMA
+// copies; stage 4 also reduces the next step's signal speeds.
 // The step's signal speeds come from one reduction over the state (ordered
 // bits, NaN propagates); dt = C min(min(dx/cx, dy/cy), dz/cz) is formed on
-// the host in FP64.  This first 3D path keeps the fluxes in global memory (a
-// correctness-first layout: about twice the bytes of a fused tile kernel).
+// the host in FP64.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
