@@ -289,6 +289,7 @@ struct Smem {
     float fx[NF3][TY][FXW];
     float fy[NF3][FYH][TX];
     float rk[2][2][NF3][NT];     // U0 and the RK accumulator of the own cell, planes k and k+1
+    float hy[NF3][TY][TX];       // y hyper-diffusion of plane k (the y sweep of phase 1)
 };
 
 struct Coef {
@@ -555,6 +556,38 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
 #pragma unroll
             for (int f = 0; f < NF3; ++f) S.fx[f][r][fxc] = F[f];
         }
+        if (cf.hd) {   // y sweep: H_y of the tile's TY rows for fields 2w, 2w+1 of column lane
+            static_assert(TY == 4 && RH == 10 && NF3 == 2 * (NT / 32), "y-sweep mapping");
+            const float* scol = &S.full[kb][NF3][0][HXS + lane];   // staged rows 0..RH-1 = y0-3 ..
+            float bsf[TY + 1];   // shock term of the faces between rows L and L+1, L = 2 .. 6
+#pragma unroll
+            for (int q = 0; q <= TY; ++q) bsf[q] = cf.bsh[1] * (scol[(2 + q) * RW] + scol[(3 + q) * RW]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int f = 2 * w + h;
+                const float* ucol = &S.full[kb][f][0][HXS + lane];
+                float u[RH];
+#pragma unroll
+                for (int i = 0; i < RH; ++i) u[i] = ucol[i * RW];
+                float d1[TY + 3], a1[TY + 3], a3[TY + 3];   // faces L = 1 .. 7 (between rows L, L+1)
+#pragma unroll
+                for (int q = 0; q < TY + 3; ++q) {
+                    float d3;
+                    face13(u[q], u[q + 1], u[q + 2], u[q + 3], d1[q], d3);
+                    a1[q] = fabsf(d1[q]); a3[q] = fabsf(d3);
+                }
+                float gy[TY + 1];   // face fluxes at faces L = 2 .. 6
+#pragma unroll
+                for (int q = 1; q <= TY + 1; ++q) {
+                    const float m1 = fmaxf(fmaxf(a1[q - 1], a1[q]), a1[q + 1]);
+                    const float m3 = fmaxf(fmaxf(a3[q - 1], a3[q]), a3[q + 1]);
+                    const float r = m1 > 0.0f ? m3 * rcpf(m1) : 0.0f;
+                    gy[q - 1] = __fmaf_rn(cf.a[f][1], r, bsf[q - 1]) * d1[q];
+                }
+#pragma unroll
+                for (int r = 0; r < TY; ++r) S.hy[f][r][lane] = (gy[r + 1] - gy[r]) * cf.idd[1];
+            }
+        }
         {   // z flux of plane k+2, own column
             float u[NF3], F[NF3];
 #pragma unroll
@@ -568,12 +601,10 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
         if (!valid) continue;
 
         const float* sc = &S.full[kb][NF3][G3 + w][HXS + lane];
-        float bxl = 0.f, bxr = 0.f, byl = 0.f, byr = 0.f, bzr = 0.f;
+        float bxl = 0.f, bxr = 0.f, bzr = 0.f;
         if (cf.hd) {
             bxl = cf.bsh[0] * (sc[-1] + sc[0]);
             bxr = cf.bsh[0] * (sc[0] + sc[1]);
-            byl = cf.bsh[1] * (sc[-RW] + sc[0]);
-            byr = cf.bsh[1] * (sc[0] + sc[RW]);
             bzr = cf.bsh[2] * (sc[0] + S.col[(k + 1) % 4][NF3][tid]);
         }
         const int s1 = (k + 1) % 4, s2 = (k + 2) % 4, s3 = (k + 3) % 4;
@@ -585,7 +616,7 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
             float hsum = 0.0f;
             if (cf.hd) {
                 const float hx = hd_line(uc, 1, cf.a[f][0], bxl, bxr) * cf.idd[0];
-                const float hy = hd_line(uc, RW, cf.a[f][1], byl, byr) * cf.idd[1];
+                const float hy = S.hy[f][w][lane];
                 // z: the new face k+1 from planes k .. k+3, then face k+1/2
                 float d1n, d3n;
                 face13(uc[0], S.col[s1][f][tid], S.col[s2][f][tid], S.col[s3][f][tid], d1n, d3n);
