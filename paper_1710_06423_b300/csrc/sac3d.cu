@@ -752,13 +752,16 @@ static cudaError_t launch_f32(const float* in, const float* sh, const float* u0,
 // column tile (32 x 4 x 1), all fields at once.
 static bool encode_maps3(sac3_ctx* c)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
+    // looked up once (thread-safe initialisation of a function-local static)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !encode)
-            return false;
-    }
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode) return false;
     const Grid3& g = c->g;
     const cuuint64_t dims[4] = {(cuuint64_t)g.ex, (cuuint64_t)g.ey, (cuuint64_t)g.ez, (cuuint64_t)NF3};
     const cuuint64_t str[3] = {(cuuint64_t)g.ex * 4, (cuuint64_t)(g.ex * g.ey) * 4, (cuuint64_t)g.ne * 4};
