@@ -14,9 +14,9 @@
 //             + D_z F_z) (hyper-diffusion with the maxima over three faces,
 //             fourth-order flux differences) and the classical RK4 register
 //             update (K = k1 + 2 k2 + 2 k3, U = U0 + dt/6 (K + k4)).
-// FP32 (the performance path): ghosts3, shock3_f32 and one fused stage kernel
-// (f3::stage3_f32) that marches column tiles through z with tensor-map TMA
-// copies; stage 4 also reduces the next step's signal speeds.
+// FP32 (the performance path): ghosts3, f3::shock3_f32 and one fused stage
+// kernel (f3::stage3_f32); both f3 kernels march column tiles through z fed by
+// tensor-map TMA copies; stage 4 also reduces the next step's signal speeds.
 // The step's signal speeds come from one reduction over the state (ordered
 // bits, NaN propagates); dt = C min(min(dx/cx, dy/cy), dz/cz) is formed on
 // the host in FP64.
@@ -677,19 +677,106 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
 }
 
 // shock indicator s = max(0, -div v) on [-1, n+1) in every direction, from the
-// stage input directly; block (128) over x, grid (x blocks, y, z)
-__global__ void shock3_f32(const float* __restrict__ s, float* __restrict__ sh, Grid3 g, float i12x, float i12y,
-                           float i12z)
+// stage input.  One CTA owns 32 x 4 output columns and marches SKZ planes along
+// z.  Planes of (rho, m_x, m_y, m_z) with a 2-cell x/y halo arrive by one
+// tensor-map TMA copy each into a ring of four buffers (plane q in buffer q mod
+// 4, one mbarrier per buffer; plane k+4 is copied once plane k is done); v_x and
+// v_y of plane k are formed once per cell in shared memory, v_z of the own
+// column at planes k .. k+2 from the ring and at k-1, k-2 from two rolled
+// registers.  Same arithmetic as the per-cell form.  Every copy issued is waited
+// for before the CTA leaves (bounded waits; a timeout sets *status).
+constexpr int STX = 32, STY = 4, SNT = STX * STY, SRW = 40, SRH = STY + 4, SKZ = 32, SNB = 4;
+struct ShSmem {
+    float pl[SNB][4][SRH][SRW];   // x = 32 bx - 4 + c, y = yo - 2 + r (yo = STY by - 1)
+    float vx[STY][SRW];           // v_x of the tile rows, by staged column
+    float vy[SRH][STX];           // v_y of the staged rows, tile columns
+};
+static_assert((4 * SRH * SRW * sizeof(float)) % 128 == 0, "plane buffers 128-byte aligned");
+constexpr unsigned kShPlaneBytes = (unsigned)(4 * SRH * SRW * sizeof(float));
+__global__ void __launch_bounds__(SNT) shock3_f32(float* __restrict__ sh, Grid3 g, float i12x, float i12y, float i12z,
+                                                  int ntx, int* __restrict__ status,
+                                                  const __grid_constant__ CUtensorMap tm)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x - 1, j = blockIdx.y - 1, k = blockIdx.z - 1;
-    if (i > g.nx) return;
-    const long long ne = g.ne, c = g.at(i, j, k), sy = g.ex, sz = g.ex * g.ey;
-    const auto vel = [&](long long q, int d) { return s[(1 + d) * ne + q] * rcpf(s[q]); };
-    const auto dcen = [&](int d, long long st) {
-        return __fmaf_rn(8.0f, vel(c + st, d) - vel(c - st, d), -(vel(c + 2 * st, d) - vel(c - 2 * st, d)));
+    __shared__ __align__(128) ShSmem S;
+    __shared__ __align__(8) unsigned long long bar[SNB];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int bx = (int)(blockIdx.x % ntx), by = (int)(blockIdx.x / ntx);
+    const int xo = STX * bx - 1, yo = STY * by - 1;
+    const int k0 = SKZ * (int)blockIdx.y - 1, k1 = min(k0 + SKZ, g.nz + 1);
+    const int x = xo + lane, y = yo + w;
+    const bool valid = x <= g.nx && y <= g.ny;
+    const long long P = g.ex * g.ey;
+    const int c0 = lane + 3, r0 = w + 2;   // own output cell in a staged plane
+    if (*status != 0) return;
+    if (tid == 0)
+        for (int b = 0; b < SNB; ++b) mbar_init(&bar[b]);
+    __syncthreads();
+    unsigned phase = 0, pending = 0;   // per buffer: parity of the next completion; copy issued, not yet waited
+    const auto buf = [](int q) { return (q + SNB) % SNB; };   // q >= -3
+    const auto issue = [&](int q) {
+        const int b = buf(q);
+        pending |= 1u << b;
+        if (tid == 0) {
+            mbar_expect_tx(&bar[b], kShPlaneBytes);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma4(&S.pl[b][0][0][0], &tm, STX * bx, STY * by, q + G3, 0, &bar[b]);
+        }
     };
-    const float div = (dcen(0, 1) * i12x + dcen(1, sy) * i12y) + dcen(2, sz) * i12z;
-    sh[c] = fmaxf(0.0f, -div);
+    const auto wait = [&](int q) {   // true on timeout
+        const int b = buf(q);
+        const bool to = !mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
+        phase ^= 1u << b;
+        pending &= ~(1u << b);
+        return to;
+    };
+    const auto give_up = [&]() {   // uniform: record the timeout, let copies in flight land, leave
+        if (tid == 0) {
+            atomicExch(status, 1);
+            for (int b = 0; b < SNB; ++b)
+                if (pending & (1u << b)) mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
+        }
+    };
+    const auto vz_of = [&](int b) { return S.pl[b][3][r0][c0] * rcpf(S.pl[b][0][r0][c0]); };
+
+    // planes k0-2 .. k0+1; v_z of the first two; then k0+2, k0+3 into their buffers
+    for (int q = k0 - 2; q <= k0 + 1; ++q) issue(q);
+    bool to = wait(k0 - 2);
+    to = wait(k0 - 1) || to;
+    if (__syncthreads_or(to)) { give_up(); return; }
+    float vzm2 = vz_of(buf(k0 - 2)), vzm1 = vz_of(buf(k0 - 1));
+    __syncthreads();   // the buffers of k0-2, k0-1 are free
+    issue(k0 + 2);     // read at step k0 (k1 >= k0 + 1)
+    if (k0 + 3 <= k1 + 1) issue(k0 + 3);
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+        to = false;
+        if (k == k0) { to = wait(k0); to = wait(k0 + 1) || to; }
+        to = wait(k + 2) || to;
+        if (__syncthreads_or(to)) { give_up(); return; }
+        const int bk = buf(k);
+        for (int i = tid; i < STY * (STX + 4); i += SNT) {   // v_x: tile rows, staged columns 1 .. 36
+            const int r = i / (STX + 4), c = 1 + i - (i / (STX + 4)) * (STX + 4);
+            S.vx[r][c] = S.pl[bk][1][r + 2][c] * rcpf(S.pl[bk][0][r + 2][c]);
+        }
+        for (int i = tid; i < SRH * STX; i += SNT) {          // v_y: staged rows 0 .. 7, tile columns
+            const int r = i / STX, c = i - (i / STX) * STX;
+            S.vy[r][c] = S.pl[bk][2][r][c + 3] * rcpf(S.pl[bk][0][r][c + 3]);
+        }
+        const float vz0 = vz_of(bk), vzp1 = vz_of(buf(k + 1)), vzp2 = vz_of(buf(k + 2));
+        __syncthreads();
+        if (valid) {
+            const float* vr = &S.vx[w][c0];
+            const float* vc = &S.vy[r0][lane];
+            const float dvx = __fmaf_rn(8.0f, vr[1] - vr[-1], -(vr[2] - vr[-2]));
+            const float dvy = __fmaf_rn(8.0f, vc[STX] - vc[-STX], -(vc[2 * STX] - vc[-2 * STX]));
+            const float dvz = __fmaf_rn(8.0f, vzp1 - vzm1, -(vzp2 - vzm2));
+            const float div = (dvx * i12x + dvy * i12y) + dvz * i12z;
+            sh[(long long)(k + G3) * P + (long long)(y + G3) * g.ex + (x + GX)] = fmaxf(0.0f, -div);
+        }
+        vzm2 = vzm1; vzm1 = vz0;
+        __syncthreads();   // plane k's buffer and v_x, v_y are free
+        if (k + 4 <= k1 + 1) issue(k + 4);   // read at step k+2 as its plane +2
+    }
 }
 }  // namespace f3
 
@@ -709,6 +796,7 @@ struct sac3_ctx {
     int* status = nullptr;                  // FP32 stage kernels: 1 = a copy wait timed out
     CUtensorMap m_full[3], m_col[3];        // FP32: stage inputs U0, SA, SB (plane box, column box)
     CUtensorMap m_sh_full, m_sh_col, m_acc_col;
+    CUtensorMap m_shk[3];                   // FP32 stage inputs as (rho, m) planes of the shock kernel
     double t = 0.0;
     bool have_state = false;
     bool keys_valid = false;                // keys hold the maxima of the current state
@@ -777,6 +865,8 @@ static bool encode_maps3(sac3_ctx* c)
     bool ok = true;
     for (int r = 0; r < 3 && ok; ++r) ok = enc(&c->m_full[r], regs[r], 4, bfull) && enc(&c->m_col[r], regs[r], 4, bcol);
     ok = ok && enc(&c->m_sh_full, c->sh, 3, bfull) && enc(&c->m_sh_col, c->sh, 3, bcol) && enc(&c->m_acc_col, c->acc, 4, bcol);
+    const cuuint32_t bshk[4] = {(cuuint32_t)f3::SRW, (cuuint32_t)f3::SRH, 1, 4};
+    for (int r = 0; r < 3 && ok; ++r) ok = enc(&c->m_shk[r], regs[r], 4, bshk);
     return ok;
 }
 
@@ -811,15 +901,18 @@ static int fused_f32(sac3_ctx* c, double dt, const double cm[3], const double dd
     float* sb = (float*)c->sb;
     float* sh = (float*)c->sh;
     float* acc = (float*)c->acc;
-    const dim3 sgrid((unsigned)((g.nx + 2 + 127) / 128), (unsigned)(g.ny + 2), (unsigned)(g.nz + 2));
+    const int sntx = (g.nx + 2 + f3::STX - 1) / f3::STX, snty = (g.ny + 2 + f3::STY - 1) / f3::STY;
+    const dim3 sgrid((unsigned)(sntx * snty), (unsigned)((g.nz + 2 + f3::SKZ - 1) / f3::SKZ));
     for (int stage = 1; stage <= 4; ++stage) {
         float* in = stage == 1 ? u0 : (stage == 2 ? sa : (stage == 3 ? sb : sa));
         float* out = stage == 1 ? sa : (stage == 2 ? sb : (stage == 3 ? sa : u0));
         ghosts3<float><<<(int)(g.ey * g.ez), 128, 0, c->stream>>>(in, g);
-        if (cf.hd) f3::shock3_f32<<<sgrid, 128, 0, c->stream>>>(in, sh, g, cf.i12[0], cf.i12[1], cf.i12[2]);
+        const int ri = stage == 1 ? 0 : (stage == 3 ? 2 : 1);   // input register: U0, SA, SB, SA
+        if (cf.hd)
+            f3::shock3_f32<<<sgrid, f3::SNT, 0, c->stream>>>(sh, g, cf.i12[0], cf.i12[1], cf.i12[2], sntx, c->status,
+                                                           c->m_shk[ri]);
         // stage 4 reduces the signal speeds of the new state for the next step
         if (stage == 4) CK3(cudaMemsetAsync(c->keys, 0, 3 * sizeof(unsigned long long), c->stream));
-        const int ri = stage == 1 ? 0 : (stage == 3 ? 2 : 1);   // input register: U0, SA, SB, SA
         const f3::Maps m{c->m_full[ri], c->m_col[ri], c->m_sh_full, c->m_sh_col, c->m_col[0], c->m_acc_col};
         cudaError_t e;
         switch (stage) {
