@@ -261,7 +261,7 @@ __global__ void export3(const T* __restrict__ u, double* __restrict__ w, Grid3 g
 }
 
 // ---------------------------------------------------------------------------
-// FP32 fused RK stage.  One CTA owns TX x TY columns and marches through KZ
+// FP32 fused RK stage.  One CTA owns TX x TY columns and marches through kz
 // planes along z.  While it works on plane k, one thread's tensor-map TMA
 // copies bring plane k+1 with its x/y halo (all eight fields in one 4D box, the
 // shock indicator in one 3D box), the RK registers of plane k+1 and the column
@@ -279,7 +279,6 @@ constexpr int TX = 32, TY = 4, NT = TX * TY;   // one warp per y row of the tile
 constexpr int HXS = 4, RW = TX + 2 * HXS;      // staged x range i0-4 .. i0+TX+3
 constexpr int RH = TY + 2 * G3;                // staged rows j0-3 .. j0+TY+2
 constexpr int NS = NF3 + 1;                    // eight fields and the shock indicator
-constexpr int KZ = 32;                         // planes per CTA
 constexpr int FXW = TX + 4, FYH = TY + 4;      // flux extents: x i0-2 .. i0+TX+1, y j0-2 .. j0+TY+1
 
 struct Smem {
@@ -300,6 +299,7 @@ struct Coef {
     float gm1, gamma, dt, h, d6;
     int hd;
     int drop;          // test hook (sac3_debug_drop_copies): issue no copies, so the first wait runs out
+    int kz;            // planes per CTA (z chunk)
 };
 
 __device__ __forceinline__ float rcpf(float x)
@@ -430,7 +430,7 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
     Smem& S = *reinterpret_cast<Smem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int i0 = (int)(blockIdx.x % ntx) * TX, j0 = (int)(blockIdx.x / ntx) * TY;
-    const int k0 = blockIdx.y * KZ, k1 = min(k0 + KZ, g.nz);
+    const int k0 = blockIdx.y * cf.kz, k1 = min(k0 + cf.kz, g.nz);
     const int x = i0 + lane, y = j0 + w;
     const bool valid = x < g.nx && y < g.ny;
     const long long P = g.ex * g.ey, ne = g.ne;
@@ -677,7 +677,7 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
 }
 
 // shock indicator s = max(0, -div v) on [-1, n+1) in every direction, from the
-// stage input.  One CTA owns 32 x 4 output columns and marches SKZ planes along
+// stage input.  One CTA owns 32 x 4 output columns and marches skz planes along
 // z.  Planes of (rho, m_x, m_y, m_z) with a 2-cell x/y halo arrive by one
 // tensor-map TMA copy each into a ring of four buffers (plane q in buffer q mod
 // 4, one mbarrier per buffer; plane k+4 is copied once plane k is done); v_x and
@@ -685,7 +685,7 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
 // column at planes k .. k+2 from the ring and at k-1, k-2 from two rolled
 // registers.  Same arithmetic as the per-cell form.  Every copy issued is waited
 // for before the CTA leaves (bounded waits; a timeout sets *status).
-constexpr int STX = 32, STY = 4, SNT = STX * STY, SRW = 40, SRH = STY + 4, SKZ = 32, SNB = 4;
+constexpr int STX = 32, STY = 4, SNT = STX * STY, SRW = 40, SRH = STY + 4, SNB = 4;
 struct ShSmem {
     float pl[SNB][4][SRH][SRW];   // x = 32 bx - 4 + c, y = yo - 2 + r (yo = STY by - 1)
     float vx[STY][SRW];           // v_x of the tile rows, by staged column
@@ -694,7 +694,7 @@ struct ShSmem {
 static_assert((4 * SRH * SRW * sizeof(float)) % 128 == 0, "plane buffers 128-byte aligned");
 constexpr unsigned kShPlaneBytes = (unsigned)(4 * SRH * SRW * sizeof(float));
 __global__ void __launch_bounds__(SNT) shock3_f32(float* __restrict__ sh, Grid3 g, float i12x, float i12y, float i12z,
-                                                  int ntx, int* __restrict__ status,
+                                                  int ntx, int skz, int* __restrict__ status,
                                                   const __grid_constant__ CUtensorMap tm)
 {
     __shared__ __align__(128) ShSmem S;
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(SNT) shock3_f32(float* __restrict__ sh, Grid3 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int bx = (int)(blockIdx.x % ntx), by = (int)(blockIdx.x / ntx);
     const int xo = STX * bx - 1, yo = STY * by - 1;
-    const int k0 = SKZ * (int)blockIdx.y - 1, k1 = min(k0 + SKZ, g.nz + 1);
+    const int k0 = skz * (int)blockIdx.y - 1, k1 = min(k0 + skz, g.nz + 1);
     const int x = xo + lane, y = yo + w;
     const bool valid = x <= g.nx && y <= g.ny;
     const long long P = g.ex * g.ey;
@@ -830,7 +830,7 @@ static cudaError_t launch_f32(const float* in, const float* sh, const float* u0,
                               const f3::Maps& m, cudaStream_t st)
 {
     const int ntx = (g.nx + f3::TX - 1) / f3::TX, nty = (g.ny + f3::TY - 1) / f3::TY;
-    const dim3 grid((unsigned)(ntx * nty), (unsigned)((g.nz + f3::KZ - 1) / f3::KZ));
+    const dim3 grid((unsigned)(ntx * nty), (unsigned)((g.nz + cf.kz - 1) / cf.kz));
     f3::stage3_f32<S><<<grid, f3::NT, sizeof(f3::Smem), st>>>(in, sh, u0, acc, out, g, cf, ntx, keys, status, m);
     return cudaGetLastError();
 }
@@ -896,20 +896,28 @@ static int fused_f32(sac3_ctx* c, double dt, const double cm[3], const double dd
     cf.dt = (float)dt; cf.h = (float)(0.5 * dt); cf.d6 = (float)(dt / 6.0);
     cf.hd = c->p.hyperdiffusion != 0;
     cf.drop = c->drop_copies;
+    {   // z chunk: 64 planes when that still leaves at least four CTAs per resident slot
+        // (2 per SM), else 32 (longer chunks repeat the 6-plane prologue less often)
+        const long long cols = (long long)((g.nx + f3::TX - 1) / f3::TX) * ((g.ny + f3::TY - 1) / f3::TY);
+        int nsm = 148, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cf.kz = cols * ((g.nz + 63) / 64) >= 4LL * 2 * nsm ? 64 : 32;
+    }
     float* u0 = (float*)c->u0;
     float* sa = (float*)c->sa;
     float* sb = (float*)c->sb;
     float* sh = (float*)c->sh;
     float* acc = (float*)c->acc;
     const int sntx = (g.nx + 2 + f3::STX - 1) / f3::STX, snty = (g.ny + 2 + f3::STY - 1) / f3::STY;
-    const dim3 sgrid((unsigned)(sntx * snty), (unsigned)((g.nz + 2 + f3::SKZ - 1) / f3::SKZ));
+    const dim3 sgrid((unsigned)(sntx * snty), (unsigned)((g.nz + 2 + cf.kz - 1) / cf.kz));
     for (int stage = 1; stage <= 4; ++stage) {
         float* in = stage == 1 ? u0 : (stage == 2 ? sa : (stage == 3 ? sb : sa));
         float* out = stage == 1 ? sa : (stage == 2 ? sb : (stage == 3 ? sa : u0));
         ghosts3<float><<<(int)(g.ey * g.ez), 128, 0, c->stream>>>(in, g);
         const int ri = stage == 1 ? 0 : (stage == 3 ? 2 : 1);   // input register: U0, SA, SB, SA
         if (cf.hd)
-            f3::shock3_f32<<<sgrid, f3::SNT, 0, c->stream>>>(sh, g, cf.i12[0], cf.i12[1], cf.i12[2], sntx, c->status,
+            f3::shock3_f32<<<sgrid, f3::SNT, 0, c->stream>>>(sh, g, cf.i12[0], cf.i12[1], cf.i12[2], sntx, cf.kz, c->status,
                                                            c->m_shk[ri]);
         // stage 4 reduces the signal speeds of the new state for the next step
         if (stage == 4) CK3(cudaMemsetAsync(c->keys, 0, 3 * sizeof(unsigned long long), c->stream));
