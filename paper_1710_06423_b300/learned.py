@@ -7,7 +7,7 @@ solver generates: the fine run (grid r*n, step dt_c/r) is block-averaged
 (r x r) to the coarse grid at times t_k and t_k + dt_c; the coarse solver
 steps the first average once, and the target is the remaining difference to
 the second, divided by out_scale.  The plain fine solver is both the source of
-the training data and the judge of the error (relative L1 per field against
+the training data and the reference for the error (relative L1 per field against
 its block average at the horizon).
 
 Every array operation runs in the library's CUDA kernels (solver steps, block

@@ -56,7 +56,7 @@ def test_fp32_matches_oracle(oracle_mod, inputs_mod):
         s.steps(steps)
         got, t = s.get_state()
     assert t == pytest.approx(t_ref, rel=1e-6)
-    # the velocity fields start near zero: judge m by the L1 norm of the whole momentum
+    # the velocity fields start near zero: measure m by the L1 norm of the whole momentum
     err = l1rel(got, ref)
     assert err[0] <= TOL_FP32_L1 and err[3] <= TOL_FP32_L1, err
     m_err = np.abs(got[1:3] - ref[1:3]).sum() / np.abs(ref[1:3]).sum()

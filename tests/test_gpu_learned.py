@@ -45,7 +45,7 @@ def test_trained_network_reduces_one_step_residual_on_held_out_run(trained):
 
 def test_learned_rollout_beats_plain_coarse(trained):
     """Held-out family member: 60 coarse steps with and without the correction,
-    judged against the block-averaged fine run at the same time."""
+    compared with the block-averaged fine run at the same time."""
     import torch
     from paper_1710_06423_b300 import learned
     from paper_1710_06423_b300.sac import FP32, Solver, block_average
