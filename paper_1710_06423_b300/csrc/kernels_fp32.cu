@@ -28,7 +28,7 @@ cudaError_t set_attr()
 int g_resident = 296;   // persistent grid: resident CTAs on the device (2 per SM)
 
 // Tensor maps of the stage inputs (3D: pitch float2 x padded rows x 3 planes;
-// box RXP x RY x 1), encoded once per buffer and layout (the driver's encoder
+// box RXP x RY x 1), encoded once per buffer and layout (the CUDA driver API's encoder
 // is reached through the runtime's entry-point query: no link to libcuda).
 struct TmEntry {
     const void* p;
