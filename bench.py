@@ -152,12 +152,13 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def cpu_oracle_rate(side: int, steps: int, budget_s: float = 20.0):
-    """Oracle cell-updates/s (per RK4 step) on a side x side sample of the workload."""
+def cpu_oracle_rate(side: int, steps: int, budget_s: float = 20.0, threads: int = 0):
+    """Oracle cell-updates/s (per RK4 step) on a side x side sample of the workload
+    (threads = 0: all host cores)."""
     import oracle
     from paper_1710_06423_b300 import inputs
     oracle.build()
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     pr = oracle.Problem(nx=side, ny=side, nthreads=threads)
     w = inputs.orszag_tang(side, noise=1e-3, seed=20171018)
     done, t0 = 0, time.perf_counter()
@@ -530,8 +531,10 @@ def run_ours(args, ws, rank, local, pg):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         rate, threads, done, el = cpu_oracle_rate(1000, 30, budget_s=20.0)
+        rate1, _, done1, el1 = cpu_oracle_rate(1000, 30, budget_s=4.0, threads=1)
         cpu = {"value": rate, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
-               "sample": f"orszag-tang 1000x1000 window of the workload, {done} RK4 steps in {el:.1f} s (FP64 oracle, OpenMP over rows)"}
+               "sample": f"orszag-tang 1000x1000 window of the workload, {done} RK4 steps in {el:.1f} s (FP64 oracle, OpenMP over rows)",
+               "one_thread": {"value": rate1, "sample": f"the same window, {done1} RK4 steps in {el1:.1f} s on one thread"}}
 
     line = {
         "metric": "cell-updates/s per RK step", "value": value, "unit": "cell-updates/s",
