@@ -180,6 +180,18 @@ int sac_cmax(sac_ctx *c, double *cmax_x, double *cmax_y);
  * Synchronous. */
 int sac_sums(sac_ctx *c, double sums[6]);
 
+/* Discrete divergence of the total magnetic field B = B~ + B_b of the current
+ * state (section 2's fourth-order central difference in x and y, the one the
+ * flux derivatives use), evaluated in FP64 on the device from the stored
+ * values.  A cell counts when its five-point stencil in each direction stays
+ * inside the interior or wraps across a periodic side (non-periodic sides
+ * drop two cells); a direction of one cell contributes no derivative.
+ * max_abs = max |div B|, mean_abs = sum |div B| / ncells (0 when no cell
+ * counts), ncells = the number of cells counted; any output may be NULL.
+ * Deterministic (fixed reduction order).  Synchronous.
+ * Errors: SAC_ERR_ARG, SAC_ERR_STATE (no state set), SAC_ERR_CUDA. */
+int sac_divb(sac_ctx *c, double *max_abs, double *mean_abs, long long *ncells);
+
 /* Per-kernel timing: nsteps CFL steps launched kernel by kernel (no graph)
  * with CUDA events around every launch on the context's stream.  ms[0] is
  * the mean duration of the step-control kernel, ms[1..4] those of the RK

@@ -76,6 +76,7 @@ def _load():
         lib.orc_ext_size.restype = ctypes.c_size_t
         lib.orc_rhs.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
         lib.orc_cmax.argtypes = [P, dp, dp, dp, dp]
+        lib.orc_divb.argtypes = [P, dp, dp, dp, ctypes.POINTER(ctypes.c_ubyte)]
         lib.orc_cfl_dt.argtypes = [P, ctypes.c_double, ctypes.c_double]
         lib.orc_cfl_dt.restype = ctypes.c_double
         lib.orc_rk4_step.argtypes = [P, dp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -175,6 +176,21 @@ def cmax(pr: Problem, w, bg=None) -> tuple[float, float]:
     cx, cy = ctypes.c_double(), ctypes.c_double()
     lib.orc_cmax(ctypes.byref(p), _dp(w), _dp(bg), ctypes.byref(cx), ctypes.byref(cy))
     return cx.value, cy.value
+
+
+def div_b(pr: Problem, w, bg=None) -> tuple[np.ndarray, np.ndarray]:
+    """Discrete div B of the total field per interior cell, fourth-order
+    central differences; returns (div [ny][nx], mask [ny][nx] of the cells
+    whose stencil exists: non-periodic sides leave out two cells)."""
+    lib = _load()
+    p = pr._c()
+    w = _state(w, pr, NF)
+    bg = None if bg is None else _state(bg, pr, NB)
+    div = np.zeros((pr.ny, pr.nx))
+    mask = np.zeros((pr.ny, pr.nx), dtype=np.uint8)
+    lib.orc_divb(ctypes.byref(p), _dp(w), _dp(bg), _dp(div),
+                 mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+    return div, mask.astype(bool)
 
 
 def cfl_dt(pr: Problem, cx: float, cy: float) -> float:

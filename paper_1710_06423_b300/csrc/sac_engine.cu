@@ -162,6 +162,69 @@ __global__ void sums_final_kernel(const double* __restrict__ part, int nb, doubl
     }
 }
 
+// ---- discrete divergence of the total magnetic field --------------------------
+// div B = D_x Bx + D_y By with the fourth-order central difference of
+// section 2 (D f = (f[-2] - 8 f[-1] + 8 f[+1] - f[+2]) / 12h), on B = B~ + B_b,
+// evaluated in FP64 from the stored values.  A cell counts when its stencil
+// stays inside the interior or wraps across a periodic side; a direction of
+// one cell contributes no derivative.  Per block: max |div B| and sum |div B|.
+__device__ inline bool divb_cell_in(int i, int n, int bc) {
+    return n == 1 || bc == BC_PERIODIC || (i >= 2 && i < n - 2);
+}
+
+template <typename T, bool BG>
+__global__ void divb_partial_kernel(const T* __restrict__ w, const T* __restrict__ bg, Layout L, int bc_x, int bc_y,
+                                    double inv12dx, double inv12dy, double* __restrict__ part)
+{
+    __shared__ double red[2][32];
+    double mx = 0.0, sm = 0.0;
+    const long long n = (long long)L.nx * L.ny;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(v / L.nx), i = (int)(v % L.nx);
+        if (!divb_cell_in(i, L.nx, bc_x) || !divb_cell_in(j, L.ny, bc_y)) continue;
+        auto b = [&](int f, int ii, int jj) {
+            double x = (double)w[L.idx(f, ii, jj, false)];
+            if (BG) x += (double)bg[L.idx(f - 2, ii, jj, true)];   // background order: rho_b, e_b, Bx_b, By_b
+            return x;
+        };
+        double d = 0.0;
+        if (L.nx > 1) {
+            const int m2 = wrapi(i - 2, L.nx), m1 = wrapi(i - 1, L.nx), p1 = wrapi(i + 1, L.nx), p2 = wrapi(i + 2, L.nx);
+            d += (b(4, m2, j) - 8.0 * b(4, m1, j) + 8.0 * b(4, p1, j) - b(4, p2, j)) * inv12dx;
+        }
+        if (L.ny > 1) {
+            const int m2 = wrapi(j - 2, L.ny), m1 = wrapi(j - 1, L.ny), p1 = wrapi(j + 1, L.ny), p2 = wrapi(j + 2, L.ny);
+            d += (b(5, i, m2) - 8.0 * b(5, i, m1) + 8.0 * b(5, i, p1) - b(5, i, p2)) * inv12dy;
+        }
+        const double a = fabs(d);
+        mx = fmax(mx, a);
+        sm += a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = mx; red[1][threadIdx.x >> 5] = sm; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a = fmax(a, red[0][k]); s += red[1][k]; }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = s;
+    }
+}
+
+__global__ void divb_final_kernel(const double* __restrict__ part, int nb, double* __restrict__ out)
+{
+    if (threadIdx.x == 0) {
+        double a = 0.0, s = 0.0;
+        for (int b = 0; b < nb; ++b) { a = fmax(a, part[2 * b]); s += part[2 * b + 1]; }
+        out[0] = a;
+        out[1] = s;
+    }
+}
+
 int grid_for(long long n, int block) {
     long long g = (n + block - 1) / block;
     return (int)(g < 1 ? 1 : (g > 148 * 16 ? 148 * 16 : g));
@@ -682,6 +745,46 @@ int sac_sums(sac_ctx* c, double sums[6])
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(sums, c->part + kSumBlocks * NF, NF * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return pull_scalars(c);
+}
+
+int sac_divb(sac_ctx* c, double* max_abs, double* mean_abs, long long* ncells)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
+    CK(cudaSetDevice(c->p.device));
+    const double inv12dx = c->p.nx / (12.0 * (c->p.x1 - c->p.x0));
+    const double inv12dy = c->p.ny / (12.0 * (c->p.y1 - c->p.y0));
+    const int bx = c->p.bc_x, by = c->p.bc_y;
+    // part holds (kSumBlocks + 1) * NF doubles; this needs 2 * kSumBlocks + 2
+    double* out = c->part + 2 * kSumBlocks;
+    if (c->fp32) {
+        if (c->p.has_background)
+            divb_partial_kernel<float, true><<<kSumBlocks, 256, 0, c->stream>>>(
+                (const float*)c->u0, (const float*)c->bg, c->L, bx, by, inv12dx, inv12dy, c->part);
+        else
+            divb_partial_kernel<float, false><<<kSumBlocks, 256, 0, c->stream>>>(
+                (const float*)c->u0, nullptr, c->L, bx, by, inv12dx, inv12dy, c->part);
+    } else {
+        if (c->p.has_background)
+            divb_partial_kernel<double, true><<<kSumBlocks, 256, 0, c->stream>>>(
+                (const double*)c->u0, (const double*)c->bg, c->L, bx, by, inv12dx, inv12dy, c->part);
+        else
+            divb_partial_kernel<double, false><<<kSumBlocks, 256, 0, c->stream>>>(
+                (const double*)c->u0, nullptr, c->L, bx, by, inv12dx, inv12dy, c->part);
+    }
+    CK(cudaGetLastError());
+    divb_final_kernel<<<1, 32, 0, c->stream>>>(c->part, kSumBlocks, out);
+    CK(cudaGetLastError());
+    double h[2];
+    CK(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    const int rc = pull_scalars(c);
+    if (rc != SAC_OK) return rc;
+    auto count = [](int n, int bc) -> long long { return (n == 1 || bc == BC_PERIODIC) ? n : (n > 4 ? n - 4 : 0); };
+    const long long nc = count(c->p.nx, bx) * count(c->p.ny, by);
+    if (max_abs) *max_abs = h[0];
+    if (mean_abs) *mean_abs = nc > 0 ? h[1] / (double)nc : 0.0;
+    if (ncells) *ncells = nc;
+    return SAC_OK;
 }
 
 int sac_profile_stages(sac_ctx* c, int nsteps, double ms[5])

@@ -26,7 +26,7 @@ NF, NB = 6, 4
 EXPORTS = (
     "sac_default_params", "sac_init", "sac_free", "sac_last_error", "sac_status_string",
     "sac_set_state", "sac_get_state", "sac_set_state_dev", "sac_get_state_dev",
-    "sac_step", "sac_steps", "sac_run_to", "sac_set_fixed_dt", "sac_dt", "sac_time", "sac_cmax", "sac_sums",
+    "sac_step", "sac_steps", "sac_run_to", "sac_set_fixed_dt", "sac_dt", "sac_time", "sac_cmax", "sac_sums", "sac_divb",
     "sac_profile_stages", "sac_sync", "sac_debug_drop_copies",
     "sac_batch_init", "sac_batch_free", "sac_batch_last_error", "sac_batch_set_state",
     "sac_batch_get_state", "sac_batch_steps", "sac_batch_sync", "sac_batch_time", "sac_batch_tune",
@@ -115,6 +115,7 @@ def load() -> ctypes.CDLL:
         "sac_time": (i, [vp, dp, ctypes.POINTER(L)]),
         "sac_cmax": (i, [vp, dp, dp]),
         "sac_sums": (i, [vp, dp]),
+        "sac_divb": (i, [vp, dp, dp, ctypes.POINTER(ctypes.c_longlong)]),
         "sac_profile_stages": (i, [vp, i, dp]),
         "sac_sync": (i, [vp]),
         "sac_debug_drop_copies": (i, [vp, i]),
@@ -297,6 +298,12 @@ class Solver:
         out = np.zeros(6)
         self._check(load().sac_sums(self._ctx, _dp(out)), "sac_sums")
         return out
+
+    def divb(self):
+        """(max |div B|, mean |div B|, cells counted) of the total field, FP64."""
+        a, m, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+        self._check(load().sac_divb(self._ctx, ctypes.byref(a), ctypes.byref(m), ctypes.byref(n)), "sac_divb")
+        return a.value, m.value, n.value
 
     def profile_stages(self, nsteps: int) -> np.ndarray:
         """Mean CUDA-event durations [ms]: step control, stage 1..4 kernels."""
