@@ -244,15 +244,19 @@ int sac_batch_sync(sac_batch *b);
 /* Time and steps taken of one run.  Synchronous. */
 int sac_batch_time(sac_batch *b, int run, double *t, long *steps);
 
-/* Autotuner: times every candidate launch configuration (persistent or one
- * CTA per tile, 1 or 2 resident CTAs per SM, three tile orders) on `trials`
+/* Autotuner: times every candidate launch configuration (persistent mode:
+ * 0 = one CTA per tile, 1 = persistent CTAs taking tiles from an atomic queue
+ * head, 2 = persistent CTAs walking the queue with a fixed stride; 1 or 2
+ * resident CTAs per SM; three tile orders) on `trials`
  * RK steps of the current states, keeps the fastest and restores the states
  * it advanced (every run must have a state).  config[3] (may be NULL)
  * receives (persistent, ctas_per_sm, order); ms (may be NULL) the mean time
  * of one batch RK step with that configuration.  Synchronous. */
 int sac_batch_tune(sac_batch *b, int trials, int config[3], double *ms);
 
-/* Set the launch configuration directly (values as sac_batch_tune reports). */
+/* Set the launch configuration directly (values as sac_batch_tune reports:
+ * persistent 0..2, ctas_per_sm 1..2, order 0..2).  Every configuration gives
+ * bitwise the same results.  Errors: SAC_ERR_ARG (out of range). */
 int sac_batch_set_config(sac_batch *b, int persistent, int ctas_per_sm, int order);
 
 /* ---------------------------------------------------------------------------

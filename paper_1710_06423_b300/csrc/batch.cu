@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
     __shared__ unsigned long long red[2][f32k::NW];
     __shared__ __align__(16) StageArgs<float> sa[2];   // current / next tile's run
     __shared__ int tile_s[2];
+    __shared__ int run_s[2], skip_s[2], coef_s;   // run whose arguments sa[k] hold, its skip flag; run of S.ax/S.ay
     __shared__ __align__(8) unsigned long long bar;   // staging completion (persistent mode)
     f32k::Smem& S = *reinterpret_cast<f32k::Smem*>(smem_raw);
     if (!b.persistent) {
@@ -76,22 +77,29 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
     // persistent: tiles from the queue; the next tile is fetched when a tile
     // starts so that its region streams into shared memory (one TMA tensor copy
     // per plane with the next run's tensor map, else bulk row copies) during the
-    // current tile's Y sweep
+    // current tile's Y sweep.  persistent == 1 takes tiles from an atomic queue
+    // head; persistent == 2 walks the queue with a fixed stride (tile
+    // blockIdx.x + k * gridDim.x), so the next index needs no atomic round trip.
+    // A run's arguments are reloaded only when the run changes, and stage 4
+    // folds its signal-speed maximum into the run's key once per run change.
     const bool tma = b.tmaps != nullptr && (f32k::smem_u32(&S.u[0][0][0]) & 127u) == 0;
+    const bool strided = b.persistent == 2;
     const auto tmap = [&](int run) { return tma ? &b.tmaps[run * 4 + (STAGE - 1)] : nullptr; };
     if (threadIdx.x == 0) {
         f32k::mbar_init(&bar, 1);
-        tile_s[0] = (int)atomicAdd(&b.counters[STAGE - 1], 1u);
+        if (!strided) tile_s[0] = (int)atomicAdd(&b.counters[STAGE - 1], 1u);
     }
     __syncthreads();
-    int cur = tile_s[0], buf = 0;
+    int nxt = strided ? (int)blockIdx.x : tile_s[0], buf = 0;
     unsigned phase = 0;
     bool failed = false;
-    if (cur >= b.ntiles) return;
-    int4 d = b.tiles[cur];
+    if (nxt >= b.ntiles) return;
+    int4 d = b.tiles[nxt];
     load_args<STAGE>(b, d.x, sa[0]);
     __syncthreads();
     bool staged = !sa[0].sc->skip;
+    if (threadIdx.x == 0) { run_s[0] = d.x; skip_s[0] = !staged; run_s[1] = -1; coef_s = -1; }
+    unsigned long long m[2] = {0ull, 0ull};
     if (staged) {
         f32k::NextTile first = f32k::next_tile(sa[0], true, d.y * f32k::TX, d.z * f32k::TY);
         first.tm = tmap(d.x);
@@ -99,28 +107,43 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
 #pragma unroll
         for (int p = 0; p < 3; ++p) f32k::stage_plane_bulk(first, S, p, &bar);
     }
+    __syncthreads();   // run_s, skip_s, coef_s set (later updates are ordered by the loop's barriers)
     while (true) {
-        if (threadIdx.x == 0) tile_s[buf ^ 1] = (int)atomicAdd(&b.counters[STAGE - 1], 1u);
-        __syncthreads();
-        const int nxt = tile_s[buf ^ 1];
-        int4 dn = make_int4(0, 0, 0, 0);
+        if (strided) {
+            nxt += (int)gridDim.x;
+        } else {
+            if (threadIdx.x == 0) tile_s[buf ^ 1] = (int)atomicAdd(&b.counters[STAGE - 1], 1u);
+            __syncthreads();
+            nxt = tile_s[buf ^ 1];
+        }
+        int4 dn = make_int4(-1, 0, 0, 0);
+        bool reload = false;
         if (nxt < b.ntiles) {
             dn = b.tiles[nxt];
-            load_args<STAGE>(b, dn.x, sa[buf ^ 1]);
+            reload = run_s[buf ^ 1] != dn.x;
+            if (reload) load_args<STAGE>(b, dn.x, sa[buf ^ 1]);
         }
+        const bool coef = coef_s != d.x;
         __syncthreads();
+        const int skip_n = reload ? sa[buf ^ 1].sc->skip : skip_s[buf ^ 1];
+        if (threadIdx.x == 0) {
+            if (reload) { run_s[buf ^ 1] = dn.x; skip_s[buf ^ 1] = skip_n; }
+            if (staged) coef_s = d.x;
+        }
         const StageArgs<float>& A = sa[buf];
-        const bool nstage = nxt < b.ntiles && !sa[buf ^ 1].sc->skip;
+        const bool nstage = nxt < b.ntiles && !skip_n;
         f32k::NextTile nt = f32k::next_tile(sa[buf ^ 1], nstage, dn.y * f32k::TX, dn.z * f32k::TY);
         nt.tm = nstage ? tmap(dn.x) : nullptr;
         if (staged) {
-            f32k::store_hd_coeffs(A, S, threadIdx.x);
+            if (coef) f32k::store_hd_coeffs(A, S, threadIdx.x);   // visible after the tile's staging barrier
             const f32k::StepConsts K = f32k::load_step_consts(A.sc);
-            unsigned long long m[2] = {0ull, 0ull};
             f32k::tile_body<STAGE, BG, HD, true, false>(A, d.y * f32k::TX, d.z * f32k::TY, S, K, m, nt,
                                                        &bar, &phase, &failed);
             if (failed) return;
-            if (STAGE == 4) f32k::block_speed_max(m, red, A.sc);
+            if (STAGE == 4 && dn.x != d.x) {   // last tile of this run in the CTA's sequence (for now)
+                f32k::block_speed_max(m, red, A.sc);
+                m[0] = m[1] = 0ull;
+            }
         } else if (nstage) {
             // this tile's run is done or failed: nothing was staged for it, so
             // the next tile's region is copied now
@@ -293,7 +316,7 @@ static cudaError_t capture_batch(sac_batch* b, int nsteps, cudaGraphExec_t* out)
 
 static int apply_config(sac_batch* b, int persistent, int ctas, int order)
 {
-    if ((persistent != 0 && persistent != 1) || ctas < 1 || ctas > 2 || order < 0 || order > 2)
+    if (persistent < 0 || persistent > 2 || ctas < 1 || ctas > 2 || order < 0 || order > 2)
         return bfail(b, SAC_ERR_ARG, "bad configuration (%d, %d, %d)", persistent, ctas, order);
     std::vector<int4> t = make_tiles(b, order);
     BK(cudaMemcpyAsync(b->d_tiles, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
@@ -479,14 +502,15 @@ int sac_batch_tune(sac_batch* b, int trials, int config[3], double* ms_out)
             rc = bfail(b, SAC_ERR_CUDA, "tuner snapshot copy");
     }
     if (rc == SAC_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) rc = bfail(b, SAC_ERR_CUDA, "sync");
-    const int cand[9][3] = {{1, 2, 0}, {1, 2, 1}, {1, 2, 2}, {1, 1, 0}, {1, 1, 1}, {1, 1, 2},
-                            {0, 2, 0}, {0, 2, 1}, {0, 2, 2}};
+    const int cand[][3] = {{1, 2, 0}, {1, 2, 1}, {1, 2, 2}, {1, 1, 0}, {1, 1, 1}, {1, 1, 2},
+                           {0, 2, 0}, {0, 2, 1}, {0, 2, 2}, {2, 2, 0}, {2, 2, 1}, {2, 2, 2}};
+    const int ncand = (int)(sizeof cand / sizeof cand[0]);
     double best = 1e300;
     int bi = 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (rc == SAC_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         rc = bfail(b, SAC_ERR_CUDA, "events");
-    for (int k = 0; k < 9 && rc == SAC_OK; ++k) {
+    for (int k = 0; k < ncand && rc == SAC_OK; ++k) {
         if ((rc = apply_config(b, cand[k][0], cand[k][1], cand[k][2])) != SAC_OK) break;
         if (enqueue_batch_step(b, b->stream) != cudaSuccess) { rc = bfail(b, SAC_ERR_CUDA, "trial"); break; }
         cudaEventRecord(e0, b->stream);

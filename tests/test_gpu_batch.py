@@ -36,7 +36,7 @@ def small_batch(inputs_mod):
     return runs, states
 
 
-@pytest.mark.parametrize("config", [(1, 2, 0), (1, 1, 2), (0, 2, 1)])
+@pytest.mark.parametrize("config", [(1, 2, 0), (1, 1, 2), (0, 2, 1), (2, 2, 1), (2, 1, 2)])
 def test_batch_equals_single_runs_bitwise(small_batch, config):
     from paper_1710_06423_b300.sac import Batch
     runs, states = small_batch
@@ -52,6 +52,42 @@ def test_batch_equals_single_runs_bitwise(small_batch, config):
         ref, tr = _single(kw, w, steps)
         assert got[i][1] == tr
         assert np.array_equal(got[i][0], ref), i
+
+
+@pytest.mark.parametrize("config", [(2, 2, 0), (2, 2, 2), (1, 2, 2)])
+def test_many_tiles_per_cta_equal_single_runs_bitwise(inputs_mod, config):
+    """More tiles than resident CTAs, so each persistent CTA walks several tiles
+    across run boundaries (arguments reused within a run, reloaded on a change,
+    one signal-speed fold per run change in stage 4)."""
+    from paper_1710_06423_b300.sac import Batch
+    sizes = [1000, 33, 130, 512, 70, 260]
+    runs, states = [], []
+    for k, n in enumerate(sizes):
+        kw, w = _family_run(inputs_mod, n, k, seed=77)
+        runs.append(kw)
+        states.append(w)
+    steps = 3
+    with Batch(runs) as b:
+        b.set_config(*config)
+        for i, w in enumerate(states):
+            b.set_state(i, w, None, 0.0)
+        b.steps(steps)
+        b.sync()
+        got = [b.get_state(i) for i in range(len(runs))]
+    for i, (kw, w) in enumerate(zip(runs, states)):
+        ref, tr = _single(kw, w, steps)
+        assert got[i][1] == tr, i
+        assert np.array_equal(got[i][0], ref), i
+
+
+def test_bad_config_rejected(small_batch):
+    from paper_1710_06423_b300.sac import SAC_ERR_ARG, Batch, SacError
+    runs, _ = small_batch
+    with Batch(runs) as b:
+        for cfg in ((3, 2, 0), (-1, 2, 0), (1, 3, 0), (1, 2, 3)):
+            with pytest.raises(SacError) as err:
+                b.set_config(*cfg)
+            assert err.value.code == SAC_ERR_ARG
 
 
 def test_batch_runs_keep_their_own_step(small_batch):
