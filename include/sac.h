@@ -398,6 +398,16 @@ int sac3_step(sac3_ctx *c, double dt, double *dt_taken);
 /* n CFL steps. */
 int sac3_steps(sac3_ctx *c, long n);
 double sac3_time(const sac3_ctx *c);
+/* Conservation sums over the interior of the current state, accumulated in
+ * FP64 on the device in a fixed order: sums[f] = sum_ijk w[f][k][j][i] for the
+ * eight fields.  Errors: SAC_ERR_ARG, SAC_ERR_STATE (no state), SAC_ERR_CUDA. */
+int sac3_sums(sac3_ctx *c, double sums[8]);
+/* Discrete divergence of B of the current state: Dx Bx + Dy By + Dz Bz with
+ * section 2's fourth-order central difference (neighbours wrapped across the
+ * periodic box), in FP64 from the stored values; max_abs = max |div B|,
+ * mean_abs = mean |div B| over all cells (either may be NULL).  Deterministic.
+ * Errors: SAC_ERR_ARG, SAC_ERR_STATE (no state), SAC_ERR_CUDA. */
+int sac3_divb(sac3_ctx *c, double *max_abs, double *mean_abs);
 /* Test hook of the bounded copy waits of the FP32 3D stage kernel (as
  * sac_debug_drop_copies): with on != 0 no copy is issued, each stage's wait
  * gives up after about one second and sac3_step returns SAC_ERR_TIMEOUT with

@@ -277,6 +277,7 @@ def _load3():
         d = ctypes.c_double
         lib.orc3_rhs.argtypes = [P, dp, d, d, d, dp]
         lib.orc3_cmax.argtypes = [P, dp, dp, dp, dp]
+        lib.orc3_divb.argtypes = [P, dp, dp]
         lib.orc3_cfl_dt.argtypes = [P, d, d, d]
         lib.orc3_cfl_dt.restype = d
         lib.orc3_rk4_step.argtypes = [P, dp, d, d, d, d]
@@ -339,6 +340,15 @@ def cmax3(pr: Problem3, w) -> tuple[float, float, float]:
     c = [ctypes.c_double() for _ in range(3)]
     lib.orc3_cmax(ctypes.byref(pr._c()), _dp(w), *[ctypes.byref(x) for x in c])
     return tuple(x.value for x in c)
+
+
+def div_b3(pr: Problem3, w) -> np.ndarray:
+    """Discrete div B per cell [nz][ny][nx] (fourth-order central differences, periodic box)."""
+    lib = _load3()
+    w = _state3(w, pr)
+    div = np.zeros((pr.nz, pr.ny, pr.nx))
+    lib.orc3_divb(ctypes.byref(pr._c()), _dp(w), _dp(div))
+    return div
 
 
 def cfl_dt3(pr: Problem3, cx: float, cy: float, cz: float) -> float:

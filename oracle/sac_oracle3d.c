@@ -196,6 +196,37 @@ void orc3_cmax(const orc3_params *p, const double *w, double *cx, double *cy, do
     *cx = ax; *cy = ay; *cz = az;
 }
 
+
+/*
+ * Discrete divergence of B per cell (section 2's fourth-order central
+ * difference, the one the flux derivatives use, in each of the three
+ * directions; periodic box):
+ *     div = Dx(Bx) + Dy(By) + Dz(Bz),
+ *     Dx(f)(i) = (f(i-2) - 8 f(i-1) + 8 f(i+1) - f(i+2)) / (12 dx),
+ * neighbours wrapped across the box.  div has the layout of one field,
+ * [nz][ny][nx].
+ */
+void orc3_divb(const orc3_params *p, const double *w, double *div)
+{
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const size_t n = (size_t)nx * ny * nz;
+    const double *bx = w + 5 * n, *by = w + 6 * n, *bz = w + 7 * n;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double fx[5], fy[5], fz[5];
+                for (int o = -2; o <= 2; ++o) {
+                    fx[o + 2] = bx[((size_t)k * ny + j) * nx + wrap3(i + o, nx)];
+                    fy[o + 2] = by[((size_t)k * ny + wrap3(j + o, ny)) * nx + i];
+                    fz[o + 2] = bz[((size_t)wrap3(k + o, nz) * ny + j) * nx + i];
+                }
+                const double dxb = (fx[0] - 8.0 * fx[1] + 8.0 * fx[3] - fx[4]) / (12.0 * p->dx);
+                const double dyb = (fy[0] - 8.0 * fy[1] + 8.0 * fy[3] - fy[4]) / (12.0 * p->dy);
+                const double dzb = (fz[0] - 8.0 * fz[1] + 8.0 * fz[3] - fz[4]) / (12.0 * p->dz);
+                div[((size_t)k * ny + j) * nx + i] = (dxb + dyb) + dzb;
+            }
+}
+
 double orc3_cfl_dt(const orc3_params *p, double cx, double cy, double cz)
 {
     return p->courant * fmin(fmin(p->dx / cx, p->dy / cy), p->dz / cz);

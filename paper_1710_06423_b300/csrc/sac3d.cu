@@ -236,6 +236,66 @@ __global__ void cmax3_kernel(const T* __restrict__ s, Grid3 g, T gamma, unsigned
     }
 }
 
+// FP64 diagnostics of the current state, in a fixed reduction order: the
+// eight field sums over the interior, and the discrete div B = Dx Bx + Dy By +
+// Dz Bz with section 2's fourth-order central difference (neighbours wrapped
+// across the periodic box), as sum |div B| and max |div B|.  Per block:
+// part[b][0..7] field sums, [8] sum |div B|, [9] max |div B|.
+constexpr int kDiagBlocks = 296, kDiagVals = NF3 + 2;
+template <typename T>
+__global__ void __launch_bounds__(256) diag3_partial(const T* __restrict__ s, Grid3 g, double i12x, double i12y,
+                                                     double i12z, double* __restrict__ part)
+{
+    __shared__ double red[kDiagVals][8];
+    double acc[NF3 + 1], mx = 0.0;
+#pragma unroll
+    for (int f = 0; f <= NF3; ++f) acc[f] = 0.0;
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    const auto b = [&](int f, int i, int j, int k) { return (double)s[(long long)f * g.ne + g.at(i, j, k)]; };
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(v % g.nx);
+        const long long r = v / g.nx;
+        const int j = (int)(r % g.ny), k = (int)(r / g.ny);
+#pragma unroll
+        for (int f = 0; f < NF3; ++f) acc[f] += b(f, i, j, k);
+        const int xm2 = wrapn(i - 2, g.nx), xm1 = wrapn(i - 1, g.nx), xp1 = wrapn(i + 1, g.nx), xp2 = wrapn(i + 2, g.nx);
+        const int ym2 = wrapn(j - 2, g.ny), ym1 = wrapn(j - 1, g.ny), yp1 = wrapn(j + 1, g.ny), yp2 = wrapn(j + 2, g.ny);
+        const int zm2 = wrapn(k - 2, g.nz), zm1 = wrapn(k - 1, g.nz), zp1 = wrapn(k + 1, g.nz), zp2 = wrapn(k + 2, g.nz);
+        const double dxb = (b(5, xm2, j, k) - 8.0 * b(5, xm1, j, k) + 8.0 * b(5, xp1, j, k) - b(5, xp2, j, k)) * i12x;
+        const double dyb = (b(6, i, ym2, k) - 8.0 * b(6, i, ym1, k) + 8.0 * b(6, i, yp1, k) - b(6, i, yp2, k)) * i12y;
+        const double dzb = (b(7, i, j, zm2) - 8.0 * b(7, i, j, zm1) + 8.0 * b(7, i, j, zp1) - b(7, i, j, zp2)) * i12z;
+        const double a = fabs((dxb + dyb) + dzb);
+        acc[NF3] += a;
+        mx = fmax(mx, a);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kDiagVals; ++q) {
+        double x = q <= NF3 ? acc[q] : mx;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = q <= NF3 ? x + y : fmax(x, y);
+        }
+        if (lane == 0) red[q][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kDiagVals) {
+        const int q = threadIdx.x;
+        double x = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) x = q <= NF3 ? x + red[q][k] : fmax(x, red[q][k]);
+        part[blockIdx.x * kDiagVals + q] = x;
+    }
+}
+__global__ void diag3_final(const double* __restrict__ part, int nb, double* __restrict__ out)
+{
+    const int q = threadIdx.x;
+    if (q < kDiagVals) {
+        double x = 0.0;
+        for (int k = 0; k < nb; ++k) x = q <= NF3 ? x + part[k * kDiagVals + q] : fmax(x, part[k * kDiagVals + q]);
+        out[q] = x;
+    }
+}
+
 // FP64 host copy [8][nz][ny][nx] <-> extended device field (interior), converting to T
 template <typename T>
 __global__ void import3(const double* __restrict__ w, T* __restrict__ u, Grid3 g)
@@ -794,6 +854,7 @@ struct sac3_ctx {
     double* wbuf = nullptr;                 // device FP64 staging of a host state
     unsigned long long* keys = nullptr;     // signal-speed keys (3)
     int* status = nullptr;                  // FP32 stage kernels: 1 = a copy wait timed out
+    double* diag = nullptr;                 // diagnostics: per-block partials, then the totals
     CUtensorMap m_full[3], m_col[3];        // FP32: stage inputs U0, SA, SB (plane box, column box)
     CUtensorMap m_sh_full, m_sh_col, m_acc_col;
     CUtensorMap m_shk[3];                   // FP32 stage inputs as (rho, m) planes of the shock kernel
@@ -1032,7 +1093,7 @@ void sac3_free(sac3_ctx* c)
     cudaGetDevice(&prev);
     cudaSetDevice(c->p.device);
     cudaFree(c->u0); cudaFree(c->sa); cudaFree(c->sb); cudaFree(c->acc); cudaFree(c->v); cudaFree(c->fl); cudaFree(c->sh);
-    cudaFree(c->wbuf); cudaFree(c->keys); cudaFree(c->status);
+    cudaFree(c->wbuf); cudaFree(c->keys); cudaFree(c->status); cudaFree(c->diag);
     cudaSetDevice(prev);
     delete c;
 }
@@ -1070,7 +1131,8 @@ int sac3_init(const sac3_params* p, sac3_ctx** out)
          (!c->fp32 && (cudaMalloc(&c->v, 3 * fb) != cudaSuccess || cudaMalloc(&c->fl, 3 * NF3 * fb) != cudaSuccess)) ||
          cudaMalloc(&c->wbuf, (size_t)NF3 * n * sizeof(double)) != cudaSuccess ||
          cudaMalloc(&c->keys, 3 * sizeof(unsigned long long)) != cudaSuccess ||
-         cudaMalloc(&c->status, sizeof(int)) != cudaSuccess)) {
+         cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
+         cudaMalloc(&c->diag, (size_t)(kDiagBlocks + 1) * kDiagVals * sizeof(double)) != cudaSuccess)) {
         cudaGetLastError();
         rc = fail3(c, SAC_ERR_OOM, "device allocation failed");
     }
@@ -1136,6 +1198,49 @@ int sac3_steps(sac3_ctx* c, long n)
 }
 
 double sac3_time(const sac3_ctx* c) { return c ? c->t : 0.0; }
+
+// FP64 diagnostics of the current state into out[kDiagVals] (synchronous)
+static int diag3(sac3_ctx* c, double* out)
+{
+    if (!c->have_state) return fail3(c, SAC_ERR_STATE, "no state set");
+    CK3(cudaSetDevice(c->p.device));
+    const sac3_params& p = c->p;
+    const double i12x = p.nx / (12.0 * (p.x1 - p.x0)), i12y = p.ny / (12.0 * (p.y1 - p.y0)),
+                 i12z = p.nz / (12.0 * (p.z1 - p.z0));
+    if (c->fp32)
+        diag3_partial<float><<<kDiagBlocks, 256, 0, c->stream>>>((const float*)c->u0, c->g, i12x, i12y, i12z, c->diag);
+    else
+        diag3_partial<double><<<kDiagBlocks, 256, 0, c->stream>>>((const double*)c->u0, c->g, i12x, i12y, i12z, c->diag);
+    CK3(cudaGetLastError());
+    double* tot = c->diag + (size_t)kDiagBlocks * kDiagVals;
+    diag3_final<<<1, 32, 0, c->stream>>>(c->diag, kDiagBlocks, tot);
+    CK3(cudaGetLastError());
+    CK3(cudaMemcpyAsync(out, tot, kDiagVals * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK3(cudaStreamSynchronize(c->stream));
+    return SAC_OK;
+}
+
+int sac3_sums(sac3_ctx* c, double sums[8])
+{
+    if (!c || !sums) return fail3(c, SAC_ERR_ARG, "bad arguments");
+    double d[kDiagVals];
+    const int rc = diag3(c, d);
+    if (rc != SAC_OK) return rc;
+    for (int f = 0; f < NF3; ++f) sums[f] = d[f];
+    return SAC_OK;
+}
+
+int sac3_divb(sac3_ctx* c, double* max_abs, double* mean_abs)
+{
+    if (!c) return SAC_ERR_ARG;
+    double d[kDiagVals];
+    const int rc = diag3(c, d);
+    if (rc != SAC_OK) return rc;
+    const double n = (double)c->g.nx * c->g.ny * c->g.nz;
+    if (max_abs) *max_abs = d[NF3 + 1];
+    if (mean_abs) *mean_abs = d[NF3] / n;
+    return SAC_OK;
+}
 
 int sac3_debug_drop_copies(sac3_ctx* c, int on)
 {

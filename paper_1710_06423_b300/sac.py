@@ -36,7 +36,7 @@ EXPORTS = (
     "sac_cnn_apply", "sac_cnn_perturb", "sac_block_average",
     "sac_step_noalloc",
     "sac3_default_params", "sac3_init", "sac3_free", "sac3_last_error", "sac3_set_state", "sac3_get_state",
-    "sac3_step", "sac3_steps", "sac3_time", "sac3_debug_drop_copies",
+    "sac3_step", "sac3_steps", "sac3_time", "sac3_sums", "sac3_divb", "sac3_debug_drop_copies",
 )
 
 
@@ -152,6 +152,8 @@ def load() -> ctypes.CDLL:
         "sac3_step": (i, [vp, d, dp]),
         "sac3_steps": (i, [vp, L]),
         "sac3_time": (d, [vp]),
+        "sac3_sums": (i, [vp, dp]),
+        "sac3_divb": (i, [vp, dp, dp]),
         "sac3_debug_drop_copies": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
@@ -591,6 +593,18 @@ class Solver3:
 
     def time(self) -> float:
         return load().sac3_time(self._ctx)
+
+    def sums(self) -> np.ndarray:
+        """FP64 sums of the eight fields over the interior."""
+        out = np.zeros(8)
+        self._check(load().sac3_sums(self._ctx, _dp(out)), "sac3_sums")
+        return out
+
+    def divb(self):
+        """(max |div B|, mean |div B|) of the current state, FP64."""
+        a, m = ctypes.c_double(), ctypes.c_double()
+        self._check(load().sac3_divb(self._ctx, ctypes.byref(a), ctypes.byref(m)), "sac3_divb")
+        return a.value, m.value
 
     def debug_drop_copies(self, on: bool):
         """Test hook of the bounded copy waits (see sac3_debug_drop_copies)."""

@@ -3,7 +3,9 @@ of the same stored state: max |div B|, mean |div B| and the count of cells
 whose stencil exists, for both precisions, periodic and non-periodic sides,
 with and without a background, before and after steps.  With hyper-diffusion
 off the central differences commute, so the divergence the device reports
-stays where it started."""
+stays where it started.  The 3D form's sums and div B (sac3_sums, sac3_divb)
+are checked the same way against sums of the stored state and the oracle's
+3D div B."""
 import numpy as np
 import pytest
 
@@ -98,3 +100,58 @@ def test_divb_needs_a_state():
         with pytest.raises(SacError) as err:
             s.divb()
         assert err.value.code == SAC_ERR_STATE
+
+
+# ---- the 3D form: sac3_sums and sac3_divb against the oracle ----------------------
+
+def _ot3_noisy(inputs, nx, ny, nz, seed):
+    w = inputs.ot_3d(nx, ny, nz, compress=0.3)
+    rng = np.random.default_rng(seed)
+    w[5:8] += 1e-3 * rng.standard_normal((3, nz, ny, nx))
+    return w
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("nx,ny,nz", [(40, 24, 20), (33, 17, 9)])
+def test_3d_sums_and_divb_match_oracle(oracle_mod, inputs_mod, precision, nx, ny, nz):
+    from paper_1710_06423_b300.sac import FP32, FP64, Solver3
+    prec = FP64 if precision == "fp64" else FP32
+    w = _ot3_noisy(inputs_mod, nx, ny, nz, seed=nx + nz)
+    box = dict(x1=1.0, y1=0.8, z1=1.3)
+    pr = oracle_mod.Problem3(nx=nx, ny=ny, nz=nz, **box)
+    with Solver3(nx=nx, ny=ny, nz=nz, precision=prec, **box) as s:
+        s.set_state(w, 0.0)
+        for _ in range(2):
+            got, _ = s.get_state()
+            sums = s.sums()
+            want = got.reshape(8, -1).sum(axis=1)
+            scale = np.abs(got).reshape(8, -1).sum(axis=1)
+            assert np.all(np.abs(sums - want) <= 1e-12 * scale), (sums, want)
+            div = np.abs(oracle_mod.div_b3(pr, got))
+            mx, mean = s.divb()
+            assert mx == pytest.approx(div.max(), rel=TOL_DIVB, abs=0)
+            assert mean == pytest.approx(div.mean(), rel=TOL_DIVB, abs=0)
+            assert s.divb() == (mx, mean)
+            s.steps(2)
+
+
+def test_3d_divb_carried_without_hyperdiffusion(inputs_mod):
+    from paper_1710_06423_b300.sac import FP64, Solver3
+    n = 24
+    w = _ot3_noisy(inputs_mod, n, n, n, seed=3)
+    with Solver3(nx=n, ny=n, nz=n, precision=FP64, hyperdiffusion=0) as s:
+        s.set_state(w, 0.0)
+        m0, a0 = s.divb()
+        s.steps(10)
+        m1, a1 = s.divb()
+    assert m0 > 0.05
+    assert m1 == pytest.approx(m0, rel=1e-10) and a1 == pytest.approx(a0, rel=1e-10)
+
+
+def test_3d_diagnostics_need_a_state():
+    from paper_1710_06423_b300.sac import FP32, SAC_ERR_STATE, SacError, Solver3
+    with Solver3(nx=8, ny=8, nz=8, precision=FP32) as s:
+        for call in (s.sums, s.divb):
+            with pytest.raises(SacError) as err:
+                call()
+            assert err.value.code == SAC_ERR_STATE

@@ -13,6 +13,11 @@ difference applied to the total field B = B_b + B~).
 * a field built from a discrete vector potential with the same difference
   (Bx = D_y A, By = -D_x A) has zero divergence, which fails if the x and y
   derivatives were swapped or a component taken from the wrong field.
+
+The 3D form's div B (Dx Bx + Dy By + Dz Bz on a periodic box) is pinned the
+same way: the closed form with a different wavenumber per axis, a z-uniform
+field equal to the 2D divergence in every plane, and zero for the discrete
+curl of a vector potential (fails for exchanged components).
 """
 import numpy as np
 import pytest
@@ -123,3 +128,71 @@ def test_divb_zero_for_discrete_vector_potential(oracle_mod):
     w2[4], w2[5] = w[5].copy(), w[4].copy()
     div2, _ = o.div_b(pr, w2)
     assert np.abs(div2).max() > 1e-2 * scale
+
+
+# ---- the 3D form: div B = Dx Bx + Dy By + Dz Bz on a periodic box ----------------
+
+def test_divb3_closed_form_sines(oracle_mod):
+    o = oracle_mod
+    nx, ny, nz = 20, 12, 16
+    pr = o.Problem3(nx=nx, ny=ny, nz=nz, x1=2.0, y0=-1.0, y1=0.5, z1=0.8)
+    h = ((pr.x1 - pr.x0) / nx, (pr.y1 - pr.y0) / ny, (pr.z1 - pr.z0) / nz)
+    x = pr.x0 + (np.arange(nx) + 0.5) * h[0]
+    y = pr.y0 + (np.arange(ny) + 0.5) * h[1]
+    z = pr.z0 + (np.arange(nz) + 0.5) * h[2]
+    a = 2 * np.pi * 3 / (pr.x1 - pr.x0)
+    b = 2 * np.pi * 2 / (pr.y1 - pr.y0)
+    c = 2 * np.pi * 1 / (pr.z1 - pr.z0)
+    w = np.zeros((8, nz, ny, nx))
+    w[5] = 0.7 * np.sin(a * x)[None, None, :]
+    w[6] = 1.3 * np.cos(b * y)[None, :, None]
+    w[7] = -0.4 * np.sin(c * z + 0.3)[:, None, None]
+
+    def factor(k, hh):
+        return (8 * np.sin(k * hh) - np.sin(2 * k * hh)) / (6 * k * hh)
+
+    want = (0.7 * a * factor(a, h[0]) * np.cos(a * x)[None, None, :]
+            - 1.3 * b * factor(b, h[1]) * np.sin(b * y)[None, :, None]
+            - 0.4 * c * factor(c, h[2]) * np.cos(c * z + 0.3)[:, None, None])
+    div = o.div_b3(pr, w)
+    np.testing.assert_allclose(div, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def test_divb3_z_uniform_equals_2d(oracle_mod):
+    o = oracle_mod
+    nx, ny, nz = 14, 10, 6
+    rng = np.random.default_rng(8)
+    b2 = rng.standard_normal((2, ny, nx))
+    w3 = np.zeros((8, nz, ny, nx))
+    w3[5] = b2[0][None]
+    w3[6] = b2[1][None]
+    w3[7] = 0.37                       # a uniform B_z has no z derivative
+    w2 = np.zeros((6, ny, nx))
+    w2[4], w2[5] = b2
+    d3 = o.div_b3(o.Problem3(nx=nx, ny=ny, nz=nz, x1=1.5, y1=0.7), w3)
+    d2, m2 = o.div_b(o.Problem(nx=nx, ny=ny, x1=1.5, y1=0.7), w2)
+    assert m2.all()
+    for k in range(nz):
+        np.testing.assert_allclose(d3[k], d2, rtol=0, atol=1e-13 * np.abs(d2).max())
+
+
+def test_divb3_zero_for_discrete_curl(oracle_mod):
+    o = oracle_mod
+    nx, ny, nz = 12, 10, 8
+    pr = o.Problem3(nx=nx, ny=ny, nz=nz, x1=1.2, y1=0.9, z1=2.0)
+    h = (pr.x1 / nx, pr.y1 / ny, pr.z1 / nz)
+    A = np.random.default_rng(9).standard_normal((3, nz, ny, nx))
+
+    def D(f, axis):   # axis 2: x, 1: y, 0: z of a [nz][ny][nx] array
+        hh = h[2 - axis]
+        return ((np.roll(f, 2, axis) - np.roll(f, -2, axis)) + 8 * (np.roll(f, -1, axis) - np.roll(f, 1, axis))) / (12 * hh)
+
+    w = np.zeros((8, nz, ny, nx))
+    w[5] = D(A[2], 1) - D(A[1], 0)     # Bx = dAz/dy - dAy/dz
+    w[6] = D(A[0], 0) - D(A[2], 2)     # By = dAx/dz - dAz/dx
+    w[7] = D(A[1], 2) - D(A[0], 1)     # Bz = dAy/dx - dAx/dy
+    scale = np.abs(w[5:]).max() / min(h)
+    assert np.abs(o.div_b3(pr, w)).max() < 1e-12 * scale
+    w2 = w.copy()
+    w2[5], w2[7] = w[7].copy(), w[5].copy()
+    assert np.abs(o.div_b3(pr, w2)).max() > 1e-2 * scale
