@@ -44,7 +44,7 @@ def test_params_struct_layout_matches_header(lib):
     assert p.x1 == 1.0 and p.y1 == 1.0 and p.stream is None
 
 
-@pytest.mark.parametrize("field,value", [("nx", 0), ("ny", -3), ("gamma", 1.0), ("courant", 0.0),
+@pytest.mark.parametrize("field,value", [("nx", 0), ("ny", -3), ("nx", 65537), ("ny", 1 << 20), ("gamma", 1.0), ("courant", 0.0),
                                          ("bc_x", 7), ("precision", 5), ("x1", 0.0)])
 def test_bad_params_rejected_before_any_device_call(lib, field, value):
     from paper_1710_06423_b300 import sac

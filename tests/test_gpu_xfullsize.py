@@ -9,6 +9,8 @@
   per stage, so a cell depends only on cells within 12 of it; the oracle run
   on a periodically-wrapped window with a 12-cell margin is exact inside the
   margin when given the GPU's step size and signal speeds.
+* The longest side the API accepts (65536 cells) along x and along y, two
+  steps in both precisions against the oracle over the whole grid.
 """
 import numpy as np
 import pytest
@@ -63,6 +65,26 @@ def test_ot1000_fp32_200_steps(ot1000):
     assert np.all(sym <= 2 * TOL_FP32_L1), sym
     scale = np.abs(w0).reshape(6, -1).sum(axis=1)
     assert np.all(np.abs(s1 - s0) <= 1e-5 * scale), (s1 - s0) / scale
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("nx,ny", [(65536, 12), (12, 65536)])
+def test_longest_sides(oracle_mod, inputs_mod, precision, nx, ny):
+    """The largest side the API accepts (65536 cells), in x and in y: two CFL
+    steps against the oracle over the whole grid."""
+    kw = problem_kwargs(nx, ny)
+    w0 = inputs_mod.orszag_tang(nx, ny, noise=1e-3, seed=7)
+    ref, t_ref, _ = oracle_mod.run(oracle_problem(oracle_mod, kw), w0, max_steps=2)
+    with solver(kw, precision) as s:
+        s.set_state(w0, None, 0.0)
+        s.steps(2)
+        got, t = s.get_state()
+    if precision == FP64:
+        assert t == pytest.approx(t_ref, rel=1e-14)
+        assert np.all(maxrel(got, ref) <= TOL_FP64), maxrel(got, ref)
+    else:
+        assert t == pytest.approx(t_ref, rel=1e-6)
+        assert np.all(l1rel(got, ref) <= TOL_FP32_L1), l1rel(got, ref)
 
 
 def _window(w, j0, i0, size, margin):
