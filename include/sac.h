@@ -188,6 +188,7 @@ int sac_sums(sac_ctx *c, double sums[6]);
  * drop two cells); a direction of one cell contributes no derivative.
  * max_abs = max |div B|, mean_abs = sum |div B| / ncells (0 when no cell
  * counts), ncells = the number of cells counted; any output may be NULL.
+ * A NaN anywhere in the counted stencils makes both max_abs and mean_abs NaN.
  * Deterministic (fixed reduction order).  Synchronous.
  * Errors: SAC_ERR_ARG, SAC_ERR_STATE (no state set), SAC_ERR_CUDA. */
 int sac_divb(sac_ctx *c, double *max_abs, double *mean_abs, long long *ncells);
@@ -405,7 +406,8 @@ int sac3_sums(sac3_ctx *c, double sums[8]);
 /* Discrete divergence of B of the current state: Dx Bx + Dy By + Dz Bz with
  * section 2's fourth-order central difference (neighbours wrapped across the
  * periodic box), in FP64 from the stored values; max_abs = max |div B|,
- * mean_abs = mean |div B| over all cells (either may be NULL).  Deterministic.
+ * mean_abs = mean |div B| over all cells (either may be NULL); a NaN anywhere
+ * makes both NaN.  Deterministic.
  * Errors: SAC_ERR_ARG, SAC_ERR_STATE (no state), SAC_ERR_CUDA. */
 int sac3_divb(sac3_ctx *c, double *max_abs, double *mean_abs);
 /* Test hook of the bounded copy waits of the FP32 3D stage kernel (as

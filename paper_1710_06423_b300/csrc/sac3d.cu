@@ -242,6 +242,8 @@ __global__ void cmax3_kernel(const T* __restrict__ s, Grid3 g, T gamma, unsigned
 // across the periodic box), as sum |div B| and max |div B|.  Per block:
 // part[b][0..7] field sums, [8] sum |div B|, [9] max |div B|.
 constexpr int kDiagBlocks = 296, kDiagVals = NF3 + 2;
+// maximum that keeps a NaN (fmax would drop it)
+__device__ inline double max_nan3(double a, double b) { return (a > b || a != a) ? a : b; }
 template <typename T>
 __global__ void __launch_bounds__(256) diag3_partial(const T* __restrict__ s, Grid3 g, double i12x, double i12y,
                                                      double i12z, double* __restrict__ part)
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(256) diag3_partial(const T* __restrict__ s, Gr
         const double dzb = (b(7, i, j, zm2) - 8.0 * b(7, i, j, zm1) + 8.0 * b(7, i, j, zp1) - b(7, i, j, zp2)) * i12z;
         const double a = fabs((dxb + dyb) + dzb);
         acc[NF3] += a;
-        mx = fmax(mx, a);
+        mx = max_nan3(mx, a);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(256) diag3_partial(const T* __restrict__ s, Gr
         double x = q <= NF3 ? acc[q] : mx;
         for (int o = 16; o > 0; o >>= 1) {
             const double y = __shfl_xor_sync(0xffffffffu, x, o);
-            x = q <= NF3 ? x + y : fmax(x, y);
+            x = q <= NF3 ? x + y : max_nan3(x, y);
         }
         if (lane == 0) red[q][w] = x;
     }
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(256) diag3_partial(const T* __restrict__ s, Gr
     if (threadIdx.x < kDiagVals) {
         const int q = threadIdx.x;
         double x = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) x = q <= NF3 ? x + red[q][k] : fmax(x, red[q][k]);
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) x = q <= NF3 ? x + red[q][k] : max_nan3(x, red[q][k]);
         part[blockIdx.x * kDiagVals + q] = x;
     }
 }
@@ -291,7 +293,7 @@ __global__ void diag3_final(const double* __restrict__ part, int nb, double* __r
     const int q = threadIdx.x;
     if (q < kDiagVals) {
         double x = 0.0;
-        for (int k = 0; k < nb; ++k) x = q <= NF3 ? x + part[k * kDiagVals + q] : fmax(x, part[k * kDiagVals + q]);
+        for (int k = 0; k < nb; ++k) x = q <= NF3 ? x + part[k * kDiagVals + q] : max_nan3(x, part[k * kDiagVals + q]);
         out[q] = x;
     }
 }

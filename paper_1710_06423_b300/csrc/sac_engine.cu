@@ -168,6 +168,9 @@ __global__ void sums_final_kernel(const double* __restrict__ part, int nb, doubl
 // evaluated in FP64 from the stored values.  A cell counts when its stencil
 // stays inside the interior or wraps across a periodic side; a direction of
 // one cell contributes no derivative.  Per block: max |div B| and sum |div B|.
+// maximum that keeps a NaN (fmax would drop it): a non-finite state shows in both outputs
+__device__ inline double max_nan(double a, double b) { return (a > b || a != a) ? a : b; }
+
 __device__ inline bool divb_cell_in(int i, int n, int bc) {
     return n == 1 || bc == BC_PERIODIC || (i >= 2 && i < n - 2);
 }
@@ -198,18 +201,18 @@ __global__ void divb_partial_kernel(const T* __restrict__ w, const T* __restrict
             d += (b(5, i, m2) - 8.0 * b(5, i, m1) + 8.0 * b(5, i, p1) - b(5, i, p2)) * inv12dy;
         }
         const double a = fabs(d);
-        mx = fmax(mx, a);
+        mx = max_nan(mx, a);
         sm += a;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mx = max_nan(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         sm += __shfl_xor_sync(0xffffffffu, sm, o);
     }
     if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = mx; red[1][threadIdx.x >> 5] = sm; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a = fmax(a, red[0][k]); s += red[1][k]; }
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a = max_nan(a, red[0][k]); s += red[1][k]; }
         part[2 * blockIdx.x] = a;
         part[2 * blockIdx.x + 1] = s;
     }
@@ -219,7 +222,7 @@ __global__ void divb_final_kernel(const double* __restrict__ part, int nb, doubl
 {
     if (threadIdx.x == 0) {
         double a = 0.0, s = 0.0;
-        for (int b = 0; b < nb; ++b) { a = fmax(a, part[2 * b]); s += part[2 * b + 1]; }
+        for (int b = 0; b < nb; ++b) { a = max_nan(a, part[2 * b]); s += part[2 * b + 1]; }
         out[0] = a;
         out[1] = s;
     }

@@ -155,3 +155,23 @@ def test_3d_diagnostics_need_a_state():
             with pytest.raises(SacError) as err:
                 call()
             assert err.value.code == SAC_ERR_STATE
+
+
+def test_divb_keeps_a_nan(inputs_mod):
+    """A NaN in B shows in both outputs (a plain fmax would drop it from the maximum)."""
+    import math
+    from paper_1710_06423_b300.sac import FP32, FP64, Solver, Solver3
+    n = 40
+    w = _noisy_ot(inputs_mod, n, n, seed=1)
+    w[4, 17, 23] = np.nan
+    for prec in (FP64, FP32):
+        with Solver(**problem_kwargs(n, n), precision=prec) as s:
+            s.set_state(w, None, 0.0)
+            mx, mean, _ = s.divb()
+        assert math.isnan(mx) and math.isnan(mean)
+    w3 = _ot3_noisy(inputs_mod, 16, 16, 16, seed=2)
+    w3[7, 3, 4, 5] = np.nan
+    with Solver3(nx=16, ny=16, nz=16, precision=FP32) as s3:
+        s3.set_state(w3, 0.0)
+        mx, mean = s3.divb()
+    assert math.isnan(mx) and math.isnan(mean)
