@@ -245,10 +245,12 @@ int sac_batch_sync(sac_batch *b);
 /* Time and steps taken of one run.  Synchronous. */
 int sac_batch_time(sac_batch *b, int run, double *t, long *steps);
 
-/* Autotuner: times every candidate launch configuration (persistent mode:
- * 0 = one CTA per tile, 1 = persistent CTAs taking tiles from an atomic queue
- * head, 2 = persistent CTAs walking the queue with a fixed stride; 1 or 2
- * resident CTAs per SM; three tile orders) on `trials`
+/* Autotuner: times twelve launch configurations (persistent mode 0 = one CTA
+ * per tile, 1 = persistent CTAs taking tiles from an atomic queue head, 2 =
+ * persistent CTAs walking the queue with a fixed stride; 1 or 2 resident CTAs
+ * per SM; tile order 0 = runs as given, 1 = largest run first, 2 = largest
+ * first with tiles interleaved across runs): modes 0 and 2 at 2 CTAs per SM and
+ * mode 1 at 1 and 2, each with all three orders, on `trials`
  * RK steps of the current states, keeps the fastest and restores the states
  * it advanced (every run must have a state).  config[3] (may be NULL)
  * receives (persistent, ctas_per_sm, order); ms (may be NULL) the mean time
