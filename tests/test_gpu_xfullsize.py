@@ -11,6 +11,8 @@
   margin when given the GPU's step size and signal speeds.
 * The longest side the API accepts (65536 cells) along x and along y, two
   steps in both precisions against the oracle over the whole grid.
+* The 64-run batch of the benchmark in its autotuned launch configuration:
+  one run of every size bit for bit equal to a single-run context.
 """
 import numpy as np
 import pytest
@@ -85,6 +87,37 @@ def test_longest_sides(oracle_mod, inputs_mod, precision, nx, ny):
     else:
         assert t == pytest.approx(t_ref, rel=1e-6)
         assert np.all(l1rel(got, ref) <= TOL_FP32_L1), l1rel(got, ref)
+
+
+def test_c3_batch_config_equals_single_runs(inputs_mod):
+    """The 64-run batch the benchmark times (seeded sizes from {256, 512, 1000,
+    2044}^2, Orszag-Tang family members, autotuned launch configuration), two
+    steps: the first run of every size equals a single-run context bit for bit
+    (the single runs are the ones checked against the oracle above)."""
+    from paper_1710_06423_b300.sac import Batch, Solver
+    sizes = inputs_mod.batch_sizes(2024, 64)
+
+    def state(k):
+        b0, gamma, phases = inputs_mod.ot_family_params(2024, k)
+        return inputs_mod.orszag_tang(sizes[k], b0=b0, gamma=gamma, phases=phases)
+
+    runs = [dict(nx=n, ny=n, gamma=inputs_mod.ot_family_params(2024, k)[1]) for k, n in enumerate(sizes)]
+    pick = [sizes.index(n) for n in sorted(set(sizes))]
+    steps = 2
+    with Batch(runs) as b:
+        for k in range(len(sizes)):
+            b.set_state(k, state(k), None, 0.0)
+        b.tune(trials=1)                 # restores the states it advanced
+        b.steps(steps)
+        b.sync()
+        got = {k: b.get_state(k) for k in pick}
+    for k in pick:
+        with Solver(**runs[k], precision=FP32) as s:
+            s.set_state(state(k), None, 0.0)
+            s.steps(steps)
+            ref, t = s.get_state()
+        assert got[k][1] == t, k
+        assert np.array_equal(got[k][0], ref), (k, sizes[k])
 
 
 def _window(w, j0, i0, size, margin):
