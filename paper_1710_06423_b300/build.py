@@ -31,6 +31,7 @@ UNITS = [
     ("cnn.cu", []),
     ("noalloc.cu", []),
     ("sac3d.cu", ["--fmad=false"]),
+    ("sac3d_f32.cu", []),
 ]
 
 
