@@ -411,8 +411,9 @@ stage3_f32(const float* __restrict__ in, const float* __restrict__ sh, const flo
 // shock indicator s = max(0, -div v) on [-1, n+1) in every direction, from the
 // stage input.  One CTA owns 32 x 4 output columns and marches skz planes along
 // z.  Planes of (rho, m_x, m_y, m_z) with a 2-cell x/y halo arrive by one
-// tensor-map TMA copy each into a ring of four buffers (plane q in buffer q mod
-// 4, one mbarrier per buffer; plane k+4 is copied once plane k is done); v_x and
+// tensor-map TMA copy each into a ring of SNB = 4 buffers (plane q in buffer
+// q mod SNB, one mbarrier per buffer; plane k+SNB is copied once plane k is
+// done); v_x and
 // v_y of plane k are formed once per cell in shared memory, v_z of the own
 // column at planes k .. k+2 from the ring and at k-1, k-2 from two rolled
 // registers.  Same arithmetic as the per-cell form.  Every copy issued is waited
@@ -443,7 +444,7 @@ __global__ void __launch_bounds__(SNT) shock3_f32(float* __restrict__ sh, Grid3 
         for (int b = 0; b < SNB; ++b) mbar_init(&bar[b]);
     __syncthreads();
     unsigned phase = 0, pending = 0;   // per buffer: parity of the next completion; copy issued, not yet waited
-    const auto buf = [](int q) { return (q + SNB) % SNB; };   // q >= -3
+    const auto buf = [](int q) { return (q + SNB) % SNB; };   // q >= -3 > -SNB
     const auto issue = [&](int q) {
         const int b = buf(q);
         pending |= 1u << b;
@@ -469,15 +470,16 @@ __global__ void __launch_bounds__(SNT) shock3_f32(float* __restrict__ sh, Grid3 
     };
     const auto vz_of = [&](int b) { return S.pl[b][3][r0][c0] * rcpf(S.pl[b][0][r0][c0]); };
 
-    // planes k0-2 .. k0+1; v_z of the first two; then k0+2, k0+3 into their buffers
-    for (int q = k0 - 2; q <= k0 + 1; ++q) issue(q);
+    // planes k0-2 .. k0+SNB-3 (never past k1+1, the last plane a step reads);
+    // v_z of the first two; then k0+SNB-2, k0+SNB-1 into their buffers
+    for (int q = k0 - 2; q <= k0 + SNB - 3 && q <= k1 + 1; ++q) issue(q);
     bool to = wait(k0 - 2);
     to = wait(k0 - 1) || to;
     if (__syncthreads_or(to)) { give_up(); return; }
     float vzm2 = vz_of(buf(k0 - 2)), vzm1 = vz_of(buf(k0 - 1));
     __syncthreads();   // the buffers of k0-2, k0-1 are free
-    issue(k0 + 2);     // read at step k0 (k1 >= k0 + 1)
-    if (k0 + 3 <= k1 + 1) issue(k0 + 3);
+    if (k0 + SNB - 2 <= k1 + 1) issue(k0 + SNB - 2);
+    if (k0 + SNB - 1 <= k1 + 1) issue(k0 + SNB - 1);
 #pragma unroll 1
     for (int k = k0; k < k1; ++k) {
         to = false;
@@ -506,7 +508,7 @@ __global__ void __launch_bounds__(SNT) shock3_f32(float* __restrict__ sh, Grid3 
         }
         vzm2 = vzm1; vzm1 = vz0;
         __syncthreads();   // plane k's buffer and v_x, v_y are free
-        if (k + 4 <= k1 + 1) issue(k + 4);   // read at step k+2 as its plane +2
+        if (k + SNB <= k1 + 1) issue(k + SNB);   // into plane k's buffer
     }
 }
 }  // namespace f3
