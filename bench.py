@@ -40,6 +40,11 @@ STAGE_VALUES_FP32 = (12, 24, 30, 24)
 # RK register; profiles/stage_fp32_dram_ot4000.md).  Traffic scales with the cells
 # processed; the figures hold for the stage kernel as of that capture.
 STAGE_TRAFFIC_B_PER_CELL_FP32 = (45.6, 93.8, 120.2, 97.6)
+# kernels one graph-replayed RK4 step launches on a grid with a periodic or
+# outflow side: the step-control kernel, then per stage the stage kernel and
+# the ghost-frame kernel (the batch step: its begin kernel, then per stage the
+# batch stage kernel and the batch ghost-frame kernel)
+LAUNCHES_PER_STEP = 1 + 4 * 2
 
 
 def parse():
@@ -293,7 +298,7 @@ def run_batched(args, ws, local, pg, torch):
             "steps": args.batch_steps, "runs": len(sizes), "sizes": counts, "cells": cells,
             "tuned_config": {"persistent": cfg[0], "ctas_per_sm": cfg[1], "order": cfg[2]},
             "gb_per_s": gbs, "roofline_frac": gbs / peak, "peak_kind": f"of {peak_kind}",
-            "per_size": per_size, "gpu_launches": 5 * args.batch_steps}
+            "per_size": per_size, "gpu_launches": LAUNCHES_PER_STEP * args.batch_steps}
 
 
 def run_learned(args, local):
@@ -547,7 +552,7 @@ def run_ours(args, ws, rank, local, pg):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clocks,
         "extra": extra,
     }
