@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--learned", action="store_true",
                     help="run the learned coarse-grid correction experiment instead (several minutes)")
     ap.add_argument("--t-end", type=float, default=0.5, help="horizon of the learned experiment")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="time only the 64-run batched workload (one JSON line)")
+    ap.add_argument("--no-per-size", action="store_true",
+                    help="with --only-batched: skip the per-size batches")
     ap.add_argument("--only-3d", type=int, default=0, metavar="N",
                     help="time only the 3D form on an N^3 box and print its line (for profiling)")
     return ap.parse_args()
@@ -240,7 +244,7 @@ def time_device_steps(solver, steps, warmup, pg, torch):
     return reduce_max(ev0.elapsed_time(ev1), pg, "cuda")
 
 
-def run_batched(args, ws, local, pg, torch):
+def run_batched(args, ws, local, pg, torch, per_size=True):
     """64 independent Orszag-Tang-family runs (seeded sizes from {256, 512, 1000, 2044}^2,
     B0 x U[0.5, 1.5], gamma in {1.4, 5/3}, seeded phases), one launch per RK stage."""
     from paper_1710_06423_b300 import inputs
@@ -272,8 +276,8 @@ def run_batched(args, ws, local, pg, torch):
     b.close()
     value = ws * cells * args.batch_steps / (ms * 1e-3)
     # per size class: the runs of one size as a batch of their own (autotuned, 100 steps)
-    per_size = {}
-    for n in sorted(set(sizes)):
+    per_size_res = {}
+    for n in (sorted(set(sizes)) if per_size else []):
         ks = [k for k, m in enumerate(sizes) if m == n]
         bs = Batch([runs[k] for k in ks], device=local)
         for j, k in enumerate(ks):
@@ -290,7 +294,7 @@ def run_batched(args, ws, local, pg, torch):
         bs.sync()
         ms_n = reduce_max(e0.elapsed_time(e1), pg, "cuda")
         bs.close()
-        per_size[str(n)] = {"runs": len(ks), "value": ws * len(ks) * n * n * 100 / (ms_n * 1e-3),
+        per_size_res[str(n)] = {"runs": len(ks), "value": ws * len(ks) * n * n * 100 / (ms_n * 1e-3),
                             "tuned_config": {"persistent": cfg_n[0], "ctas_per_sm": cfg_n[1], "order": cfg_n[2]}}
     peak, peak_kind = measured_peaks()
     gbs = value * 4 * 90 / 1e9
@@ -298,7 +302,7 @@ def run_batched(args, ws, local, pg, torch):
             "steps": args.batch_steps, "runs": len(sizes), "sizes": counts, "cells": cells,
             "tuned_config": {"persistent": cfg[0], "ctas_per_sm": cfg[1], "order": cfg[2]},
             "gb_per_s": gbs, "roofline_frac": gbs / peak, "peak_kind": f"of {peak_kind}",
-            "per_size": per_size, "gpu_launches": LAUNCHES_PER_STEP * args.batch_steps}
+            "per_size": per_size_res, "gpu_launches": LAUNCHES_PER_STEP * args.batch_steps}
 
 
 def run_learned(args, local):
@@ -569,6 +573,12 @@ def main():
         elif args.learned:
             if rank == 0:
                 run_learned(args, local)
+        elif args.only_batched:
+            import torch
+            torch.cuda.set_device(local)
+            res = run_batched(args, ws, local, pg, torch, per_size=not args.no_per_size)
+            if rank == 0:
+                print(json.dumps({"metric": "batched cell-updates/s per RK step", **res}), flush=True)
         elif args.only_3d:
             import torch
             torch.cuda.set_device(local)
