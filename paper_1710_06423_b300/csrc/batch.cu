@@ -140,7 +140,9 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
             f32k::tile_body<STAGE, BG, HD, true, false>(A, d.y * f32k::TX, d.z * f32k::TY, S, K, m, nt,
                                                        &bar, &phase, &failed);
             if (failed) return;
-            if (STAGE == 4 && dn.x != d.x) {   // last tile of this run in the CTA's sequence (for now)
+            // the next tile belongs to another run (or there is none): fold this run's
+            // maximum now; a later tile of the same run folds again (atomicMax)
+            if (STAGE == 4 && dn.x != d.x) {
                 f32k::block_speed_max(m, red, A.sc);
                 m[0] = m[1] = 0ull;
             }
