@@ -1,5 +1,6 @@
 /*
- * sac.h -- C ABI of the B300 SAC-family 2D ideal-MHD step (arXiv 1710.06423).
+ * sac.h -- C ABI of the B300 SAC-family 2D ideal-MHD step (arXiv 1710.06423),
+ * with batched runs, a learned coarse-grid correction and a 3D form (sac3_*).
  *
  * The library advances the 2D ideal-MHD equations of section 2 of the paper
  * (mass, momentum, energy and induction in conservative form, total pressure
@@ -27,7 +28,8 @@
  *     safe.  Calls marked ASYNC only enqueue work on that stream.
  *   - Errors found on the device (non-finite state or step) are recorded in
  *     the context and reported by the next synchronising call
- *     (sac_run_to, sac_step, sac_get_state*, sac_dt, sac_time, sac_sync).
+ *     (sac_run_to, sac_step, sac_get_state*, sac_dt, sac_time, sac_cmax,
+ *     sac_sums, sac_divb, sac_sync).
  *     After SAC_ERR_NONFINITE the state is left as computed, for inspection,
  *     and further steps are skipped until sac_set_state*.
  */
