@@ -161,3 +161,39 @@ def test_family_batch_shape(inputs_mod):
     for i in picks:
         ref, tr = _single(runs[i], states[i], 4)
         assert np.array_equal(got[i][0], ref) and got[i][1] == tr
+
+
+@pytest.mark.parametrize("config", [(1, 2, 1), (2, 2, 0), (0, 2, 2)])
+def test_batch_with_background_and_open_sides_equals_single_runs(config):
+    """Runs with a static background and fixed/outflow/periodic sides (the
+    background instantiation of the batch kernel and the non-periodic ghost
+    frames): bit for bit the same as single-run contexts."""
+    from gpu_helpers import smooth_background
+    from paper_1710_06423_b300.sac import Batch, Solver
+    import paper_1710_06423_b300.inputs as inputs
+    cases = [(70, 45, 0, 2), (96, 64, 2, 1), (33, 90, 1, 0), (128, 40, 2, 2)]
+    runs, states = [], []
+    for k, (nx, ny, bx, by) in enumerate(cases):
+        bg = smooth_background(ny, nx, seed=k + 1)
+        w = inputs.orszag_tang(nx, ny, noise=1e-3, seed=k)
+        w[0] += 0.3 - bg[0]
+        w[3] += 0.5 - bg[1]
+        w[4] -= bg[2]
+        w[5] -= bg[3]
+        runs.append(dict(nx=nx, ny=ny, bc_x=bx, bc_y=by, has_background=1))
+        states.append((w, bg))
+    steps = 4
+    with Batch(runs) as b:
+        b.set_config(*config)
+        for i, (w, bg) in enumerate(states):
+            b.set_state(i, w, bg, 0.0)
+        b.steps(steps)
+        b.sync()
+        got = [b.get_state(i) for i in range(len(runs))]
+    for i, (kw, (w, bg)) in enumerate(zip(runs, states)):
+        with Solver(**kw, precision=FP32) as s:
+            s.set_state(w, bg, 0.0)
+            s.steps(steps)
+            ref, t = s.get_state()
+        assert got[i][1] == t, i
+        assert np.array_equal(got[i][0], ref), i
