@@ -197,3 +197,34 @@ def test_batch_with_background_and_open_sides_equals_single_runs(config):
             ref, t = s.get_state()
         assert got[i][1] == t, i
         assert np.array_equal(got[i][0], ref), i
+
+
+@pytest.mark.parametrize("config", [(1, 2, 2), (2, 2, 1), (0, 2, 0)])
+def test_batch_with_one_row_and_tiny_runs_equals_single_runs(config):
+    """Degenerate grids in one batch: the Brio-Wu tube (800 x 1, fixed sides,
+    gamma 2), a 5 x 3 periodic grid, a 1 x 40 column and a multi-tile run."""
+    from paper_1710_06423_b300.sac import Batch, Solver
+    import paper_1710_06423_b300.inputs as inputs
+    runs = [dict(nx=800, ny=1, gamma=2.0, bc_x=1, bc_y=1),
+            dict(nx=5, ny=3),
+            dict(nx=1, ny=40, bc_y=2),
+            dict(nx=100, ny=70)]
+    states = [inputs.brio_wu(800, 1, gamma=2.0),
+              inputs.orszag_tang(5, 3, noise=1e-3, seed=3),
+              inputs.orszag_tang(1, 40, noise=1e-3, seed=4),
+              inputs.orszag_tang(100, 70, noise=1e-3, seed=5)]
+    steps = 5
+    with Batch(runs) as b:
+        b.set_config(*config)
+        for i, w in enumerate(states):
+            b.set_state(i, w, None, 0.0)
+        b.steps(steps)
+        b.sync()
+        got = [b.get_state(i) for i in range(len(runs))]
+    for i, (kw, w) in enumerate(zip(runs, states)):
+        with Solver(**kw, precision=FP32) as s:
+            s.set_state(w, None, 0.0)
+            s.steps(steps)
+            ref, t = s.get_state()
+        assert got[i][1] == t, i
+        assert np.array_equal(got[i][0], ref), i
