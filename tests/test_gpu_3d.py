@@ -101,3 +101,31 @@ def test_nonfinite_state_is_reported():
         s.set_state(w, 0.0)
         with pytest.raises(SacError):
             s.step()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("nx,ny,nz", [(40, 24, 1), (1, 30, 20), (17, 1, 9)])
+def test_one_cell_thick_boxes_match_oracle(oracle_mod, inputs_mod, precision, nx, ny, nz):
+    """Degenerate boxes (one cell along z, x or y): the periodic wrap of a
+    single plane, row or column, against the 3D oracle."""
+    from paper_1710_06423_b300.sac import FP32, FP64, Solver3
+    prec = FP64 if precision == "fp64" else FP32
+    steps = 3
+    w = inputs_mod.ot_3d(nx, ny, nz, compress=0.3)
+    pr = oracle_mod.Problem3(nx=nx, ny=ny, nz=nz)
+    ref, t_ref, _ = oracle_mod.run3(pr, w, max_steps=steps)
+    with Solver3(nx=nx, ny=ny, nz=nz, precision=prec) as s:
+        s.set_state(w, 0.0)
+        s.steps(steps)
+        got, t = s.get_state()
+    live = [f for f in range(8) if np.abs(ref[f]).sum() > 0]
+    for f in range(8):
+        if f not in live:
+            assert np.abs(got[f]).max() <= (0.0 if prec == FP64 else 1e-6), f
+    if prec == FP64:
+        assert t == t_ref
+        assert np.all(_rel(got[live], ref[live]) <= TOL_FP64), _rel(got[live], ref[live])
+    else:
+        assert t == pytest.approx(t_ref, rel=1e-5)
+        err = l1rel(got[live].reshape(len(live), -1), ref[live].reshape(len(live), -1))
+        assert np.all(err <= TOL_FP32_L1), err
