@@ -46,6 +46,33 @@ def test_noalloc_step_matches_context_step_twice(inputs_mod):
         assert np.array_equal(g, r)          # same kernels, same arithmetic
 
 
+@pytest.mark.parametrize("case", ["brio_wu_fixed", "outflow", "in_place"])
+def test_noalloc_edge_cases_equal_context_step(inputs_mod, case):
+    """The 1D Brio-Wu tube with fixed sides (held ghosts taken from the input
+    state, as sac_set_state takes them), an outflow grid, and an in-place call
+    (w_out == w_in): bit for bit the context path's step."""
+    import torch
+    from paper_1710_06423_b300 import sac
+    if case == "brio_wu_fixed":
+        kw = dict(nx=800, ny=1, gamma=2.0, bc_x=1, bc_y=1)
+        w0 = inputs_mod.brio_wu(800, 1, gamma=2.0)
+    else:
+        kw = dict(nx=37, ny=29, bc_x=2, bc_y=2) if case == "outflow" else dict(nx=64, ny=48)
+        w0 = inputs_mod.orszag_tang(kw["nx"], kw["ny"], noise=1e-3, seed=2)
+    dev = torch.from_numpy(w0.astype(np.float32)).cuda().contiguous()
+    with sac.Solver(**kw, precision=sac.FP32) as s:
+        s.set_state_dev(dev, None, 0.0)
+        dt_ref = s.step(0.0)
+        ref = torch.empty_like(dev)
+        s.get_state_dev(ref)
+    a = dev.clone()
+    b = a if case == "in_place" else torch.empty_like(dev)
+    dt = sac.step_noalloc(a, b, 0.0, **kw)
+    torch.cuda.synchronize()
+    assert dt == dt_ref
+    assert torch.equal(b, ref)
+
+
 def test_noalloc_rejects_grids_beyond_its_memory():
     import torch
     from paper_1710_06423_b300 import sac
