@@ -175,3 +175,20 @@ def test_divb_keeps_a_nan(inputs_mod):
         s3.set_state(w3, 0.0)
         mx, mean = s3.divb()
     assert math.isnan(mx) and math.isnan(mean)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_3d_sums_conserved_on_the_periodic_box(inputs_mod, precision, tol):
+    """Flux-form differences on a periodic box conserve every field's sum: the
+    device sums after several steps equal the starting sums (to rounding)."""
+    from paper_1710_06423_b300.sac import FP32, FP64, Solver3
+    prec = FP64 if precision == "fp64" else FP32
+    n = 20
+    w = _ot3_noisy(inputs_mod, n, n, n, seed=6)
+    with Solver3(nx=n, ny=n, nz=n, precision=prec) as s:
+        s.set_state(w, 0.0)
+        s0 = s.sums()
+        scale = np.abs(s.get_state()[0]).reshape(8, -1).sum(axis=1)
+        s.steps(6)
+        s1 = s.sums()
+    assert np.all(np.abs(s1 - s0) <= tol * scale), (s1 - s0) / scale
