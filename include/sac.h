@@ -402,6 +402,12 @@ int sac3_get_state(sac3_ctx *c, double *w, double *t);
 int sac3_step(sac3_ctx *c, double dt, double *dt_taken);
 /* n CFL steps. */
 int sac3_steps(sac3_ctx *c, long n);
+/* CFL steps until t_end (the last step is clipped so that the time lands
+ * exactly on t_end) or until max_steps steps (max_steps < 0: no limit);
+ * *steps_taken (may be NULL) receives the number of steps.  Errors:
+ * SAC_ERR_ARG (t_end not finite), SAC_ERR_STATE, SAC_ERR_NONFINITE,
+ * SAC_ERR_TIMEOUT, SAC_ERR_CUDA. */
+int sac3_run_to(sac3_ctx *c, double t_end, long max_steps, long *steps_taken);
 double sac3_time(const sac3_ctx *c);
 /* Conservation sums over the interior of the current state, accumulated in
  * FP64 on the device in a fixed order: sums[f] = sum_ijk w[f][k][j][i] for the

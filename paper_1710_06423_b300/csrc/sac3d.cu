@@ -450,7 +450,7 @@ static int fused_f32(sac3_ctx* c, double dt, const double cm[3], const double dd
 }
 
 template <typename T>
-static int step3(sac3_ctx* c, double dt_in, double* dt_taken)
+static int step3(sac3_ctx* c, double dt_in, double* dt_taken, double t_end = std::numeric_limits<double>::infinity())
 {
     const Grid3& g = c->g;
     const long long n = (long long)g.nx * g.ny * g.nz;
@@ -472,7 +472,14 @@ static int step3(sac3_ctx* c, double dt_in, double* dt_taken)
     double dt = dt_in > 0.0 ? dt_in : c->p.courant * fmin(fmin(dd[0] / cm[0], dd[1] / cm[1]), dd[2] / cm[2]);
     if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(cm[0]) || !std::isfinite(cm[1]) || !std::isfinite(cm[2]))
         return fail3(c, SAC_ERR_NONFINITE, "non-finite state or step at t = %g", c->t);
-    if (c->fp32) return fused_f32(c, dt, cm, dd, dt_taken);
+    // the last step of a run to t_end is clipped so that t lands exactly on t_end
+    const bool last = c->t + dt >= t_end;
+    if (last) dt = t_end - c->t;
+    if (c->fp32) {
+        const int rc = fused_f32(c, dt, cm, dd, dt_taken);
+        if (rc == SAC_OK && last) c->t = t_end;
+        return rc;
+    }
     Coef3 cf;
     for (int f = 0; f < NF3; ++f) cf.c2[f] = c->p.c2[f];
     cf.c_shk = c->p.c_shk;
@@ -504,7 +511,7 @@ static int step3(sac3_ctx* c, double dt_in, double* dt_taken)
         CK3(cudaGetLastError());
     }
     CK3(cudaStreamSynchronize(c->stream));
-    c->t += dt;
+    c->t = last ? t_end : c->t + dt;
     if (dt_taken) *dt_taken = dt;
     return SAC_OK;
 }
@@ -635,6 +642,26 @@ int sac3_steps(sac3_ctx* c, long n)
         const int rc = sac3_step(c, 0.0, nullptr);
         if (rc != SAC_OK) return rc;
     }
+    return SAC_OK;
+}
+
+int sac3_run_to(sac3_ctx* c, double t_end, long max_steps, long* steps_taken)
+{
+    if (steps_taken) *steps_taken = 0;
+    if (!c) return SAC_ERR_ARG;
+    if (!c->have_state) return fail3(c, SAC_ERR_STATE, "no state set");
+    if (!std::isfinite(t_end)) return fail3(c, SAC_ERR_ARG, "t_end must be finite");
+    CK3(cudaSetDevice(c->p.device));
+    long n = 0;
+    while (c->t < t_end && (max_steps < 0 || n < max_steps)) {
+        const int rc = c->fp32 ? step3<float>(c, 0.0, nullptr, t_end) : step3<double>(c, 0.0, nullptr, t_end);
+        if (rc != SAC_OK) {
+            if (steps_taken) *steps_taken = n;
+            return rc;
+        }
+        ++n;
+    }
+    if (steps_taken) *steps_taken = n;
     return SAC_OK;
 }
 

@@ -36,7 +36,7 @@ EXPORTS = (
     "sac_cnn_apply", "sac_cnn_perturb", "sac_block_average",
     "sac_step_noalloc",
     "sac3_default_params", "sac3_init", "sac3_free", "sac3_last_error", "sac3_set_state", "sac3_get_state",
-    "sac3_step", "sac3_steps", "sac3_time", "sac3_sums", "sac3_divb", "sac3_debug_drop_copies",
+    "sac3_step", "sac3_steps", "sac3_run_to", "sac3_time", "sac3_sums", "sac3_divb", "sac3_debug_drop_copies",
 )
 
 
@@ -151,6 +151,7 @@ def load() -> ctypes.CDLL:
         "sac3_get_state": (i, [vp, dp, dp]),
         "sac3_step": (i, [vp, d, dp]),
         "sac3_steps": (i, [vp, L]),
+        "sac3_run_to": (i, [vp, d, L, ctypes.POINTER(L)]),
         "sac3_time": (d, [vp]),
         "sac3_sums": (i, [vp, dp]),
         "sac3_divb": (i, [vp, dp, dp]),
@@ -590,6 +591,12 @@ class Solver3:
 
     def steps(self, n: int):
         self._check(load().sac3_steps(self._ctx, n), "sac3_steps")
+
+    def run_to(self, t_end: float, max_steps: int = -1) -> int:
+        """CFL steps until t_end (the last one clipped onto it); returns the step count."""
+        n = ctypes.c_long(0)
+        self._check(load().sac3_run_to(self._ctx, float(t_end), int(max_steps), ctypes.byref(n)), "sac3_run_to")
+        return n.value
 
     def time(self) -> float:
         return load().sac3_time(self._ctx)

@@ -129,3 +129,42 @@ def test_one_cell_thick_boxes_match_oracle(oracle_mod, inputs_mod, precision, nx
         assert t == pytest.approx(t_ref, rel=1e-5)
         err = l1rel(got[live].reshape(len(live), -1), ref[live].reshape(len(live), -1))
         assert np.all(err <= TOL_FP32_L1), err
+
+
+def _oracle_run_to(oracle, pr, w, t_end):
+    """CFL steps of the oracle until t_end, the last one clipped onto it."""
+    t, n = 0.0, 0
+    while t < t_end:
+        cm = oracle.cmax3(pr, w)
+        dt = oracle.cfl_dt3(pr, *cm)
+        last = t + dt >= t_end
+        if last:
+            dt = t_end - t
+        w = oracle.rk4_step3(pr, w, dt, cm)
+        t = t_end if last else t + dt
+        n += 1
+    return w, n
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_run_to_lands_on_t_end(oracle_mod, inputs_mod, precision):
+    from paper_1710_06423_b300.sac import FP32, FP64, Solver3
+    prec = FP64 if precision == "fp64" else FP32
+    nx, ny, nz = 18, 14, 10
+    t_end = 0.0312
+    w = inputs_mod.ot_3d(nx, ny, nz, compress=0.3)
+    pr = oracle_mod.Problem3(nx=nx, ny=ny, nz=nz)
+    ref, n_ref = _oracle_run_to(oracle_mod, pr, w, t_end)
+    with Solver3(nx=nx, ny=ny, nz=nz, precision=prec) as s:
+        s.set_state(w, 0.0)
+        n = s.run_to(t_end)
+        got, t = s.get_state()
+        assert s.run_to(t_end) == 0            # already there: no further step
+    assert t == t_end and n >= 2
+    if prec == FP64:
+        assert n == n_ref
+        assert np.all(_rel(got, ref) <= TOL_FP64), _rel(got, ref)
+    else:
+        assert abs(n - n_ref) <= 1
+        err = l1rel(got.reshape(8, -1), ref.reshape(8, -1))
+        assert np.all(err <= TOL_FP32_L1), err
