@@ -35,11 +35,29 @@ PAPER_8000_HD = 8000 * 8000 * 100 / 163.60   # Table 1: 8000^2, 100 iterations w
 #   s3: read S2, U0, D / write S3, D;         s4: read S3, U0, D / write U0
 # halo re-reads of the stencil input are served by L2 and are not algorithmic bytes
 STAGE_VALUES_FP32 = (12, 24, 30, 24)
+# algorithmic bytes per cell-stage of the hot path's byte model (classical RK4,
+# three registers plus a ping-pong pair, 24 FP32 values per cell-stage on
+# average, no background): the figure the roofline fraction divides by
+MODEL_BYTES_PER_CELL_STAGE = 96
 # DRAM bytes per cell of each stage_fp32 launch (stages 1..4) measured by ncu as
-# dram__bytes_read.sum + dram__bytes_write.sum on the 4000^2 workload (three times L2 per
-# RK register; profiles/stage_fp32_dram_ot4000.md).  Traffic scales with the cells
-# processed; the figures hold for the stage kernel as of that capture.
+# dram__bytes_read.sum + dram__bytes_write.sum on the 4000^2 workload (three times L2
+# per RK register), with the SHA-256 of the FP32 stage sources at the time of that
+# capture: when the sources differ, the figures no longer describe the kernel and
+# `roofline.traffic` is reported as null.
 STAGE_TRAFFIC_B_PER_CELL_FP32 = (45.6, 93.8, 120.2, 97.6)
+STAGE_TRAFFIC_SOURCES_SHA = None
+STAGE_SOURCES = ("stage_fp32.cuh", "kernels_fp32.cu", "speed.cuh", "sac_internal.cuh")
+
+
+def stage_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1710_06423_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 # kernels one graph-replayed RK4 step launches on a grid with a periodic or
 # outflow side: the step-control kernel, then per stage the stage kernel and
 # the ghost-frame kernel (the batch step: its begin kernel, then per stage the
@@ -210,13 +228,18 @@ def run_reference(args, ws, rank):
     el = time.perf_counter() - t0
     value = side * side * n / el
     sample = f"orszag-tang {side}x{side} window of the workload, {n} RK4 steps, FP64 oracle"
+    config = workload_config(args, ws)
+    config["sample"] = (f"each step is one RK4 step of a {side}x{side} window of this workload (the same "
+                        f"initial state and noise); value = window cells x steps / seconds")
     line = {
         "impl": "reference", "metric": "cell-updates/s per RK step", "value": value,
         "unit": "cell-updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * el / max(n, 1) * (args.size * args.size) / (side * side),
+        "ms_per_step": 1e3 * el / max(n, 1),
+        "ms_per_step_basis": f"measured: one RK4 step of the {side}x{side} window",
+        "full_grid_ms_per_step_extrapolated": 1e3 * el / max(n, 1) * (args.size * args.size) / (side * side),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_8000_HD,
         "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, ws),
+        "config": config,
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -248,7 +271,7 @@ def run_batched(args, ws, local, pg, torch, per_size=True):
     """64 independent Orszag-Tang-family runs (seeded sizes from {256, 512, 1000, 2044}^2,
     B0 x U[0.5, 1.5], gamma in {1.4, 5/3}, seeded phases), one launch per RK stage."""
     from paper_1710_06423_b300 import inputs
-    from paper_1710_06423_b300.sac import Batch
+    from paper_1710_06423_b300.sac import TILE_NAMES, Batch
     sizes = inputs.batch_sizes(2024, 64)
     runs = []
     for k, n in enumerate(sizes):
@@ -259,6 +282,7 @@ def run_batched(args, ws, local, pg, torch, per_size=True):
         b0, gamma, phases = inputs.ot_family_params(2024, k)
         b.set_state(k, inputs.orszag_tang(n, b0=b0, gamma=gamma, phases=phases), None, 0.0)
     cfg, tune_ms = b.tune(trials=3)
+    tile = b.config()[3]
     b.steps(args.warmup)
     b.sync()
     if pg:
@@ -284,6 +308,7 @@ def run_batched(args, ws, local, pg, torch, per_size=True):
             b0, gamma, phases = inputs.ot_family_params(2024, k)
             bs.set_state(j, inputs.orszag_tang(n, b0=b0, gamma=gamma, phases=phases), None, 0.0)
         cfg_n, _ = bs.tune(trials=2)
+        tile_n = bs.config()[3]
         bs.steps(args.warmup)
         bs.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -295,12 +320,13 @@ def run_batched(args, ws, local, pg, torch, per_size=True):
         ms_n = reduce_max(e0.elapsed_time(e1), pg, "cuda")
         bs.close()
         per_size_res[str(n)] = {"runs": len(ks), "value": ws * len(ks) * n * n * 100 / (ms_n * 1e-3),
-                            "tuned_config": {"persistent": cfg_n[0], "ctas_per_sm": cfg_n[1], "order": cfg_n[2]}}
+                            "tuned_config": {"persistent": cfg_n[0], "ctas_per_sm": cfg_n[1], "order": cfg_n[2],
+                                             "tile": TILE_NAMES[tile_n]}}
     peak, peak_kind = measured_peaks()
     gbs = value * 4 * 90 / 1e9
     return {"value": value, "unit": "cell-updates/s", "ms_per_step": ms / args.batch_steps,
             "steps": args.batch_steps, "runs": len(sizes), "sizes": counts, "cells": cells,
-            "tuned_config": {"persistent": cfg[0], "ctas_per_sm": cfg[1], "order": cfg[2]},
+            "tuned_config": {"persistent": cfg[0], "ctas_per_sm": cfg[1], "order": cfg[2], "tile": TILE_NAMES[tile]},
             "gb_per_s": gbs, "roofline_frac": gbs / peak, "peak_kind": f"of {peak_kind}",
             "per_size": per_size_res, "gpu_launches": LAUNCHES_PER_STEP * args.batch_steps}
 
@@ -446,7 +472,7 @@ def run_3d(args, ws, local, pg, torch, n=256):
 def run_ours(args, ws, rank, local, pg):
     import torch
     from paper_1710_06423_b300 import inputs
-    from paper_1710_06423_b300.sac import FP32, FP64, Solver
+    from paper_1710_06423_b300.sac import FP32, FP64, TILE_NAMES, Solver
 
     torch.cuda.set_device(local)
     n = args.size
@@ -460,6 +486,7 @@ def run_ours(args, ws, rank, local, pg):
 
     s = Solver(**kw)
     s.set_state(pinned.numpy(), None, 0.0)
+    tile, tune_ms = s.tune(trials=3)      # tile-shape autotuner (state restored)
     with Clocks(local) as clk:
         ms = time_device_steps(s, args.steps, args.warmup, pg, torch)
     clocks = clk.summary()
@@ -468,16 +495,26 @@ def run_ours(args, ws, rank, local, pg):
     # per-kernel durations (CUDA events on the context's stream) for the roofline
     prof = s.profile_stages(max(3, min(10, args.steps)))
     stage_ms = [float(x) for x in prof[1:]]
-    stage_bytes = [v * 4 * cells for v in STAGE_VALUES_FP32]
     peak, peak_kind = measured_peaks()
-    achieved = sum(stage_bytes) / (sum(stage_ms) * 1e-3) / 1e9
-    # per average stage launch, like `achieved` (measured bytes per cell x cells of one launch)
-    traffic = sum(STAGE_TRAFFIC_B_PER_CELL_FP32) / 4 * cells
+    # per average stage launch: the byte model's 96 B per cell x the cells of one
+    # launch, over the mean stage-kernel duration
+    achieved = MODEL_BYTES_PER_CELL_STAGE * cells / (sum(stage_ms) / 4 * 1e-3) / 1e9
+    kernel_bpc = 4 * sum(STAGE_VALUES_FP32) / 4          # what this kernel's register scheme must move
+    sha = stage_sources_sha()
+    fresh = STAGE_TRAFFIC_SOURCES_SHA is not None and sha == STAGE_TRAFFIC_SOURCES_SHA
+    traffic = sum(STAGE_TRAFFIC_B_PER_CELL_FP32) / 4 * cells if fresh else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "traffic_unit": "DRAM bytes per stage launch (ncu, 4000^2 per-cell figures x cells)",
+                "traffic_unit": "DRAM bytes per average stage launch",
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the stage kernel on the "
+                                   "4000^2 workload, per-cell figures x the cells of one 8000^2 launch; stage "
+                                   f"sources sha {STAGE_TRAFFIC_SOURCES_SHA}") if fresh else
+                                  f"null: the stage sources (sha {sha}) changed since the last capture",
                 "kernel": "stage_fp32 (all four RK stages)",
-                "bytes_per_cell_stage": 4 * sum(STAGE_VALUES_FP32) / 4,
+                "bytes_per_cell_stage": MODEL_BYTES_PER_CELL_STAGE,
+                "bytes_basis": "classical RK4 byte model: 24 FP32 values per cell-stage on average, no background",
+                "kernel_bytes_per_cell_stage": kernel_bpc,
+                "frac_kernel_bytes": kernel_bpc * cells / (sum(stage_ms) / 4 * 1e-3) / 1e9 / peak,
                 "stage_ms": stage_ms, "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "of fallback"}
     del s
@@ -516,8 +553,16 @@ def run_ours(args, ws, rank, local, pg):
                 continue
             sm_ = Solver(nx=m, ny=m, precision=FP32, device=local)
             sm_.set_state(inputs.orszag_tang(m, noise=1e-3, seed=20171018), None, 0.0)
+            tile_m, _ = sm_.tune(trials=3)
             msm = time_device_steps(sm_, args.steps, args.warmup, pg, torch)
-            extra[f"ot{m}"] = {"value": ws * m * m * args.steps / (msm * 1e-3), "ms_per_step": msm / args.steps}
+            prof_m = sm_.profile_stages(5)
+            cells_m = m * m
+            ach_m = MODEL_BYTES_PER_CELL_STAGE * cells_m / (sum(prof_m[1:]) / 4 * 1e-3) / 1e9
+            extra[f"ot{m}"] = {"value": ws * m * m * args.steps / (msm * 1e-3), "ms_per_step": msm / args.steps,
+                               "tile": TILE_NAMES[tile_m],
+                               "roofline_frac_step": ws * m * m * args.steps / (msm * 1e-3) * 4
+                               * MODEL_BYTES_PER_CELL_STAGE / 1e9 / ws / measured_peaks()[0],
+                               "roofline_frac_kernels": ach_m / measured_peaks()[0]}
             del sm_
         s4 = Solver(**kw, hd_single_face=1)
         s4.set_state(pinned.numpy(), None, 0.0)
@@ -551,7 +596,7 @@ def run_ours(args, ws, rank, local, pg):
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_8000_HD,
         "dtype": "f32", "data": "synthetic",
-        "config": workload_config(args, ws),
+        "config": {**workload_config(args, ws), "tile": TILE_NAMES[tile], "tile_tuner_ms_per_step": tune_ms},
         "cell_stage_rate": 4 * value,
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -204,6 +204,91 @@ int sac_profile_stages(sac_ctx *c, int nsteps, double ms[5]);
 /* Wait for the context's stream and report a pending device error. */
 int sac_sync(sac_ctx *c);
 
+/* Tile shapes of the FP32 stage kernels (not in the paper, which gives no
+ * kernel design): a CTA stages a tile plus its 3-cell halo of the stage input
+ * in shared memory (section 2's stencil reaches 3 cells) and updates the tile.
+ * SAC_TILE_32x32: 32 x 32 cells, 256 threads, 2 CTAs per SM (the default);
+ * SAC_TILE_64x16: 64 x 16 cells, 256 threads, 2 CTAs per SM;
+ * SAC_TILE_32x16: 32 x 16 cells, 128 threads, 3 CTAs per SM.
+ * Every shape gives bit-for-bit the same results (each cell's arithmetic does
+ * not depend on where the tile boundaries fall); they differ in halo overhead
+ * per cell and in how evenly the tiles fill the GPU. */
+enum { SAC_TILE_32x32 = 0, SAC_TILE_64x16 = 1, SAC_TILE_32x16 = 2 };
+
+/* Use tile shape `tile` (SAC_TILE_*) for the later steps of an FP32 context
+ * (the gravity and single-face variants always run 32 x 32).  Waits for the
+ * context's stream.  Errors: SAC_ERR_ARG (unknown shape, FP64 context). */
+int sac_set_tile(sac_ctx *c, int tile);
+
+/* The context's current tile shape.  Errors: SAC_ERR_ARG. */
+int sac_get_tile(const sac_ctx *c, int *tile);
+
+/* Autotuner of the tile shape: for every shape, one warm-up CFL step and
+ * `trials` timed CFL steps (CUDA events on the context's stream) from the
+ * current state, which is restored afterwards together with time, step count
+ * and signal speeds; the fastest shape is kept, reported in *tile (may be
+ * NULL) with its mean step time in *ms (may be NULL), and remembered for
+ * contexts of the same grid size, hyper-diffusion and background flags that
+ * this process creates later (they start with it).  Allocates one state-sized
+ * snapshot for the duration of the call.  Synchronous.
+ * Errors: SAC_ERR_ARG (FP64 context, trials < 1), SAC_ERR_STATE (no state),
+ * SAC_ERR_OOM, SAC_ERR_CUDA, or a device error pending before the call. */
+int sac_tune(sac_ctx *c, int trials, int *tile, double *ms);
+
+/* ---------------------------------------------------------------------------
+ * Block decomposition (section 3 of the paper: the grid is split into equal
+ * sub-domains, and before every RK stage each sub-domain receives from its
+ * neighbours the boundary cells its stencil reaches; section 2's maximum wave
+ * speed is a maximum over the whole domain).  A sub-domain is an ordinary
+ * context of the block's size whose split sides are SAC_BC_FIXED (their ghost
+ * cells are left to the caller); the calls below step it stage by stage, move
+ * its 3-cell halo strips through caller-owned device buffers, and read or set
+ * the running signal-speed maxima so that the caller can reduce them over all
+ * sub-domains.  One RK step of a decomposed grid is, on every sub-domain:
+ *   for stage 1..4: sac_stage(c, stage), then for each split direction (x
+ *   first, then y): sac_halo_pack of the two sides, exchange with the
+ *   neighbours, sac_halo_unpack of the two sides;
+ *   after stage 4: sac_get_cmax_bits, a maximum over all sub-domains,
+ *   sac_set_cmax_bits (also once after sac_set_state, with a halo exchange).
+ * The x strips span the ghost-extended height and the y strips the
+ * ghost-extended width, so exchanging x before y fills the corner ghosts.
+ * These calls only enqueue work on the context's stream (ASYNC).
+ * ------------------------------------------------------------------------- */
+
+/* Cell size of the context's later steps (dx, dy > 0; default
+ * (x1 - x0) / nx, (y1 - y0) / ny): a block of a decomposed grid takes the
+ * grid's cell size bit for bit, which (x1 - x0) / nx of the block's own extent
+ * cannot always give in FP64.  Also used by sac_divb.  Waits for the stream.
+ * Errors: SAC_ERR_ARG. */
+int sac_set_cell_size(sac_ctx *c, double dx, double dy);
+
+/* Enqueue RK stage `stage` (1..4) of one step; stage 1 first starts the step
+ * (CFL dt from the current signal-speed maxima, time advance), exactly as
+ * sac_step does.  Stages must come in order.  ASYNC.
+ * Errors: SAC_ERR_ARG, SAC_ERR_STATE (no state, or out of order), SAC_ERR_CUDA. */
+int sac_stage(sac_ctx *c, int stage);
+
+/* Number of elements (of the context's precision) of the packed strip of side
+ * `side` (0 left, 1 right, 2 bottom, 3 top): 6 fields x 3 columns x (ny + 6)
+ * rows for 0/1, 6 x (nx + 6) columns x 3 rows for 2/3, layout [6][rows][cols].
+ * Errors: SAC_ERR_ARG (bad side, fewer than 3 cells across the strip). */
+int sac_halo_size(sac_ctx *c, int side, long long *n);
+
+/* Pack the 3 interior cells next to `side` of the latest stage output (the
+ * step-start state after sac_set_state or a full step) into the DEVICE buffer
+ * strip_dev; unpack a received strip into the 3 ghost cells beyond `side` of
+ * that output.  ASYNC.  Errors: SAC_ERR_ARG, SAC_ERR_STATE, SAC_ERR_CUDA. */
+int sac_halo_pack(sac_ctx *c, int side, void *strip_dev);
+int sac_halo_unpack(sac_ctx *c, int side, const void *strip_dev);
+
+/* Copy the two running signal-speed maxima (x, y) to / from a DEVICE buffer
+ * of two 64-bit integers.  The keys are non-negative as signed 64-bit values,
+ * order like the speeds, and a NaN speed gives the largest key, so the signed
+ * maximum of the keys over sub-domains is the key of the global maximum (and
+ * a NaN anywhere stays a NaN).  ASYNC.  Errors: SAC_ERR_ARG, SAC_ERR_STATE. */
+int sac_get_cmax_bits(sac_ctx *c, void *bits_dev);
+int sac_set_cmax_bits(sac_ctx *c, const void *bits_dev);
+
 /* Test hook of the bounded device waits (FP32 contexts).  Each FP32 stage
  * kernel waits on an mbarrier for its staging copies and gives up after about
  * one second, recording SAC_ERR_TIMEOUT in the run's device status instead of
@@ -217,8 +302,8 @@ int sac_debug_drop_copies(sac_ctx *c, int on);
 /* ---------------------------------------------------------------------------
  * Batched runs: many independent runs of uneven grid size advanced together.
  * Each RK stage of all runs is ONE kernel launch over a shared queue of
- * 32x32 tiles (persistent CTAs pulling tiles from an atomic counter, or one
- * CTA per tile), each run keeps its own CFL step, time and error status, and
+ * tiles (persistent CTAs pulling tiles from an atomic counter, or one CTA per
+ * tile; 32x32 tiles unless tuned), each run keeps its own CFL step, time and error status, and
  * each RK step of the whole batch is replayed from a CUDA graph.  Every run
  * must be SAC_FP32, on the same device and stream, with the same
  * hyperdiffusion and has_background flags.  The per-run arithmetic is that of
@@ -247,22 +332,34 @@ int sac_batch_sync(sac_batch *b);
 /* Time and steps taken of one run.  Synchronous. */
 int sac_batch_time(sac_batch *b, int run, double *t, long *steps);
 
-/* Autotuner: times twelve launch configurations (persistent mode 0 = one CTA
- * per tile, 1 = persistent CTAs taking tiles from an atomic queue head, 2 =
- * persistent CTAs walking the queue with a fixed stride; 1 or 2 resident CTAs
- * per SM; tile order 0 = runs as given, 1 = largest run first, 2 = largest
- * first with tiles interleaved across runs): modes 0 and 2 at 2 CTAs per SM and
- * mode 1 at 1 and 2, each with all three orders, on `trials`
+/* Autotuner: times 36 launch configurations, the twelve launch modes (persistent
+ * mode 0 = one CTA per tile, 1 = persistent CTAs taking tiles from an atomic
+ * queue head, 2 = persistent CTAs walking the queue with a fixed stride;
+ * ctas_per_sm 1 = one resident CTA per SM, 2 = as many as the tile shape
+ * allows (two, or three for SAC_TILE_32x16); tile order 0 = runs as given,
+ * 1 = largest run first, 2 = largest first with tiles interleaved across
+ * runs: modes 0 and 2 at ctas_per_sm 2 and mode 1 at 1 and 2, each with all
+ * three orders) for each of the three tile shapes (SAC_TILE_*), on `trials`
  * RK steps of the current states, keeps the fastest and restores the states
  * it advanced (every run must have a state).  config[3] (may be NULL)
  * receives (persistent, ctas_per_sm, order); ms (may be NULL) the mean time
- * of one batch RK step with that configuration.  Synchronous. */
+ * of one batch RK step with that configuration; sac_batch_get_config also
+ * reports the tile shape.  Synchronous. */
 int sac_batch_tune(sac_batch *b, int trials, int config[3], double *ms);
 
 /* Set the launch configuration directly (values as sac_batch_tune reports:
- * persistent 0..2, ctas_per_sm 1..2, order 0..2).  Every configuration gives
- * bitwise the same results.  Errors: SAC_ERR_ARG (out of range). */
+ * persistent 0..2, ctas_per_sm 1..2, order 0..2); the tile shape is kept.
+ * Every configuration gives bitwise the same results.
+ * Errors: SAC_ERR_ARG (out of range). */
 int sac_batch_set_config(sac_batch *b, int persistent, int ctas_per_sm, int order);
+
+/* Set the tile shape (SAC_TILE_*) of every run of the batch; the launch mode
+ * is kept.  Bitwise the same results.  Errors: SAC_ERR_ARG. */
+int sac_batch_set_tile(sac_batch *b, int tile);
+
+/* The current configuration: config[4] = (persistent, ctas_per_sm, order,
+ * tile shape).  Errors: SAC_ERR_ARG. */
+int sac_batch_get_config(const sac_batch *b, int config[4]);
 
 /* ---------------------------------------------------------------------------
  * Learned coarse-grid correction (not in the paper; a form built on the
@@ -323,12 +420,14 @@ int sac_block_average(const float *fine_dev, int nfields, int nxf, int nyf, int 
 
 /* ---------------------------------------------------------------------------
  * Allocation-free step.  The paper has no counterpart: this entry point serves
- * callers that cannot allocate device memory (code that runs while a CUDA graph
- * is being captured, allocator-restricted plugins, or real-time loops that
- * forbid allocation): it runs one SAC_FP32 RK4 step with the same kernels as
- * sac_step but keeps its working memory (ghost-padded RK registers and step
- * scalars) in a fixed array of 7,244,032 bytes compiled into the library.
- * Every GPU that loads the library holds that array until the process exits.
+ * callers that cannot allocate device memory, for example a plug-in whose host
+ * application owns all device memory through its own allocator, or a real-time
+ * loop in which an allocation (which may synchronise the device and has no
+ * latency bound) is not allowed.  It runs one SAC_FP32 RK4 step with the same
+ * kernels as sac_step but keeps its working memory (ghost-padded RK registers
+ * and step scalars) in a fixed array of 7,244,032 bytes compiled into the
+ * library.  Every GPU that loads the library holds that array until the
+ * process exits.
  *
  *   p         run parameters; precision must be SAC_FP32 and has_background 0
  *             (device and stream are used as given)
@@ -337,18 +436,24 @@ int sac_block_average(const float *fine_dev, int nfields, int nxf, int nyf, int 
  *   dt        > 0: step size; <= 0: the CFL step of w_in
  *   dt_taken  host pointer or NULL.  Non-NULL: the call waits for the stream and
  *             stores the step taken.  NULL: the call only enqueues work.
+ * The library cannot check the sizes of w_in and w_out: both must hold
+ * 6 * nx * ny floats on p->device.
  * The grid must fit the fixed memory: its padded plane (as sac_init pads it)
  * holds at most 75,456 float2 elements (any grid up to 256 x 256 qualifies);
  * larger grids are rejected with SAC_ERR_TOO_LARGE before any GPU work.
  * Fixed boundaries hold the nearest interior cell of w_in.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and sets
- * kernel attributes, so make it before any stream capture.  It calls no
- * cudaMalloc/cudaFree or any allocating routine.  All calls share the one
- * array: calls that overlap on the GPU (other streams, other host threads)
- * race and must be serialised by the caller.  The state is the only input:
- * the array's previous contents are overwritten (scalars reset) each call.
- * Returns SAC_OK, SAC_ERR_ARG, SAC_ERR_TOO_LARGE, SAC_ERR_CUDA, or
- * SAC_ERR_NONFINITE (only detectable when dt_taken is non-NULL).
+ * device does a one-time set-up: it looks up the array's device address
+ * (cudaGetSymbolAddress) and sets kernel attributes, under a lock, so first
+ * calls from several host threads are safe; make that first call before any
+ * stream capture.  No call allocates: no cudaMalloc/cudaFree and no allocating
+ * library routine.  All calls share the one array: calls that overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  The state is the only input: the array's previous contents are
+ * overwritten (scalars reset) each call.
+ * Returns SAC_OK, SAC_ERR_ARG, SAC_ERR_TOO_LARGE, SAC_ERR_CUDA, and, only when
+ * dt_taken is non-NULL, SAC_ERR_NONFINITE (non-finite state or step) or
+ * SAC_ERR_TIMEOUT (a stage kernel's bounded staging wait gave up).  After any
+ * error the contents of w_out are undefined.
  * ------------------------------------------------------------------------- */
 #define SAC_ERR_TOO_LARGE (-7)
 int sac_step_noalloc(const sac_params *p, const float *w_in, float *w_out, double dt, double *dt_taken);

@@ -21,7 +21,11 @@ shifts, ``np.einsum``/``np.tensordot`` for the channel sums):
   * the correction u <- u + scale_out * f(features(u));
   * the loss 0.5 * mean over (channel, pixel) of (f(x) - target)^2 and its
     gradient by the chain rule (adjoint of each conv: correlation with the
-    flipped kernel for the input, outer products summed over pixels for W).
+    flipped kernel for the input, outer products summed over pixels for W);
+  * the same network with BF16 storage (``forward_bf16``,
+    ``loss_and_grads_bf16``): the form fixes BF16 weights and activations
+    with wider accumulation, so these round every stored value to BF16 and
+    keep every sum in FP64.
 """
 from __future__ import annotations
 
@@ -84,6 +88,57 @@ def loss_and_grads(params, x, target):
         grads[k] = (dw, db)
         if k > 0:
             dy = dx * (acts[k] > 0.0)           # ReLU of the layer below
+    return loss, grads
+
+
+def round_bf16(x):
+    """Round FP64 values to the nearest BF16 value (8 significant bits, ties to
+    even), returned as FP64.  x = m 2^e with m in [0.5, 1): the BF16 neighbours
+    are multiples of 2^(e-8), and dividing by that power of two is exact, so
+    np.rint (half to even) on the quotient is the rounding itself.  The
+    network stores weights and activations in BF16 (finite, normal range)."""
+    x = np.asarray(x, dtype=np.float64)
+    _, e = np.frexp(x)
+    q = np.ldexp(1.0, e - 8)
+    return np.rint(x / q) * q
+
+
+def forward_bf16(params, x):
+    """The network with BF16 storage: weights, input features and the three
+    hidden activations rounded to BF16; sums, biases and the output in FP64."""
+    pb = [(round_bf16(w), b) for w, b in params]
+    acts = [round_bf16(x)]
+    h = acts[0]
+    for k, (w, b) in enumerate(pb):
+        z = conv3x3(h, w, b)
+        h = round_bf16(np.maximum(z, 0.0)) if k < len(pb) - 1 else z
+        acts.append(h)
+    return h, acts
+
+
+def loss_and_grads_bf16(params, x, target, return_stored=False):
+    """loss_and_grads with BF16 storage of what the network stores: the output
+    gradient r / n and every hidden input gradient are rounded to BF16 after
+    the ReLU mask; the weight and bias gradients are exact FP64 sums of those
+    stored values.  return_stored: also return (acts, dys), the stored layer
+    inputs and the stored output gradient of every layer."""
+    pb = [(round_bf16(w), b) for w, b in params]
+    y, acts = forward_bf16(params, x)
+    r = y - target
+    n = r.size
+    loss = 0.5 * float(np.sum(r * r)) / n
+    dy = round_bf16(r / n)
+    grads = [None] * len(pb)
+    dys = [None] * len(pb)
+    for k in range(len(pb) - 1, -1, -1):
+        w, b = pb[k]
+        dys[k] = dy
+        dx, dw, db = conv3x3_backward(acts[k], w, dy)
+        grads[k] = (dw, db)
+        if k > 0:
+            dy = round_bf16(dx * (acts[k] > 0.0))
+    if return_stored:
+        return loss, grads, (acts, dys)
     return loss, grads
 
 

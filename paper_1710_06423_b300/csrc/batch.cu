@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -48,16 +49,19 @@ __device__ __forceinline__ void load_args(const BatchArgs& b, int run, StageArgs
     for (int k = threadIdx.x; k < (int)(sizeof(StageArgs<float>) / sizeof(int)); k += blockDim.x) d[k] = src[k];
 }
 
-template <int STAGE, bool BG, bool HD>
-__global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs b)
+template <class G, int STAGE, bool BG, bool HD>
+__global__ void __launch_bounds__(G::NT, G::MINB) stage_fp32_batch(const BatchArgs b)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ unsigned long long red[2][f32k::NW];
-    __shared__ __align__(16) StageArgs<float> sa[2];   // current / next tile's run
+    __shared__ unsigned long long red[2][G::NW];
+    // current / next tile's run (raw storage: StageArgs has member initialisers,
+    // and the arguments are always copied in by load_args)
+    __shared__ __align__(16) unsigned char sa_raw[2 * sizeof(StageArgs<float>)];
+    StageArgs<float>* sa = reinterpret_cast<StageArgs<float>*>(sa_raw);
     __shared__ int tile_s[2];
     __shared__ int run_s[2], skip_s[2], coef_s;   // run whose arguments sa[k] hold, its skip flag; run of S.ax/S.ay
     __shared__ __align__(8) unsigned long long bar;   // staging completion (persistent mode)
-    f32k::Smem& S = *reinterpret_cast<f32k::Smem*>(smem_raw);
+    f32k::Smem<G>& S = *reinterpret_cast<f32k::Smem<G>*>(smem_raw);
     if (!b.persistent) {
         // one tile per CTA: stage inside the tile
         const int t = blockIdx.x;
@@ -69,7 +73,7 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
             f32k::store_hd_coeffs(sa[0], S, threadIdx.x);   // visible after the tile's staging barrier
             const f32k::StepConsts K = f32k::load_step_consts(sa[0].sc);
             unsigned long long m[2] = {0ull, 0ull};
-            f32k::tile_body<STAGE, BG, HD, false, false>(sa[0], d.y * f32k::TX, d.z * f32k::TY, S, K, m);
+            f32k::tile_body<G, STAGE, BG, HD, false, false>(sa[0], d.y * G::TX, d.z * G::TY, S, K, m);
             if (STAGE == 4) f32k::block_speed_max(m, red, sa[0].sc);
         }
         return;
@@ -101,9 +105,10 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
     if (threadIdx.x == 0) { run_s[0] = d.x; skip_s[0] = !staged; run_s[1] = -1; coef_s = -1; }
     unsigned long long m[2] = {0ull, 0ull};
     if (staged) {
-        f32k::NextTile first = f32k::next_tile(sa[0], true, d.y * f32k::TX, d.z * f32k::TY);
+        f32k::NextTile first = f32k::next_tile(sa[0], true, d.y * G::TX, d.z * G::TY);
         first.tm = tmap(d.x);
-        if (threadIdx.x == 0) f32k::mbar_expect_tx(&bar, first.tm ? f32k::kTileBytesTM : f32k::kTileBytes);
+        if (threadIdx.x == 0)
+            f32k::mbar_expect_tx(&bar, first.tm ? f32k::tile_bytes_tm<G>() : f32k::tile_bytes<G>());
 #pragma unroll
         for (int p = 0; p < 3; ++p) f32k::stage_plane_bulk(first, S, p, &bar);
     }
@@ -132,13 +137,13 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
         }
         const StageArgs<float>& A = sa[buf];
         const bool nstage = nxt < b.ntiles && !skip_n;
-        f32k::NextTile nt = f32k::next_tile(sa[buf ^ 1], nstage, dn.y * f32k::TX, dn.z * f32k::TY);
+        f32k::NextTile nt = f32k::next_tile(sa[buf ^ 1], nstage, dn.y * G::TX, dn.z * G::TY);
         nt.tm = nstage ? tmap(dn.x) : nullptr;
         if (staged) {
             if (coef) f32k::store_hd_coeffs(A, S, threadIdx.x);   // visible after the tile's staging barrier
             const f32k::StepConsts K = f32k::load_step_consts(A.sc);
-            f32k::tile_body<STAGE, BG, HD, true, false>(A, d.y * f32k::TX, d.z * f32k::TY, S, K, m, nt,
-                                                       &bar, &phase, &failed);
+            f32k::tile_body<G, STAGE, BG, HD, true, false>(A, d.y * G::TX, d.z * G::TY, S, K, m, nt,
+                                                          &bar, &phase, &failed);
             if (failed) return;
             // the next tile belongs to another run (or there is none): fold this run's
             // maximum now; a later tile of the same run folds again (atomicMax)
@@ -149,7 +154,7 @@ __global__ void __launch_bounds__(f32k::NT, 2) stage_fp32_batch(const BatchArgs 
         } else if (nstage) {
             // this tile's run is done or failed: nothing was staged for it, so
             // the next tile's region is copied now
-            if (threadIdx.x == 0) f32k::mbar_expect_tx(&bar, nt.tm ? f32k::kTileBytesTM : f32k::kTileBytes);
+            if (threadIdx.x == 0) f32k::mbar_expect_tx(&bar, nt.tm ? f32k::tile_bytes_tm<G>() : f32k::tile_bytes<G>());
 #pragma unroll
             for (int p = 0; p < 3; ++p) f32k::stage_plane_bulk(nt, S, p, &bar);
         }
@@ -172,34 +177,62 @@ __global__ void halo_fp32_batch(const StageArgs<float>* __restrict__ args, int s
         f32k::halo_cell(w, a.L, a.bc_x, a.bc_y, t);
 }
 
-template <int S, bool BG, bool HD>
+template <class G, int S, bool BG, bool HD>
 cudaError_t set_attr()
 {
-    return cudaFuncSetAttribute(stage_fp32_batch<S, BG, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(f32k::Smem));
+    return cudaFuncSetAttribute(stage_fp32_batch<G, S, BG, HD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(f32k::Smem<G>));
 }
 
-template <bool BG, bool HD>
+template <class G, bool BG, bool HD>
 cudaError_t attr_all()
 {
-    cudaError_t e = set_attr<1, BG, HD>();
-    if (e == cudaSuccess) e = set_attr<2, BG, HD>();
-    if (e == cudaSuccess) e = set_attr<3, BG, HD>();
-    if (e == cudaSuccess) e = set_attr<4, BG, HD>();
+    cudaError_t e = set_attr<G, 1, BG, HD>();
+    if (e == cudaSuccess) e = set_attr<G, 2, BG, HD>();
+    if (e == cudaSuccess) e = set_attr<G, 3, BG, HD>();
+    if (e == cudaSuccess) e = set_attr<G, 4, BG, HD>();
     return e;
 }
 
-template <bool BG, bool HD>
-cudaError_t launch(const BatchArgs& a, int stage, int grid, cudaStream_t s)
+template <class G>
+cudaError_t attr_geometry()
 {
-    const size_t sm = sizeof(f32k::Smem);
+    cudaError_t e = attr_all<G, false, false>();
+    if (e == cudaSuccess) e = attr_all<G, false, true>();
+    if (e == cudaSuccess) e = attr_all<G, true, false>();
+    if (e == cudaSuccess) e = attr_all<G, true, true>();
+    return e;
+}
+
+template <class G, bool BG, bool HD>
+cudaError_t launch_g(const BatchArgs& a, int stage, int grid, cudaStream_t s)
+{
+    const size_t sm = sizeof(f32k::Smem<G>);
     switch (stage) {
-        case 1: stage_fp32_batch<1, BG, HD><<<grid, f32k::NT, sm, s>>>(a); break;
-        case 2: stage_fp32_batch<2, BG, HD><<<grid, f32k::NT, sm, s>>>(a); break;
-        case 3: stage_fp32_batch<3, BG, HD><<<grid, f32k::NT, sm, s>>>(a); break;
-        default: stage_fp32_batch<4, BG, HD><<<grid, f32k::NT, sm, s>>>(a); break;
+        case 1: stage_fp32_batch<G, 1, BG, HD><<<grid, G::NT, sm, s>>>(a); break;
+        case 2: stage_fp32_batch<G, 2, BG, HD><<<grid, G::NT, sm, s>>>(a); break;
+        case 3: stage_fp32_batch<G, 3, BG, HD><<<grid, G::NT, sm, s>>>(a); break;
+        default: stage_fp32_batch<G, 4, BG, HD><<<grid, G::NT, sm, s>>>(a); break;
     }
     return cudaGetLastError();
+}
+
+template <bool BG, bool HD>
+cudaError_t launch(const BatchArgs& a, int tile, int stage, int grid, cudaStream_t s)
+{
+    switch (tile) {
+        case TILE_64x16: return launch_g<f32k::G64x16, BG, HD>(a, stage, grid, s);
+        case TILE_32x16: return launch_g<f32k::G32x16, BG, HD>(a, stage, grid, s);
+        default: return launch_g<f32k::G32x32, BG, HD>(a, stage, grid, s);
+    }
+}
+
+// (cells wide, cells high, resident CTAs per SM of the launch bounds) of a tile shape
+void tile_dims(int tile, int& tx, int& ty, int& minb)
+{
+    if (tile == TILE_64x16) { tx = f32k::G64x16::TX; ty = f32k::G64x16::TY; minb = f32k::G64x16::MINB; }
+    else if (tile == TILE_32x16) { tx = f32k::G32x16::TX; ty = f32k::G32x16::TY; minb = f32k::G32x16::MINB; }
+    else { tx = f32k::G32x32::TX; ty = f32k::G32x32::TY; minb = f32k::G32x32::MINB; }
 }
 
 }  // namespace
@@ -219,7 +252,8 @@ struct sac_batch {
     unsigned* d_counters = nullptr;
     CUtensorMap* d_tmaps = nullptr;   // [n][4], or null (row copies)
     int ntiles = 0;
-    int persistent = 1, ctas_per_sm = 2, order = 1;
+    int persistent = 1, ctas_per_sm = 2, order = 1, tile = TILE_32x32;
+    std::vector<StageArgs<float>> h_args;   // host copy of d_args (re-encoded when the tile shape changes)
     cudaGraphExec_t g1 = nullptr, gN = nullptr;
     char err[512] = {0};
 };
@@ -247,8 +281,10 @@ static int bfail(sac_batch* b, int code, const char* fmt, ...)
 //  0: runs in the given order, tiles row-major within a run;
 //  1: runs by decreasing cell count (big runs first balance the tail);
 //  2: runs by decreasing cell count, tiles interleaved round-robin across runs.
-static std::vector<int4> make_tiles(const sac_batch* b, int order)
+static std::vector<int4> make_tiles(const sac_batch* b, int order, int tile)
 {
+    int tw, th, minb;
+    tile_dims(tile, tw, th, minb);
     std::vector<int> idx(b->n);
     for (int i = 0; i < b->n; ++i) idx[i] = i;
     if (order >= 1)
@@ -257,7 +293,7 @@ static std::vector<int4> make_tiles(const sac_batch* b, int order)
         });
     std::vector<std::vector<int4>> per(b->n);
     for (int r : idx) {
-        const int tx = (b->runs[r]->p.nx + f32k::TX - 1) / f32k::TX, ty = (b->runs[r]->p.ny + f32k::TY - 1) / f32k::TY;
+        const int tx = (b->runs[r]->p.nx + tw - 1) / tw, ty = (b->runs[r]->p.ny + th - 1) / th;
         for (int y = 0; y < ty; ++y)
             for (int x = 0; x < tx; ++x) per[r].push_back(make_int4(r, x, y, 0));
     }
@@ -283,11 +319,16 @@ static cudaError_t enqueue_batch_step(sac_batch* b, cudaStream_t s)
     a.args = b->d_args; a.tiles = b->d_tiles; a.ntiles = b->ntiles; a.counters = b->d_counters;
     a.tmaps = b->d_tmaps;
     a.persistent = b->persistent;
-    const int grid = b->persistent ? std::min(b->ntiles, b->ctas_per_sm * b->nsm) : b->ntiles;
+    int tw, th, minb;
+    tile_dims(b->tile, tw, th, minb);
+    // ctas_per_sm 2: as many CTAs per SM as the tile shape's launch bounds allow
+    const int per_sm = b->ctas_per_sm == 1 ? 1 : minb;
+    const int grid = b->persistent ? std::min(b->ntiles, per_sm * b->nsm) : b->ntiles;
     const int hgrid = (int)std::min<long long>((b->max_halo + 255) / 256, 2 * b->nsm);
+    const int T = b->tile;
     for (int stage = 1; stage <= 4 && e == cudaSuccess; ++stage) {
-        if (b->bg) e = b->hd ? launch<true, true>(a, stage, grid, s) : launch<true, false>(a, stage, grid, s);
-        else e = b->hd ? launch<false, true>(a, stage, grid, s) : launch<false, false>(a, stage, grid, s);
+        if (b->bg) e = b->hd ? launch<true, true>(a, T, stage, grid, s) : launch<true, false>(a, T, stage, grid, s);
+        else e = b->hd ? launch<false, true>(a, T, stage, grid, s) : launch<false, false>(a, T, stage, grid, s);
         if (e == cudaSuccess && b->any_halo) {
             halo_fp32_batch<<<dim3(hgrid, b->n), 256, 0, s>>>(b->d_args, stage);
             e = cudaGetLastError();
@@ -316,13 +357,40 @@ static cudaError_t capture_batch(sac_batch* b, int nsteps, cudaGraphExec_t* out)
     return e;
 }
 
-static int apply_config(sac_batch* b, int persistent, int ctas, int order)
+// Upload the run arguments and tensor maps for tile shape `tile` (the tensor
+// maps' boxes follow the shape); without tensor maps the kernel copies rows.
+static int set_tile_tables(sac_batch* b, int tile)
 {
-    if (persistent < 0 || persistent > 2 || ctas < 1 || ctas > 2 || order < 0 || order > 2)
-        return bfail(b, SAC_ERR_ARG, "bad configuration (%d, %d, %d)", persistent, ctas, order);
-    std::vector<int4> t = make_tiles(b, order);
+    for (auto& a : b->h_args) a.tile = tile;
+    BK(cudaMemcpy(b->d_args, b->h_args.data(), b->h_args.size() * sizeof(StageArgs<float>), cudaMemcpyHostToDevice));
+    if (b->d_tmaps) {
+        std::vector<CUtensorMap> maps(b->h_args.size());
+        bool ok = true;
+        for (size_t k = 0; k < maps.size() && ok; ++k) ok = encode_stage_tensor_map(b->h_args[k], &maps[k]) == cudaSuccess;
+        if (!ok || cudaMemcpy(b->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(b->d_tmaps);
+            b->d_tmaps = nullptr;
+        }
+    }
+    return SAC_OK;
+}
+
+static int apply_config(sac_batch* b, int persistent, int ctas, int order, int tile)
+{
+    if (persistent < 0 || persistent > 2 || ctas < 1 || ctas > 2 || order < 0 || order > 2 || tile < 0 ||
+        tile >= NTILE_SHAPES)
+        return bfail(b, SAC_ERR_ARG, "bad configuration (%d, %d, %d, %d)", persistent, ctas, order, tile);
+    BK(cudaStreamSynchronize(b->stream));
+    if (tile != b->tile) {
+        int rc = set_tile_tables(b, tile);
+        if (rc != SAC_OK) return rc;
+        b->tile = tile;
+    }
+    std::vector<int4> t = make_tiles(b, order, tile);
     BK(cudaMemcpyAsync(b->d_tiles, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
     BK(cudaStreamSynchronize(b->stream));
+    b->ntiles = (int)t.size();
     b->persistent = persistent; b->ctas_per_sm = ctas; b->order = order;
     drop_graphs(b);
     return SAC_OK;
@@ -371,15 +439,14 @@ int sac_batch_init(const sac_params* runs, int n, sac_batch** out)
     int rc = SAC_OK;
     do {
         cudaError_t e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, runs[0].device);
-        if (e == cudaSuccess) e = attr_all<false, false>();
-        if (e == cudaSuccess) e = attr_all<false, true>();
-        if (e == cudaSuccess) e = attr_all<true, false>();
-        if (e == cudaSuccess) e = attr_all<true, true>();
+        if (e == cudaSuccess) e = attr_geometry<f32k::G32x32>();
+        if (e == cudaSuccess) e = attr_geometry<f32k::G64x16>();
+        if (e == cudaSuccess) e = attr_geometry<f32k::G32x16>();
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
         if (e != cudaSuccess) { rc = bfail(b, SAC_ERR_CUDA, "set-up: %s", cudaGetErrorString(e)); break; }
         std::vector<StageArgs<float>> args(4 * n);
         std::vector<RunCtl> ctl(n);
-        long long ntiles = 0;
+        long long ntiles = 0;   // the most tiles any shape needs (the table holds any shape's queue)
         for (int i = 0; i < n; ++i) {
             const sac_ctx* c = b->runs[i];
             for (int s = 1; s <= 4; ++s) sac_fp32_stage_args(c, s, &args[4 * i + s - 1]);
@@ -388,10 +455,16 @@ int sac_batch_init(const sac_params* runs, int n, sac_batch** out)
                 b->max_halo = std::max(b->max_halo, f32k::halo_count(c->L));
             }
             ctl[i].sc = c->sc;
-            ctl[i].dx = (c->p.x1 - c->p.x0) / c->p.nx;
-            ctl[i].dy = (c->p.y1 - c->p.y0) / c->p.ny;
+            ctl[i].dx = c->dx;
+            ctl[i].dy = c->dy;
             ctl[i].courant = c->p.courant;
-            ntiles += (long long)((c->p.nx + f32k::TX - 1) / f32k::TX) * ((c->p.ny + f32k::TY - 1) / f32k::TY);
+            long long most = 0;
+            for (int t = 0; t < NTILE_SHAPES; ++t) {
+                int tw, th, minb;
+                tile_dims(t, tw, th, minb);
+                most = std::max(most, (long long)((c->p.nx + tw - 1) / tw) * ((c->p.ny + th - 1) / th));
+            }
+            ntiles += most;
         }
         if (ntiles > (1LL << 30)) { rc = bfail(b, SAC_ERR_ARG, "too many tiles"); break; }
         b->ntiles = (int)ntiles;
@@ -406,21 +479,13 @@ int sac_batch_init(const sac_params* runs, int n, sac_batch** out)
         if (e == cudaSuccess) e = cudaMemcpy(b->d_ctl, ctl.data(), n * sizeof(RunCtl), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, 4 * sizeof(unsigned));
         if (e != cudaSuccess) { rc = bfail(b, SAC_ERR_CUDA, "tables: %s", cudaGetErrorString(e)); break; }
-        {   // tensor maps of every run's stage inputs (without them the kernel copies rows)
-            std::vector<CUtensorMap> maps(args.size());
-            bool ok = true;
-            for (size_t k = 0; k < args.size() && ok; ++k) ok = encode_stage_tensor_map(args[k], &maps[k]) == cudaSuccess;
-            if (ok && cudaMalloc(&b->d_tmaps, maps.size() * sizeof(CUtensorMap)) == cudaSuccess) {
-                if (cudaMemcpy(b->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) != cudaSuccess) {
-                    cudaFree(b->d_tmaps);
-                    b->d_tmaps = nullptr;
-                }
-            } else {
-                cudaGetLastError();
-                b->d_tmaps = nullptr;
-            }
+        b->h_args = args;
+        if (cudaMalloc(&b->d_tmaps, args.size() * sizeof(CUtensorMap)) != cudaSuccess) {
+            cudaGetLastError();
+            b->d_tmaps = nullptr;
         }
-        rc = apply_config(b, 1, 2, 1);
+        if ((rc = set_tile_tables(b, TILE_32x32)) != SAC_OK) break;
+        rc = apply_config(b, 1, 2, 1, TILE_32x32);
     } while (0);
     if (rc != SAC_OK) {
         sac_batch_free(b);
@@ -482,7 +547,20 @@ int sac_batch_sync(sac_batch* b)
 int sac_batch_set_config(sac_batch* b, int persistent, int ctas_per_sm, int order)
 {
     if (!b) return SAC_ERR_ARG;
-    return apply_config(b, persistent, ctas_per_sm, order);
+    return apply_config(b, persistent, ctas_per_sm, order, b->tile);
+}
+
+int sac_batch_set_tile(sac_batch* b, int tile)
+{
+    if (!b) return SAC_ERR_ARG;
+    return apply_config(b, b->persistent, b->ctas_per_sm, b->order, tile);
+}
+
+int sac_batch_get_config(const sac_batch* b, int config[4])
+{
+    if (!b || !config) return SAC_ERR_ARG;
+    config[0] = b->persistent; config[1] = b->ctas_per_sm; config[2] = b->order; config[3] = b->tile;
+    return SAC_OK;
 }
 
 int sac_batch_tune(sac_batch* b, int trials, int config[3], double* ms_out)
@@ -504,16 +582,20 @@ int sac_batch_tune(sac_batch* b, int trials, int config[3], double* ms_out)
             rc = bfail(b, SAC_ERR_CUDA, "tuner snapshot copy");
     }
     if (rc == SAC_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) rc = bfail(b, SAC_ERR_CUDA, "sync");
-    const int cand[][3] = {{1, 2, 0}, {1, 2, 1}, {1, 2, 2}, {1, 1, 0}, {1, 1, 1}, {1, 1, 2},
-                           {0, 2, 0}, {0, 2, 1}, {0, 2, 2}, {2, 2, 0}, {2, 2, 1}, {2, 2, 2}};
-    const int ncand = (int)(sizeof cand / sizeof cand[0]);
+    const int cfg[][3] = {{1, 2, 0}, {1, 2, 1}, {1, 2, 2}, {1, 1, 0}, {1, 1, 1}, {1, 1, 2},
+                          {0, 2, 0}, {0, 2, 1}, {0, 2, 2}, {2, 2, 0}, {2, 2, 1}, {2, 2, 2}};
+    const int ncfg = (int)(sizeof cfg / sizeof cfg[0]);
+    std::vector<std::array<int, 4>> cand;
+    for (int t = 0; t < NTILE_SHAPES; ++t)
+        for (int k = 0; k < ncfg; ++k) cand.push_back({cfg[k][0], cfg[k][1], cfg[k][2], t});
+    const int ncand = (int)cand.size();
     double best = 1e300;
     int bi = 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (rc == SAC_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         rc = bfail(b, SAC_ERR_CUDA, "events");
     for (int k = 0; k < ncand && rc == SAC_OK; ++k) {
-        if ((rc = apply_config(b, cand[k][0], cand[k][1], cand[k][2])) != SAC_OK) break;
+        if ((rc = apply_config(b, cand[k][0], cand[k][1], cand[k][2], cand[k][3])) != SAC_OK) break;
         if (enqueue_batch_step(b, b->stream) != cudaSuccess) { rc = bfail(b, SAC_ERR_CUDA, "trial"); break; }
         cudaEventRecord(e0, b->stream);
         for (int t = 0; t < trials; ++t)
@@ -538,7 +620,7 @@ int sac_batch_tune(sac_batch* b, int trials, int config[3], double* ms_out)
     cudaStreamSynchronize(b->stream);
     for (void* p : snap) cudaFree(p);
     if (rc != SAC_OK) return rc;
-    rc = apply_config(b, cand[bi][0], cand[bi][1], cand[bi][2]);
+    rc = apply_config(b, cand[bi][0], cand[bi][1], cand[bi][2], cand[bi][3]);
     if (rc != SAC_OK) return rc;
     if (config) { config[0] = cand[bi][0]; config[1] = cand[bi][1]; config[2] = cand[bi][2]; }
     if (ms_out) *ms_out = best;

@@ -820,7 +820,7 @@ int sac_cnn_apply(sac_ctx* ctx, sac_cnn* c)
     float* u0 = (float*)ctx->u0;
     export_paired_kernel<<<grid_n(P * NF, 4096), 256, 0, c->stream>>>(u0, ctx->L, c->state);
     CC(cudaGetLastError());
-    CC(forward_all(c, c->state, ctx->p.gamma, (ctx->p.x1 - ctx->p.x0) / ctx->p.nx, (ctx->p.y1 - ctx->p.y0) / ctx->p.ny));
+    CC(forward_all(c, c->state, ctx->p.gamma, ctx->dx, ctx->dy));
     const int nsum = 148;
     pred_sum_kernel<<<nsum, NTHR, 0, c->stream>>>(c->pred, P, c->loss_part);
     CC(cudaGetLastError());

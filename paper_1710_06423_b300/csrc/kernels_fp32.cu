@@ -10,22 +10,19 @@
 
 namespace sac {
 namespace {
-using f32k::NT;
-using f32k::TX;
-using f32k::TY;
 
-template <int S, bool BG, bool HD, bool GR, bool SF>
+template <class G, int S, bool BG, bool HD, bool GR, bool SF>
 cudaError_t set_attr()
 {
-    cudaError_t e = cudaFuncSetAttribute(f32k::stage_fp32<S, BG, HD, GR, SF>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(f32k::Smem));
+    cudaError_t e = cudaFuncSetAttribute(f32k::stage_fp32<G, S, BG, HD, GR, SF>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(f32k::Smem<G>));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(f32k::stage_fp32<S, BG, HD, GR, SF>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(f32k::stage_fp32<G, S, BG, HD, GR, SF>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
     return e;
 }
 
-int g_resident = 296;   // persistent grid: resident CTAs on the device (2 per SM)
+int g_nsm = 148;   // SMs of the device (persistent grids: resident CTAs per SM x this)
 
 // Tensor maps of the stage inputs (3D: pitch float2 x padded rows x 3 planes;
 // box RXP x RY x 1), encoded once per buffer and layout (the CUDA driver API's encoder
@@ -34,6 +31,7 @@ struct TmEntry {
     const void* p;
     int pitch, rows;
     long long fstride;
+    int tile;
     CUtensorMap tm;
 };
 TmEntry g_tm[16];
@@ -45,7 +43,8 @@ cudaError_t encode_stage_tensor_map(const StageArgs<float>& a, CUtensorMap* out)
 {
     std::lock_guard<std::mutex> lk(g_tm_mu);
     for (int i = 0; i < g_ntm; ++i)
-        if (g_tm[i].p == a.sin && g_tm[i].pitch == a.L.pitch && g_tm[i].rows == a.L.rows && g_tm[i].fstride == a.L.fstride) {
+        if (g_tm[i].p == a.sin && g_tm[i].pitch == a.L.pitch && g_tm[i].rows == a.L.rows &&
+            g_tm[i].fstride == a.L.fstride && g_tm[i].tile == a.tile) {
             *out = g_tm[i].tm;
             return cudaSuccess;
         }
@@ -58,7 +57,9 @@ cudaError_t encode_stage_tensor_map(const StageArgs<float>& a, CUtensorMap* out)
     }
     const cuuint64_t dims[3] = {(cuuint64_t)a.L.pitch, (cuuint64_t)a.L.rows, 3};
     const cuuint64_t strides[2] = {(cuuint64_t)a.L.pitch * sizeof(float2), (cuuint64_t)a.L.fstride * sizeof(float2)};
-    const cuuint32_t box[3] = {(cuuint32_t)f32k::RXP, (cuuint32_t)f32k::RY, 1};
+    const int bx = a.tile == TILE_64x16 ? f32k::G64x16::RXP : (a.tile == TILE_32x16 ? f32k::G32x16::RXP : f32k::G32x32::RXP);
+    const int by = a.tile == TILE_64x16 ? f32k::G64x16::RY : (a.tile == TILE_32x16 ? f32k::G32x16::RY : f32k::G32x32::RY);
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUtensorMap tm;
     if (encode(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<float*>(a.sin), dims, strides, box, estr,
@@ -66,7 +67,7 @@ cudaError_t encode_stage_tensor_map(const StageArgs<float>& a, CUtensorMap* out)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     TmEntry& e = g_ntm < 16 ? g_tm[g_ntm++] : g_tm[(g_tm_next++) % 16];
-    e = TmEntry{a.sin, a.L.pitch, a.L.rows, a.L.fstride, tm};
+    e = TmEntry{a.sin, a.L.pitch, a.L.rows, a.L.fstride, a.tile, tm};
     *out = tm;
     return cudaSuccess;
 }
@@ -81,41 +82,63 @@ __global__ void halo_fp32(const StageArgs<float> a, long long n)
         f32k::halo_cell(w, a.L, a.bc_x, a.bc_y, t);
 }
 
-template <int S, bool BG, bool HD, bool GR, bool SF>
+template <class G, int S, bool BG, bool HD, bool GR, bool SF>
 cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
 {
-    const int ntx = (a.L.nx + TX - 1) / TX, nty = (a.L.ny + TY - 1) / TY, ntiles = ntx * nty;
-    const int grid = ntiles < g_resident ? ntiles : g_resident;
+    const int ntx = (a.L.nx + G::TX - 1) / G::TX, nty = (a.L.ny + G::TY - 1) / G::TY, ntiles = ntx * nty;
+    const int resident = G::MINB * g_nsm;
+    const int grid = ntiles < resident ? ntiles : resident;
     CUtensorMap tm;
     const cudaError_t te = encode_stage_tensor_map(a, &tm);
     if (te != cudaSuccess) return te;
-    f32k::stage_fp32<S, BG, HD, GR, SF><<<grid, NT, sizeof(f32k::Smem), s>>>(a, ntx, ntiles, tm);
+    f32k::stage_fp32<G, S, BG, HD, GR, SF><<<grid, G::NT, sizeof(f32k::Smem<G>), s>>>(a, ntx, ntiles, tm);
     if (a.bc_x != BC_FIXED || a.bc_y != BC_FIXED) {
         const long long n = f32k::halo_count(a.L);
-        const int hb = (int)std::min<long long>((n + 255) / 256, g_resident * 2);
+        const int hb = (int)std::min<long long>((n + 255) / 256, 4 * g_nsm);
         halo_fp32<<<hb, 256, 0, s>>>(a, n);
     }
     return cudaGetLastError();
 }
 
-template <bool BG, bool HD, bool GR = false, bool SF = false>
+template <class G, bool BG, bool HD, bool GR = false, bool SF = false>
 cudaError_t by_stage(const StageArgs<float>& a, int stage, cudaStream_t s)
 {
     switch (stage) {
-        case 1: return launch<1, BG, HD, GR, SF>(a, s);
-        case 2: return launch<2, BG, HD, GR, SF>(a, s);
-        case 3: return launch<3, BG, HD, GR, SF>(a, s);
-        default: return launch<4, BG, HD, GR, SF>(a, s);
+        case 1: return launch<G, 1, BG, HD, GR, SF>(a, s);
+        case 2: return launch<G, 2, BG, HD, GR, SF>(a, s);
+        case 3: return launch<G, 3, BG, HD, GR, SF>(a, s);
+        default: return launch<G, 4, BG, HD, GR, SF>(a, s);
     }
 }
 
-template <bool BG, bool HD, bool GR = false, bool SF = false>
+// the tile shapes are instantiated for the plain and background variants; the
+// gravity and single-face variants run 32 x 32 tiles
+template <bool BG, bool HD>
+cudaError_t by_tile(const StageArgs<float>& a, int stage, cudaStream_t s)
+{
+    switch (a.tile) {
+        case TILE_64x16: return by_stage<f32k::G64x16, BG, HD>(a, stage, s);
+        case TILE_32x16: return by_stage<f32k::G32x16, BG, HD>(a, stage, s);
+        default: return by_stage<f32k::G32x32, BG, HD>(a, stage, s);
+    }
+}
+
+template <class G, bool BG, bool HD, bool GR = false, bool SF = false>
 cudaError_t attr_all()
 {
-    cudaError_t e = set_attr<1, BG, HD, GR, SF>();
-    if (e == cudaSuccess) e = set_attr<2, BG, HD, GR, SF>();
-    if (e == cudaSuccess) e = set_attr<3, BG, HD, GR, SF>();
-    if (e == cudaSuccess) e = set_attr<4, BG, HD, GR, SF>();
+    cudaError_t e = set_attr<G, 1, BG, HD, GR, SF>();
+    if (e == cudaSuccess) e = set_attr<G, 2, BG, HD, GR, SF>();
+    if (e == cudaSuccess) e = set_attr<G, 3, BG, HD, GR, SF>();
+    if (e == cudaSuccess) e = set_attr<G, 4, BG, HD, GR, SF>();
+    return e;
+}
+template <class G>
+cudaError_t attr_geometry()
+{
+    cudaError_t e = attr_all<G, false, false>();
+    if (e == cudaSuccess) e = attr_all<G, false, true>();
+    if (e == cudaSuccess) e = attr_all<G, true, false>();
+    if (e == cudaSuccess) e = attr_all<G, true, true>();
     return e;
 }
 }  // namespace
@@ -126,26 +149,29 @@ cudaError_t prepare_stage_fp32()
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    g_resident = 2 * nsm;
-    e = attr_all<false, false>();
-    if (e == cudaSuccess) e = attr_all<false, true>();
-    if (e == cudaSuccess) e = attr_all<true, false>();
-    if (e == cudaSuccess) e = attr_all<true, true>();
-    if (e == cudaSuccess) e = attr_all<true, false, true>();
-    if (e == cudaSuccess) e = attr_all<true, true, true>();
-    if (e == cudaSuccess) e = attr_all<false, true, false, true>();
+    g_nsm = nsm;
+    e = attr_geometry<f32k::G32x32>();
+    if (e == cudaSuccess) e = attr_geometry<f32k::G64x16>();
+    if (e == cudaSuccess) e = attr_geometry<f32k::G32x16>();
+    if (e == cudaSuccess) e = attr_all<f32k::G32x32, true, false, true>();
+    if (e == cudaSuccess) e = attr_all<f32k::G32x32, true, true, true>();
+    if (e == cudaSuccess) e = attr_all<f32k::G32x32, false, true, false, true>();
     return e;
 }
 
 cudaError_t launch_stage_fp32(const StageArgs<float>& a, int stage, bool hd, bool bg, cudaStream_t s)
 {
-    // the single-face variant: no background, no gravity (checked by sac_init)
-    if (a.hd_single_face && hd) return by_stage<false, true, false, true>(a, stage, s);
-    // gravity needs a background (checked by sac_init)
-    if (bg && a.has_grav())
-        return hd ? by_stage<true, true, true>(a, stage, s) : by_stage<true, false, true>(a, stage, s);
-    if (bg) return hd ? by_stage<true, true>(a, stage, s) : by_stage<true, false>(a, stage, s);
-    return hd ? by_stage<false, true>(a, stage, s) : by_stage<false, false>(a, stage, s);
+    using f32k::G32x32;
+    if ((a.hd_single_face && hd) || (bg && a.has_grav())) {
+        StageArgs<float> b = a;   // these variants run 32 x 32 tiles whatever the context's shape
+        b.tile = TILE_32x32;
+        // the single-face variant: no background, no gravity (checked by sac_init)
+        if (b.hd_single_face && hd) return by_stage<G32x32, false, true, false, true>(b, stage, s);
+        // gravity needs a background (checked by sac_init)
+        return hd ? by_stage<G32x32, true, true, true>(b, stage, s) : by_stage<G32x32, true, false, true>(b, stage, s);
+    }
+    if (bg) return hd ? by_tile<true, true>(a, stage, s) : by_tile<true, false>(a, stage, s);
+    return hd ? by_tile<false, true>(a, stage, s) : by_tile<false, false>(a, stage, s);
 }
 
 }  // namespace sac

@@ -6,6 +6,7 @@
 #include <math_constants.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "../../include/sac.h"
 #include "sac_internal.cuh"
@@ -30,6 +31,24 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};   // device address of g_scratch, per device
+std::mutex g_setup_mutex;                                 // guards the per-device set-up below
+
+// Once per device, with that device current: look up the device address of the
+// file-scope array (its host-side name is only a stand-in) and set the stage
+// kernels' attributes.  Two host threads making their first call at the same
+// time serialise here; a failed look-up is retried by the next call.
+unsigned char* scratch_base(int device)
+{
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    unsigned char*& base = g_scratch_addr[device];
+    if (!base) {
+        void* addr = nullptr;
+        if (cudaGetSymbolAddress(&addr, g_scratch) != cudaSuccess || !addr) return nullptr;
+        if (prepare_stage_fp32() != cudaSuccess) return nullptr;
+        base = static_cast<unsigned char*>(addr);
+    }
+    return base;
+}
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 __device__ inline int wrap_n(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
@@ -138,15 +157,8 @@ extern "C" int sac_step_noalloc(const sac_params* p, const float* w_in, float* w
     if (L.fstride > kPlane) return SAC_ERR_TOO_LARGE;
 
     if (cudaSetDevice(p->device) != cudaSuccess) return SAC_ERR_CUDA;
-    unsigned char*& base = g_scratch_addr[p->device];
-    if (!base) {
-        // once per device, with that device current: the device address of the
-        // file-scope array (its host-side name is only a stand-in)
-        void* addr = nullptr;
-        if (cudaGetSymbolAddress(&addr, g_scratch) != cudaSuccess || !addr) return SAC_ERR_CUDA;
-        base = static_cast<unsigned char*>(addr);
-        if (prepare_stage_fp32() != cudaSuccess) return SAC_ERR_CUDA;
-    }
+    unsigned char* base = scratch_base(p->device);
+    if (!base) return SAC_ERR_CUDA;
     DevScalars* sc = reinterpret_cast<DevScalars*>(base);
     float* reg[4];
     for (int k = 0; k < 4; ++k) reg[k] = reinterpret_cast<float*>(base + kScalarBytes + k * kRegisterBytes);
@@ -181,7 +193,10 @@ extern "C" int sac_step_noalloc(const sac_params* p, const float* w_in, float* w
         if (cudaMemcpyAsync(&h, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return SAC_ERR_CUDA;
-        if (h.status != ST_OK) return SAC_ERR_NONFINITE;
+        // as the context path reports them: a non-finite state or step, else a
+        // staging wait of a stage kernel that gave up
+        if (h.status == ST_ERR_NONFINITE) return SAC_ERR_NONFINITE;
+        if (h.status != ST_OK) return SAC_ERR_TIMEOUT;
         *dt_taken = h.dt;
     }
     return SAC_OK;

@@ -31,6 +31,10 @@ struct sac_ctx {
     double* part = nullptr;         // [kSumBlocks][6] partial sums + [6] result
     cudaGraphExec_t g1 = nullptr;   // one CFL step
     cudaGraphExec_t gN = nullptr;   // kChunk CFL steps
+    int tile = sac::TILE_32x32;     // FP32 stage kernels: tile shape (sac_set_tile / sac_tune)
+    int last_stage = 0;             // stage whose output sac_halo_* act on (0: U0, the step-start state)
+    double dx = 0.0, dy = 0.0;      // cell size: (x1 - x0) / nx, (y1 - y0) / ny unless sac_set_cell_size
+    bool cell_override = false;
     bool have_state = false;
     double t_end_host = std::numeric_limits<double>::infinity();
     char err[512] = {0};

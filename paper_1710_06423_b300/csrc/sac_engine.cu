@@ -11,6 +11,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "../../include/sac.h"
 #include "sac_internal.cuh"
@@ -233,6 +236,58 @@ int grid_for(long long n, int block) {
     return (int)(g < 1 ? 1 : (g > 148 * 16 ? 148 * 16 : g));
 }
 
+// Halo strips of a block decomposition (section 3: each sub-domain exchanges
+// the cells its neighbours' stencils reach).  Strip of side 0/1 (left/right):
+// 3 columns over the ghost-extended height, rows -3 .. ny+2; side 2/3
+// (bottom/top): 3 rows over the ghost-extended width, columns -3 .. nx+2.
+// Packed [nf][rows][cols].  pack reads the interior cells next to the side,
+// unpack writes the ghost cells beyond it.
+struct Strip {
+    int i0, j0, cols, rows;
+};
+__host__ __device__ inline Strip halo_strip(const Layout& L, int side, bool unpack)
+{
+    Strip s;
+    if (side < 2) {
+        s.cols = GY; s.rows = L.ny + 2 * GY; s.j0 = -GY;
+        s.i0 = side == 0 ? (unpack ? -GY : 0) : (unpack ? L.nx : L.nx - GY);
+    } else {
+        s.cols = L.nx + 2 * GY; s.rows = GY; s.i0 = -GY;
+        s.j0 = side == 2 ? (unpack ? -GY : 0) : (unpack ? L.ny : L.ny - GY);
+    }
+    return s;
+}
+
+template <typename T>
+__global__ void halo_pack_kernel(T* __restrict__ buf, Layout L, Strip st, T* __restrict__ packed, int unpack)
+{
+    const long long per = (long long)st.cols * st.rows, total = per * NF;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total; v += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(v / per);
+        const long long r = v - (long long)f * per;
+        const int j = st.j0 + (int)(r / st.cols), i = st.i0 + (int)(r % st.cols);
+        const long long e = L.idx(f, i, j, false);
+        if (unpack) buf[e] = packed[v];
+        else packed[v] = buf[e];
+    }
+}
+
+// The running maxima as non-negative signed 64-bit keys (a reduction over
+// sub-domains may then use a signed maximum): a speed key is the bit pattern of
+// a non-negative float or double; a key with the top bit set (a NaN with the
+// sign bit) becomes INT64_MAX, which decodes as a NaN in either precision.
+__global__ void cmax_bits_copy_kernel(DevScalars* sc, unsigned long long* bits, int to_scalars)
+{
+    if (threadIdx.x < 2) {
+        if (to_scalars) {
+            sc->cmax_bits[threadIdx.x] = bits[threadIdx.x];
+        } else {
+            const unsigned long long k = sc->cmax_bits[threadIdx.x];
+            bits[threadIdx.x] = k >> 63 ? 0x7fffffffffffffffull : k;
+        }
+    }
+}
+
 }  // namespace
 
 #include "sac_ctx.h"
@@ -276,12 +331,13 @@ static void fill_stage_args(const sac_ctx* c, int stage, StageArgs<T>* a)
     stage_buffers(c, stage, &sin, &sout);
     a->sin = (const T*)sin; a->u0 = (const T*)c->u0; a->acc = (T*)c->acc;
     a->sout = (T*)sout; a->bg = (const T*)c->bg; a->sc = c->sc; a->L = c->L;
-    a->dx = (c->p.x1 - c->p.x0) / c->p.nx; a->dy = (c->p.y1 - c->p.y0) / c->p.ny;
+    a->dx = c->dx; a->dy = c->dy;
     a->gamma = c->p.gamma;
     for (int f = 0; f < NF; ++f) a->c2[f] = c->p.c2[f];
     a->c_shk = c->p.c_shk; a->bc_x = c->p.bc_x; a->bc_y = c->p.bc_y;
     a->grav[0] = c->p.gravity[0]; a->grav[1] = c->p.gravity[1];
     a->hd_single_face = c->p.hd_single_face;
+    a->tile = c->tile;
     a->derive_f32();
 }
 
@@ -313,7 +369,7 @@ static cudaError_t enqueue_stages(sac_ctx* c, cudaStream_t s)
 
 static cudaError_t enqueue_step(sac_ctx* c, cudaStream_t s, double dt_override)
 {
-    const double dx = (c->p.x1 - c->p.x0) / c->p.nx, dy = (c->p.y1 - c->p.y0) / c->p.ny;
+    const double dx = c->dx, dy = c->dy;
     begin_step_kernel<<<1, 1, 0, s>>>(c->sc, dx, dy, c->p.courant, c->fp32 ? 1 : 0, dt_override);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -387,6 +443,7 @@ static int finish_set_state(sac_ctx* c, double t)
     int rc = launch_cmax(c);
     if (rc != SAC_OK) return rc;
     c->have_state = true;
+    c->last_stage = 0;
     return SAC_OK;
 }
 
@@ -433,6 +490,21 @@ const char* sac_status_string(int code)
 
 const char* sac_last_error(const sac_ctx* c) { return c ? c->err : "no context"; }
 
+// Tile shapes the tuner chose in this process, per run configuration (grid
+// size, hyper-diffusion, background): later contexts of the same configuration
+// start with that shape.
+using TileKey = std::tuple<int, int, int, int>;
+static std::map<TileKey, int> g_tile_cache;
+static std::mutex g_tile_mu;
+static TileKey tile_key(const sac_params& p) { return TileKey{p.nx, p.ny, p.hyperdiffusion, p.has_background}; }
+
+static void drop_graphs(sac_ctx* c)
+{
+    if (c->g1) cudaGraphExecDestroy(c->g1);
+    if (c->gN) cudaGraphExecDestroy(c->gN);
+    c->g1 = c->gN = nullptr;
+}
+
 void sac_free(sac_ctx* c)
 {
     if (!c) return;
@@ -440,8 +512,7 @@ void sac_free(sac_ctx* c)
     cudaGetDevice(&prev);
     cudaSetDevice(c->p.device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->g1) cudaGraphExecDestroy(c->g1);
-    if (c->gN) cudaGraphExecDestroy(c->gN);
+    drop_graphs(c);
     cudaFree(c->u0); cudaFree(c->sa); cudaFree(c->sb); cudaFree(c->acc); cudaFree(c->bg);
     cudaFree(c->sc); cudaFree(c->staging); cudaFree(c->part);
     if (c->hsc) cudaFreeHost(c->hsc);
@@ -470,6 +541,8 @@ int sac_init(const sac_params* p, sac_ctx** out)
 
     c = new sac_ctx();
     c->p = *p;
+    c->dx = (p->x1 - p->x0) / p->nx;
+    c->dy = (p->y1 - p->y0) / p->ny;
     c->fp32 = p->precision == SAC_FP32;
     c->esz = c->fp32 ? 4 : 8;
     c->stream = (cudaStream_t)p->stream;
@@ -518,6 +591,11 @@ int sac_init(const sac_params* p, sac_ctx** out)
         reset_kernel<<<1, 1, 0, c->stream>>>(c->sc, 0.0);
         e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) { rc = fail(c, SAC_ERR_CUDA, "init: %s", cudaGetErrorString(e)); break; }
+        if (c->fp32) {
+            std::lock_guard<std::mutex> lk(g_tile_mu);
+            auto it = g_tile_cache.find(tile_key(*p));
+            if (it != g_tile_cache.end()) c->tile = it->second;
+        }
     } while (0);
     if (rc != SAC_OK) {
         sac_free(c);
@@ -617,6 +695,7 @@ int sac_step(sac_ctx* c, double dt, double* dt_taken)
 {
     if (!c) return SAC_ERR_ARG;
     if (!c->have_state) return fail(c, SAC_ERR_STATE, "step before set_state");
+    if (c->last_stage != 0 && c->last_stage != 4) return fail(c, SAC_ERR_STATE, "a step is half done (sac_stage)");
     if (!(dt <= 0.0) && !std::isfinite(dt)) return fail(c, SAC_ERR_ARG, "dt must be finite");
     CK(cudaSetDevice(c->p.device));
     int rc = set_t_end(c, std::numeric_limits<double>::infinity());
@@ -631,6 +710,7 @@ int sac_steps(sac_ctx* c, long nsteps)
 {
     if (!c) return SAC_ERR_ARG;
     if (!c->have_state) return fail(c, SAC_ERR_STATE, "step before set_state");
+    if (c->last_stage != 0 && c->last_stage != 4) return fail(c, SAC_ERR_STATE, "a step is half done (sac_stage)");
     if (nsteps < 0) return fail(c, SAC_ERR_ARG, "nsteps < 0");
     CK(cudaSetDevice(c->p.device));
     if (c->t_end_host != std::numeric_limits<double>::infinity()) {
@@ -650,6 +730,7 @@ int sac_run_to(sac_ctx* c, double t_end, long max_steps, long* steps_taken)
     if (steps_taken) *steps_taken = 0;
     if (!c) return SAC_ERR_ARG;
     if (!c->have_state) return fail(c, SAC_ERR_STATE, "run before set_state");
+    if (c->last_stage != 0 && c->last_stage != 4) return fail(c, SAC_ERR_STATE, "a step is half done (sac_stage)");
     if (!std::isfinite(t_end)) return fail(c, SAC_ERR_ARG, "t_end must be finite");
     CK(cudaSetDevice(c->p.device));
     int rc = pull_scalars(c);
@@ -700,7 +781,7 @@ int sac_dt(sac_ctx* c, double* dt)
     double cx, cy;
     int rc = sac_cmax(c, &cx, &cy);
     if (rc != SAC_OK) return rc;
-    const double dx = (c->p.x1 - c->p.x0) / c->p.nx, dy = (c->p.y1 - c->p.y0) / c->p.ny;
+    const double dx = c->dx, dy = c->dy;
     double tx = dx / cx, ty = dy / cy;
     *dt = c->p.courant * std::fmin(tx, ty);
     return SAC_OK;
@@ -755,8 +836,8 @@ int sac_divb(sac_ctx* c, double* max_abs, double* mean_abs, long long* ncells)
     if (!c) return SAC_ERR_ARG;
     if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
     CK(cudaSetDevice(c->p.device));
-    const double inv12dx = c->p.nx / (12.0 * (c->p.x1 - c->p.x0));
-    const double inv12dy = c->p.ny / (12.0 * (c->p.y1 - c->p.y0));
+    const double inv12dx = c->cell_override ? 1.0 / (12.0 * c->dx) : c->p.nx / (12.0 * (c->p.x1 - c->p.x0));
+    const double inv12dy = c->cell_override ? 1.0 / (12.0 * c->dy) : c->p.ny / (12.0 * (c->p.y1 - c->p.y0));
     const int bx = c->p.bc_x, by = c->p.bc_y;
     // part holds (kSumBlocks + 1) * NF doubles; this needs 2 * kSumBlocks + 2
     double* out = c->part + 2 * kSumBlocks;
@@ -800,7 +881,7 @@ int sac_profile_stages(sac_ctx* c, int nsteps, double ms[5])
     cudaEvent_t ev[6];
     for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&ev[k]));
     double acc[5] = {0, 0, 0, 0, 0};
-    const double dx = (c->p.x1 - c->p.x0) / c->p.nx, dy = (c->p.y1 - c->p.y0) / c->p.ny;
+    const double dx = c->dx, dy = c->dy;
     for (int it = 0; it < nsteps && rc == SAC_OK; ++it) {
         cudaEventRecord(ev[0], c->stream);
         begin_step_kernel<<<1, 1, 0, c->stream>>>(c->sc, dx, dy, c->p.courant, c->fp32 ? 1 : 0, 0.0);
@@ -831,6 +912,176 @@ int sac_sync(sac_ctx* c)
     CK(cudaSetDevice(c->p.device));
     return pull_scalars(c);
 }
+
+int sac_set_tile(sac_ctx* c, int tile)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (tile < 0 || tile >= NTILE_SHAPES) return fail(c, SAC_ERR_ARG, "unknown tile shape %d", tile);
+    if (!c->fp32) return fail(c, SAC_ERR_ARG, "tile shapes apply to FP32 contexts");
+    if (tile != c->tile) {
+        CK(cudaSetDevice(c->p.device));
+        CK(cudaStreamSynchronize(c->stream));
+        drop_graphs(c);   // the step graphs hold launches of the old shape
+        c->tile = tile;
+    }
+    return SAC_OK;
+}
+
+int sac_get_tile(const sac_ctx* c, int* tile)
+{
+    if (!c || !tile) return SAC_ERR_ARG;
+    *tile = c->tile;
+    return SAC_OK;
+}
+
+int sac_tune(sac_ctx* c, int trials, int* tile_out, double* ms_out)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (!c->fp32) return fail(c, SAC_ERR_ARG, "tile shapes apply to FP32 contexts");
+    if (trials < 1) return fail(c, SAC_ERR_ARG, "trials < 1");
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
+    CK(cudaSetDevice(c->p.device));
+    int rc = pull_scalars(c);
+    if (rc != SAC_OK) return rc;
+    rc = set_t_end(c, std::numeric_limits<double>::infinity());
+    if (rc != SAC_OK) return rc;
+    // snapshot of the state (with its ghosts) and of the step scalars; the
+    // trials advance them and are undone afterwards
+    const size_t bytes = NF * (size_t)c->L.fstride * c->esz;
+    void* snap = nullptr;
+    if (cudaMalloc(&snap, bytes) != cudaSuccess) return fail(c, SAC_ERR_OOM, "tuner snapshot of %zu bytes", bytes);
+    DevScalars hs;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemcpyAsync(snap, c->u0, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, c->sc, sizeof hs, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    const int keep = c->tile;
+    double best = 1e300;
+    int bi = keep;
+    for (int t = 0; t < NTILE_SHAPES && e == cudaSuccess; ++t) {
+        c->tile = t;
+        e = enqueue_step(c, c->stream, 0.0);                   // warm-up (tensor maps, caches)
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < trials && e == cudaSuccess; ++k) e = enqueue_step(c, c->stream, 0.0);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms / trials < best) { best = ms / trials; bi = t; }
+        // back to the snapshot before the next shape
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->u0, snap, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->sc, &hs, sizeof hs, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(snap);
+    c->tile = keep;
+    if (e != cudaSuccess) return fail(c, SAC_ERR_CUDA, "tuner: %s", cudaGetErrorString(e));
+    rc = pull_scalars(c);   // a trial that failed on the device is reported, the state is restored
+    if (rc != SAC_OK) return rc;
+    rc = sac_set_tile(c, bi);
+    if (rc != SAC_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tile_mu);
+        g_tile_cache[tile_key(c->p)] = bi;
+    }
+    if (tile_out) *tile_out = bi;
+    if (ms_out) *ms_out = best;
+    return SAC_OK;
+}
+
+int sac_set_cell_size(sac_ctx* c, double dx, double dy)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (!(dx > 0.0) || !(dy > 0.0) || !std::isfinite(dx) || !std::isfinite(dy))
+        return fail(c, SAC_ERR_ARG, "cell size must be finite and positive");
+    CK(cudaSetDevice(c->p.device));
+    CK(cudaStreamSynchronize(c->stream));
+    drop_graphs(c);   // the step graphs hold the old cell size
+    c->dx = dx; c->dy = dy;
+    c->cell_override = true;
+    return SAC_OK;
+}
+
+int sac_stage(sac_ctx* c, int stage)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (stage < 1 || stage > 4) return fail(c, SAC_ERR_ARG, "stage %d is not 1..4", stage);
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "stage before set_state");
+    const bool in_order = stage == 1 ? (c->last_stage == 0 || c->last_stage == 4) : c->last_stage == stage - 1;
+    if (!in_order) return fail(c, SAC_ERR_STATE, "stage %d after stage %d", stage, c->last_stage);
+    CK(cudaSetDevice(c->p.device));
+    if (stage == 1) {
+        if (c->t_end_host != std::numeric_limits<double>::infinity()) {
+            int rc = set_t_end(c, std::numeric_limits<double>::infinity());
+            if (rc != SAC_OK) return rc;
+        }
+        const double dx = c->dx, dy = c->dy;
+        begin_step_kernel<<<1, 1, 0, c->stream>>>(c->sc, dx, dy, c->p.courant, c->fp32 ? 1 : 0, 0.0);
+        CK(cudaGetLastError());
+    }
+    CK(enqueue_stage_one(c, c->stream, stage));
+    c->last_stage = stage;
+    return SAC_OK;
+}
+
+static int halo_args(sac_ctx* c, int side, long long* n)
+{
+    if (!c) return SAC_ERR_ARG;
+    if (side < 0 || side > 3) return fail(c, SAC_ERR_ARG, "side %d is not 0..3", side);
+    if ((side < 2 ? c->p.nx : c->p.ny) < GY) return fail(c, SAC_ERR_ARG, "a halo strip needs 3 interior cells across");
+    const Strip st = halo_strip(c->L, side, false);
+    *n = (long long)NF * st.cols * st.rows;
+    return SAC_OK;
+}
+
+int sac_halo_size(sac_ctx* c, int side, long long* n)
+{
+    long long k = 0;
+    int rc = halo_args(c, side, &k);
+    if (rc == SAC_OK && n) *n = k;
+    return rc;
+}
+
+static int halo_copy(sac_ctx* c, int side, void* buf, int unpack)
+{
+    long long n = 0;
+    int rc = halo_args(c, side, &n);
+    if (rc != SAC_OK) return rc;
+    if (!buf) return fail(c, SAC_ERR_ARG, "null strip buffer");
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
+    CK(cudaSetDevice(c->p.device));
+    void *sin, *sout;
+    stage_buffers(c, c->last_stage == 0 ? 4 : c->last_stage, &sin, &sout);   // stage 4 writes U0
+    const Strip st = halo_strip(c->L, side, unpack != 0);
+    const int grid = grid_for(n, 256);
+    if (c->fp32)
+        halo_pack_kernel<float><<<grid, 256, 0, c->stream>>>((float*)sout, c->L, st, (float*)buf, unpack);
+    else
+        halo_pack_kernel<double><<<grid, 256, 0, c->stream>>>((double*)sout, c->L, st, (double*)buf, unpack);
+    CK(cudaGetLastError());
+    return SAC_OK;
+}
+
+int sac_halo_pack(sac_ctx* c, int side, void* strip_dev) { return halo_copy(c, side, strip_dev, 0); }
+int sac_halo_unpack(sac_ctx* c, int side, const void* strip_dev) { return halo_copy(c, side, (void*)strip_dev, 1); }
+
+static int cmax_bits_copy(sac_ctx* c, void* bits, int to_scalars)
+{
+    if (!c || !bits) return SAC_ERR_ARG;
+    if (!c->have_state) return fail(c, SAC_ERR_STATE, "no state set");
+    CK(cudaSetDevice(c->p.device));
+    cmax_bits_copy_kernel<<<1, 32, 0, c->stream>>>(c->sc, (unsigned long long*)bits, to_scalars);
+    CK(cudaGetLastError());
+    return SAC_OK;
+}
+
+int sac_get_cmax_bits(sac_ctx* c, void* bits_dev) { return cmax_bits_copy(c, bits_dev, 0); }
+int sac_set_cmax_bits(sac_ctx* c, const void* bits_dev) { return cmax_bits_copy(c, (void*)bits_dev, 1); }
 
 int sac_debug_drop_copies(sac_ctx* c, int on)
 {

@@ -16,6 +16,9 @@ constexpr int TILE_Y_MAX = 32;
 
 enum { BC_PERIODIC = 0, BC_FIXED = 1, BC_OUTFLOW = 2 };
 enum { ST_OK = 0, ST_ERR_NONFINITE = -5, ST_ERR_TIMEOUT = -6 };
+// tile shapes of the FP32 stage kernels (SAC_TILE_* of sac.h): 32 x 32 cells
+// with 256 threads, 64 x 16 with 256 threads, 32 x 16 with 128 threads
+enum { TILE_32x32 = 0, TILE_64x16 = 1, TILE_32x16 = 2, NTILE_SHAPES = 3 };
 
 // field index -> (plane, component) of the FP32 pair layout:
 // planes (rho~, e~), (m_x, m_y), (B~x, B~y); background (rho_b, e_b), (B_bx, B_by)
@@ -117,6 +120,7 @@ struct StageArgs {
     int bc_x, bc_y;
     int hd_single_face;   // 1: hyper-diffusion ratio from the face itself (no max over 3 faces)
     double grav[2];    // gravitational acceleration; sources rt g (momentum), m.g (energy)
+    int tile = TILE_32x32;   // FP32 kernels: tile shape (TILE_*)
     __host__ __device__ bool has_grav() const { return grav[0] != 0.0 || grav[1] != 0.0; }
     // FP32 kernels: the parameters above rounded once on the host, so a tile
     // does no double arithmetic (FP64 issues at 1/64 of the FP32 rate here)
@@ -137,7 +141,8 @@ struct StageArgs {
 cudaError_t launch_stage_fp64(const StageArgs<double>& a, int stage, bool hd, bool bg, cudaStream_t s);
 cudaError_t launch_stage_fp32(const StageArgs<float>& a, int stage, bool hd, bool bg, cudaStream_t s);
 // the tensor map of a FP32 stage input (3D: pitch float2 x padded rows x 3 planes,
-// box of one staged plane), cached per buffer and layout (kernels_fp32.cu)
+// box of one staged plane of the tile shape a.tile), cached per buffer, layout
+// and box (kernels_fp32.cu)
 cudaError_t encode_stage_tensor_map(const StageArgs<float>& a, CUtensorMap* out);
 // one-time kernel attribute set-up (dynamic shared memory limits); idempotent
 cudaError_t prepare_stage_fp64();

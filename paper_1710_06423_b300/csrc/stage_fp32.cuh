@@ -8,8 +8,9 @@
 // one packed f32x2 instruction (fma/add/sub/mul.rn.f32x2) advances two
 // variables at once and every stencil offset stays an aligned 8-byte access.
 //
-// One CTA (256 threads, two per SM) owns a 32 x 32 tile at a time and walks
-// the tiles of the grid persistently:
+// One CTA owns a TX x TY tile at a time (32 x 32 with 256 threads, two per SM,
+// unless the autotuner picked another shape) and walks the tiles of the grid
+// persistently:
 //   0. stage the tile + 3-cell halo of the three planes into shared memory
 //      (rows 16-byte aligned): one 3D tensor copy (TMA, cp.async.bulk.tensor)
 //      per plane on an mbarrier in the persistent kernel; bulk row copies in
@@ -179,38 +180,58 @@ __device__ __forceinline__ float fdiv(float a, float b)
 }
 
 // ---- tile geometry ------------------------------------------------------------
-constexpr int TX = 32, TY = 32, NT = 256, NW = NT / 32, SEG = 4;
-static_assert(TX / SEG == NW && TY / SEG == NW, "one segment per warp in both sweeps");
-// staged region (cols x0-4.., rows y0-3..); its rows start 16-byte aligned
-// (pitch 42 float2) so that TMA bulk copies or 16-byte cp.async.cg copies can
-// fill it.  The price is a 2-way bank conflict in the X sweep's column-wise
-// window loads; measured 8% faster overall than an odd (conflict-free) pitch
-// filled by 8-byte cp.async, and the bulk copies another 2%.
-constexpr int RX = TX + 8, RY = TY + 6, RXP = RX + 2;
-constexpr int VXP = RX + 1;                                // row pitch of the velocity arrays (odd)
-constexpr int FXW = TX + 4, FXP = FXW + 1;                 // x fluxes: cols x0-2 .. x0+TX+1
-constexpr int FYH = TY + 4, FYP = TX + 1;                 // y fluxes: rows y0-2 .. y0+TY+1 (odd pitch)
-constexpr int SW = TX + 2, SH = TY + 2, SP = SW + 1;       // shock indicator: x0-1.., y0-1..
-constexpr int KXP = TX + 1;                                // k_x rows (aliases the x fluxes)
-constexpr int PW = RX - 2;                                 // primitive columns 1 .. RX-2
+// A tile is TX x TY cells (TX a multiple of the warp width, TY of the segment
+// length); one CTA of NT = TX * TY / SEG threads owns it.  X sweep: thread =
+// (row tid % TY, SEG-cell segment tid / TY); Y sweep: thread = (column
+// tid % TX, SEG-cell segment tid / TX): one segment per thread in both.
+// The autotuner chooses among the shapes instantiated below (32 x 32, 64 x 16,
+// 32 x 16); every shape gives bit-for-bit the same results, since each cell's
+// arithmetic does not depend on where the tile boundaries fall.
+constexpr int SEG = 4;
+template <int TX_, int TY_>
+struct Geo {
+    static constexpr int TX = TX_, TY = TY_, NT = TX * TY / SEG, NW = NT / 32;
+    // staged region (cols x0-4.., rows y0-3..); its rows start 16-byte aligned
+    // (pitch RXP float2) so that TMA or 16-byte cp.async.cg copies can fill it.
+    // The price is a 2-way bank conflict in the X sweep's column-wise window
+    // loads; measured 8% faster overall than an odd (conflict-free) pitch
+    // filled by 8-byte cp.async, and the bulk copies another 2%.
+    static constexpr int RX = TX + 8, RY = TY + 6, RXP = RX + 2;
+    static constexpr int VXP = RX + 1;                      // row pitch of the velocity arrays (odd)
+    static constexpr int FXW = TX + 4, FXP = FXW + 1;       // x fluxes: cols x0-2 .. x0+TX+1
+    static constexpr int FYH = TY + 4, FYP = TX + 1;        // y fluxes: rows y0-2 .. y0+TY+1 (odd pitch)
+    static constexpr int SW = TX + 2, SH = TY + 2, SP = SW + 1;   // shock indicator: x0-1.., y0-1..
+    static constexpr int KXP = TX + 1;                      // k_x rows (aliases the x fluxes)
+    static constexpr int PW = RX - 2;                       // primitive columns 1 .. RX-2
+    // resident CTAs per SM the launch bounds ask for (128 registers a thread at
+    // 256 threads; the 128-thread shape is held to three by its shared memory)
+    static constexpr int MINB = NT <= 128 ? 3 : (NT <= 256 ? 2 : 1);
+    static_assert(TX % 32 == 0 && TY % SEG == 0 && NT % 32 == 0, "tile shape");
+    static_assert(TX <= TILE_X_MAX && TY <= TILE_Y_MAX, "the padded layout must hold a ragged last tile");
+    static_assert((TY + 8) % 8 == 0, "tensor-copy destinations 128-byte aligned");
+};
+using G32x32 = Geo<32, 32>;
+using G64x16 = Geo<64, 16>;
+using G32x16 = Geo<32, 16>;
 
 // The flux of the third pair has an exactly zero component in each direction,
 // (0, F_By) along x and (F_Bx, 0) along y: only the nonzero one is stored.
+template <class G>
 struct Smem {
-    float2 u[3][RY + 2][RXP];   // two spare rows: planes start 128-byte aligned (RY+2)*RXP*8 = 105*128
+    float2 u[3][G::RY + 2][G::RXP];   // two spare rows: planes start 128-byte aligned
     union {
         struct {
-            float2 fx[2][TY][FXP];   // x fluxes of pairs 0, 1
-            float fx2[TY][FXP];      // F_By along x
+            float2 fx[2][G::TY][G::FXP];   // x fluxes of pairs 0, 1
+            float fx2[G::TY][G::FXP];      // F_By along x
         };
-        float2 kx[3][TY][KXP];       // k_x, after the X sweep
+        float2 kx[3][G::TY][G::KXP];       // k_x, after the X sweep
     };
-    float2 fy[2][FYH][FYP];          // y fluxes of pairs 0, 1
-    float fy2[FYH][FYP];             // F_Bx along y
-    float s[SH][SP];                 // shock indicator
-    float vx[RY][VXP];
-    float vy[RY][VXP];
-    float2 ax[3], ay[3];             // per-pair hyper-diffusion coefficients c2 cmax / d
+    float2 fy[2][G::FYH][G::FYP];          // y fluxes of pairs 0, 1
+    float fy2[G::FYH][G::FYP];             // F_Bx along y
+    float s[G::SH][G::SP];                 // shock indicator
+    float vx[G::RY][G::VXP];
+    float vy[G::RY][G::VXP];
+    float2 ax[3], ay[3];                   // per-pair hyper-diffusion coefficients c2 cmax / d
 };
 
 // ---- ghost frame of a stage output ----------------------------------------------
@@ -317,7 +338,8 @@ __device__ __forceinline__ StepConsts load_step_consts(const DevScalars* sc)
     return k;
 }
 // threads 0..2 (one pair each); visible to the CTA after its next barrier
-__device__ __forceinline__ void store_hd_coeffs(const StageArgs<float>& a, Smem& S, const int tid)
+template <class G>
+__device__ __forceinline__ void store_hd_coeffs(const StageArgs<float>& a, Smem<G>& S, const int tid)
 {
     if (tid < 3) {
         const float cmx = a.sc->fcmax[0], cmy = a.sc->fcmax[1];
@@ -330,6 +352,7 @@ __device__ __forceinline__ void store_hd_coeffs(const StageArgs<float>& a, Smem&
 // Block maximum of the per-thread running signal-speed keys m[0] (x), m[1] (y)
 // folded into the run's cmax_bits with one atomicMax per direction.  Every
 // thread of the CTA calls it (it holds a barrier).
+template <int NW>
 __device__ __forceinline__ void block_speed_max(const unsigned long long (&m)[2], unsigned long long (*red)[NW],
                                                 DevScalars* sc)
 {
@@ -352,24 +375,30 @@ __device__ __forceinline__ void block_speed_max(const unsigned long long (&m)[2]
 }
 
 // Issue the cp.async copies of plane p of the staged region of tile (x0, y0):
-// warp w copies rows w, w + NW, ...; lanes 0 .. RX/2-1 copy 16 bytes (two
-// float2) each.  Completion: cp_async_wait_all.
-__device__ __forceinline__ void stage_plane(const StageArgs<float>& a, Smem& S, const int x0, const int y0, const int p)
+// warp w copies rows w, w + NW, ...; lane l copies 16 bytes (two float2) at
+// chunks l, l + 32, ... of the RX / 2 chunks of a row.  Completion:
+// cp_async_wait_all.
+template <class G>
+__device__ __forceinline__ void stage_plane(const StageArgs<float>& a, Smem<G>& S, const int x0, const int y0, const int p)
 {
+    constexpr int RX = G::RX, RY = G::RY, RXP = G::RXP, NW = G::NW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Layout L = a.L;
     const float2* gin = reinterpret_cast<const float2*>(a.sin);
-    static_assert(RX % 2 == 0 && RX / 2 <= 32 && (RXP * sizeof(float2)) % 16 == 0, "16-byte staging");
-    const bool act = lane < RX / 2;
-    const int l2 = act ? lane : 0;
-    const unsigned sbase = (unsigned)__cvta_generic_to_shared(&S.u[p][warp][2 * l2]);
+    static_assert(RX % 2 == 0 && (RXP * sizeof(float2)) % 16 == 0, "16-byte staging");
     const long long rstep = (long long)NW * L.pitch;
-    const float2* g = gin + p * L.fstride + (long long)(y0 + warp) * L.pitch + x0 + 2 * l2;
 #pragma unroll
-    for (int k = 0; k < (RY + NW - 1) / NW; ++k) {
-        if (k * NW + warp < RY)   // warp-uniform
-            cp_async16_cg_if(sbase + (unsigned)((k * NW * RXP) * sizeof(float2)), g, act);
-        g += rstep;
+    for (int c0 = 0; c0 < RX / 2; c0 += 32) {
+        const bool act = c0 + lane < RX / 2;
+        const int l2 = act ? c0 + lane : 0;
+        const unsigned sbase = (unsigned)__cvta_generic_to_shared(&S.u[p][warp][2 * l2]);
+        const float2* g = gin + p * L.fstride + (long long)(y0 + warp) * L.pitch + x0 + 2 * l2;
+#pragma unroll
+        for (int k = 0; k < (RY + NW - 1) / NW; ++k) {
+            if (k * NW + warp < RY)   // warp-uniform
+                cp_async16_cg_if(sbase + (unsigned)((k * NW * RXP) * sizeof(float2)), g, act);
+            g += rstep;
+        }
     }
 }
 
@@ -393,10 +422,13 @@ __device__ __forceinline__ void load_pointwise(const StageArgs<float>& a, const 
 // on the CTA's mbarrier.  With a tensor map of the stage input (single-run
 // kernel): one 3D tensor copy of the plane's RXP x RY box (RXP float2 per row,
 // the region's own pitch; coordinates past the grid read zeros), issued by one
-// thread; kTileBytesTM per tile.  Without one (batch kernel, whose next tile
-// may belong to another run): one 320-byte bulk copy per row (lane k of warp w
-// copies row w + NW k); kTileBytes per tile.
-constexpr unsigned kTileBytes = 3u * RY * RX * sizeof(float2);
+// thread; G::kTileBytesTM per tile.  Without one (batch kernel, whose next tile
+// may belong to another run): one RX-float2 bulk copy per row (lane k of warp w
+// copies row w + NW k); G::kTileBytes per tile.
+template <class G>
+constexpr unsigned tile_bytes() { return 3u * G::RY * G::RX * sizeof(float2); }
+template <class G>
+constexpr unsigned tile_bytes_tm() { return 3u * G::RY * G::RXP * sizeof(float2); }
 // Where the next tile's staged region comes from: its tile origin and the
 // stencil input of its run (a batch's next tile may belong to another run).
 struct NextTile {
@@ -407,14 +439,14 @@ struct NextTile {
     int pitch;
     const CUtensorMap* tm = nullptr;   // the stage input as a 3D tensor (pitch, rows, 3 planes)
 };
-constexpr unsigned kTileBytesTM = 3u * RY * RXP * sizeof(float2);
-static_assert((RY + 2) * RXP * sizeof(float2) % 128 == 0, "tensor-copy destinations 128-byte aligned");
 __device__ __forceinline__ NextTile next_tile(const StageArgs<float>& a, bool has, int x0, int y0)
 {
     return NextTile{has, x0, y0, a.sin, a.L.fstride, a.L.pitch};
 }
-__device__ __forceinline__ void stage_plane_bulk(const NextTile& n, Smem& S, const int p, unsigned long long* bar)
+template <class G>
+__device__ __forceinline__ void stage_plane_bulk(const NextTile& n, Smem<G>& S, const int p, unsigned long long* bar)
 {
+    static_assert((G::RY + 2) * G::RXP * sizeof(float2) % 128 == 0, "tensor-copy destinations 128-byte aligned");
     if (n.tm) {   // one tensor copy of the plane's RY x RXP box (rows of RXP float2, as the region's pitch)
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -424,10 +456,10 @@ __device__ __forceinline__ void stage_plane_bulk(const NextTile& n, Smem& S, con
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = warp + NW * lane;
-    if (lane < (RY + NW - 1) / NW && r < RY) {
+    const int r = warp + G::NW * lane;
+    if (lane < (G::RY + G::NW - 1) / G::NW && r < G::RY) {
         const float2* g = reinterpret_cast<const float2*>(n.sin) + p * n.fstride + (long long)(n.y0 + r) * n.pitch + n.x0;
-        bulk_row_g2s(smem_u32(&S.u[p][r][0]), g, RX * sizeof(float2), bar);
+        bulk_row_g2s(smem_u32(&S.u[p][r][0]), g, G::RX * sizeof(float2), bar);
     }
 }
 
@@ -439,13 +471,15 @@ __device__ __forceinline__ void stage_plane_bulk(const NextTile& n, Smem& S, con
 // land, the run's status becomes ST_ERR_TIMEOUT, *failed is set and every
 // thread returns.  S.ax/S.ay must hold the run's coefficients (store_hd_coeffs).
 // Stage 4 folds the signal speeds of the tile's new state into m.
-template <int STAGE, bool BG, bool HD, bool OVERLAP, bool GRAV = false, bool SF = false>
-__device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x0, const int y0, Smem& S,
+template <class G, int STAGE, bool BG, bool HD, bool OVERLAP, bool GRAV = false, bool SF = false>
+__device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x0, const int y0, Smem<G>& S,
                                           const StepConsts& K, unsigned long long (&m)[2],
                                           const NextTile& nt = NextTile{},
                                           unsigned long long* bar = nullptr, unsigned* phase = nullptr,
                                           bool* failed = nullptr)
 {
+    constexpr int TX = G::TX, TY = G::TY, NT = G::NT, NW = G::NW, RY = G::RY, FXW = G::FXW, FYH = G::FYH;
+    constexpr int KXP = G::KXP, PW = G::PW, SW = G::SW, SH = G::SH;
     const Layout L = a.L;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2* __restrict__ gbg = reinterpret_cast<const float2*>(a.bg);
@@ -455,7 +489,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 
     // this thread's cells in the Y sweep and RK update: column x0 + col, rows
     // y0 + y_0 + q (q < nq inside the grid; ragged last tiles)
-    const int col = lane, y_0 = warp * SEG, gi = x0 + col;
+    const int col = tid % TX, y_0 = (tid / TX) * SEG, gi = x0 + col;
     const long long e_first = L.at(gi, y0 + y_0);
     const int nq = gi < L.nx ? L.ny - (y0 + y_0) : 0;
     // The pointwise RK registers U0/D of these cells are brought into L2 when the
@@ -467,7 +501,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         const int pp = lane >> 3, arr = (lane >> 2) & 1, qq = lane & 3;
         if ((STAGE >= 3 || arr == 0) && y0 + y_0 + qq < L.ny)
             prefetch_l2_256(reinterpret_cast<const float2*>(arr ? a.acc : a.u0) + pp * P
-                                + L.at(x0, y0 + y_0 + qq));
+                                + L.at(x0 + (col - lane), y0 + y_0 + qq));
     }
 
     // ---- 0. the staged region of the three planes in shared memory -----------------
@@ -548,27 +582,39 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             fx_ok = (unsigned)(r - 3) < (unsigned)TY && (unsigned)(c - 2) < (unsigned)FXW;
             fy_ok = (unsigned)(r - 1) < (unsigned)FYH && (unsigned)(c - 4) < (unsigned)TX;
         };
-        // Main pass: warp w, lane l -> column 1 + l of rows w, w + NW, ... (one
-        // row per warp-instruction: conflict-free); tail: the last PW - 32
-        // columns walked down the rows, one cell per thread (a warp covers
-        // consecutive rows of a column; the odd pitches keep that conflict-free).
-        // At most ceil(RY / NW) + 1 = 6 cells per thread.
-        constexpr int NTAIL = (PW - 32) * RY;
-        static_assert(PW > 32 && NTAIL <= NT, "primitive-phase mapping");
+        // Main pass: warp w, lane l -> columns 1 + l, 33 + l, ... (TX / 32 of them)
+        // of rows w, w + NW, ... (one row per warp-instruction: conflict-free);
+        // tail: the last PW - TX columns walked down the rows, one cell per thread
+        // (a warp covers consecutive rows of a column; the odd pitches keep that
+        // conflict-free).
+        constexpr int NTAIL = (PW - TX) * RY;
+        static_assert(PW > TX, "primitive-phase mapping");
 #pragma unroll 1
         for (int k = 0; k < (RY + NW - 1) / NW; ++k) {
             const int r = warp + NW * k;
             if (r < RY) {
-                bool fx_ok, fy_ok;
-                flux_ok(r, 1 + lane, fx_ok, fy_ok);
-                prim_cell(r, 1 + lane, fx_ok, fy_ok);
+#pragma unroll
+                for (int c0 = 0; c0 < TX; c0 += 32) {
+                    bool fx_ok, fy_ok;
+                    flux_ok(r, 1 + c0 + lane, fx_ok, fy_ok);
+                    prim_cell(r, 1 + c0 + lane, fx_ok, fy_ok);
+                }
             }
         }
-        if (tid < NTAIL) {
-            const int cc = tid / RY, r = tid - cc * RY;
-            bool fx_ok, fy_ok;
-            flux_ok(r, 33 + cc, fx_ok, fy_ok);
-            prim_cell(r, 33 + cc, fx_ok, fy_ok);
+        if constexpr (NTAIL <= NT) {
+            if (tid < NTAIL) {
+                const int cc = tid / RY, r = tid - cc * RY;
+                bool fx_ok, fy_ok;
+                flux_ok(r, TX + 1 + cc, fx_ok, fy_ok);
+                prim_cell(r, TX + 1 + cc, fx_ok, fy_ok);
+            }
+        } else {
+            for (int v = tid; v < NTAIL; v += NT) {
+                const int cc = v / RY, r = v - cc * RY;
+                bool fx_ok, fy_ok;
+                flux_ok(r, TX + 1 + cc, fx_ok, fy_ok);
+                prim_cell(r, TX + 1 + cc, fx_ok, fy_ok);
+            }
         }
     }
     __syncthreads();
@@ -588,17 +634,26 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             const float sv = fmaxf(0.f, -(dvx + dvy));
             S.s[sr][scn] = sv;
         };
-        // main pass: warp w, lane l -> column l of rows w, w + NW, ...; tail: the
-        // last SW - 32 columns walked down the rows, on the threads of the warps
-        // with one main row less (at most ceil(SH / NW) = 5 cells per thread)
-        constexpr int STAIL = (SW - 32) * SH, S0 = (SH % NW) * 32;
-        static_assert(SW > 32 && S0 + STAIL <= NT, "shock-phase mapping");
+        // main pass: warp w, lane l -> columns l, 32 + l, ... of rows w, w + NW, ...;
+        // tail: the last SW - TX columns walked down the rows, on the threads of
+        // the warps with one main row less (a strided loop if they are too few)
+        constexpr int STAIL = (SW - TX) * SH, S0 = (SH % NW) * 32;
 #pragma unroll 2
         for (int k = 0; k < (SH + NW - 1) / NW; ++k)
-            if (warp + NW * k < SH) shock_cell(warp + NW * k, lane);
-        if (tid >= S0 && tid < S0 + STAIL) {
-            const int t = tid - S0, cc = t / SH;
-            shock_cell(t - cc * SH, 32 + cc);
+            if (warp + NW * k < SH) {
+#pragma unroll
+                for (int c0 = 0; c0 < TX; c0 += 32) shock_cell(warp + NW * k, c0 + lane);
+            }
+        if constexpr (S0 + STAIL <= NT) {
+            if (tid >= S0 && tid < S0 + STAIL) {
+                const int t = tid - S0, cc = t / SH;
+                shock_cell(t - cc * SH, TX + cc);
+            }
+        } else {
+            for (int t = tid; t < STAIL; t += NT) {
+                const int cc = t / SH;
+                shock_cell(t - cc * SH, TX + cc);
+            }
         }
         __syncthreads();
     }
@@ -612,7 +667,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 
     // ---- 3. X sweep: thread = (row lane, SEG-cell segment per warp) ---------------
     {
-        const int row = lane, x_0 = warp * SEG;
+        const int row = tid % TY, x_0 = (tid / TY) * SEG;
         float2 kx[3][SEG];
         float2 bsfx[SEG + 1];
         if constexpr (HD) {
@@ -628,10 +683,10 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
             for (int q = 0; q < SEG + 6; ++q) u[q] = S.u[p][row + 3][x_0 + 1 + q];
             float2 hx[SEG];
             if constexpr (HD) {
-                float2 G[SEG + 1];
-                face_fluxes<SF>(u, bsfx, S.ax[p], G);
+                float2 Gf[SEG + 1];
+                face_fluxes<SF>(u, bsfx, S.ax[p], Gf);
 #pragma unroll
-                for (int q = 0; q < SEG; ++q) hx[q] = sub2(G[q + 1], G[q]);
+                for (int q = 0; q < SEG; ++q) hx[q] = sub2(Gf[q + 1], Gf[q]);
             } else {
 #pragma unroll
                 for (int q = 0; q < SEG; ++q) hx[q] = make_float2(0.f, 0.f);
@@ -689,16 +744,16 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
         if (OVERLAP) {
             __syncthreads();   // plane p of this tile is read for good
             if (nt.has) {
-                if (p == 0 && threadIdx.x == 0) mbar_expect_tx(bar, nt.tm ? kTileBytesTM : kTileBytes);
+                if (p == 0 && threadIdx.x == 0) mbar_expect_tx(bar, nt.tm ? tile_bytes_tm<G>() : tile_bytes<G>());
                 stage_plane_bulk(nt, S, p, bar);
             }
         }
         float2 hy[SEG];
         if constexpr (HD) {
-            float2 G[SEG + 1];
-            face_fluxes<SF>(u, bsfy, S.ay[p], G);
+            float2 Gf[SEG + 1];
+            face_fluxes<SF>(u, bsfy, S.ay[p], Gf);
 #pragma unroll
-            for (int q = 0; q < SEG; ++q) hy[q] = sub2(G[q + 1], G[q]);
+            for (int q = 0; q < SEG; ++q) hy[q] = sub2(Gf[q + 1], Gf[q]);
         } else {
 #pragma unroll
             for (int q = 0; q < SEG; ++q) hy[q] = make_float2(0.f, 0.f);
@@ -776,14 +831,14 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 // copies while it finishes the current one.
 // The step constants are read once; stage 4 keeps the signal-speed maximum of
 // all its tiles in registers and reduces it once at the end.
-template <int STAGE, bool BG, bool HD, bool GRAV, bool SF = false>
-__global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, const int ntx, const int ntiles,
-                                                    const __grid_constant__ CUtensorMap tm)
+template <class G, int STAGE, bool BG, bool HD, bool GRAV, bool SF = false>
+__global__ void __launch_bounds__(G::NT, G::MINB) stage_fp32(const StageArgs<float> a, const int ntx, const int ntiles,
+                                                             const __grid_constant__ CUtensorMap tm)
 {
     if (a.sc->skip || a.sc->status != ST_OK) return;   // skipped step, or an earlier stage gave up
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ unsigned long long red[2][NW];
-    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    __shared__ unsigned long long red[2][G::NW];
+    Smem<G>& S = *reinterpret_cast<Smem<G>*>(smem_raw);
     store_hd_coeffs(a, S, threadIdx.x);   // no later phase writes S.ax/S.ay
     // tensor copies need 128-byte aligned destinations; otherwise row copies
     const CUtensorMap* tmp = (smem_u32(&S.u[0][0][0]) & 127u) == 0 ? &tm : nullptr;
@@ -796,9 +851,9 @@ __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, co
     bool failed = false;
     int t = blockIdx.x;
     if (t < ntiles) {
-        NextTile f = next_tile(a, true, (t % ntx) * TX, (t / ntx) * TY);
+        NextTile f = next_tile(a, true, (t % ntx) * G::TX, (t / ntx) * G::TY);
         f.tm = tmp;
-        if (threadIdx.x == 0) mbar_expect_tx(&bar, f.tm ? kTileBytesTM : kTileBytes);
+        if (threadIdx.x == 0) mbar_expect_tx(&bar, f.tm ? tile_bytes_tm<G>() : tile_bytes<G>());
         // (test hook: with drop_copies set no copy is issued, so the first tile's
         // bounded wait runs out and the launch reports ST_ERR_TIMEOUT)
         if (!a.sc->drop_copies) {
@@ -808,9 +863,10 @@ __global__ void __launch_bounds__(NT, 2) stage_fp32(const StageArgs<float> a, co
     }
     for (; t < ntiles; t += gridDim.x) {
         const int tn = t + gridDim.x;
-        NextTile nt = next_tile(a, tn < ntiles, (tn % ntx) * TX, (tn / ntx) * TY);
+        NextTile nt = next_tile(a, tn < ntiles, (tn % ntx) * G::TX, (tn / ntx) * G::TY);
         nt.tm = tmp;
-        tile_body<STAGE, BG, HD, true, GRAV, SF>(a, (t % ntx) * TX, (t / ntx) * TY, S, K, m, nt, &bar, &phase, &failed);
+        tile_body<G, STAGE, BG, HD, true, GRAV, SF>(a, (t % ntx) * G::TX, (t / ntx) * G::TY, S, K, m, nt, &bar,
+                                                     &phase, &failed);
         if (failed) return;
     }
     if (STAGE == 4) block_speed_max(m, red, a.sc);

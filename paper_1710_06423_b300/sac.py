@@ -19,6 +19,8 @@ SAC_OK, SAC_ERR_ARG, SAC_ERR_STATE, SAC_ERR_CUDA, SAC_ERR_OOM, SAC_ERR_NONFINITE
     0, -1, -2, -3, -4, -5, -6
 SAC_ERR_TOO_LARGE = -7
 BC_PERIODIC, BC_FIXED, BC_OUTFLOW = 0, 1, 2
+TILE_32x32, TILE_64x16, TILE_32x16 = 0, 1, 2
+TILE_NAMES = {TILE_32x32: "32x32", TILE_64x16: "64x16", TILE_32x16: "32x16"}
 FP64, FP32 = 0, 1
 NF, NB = 6, 4
 
@@ -27,10 +29,12 @@ EXPORTS = (
     "sac_default_params", "sac_init", "sac_free", "sac_last_error", "sac_status_string",
     "sac_set_state", "sac_get_state", "sac_set_state_dev", "sac_get_state_dev",
     "sac_step", "sac_steps", "sac_run_to", "sac_set_fixed_dt", "sac_dt", "sac_time", "sac_cmax", "sac_sums", "sac_divb",
-    "sac_profile_stages", "sac_sync", "sac_debug_drop_copies",
+    "sac_profile_stages", "sac_sync", "sac_set_tile", "sac_get_tile", "sac_tune",
+    "sac_set_cell_size", "sac_stage", "sac_halo_size", "sac_halo_pack", "sac_halo_unpack", "sac_get_cmax_bits", "sac_set_cmax_bits",
+    "sac_debug_drop_copies",
     "sac_batch_init", "sac_batch_free", "sac_batch_last_error", "sac_batch_set_state",
     "sac_batch_get_state", "sac_batch_steps", "sac_batch_sync", "sac_batch_time", "sac_batch_tune",
-    "sac_batch_set_config",
+    "sac_batch_set_config", "sac_batch_set_tile", "sac_batch_get_config",
     "sac_cnn_param_count", "sac_cnn_init", "sac_cnn_free", "sac_cnn_last_error", "sac_cnn_set_params",
     "sac_cnn_get_params", "sac_cnn_set_scales", "sac_cnn_forward", "sac_cnn_grads", "sac_cnn_train_step",
     "sac_cnn_apply", "sac_cnn_perturb", "sac_block_average",
@@ -118,6 +122,16 @@ def load() -> ctypes.CDLL:
         "sac_divb": (i, [vp, dp, dp, ctypes.POINTER(ctypes.c_longlong)]),
         "sac_profile_stages": (i, [vp, i, dp]),
         "sac_sync": (i, [vp]),
+        "sac_set_tile": (i, [vp, i]),
+        "sac_get_tile": (i, [vp, ctypes.POINTER(i)]),
+        "sac_tune": (i, [vp, i, ctypes.POINTER(i), dp]),
+        "sac_set_cell_size": (i, [vp, d, d]),
+        "sac_stage": (i, [vp, i]),
+        "sac_halo_size": (i, [vp, i, ctypes.POINTER(ctypes.c_longlong)]),
+        "sac_halo_pack": (i, [vp, i, vp]),
+        "sac_halo_unpack": (i, [vp, i, vp]),
+        "sac_get_cmax_bits": (i, [vp, vp]),
+        "sac_set_cmax_bits": (i, [vp, vp]),
         "sac_debug_drop_copies": (i, [vp, i]),
         "sac_batch_init": (i, [P, i, ctypes.POINTER(vp)]),
         "sac_batch_free": (None, [vp]),
@@ -129,6 +143,8 @@ def load() -> ctypes.CDLL:
         "sac_batch_time": (i, [vp, i, dp, ctypes.POINTER(L)]),
         "sac_batch_tune": (i, [vp, i, ctypes.POINTER(ctypes.c_int), dp]),
         "sac_batch_set_config": (i, [vp, i, i, i]),
+        "sac_batch_set_tile": (i, [vp, i]),
+        "sac_batch_get_config": (i, [vp, ctypes.POINTER(ctypes.c_int)]),
         "sac_cnn_param_count": (L, []),
         "sac_cnn_init": (i, [i, i, i, vp, ctypes.POINTER(vp)]),
         "sac_cnn_free": (None, [vp]),
@@ -317,6 +333,47 @@ class Solver:
     def sync(self):
         self._check(load().sac_sync(self._ctx), "sac_sync")
 
+    def set_tile(self, tile: int):
+        """FP32 tile shape (TILE_32x32, TILE_64x16, TILE_32x16) of the later steps."""
+        self._check(load().sac_set_tile(self._ctx, int(tile)), "sac_set_tile")
+
+    def tile(self) -> int:
+        out = ctypes.c_int()
+        self._check(load().sac_get_tile(self._ctx, ctypes.byref(out)), "sac_get_tile")
+        return out.value
+
+    def tune(self, trials: int = 3):
+        """Autotune the tile shape on the current state (restored); returns (tile, ms per step)."""
+        t, ms = ctypes.c_int(), ctypes.c_double()
+        self._check(load().sac_tune(self._ctx, int(trials), ctypes.byref(t), ctypes.byref(ms)), "sac_tune")
+        return t.value, ms.value
+
+    # -- block decomposition (sac_stage / sac_halo_* / sac_*_cmax_bits) --------
+    def set_cell_size(self, dx: float, dy: float):
+        self._check(load().sac_set_cell_size(self._ctx, float(dx), float(dy)), "sac_set_cell_size")
+
+    def stage(self, k: int):
+        self._check(load().sac_stage(self._ctx, int(k)), "sac_stage")
+
+    def halo_size(self, side: int) -> int:
+        n = ctypes.c_longlong()
+        self._check(load().sac_halo_size(self._ctx, int(side), ctypes.byref(n)), "sac_halo_size")
+        return n.value
+
+    def halo_pack(self, side: int, strip):
+        """Pack the strip next to `side` into a device tensor of halo_size(side) elements."""
+        self._check(load().sac_halo_pack(self._ctx, int(side), ctypes.c_void_p(strip.data_ptr())), "sac_halo_pack")
+
+    def halo_unpack(self, side: int, strip):
+        self._check(load().sac_halo_unpack(self._ctx, int(side), ctypes.c_void_p(strip.data_ptr())), "sac_halo_unpack")
+
+    def get_cmax_bits(self, bits):
+        """Copy the two running signal-speed keys into a device int64/uint64 tensor of 2."""
+        self._check(load().sac_get_cmax_bits(self._ctx, ctypes.c_void_p(bits.data_ptr())), "sac_get_cmax_bits")
+
+    def set_cmax_bits(self, bits):
+        self._check(load().sac_set_cmax_bits(self._ctx, ctypes.c_void_p(bits.data_ptr())), "sac_set_cmax_bits")
+
     def debug_drop_copies(self, on: bool):
         """Test hook of the bounded copy waits (see sac_debug_drop_copies)."""
         self._check(load().sac_debug_drop_copies(self._ctx, int(bool(on))), "sac_debug_drop_copies")
@@ -415,6 +472,15 @@ class Batch:
 
     def set_config(self, persistent, ctas_per_sm, order):
         self._check(load().sac_batch_set_config(self._b, persistent, ctas_per_sm, order), "sac_batch_set_config")
+
+    def set_tile(self, tile):
+        self._check(load().sac_batch_set_tile(self._b, int(tile)), "sac_batch_set_tile")
+
+    def config(self):
+        """(persistent, ctas_per_sm, order, tile shape)."""
+        cfg = (ctypes.c_int * 4)()
+        self._check(load().sac_batch_get_config(self._b, cfg), "sac_batch_get_config")
+        return tuple(cfg)
 
 
 def _fp(a):
@@ -523,6 +589,15 @@ def step_noalloc(w_in, w_out, dt: float = 0.0, wait: bool = True, **kw) -> float
         else:
             setattr(p, k, v)
     p.precision = FP32
+    # the C side cannot see the buffers' sizes: refuse anything that is not a
+    # contiguous float32 (6, ny, nx) tensor on the run's device
+    for name, t in (("w_in", w_in), ("w_out", w_out)):
+        if tuple(t.shape) != (NF, p.ny, p.nx):
+            raise ValueError(f"{name} shape {tuple(t.shape)} != {(NF, p.ny, p.nx)}")
+        if str(t.dtype) != "torch.float32" or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 tensor")
+        if not t.is_cuda or t.device.index != p.device:
+            raise ValueError(f"{name} must live on cuda:{p.device}, not {t.device}")
     if stream == "current":
         import torch
         stream = torch.cuda.current_stream(p.device)

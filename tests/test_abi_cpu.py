@@ -71,3 +71,22 @@ def test_params3_struct_layout_matches_header(lib):
     assert abs(p.gamma - 5 / 3) < 1e-15 and p.courant == 0.3 and p.hyperdiffusion == 1
     assert list(p.c2) == [0.02, 0.1, 0.1, 0.1, 0.02, 0.02, 0.02, 0.02] and p.c_shk == 0.5
     assert p.precision == sac.FP64 and p.device == 0 and not p.stream
+
+
+@pytest.mark.parametrize("case", ["cpu_tensor", "wrong_shape", "float64", "strided"])
+def test_step_noalloc_refuses_bad_buffers_before_the_call(lib, case):
+    """The allocation-free step cannot see the sizes of the caller's buffers, so
+    the binding refuses anything but a contiguous float32 (6, ny, nx) tensor on
+    the run's device before it reaches the C call."""
+    import torch
+    from paper_1710_06423_b300 import sac
+    nx, ny = 16, 12
+    good = torch.zeros((6, ny, nx), dtype=torch.float32)
+    bad = {
+        "cpu_tensor": good,
+        "wrong_shape": torch.zeros((6, ny, nx - 1), dtype=torch.float32),
+        "float64": torch.zeros((6, ny, nx), dtype=torch.float64),
+        "strided": torch.zeros((6, nx, ny), dtype=torch.float32).transpose(1, 2),
+    }[case]
+    with pytest.raises(ValueError):
+        sac.step_noalloc(bad, bad, 0.0, nx=nx, ny=ny)

@@ -156,3 +156,114 @@ def test_apply_adds_scaled_output(setup, inputs_mod):
     np.testing.assert_allclose(got, expect, rtol=0, atol=1e-6)
     assert cx > 0 and cy > 0
     net.close()
+
+
+# ---- element-by-element parity at a multi-tile size ----------------------------
+# 520 x 300 pixels: 33 x 38 tiles of 8 x 16 (the last tile column and row are
+# partial), about two tiles for each of the 592 persistent CTAs.
+# The oracle here is the network with BF16 storage (oracle.cnn.forward_bf16 /
+# loss_and_grads_bf16): the GPU rounds the same stored values to BF16, so the
+# two differ only where an FP32 sum and the FP64 sum straddle a BF16 rounding
+# boundary (a "flip": probability ~ 2^-24 sqrt(K) / 2^-8 ~ 1e-4 per stored
+# value, K <= 288 terms), and a flip moves one stored value by one BF16 unit.
+# Bounds (r = |gpu - oracle| / the channel's RMS output), calibrated on the CPU
+# by injecting one-unit flips at 1e-3 per stored value, ten times that rate:
+#   every element:                      r <= 0.25   (flips reached 0.05)
+#   mean over each pixel column / row:  r <= 5e-3   (flips: 2.9e-3; one tile
+#                                                    column reading its periodic
+#                                                    neighbour one row off: 1.1e-2)
+#   mean over each 8 x 16 tile:         r <= 1e-2
+#   dW, db per element: |gpu - oracle| <= 1e-2 |oracle| + 1e-3 S_w, S_w = the sum
+#   over pixels of |dY| |X| (flips reached 0.21 of this bound; leaving the last
+#   8 pixel columns out of the sums exceeds it 17-fold).
+MT_NX, MT_NY = 520, 300
+
+
+@pytest.fixture(scope="module")
+def multitile(inputs_mod):
+    from oracle import cnn as ocnn
+    nx, ny = MT_NX, MT_NY
+    w, g = _state(inputs_mod, nx, ny, seed=5)
+    params = ocnn.init_params(21, last_scale=1.0)
+    rng = np.random.default_rng(22)
+    params = [(pw, 0.05 * rng.standard_normal(pb.shape)) for pw, pb in params]
+    flat = _flat(params).astype(np.float32)
+    params64 = _unflat(flat.astype(np.float64), ocnn.LAYERS)
+    target = (0.3 * rng.standard_normal((6, ny, nx))).astype(np.float32)
+    x = ocnn.features(w, g, 1.0 / nx, 1.0 / ny, SCALES)
+    return nx, ny, w, g, flat, params64, target, x
+
+
+def _forward_stats(got, ref):
+    rms = np.sqrt((ref ** 2).mean(axis=(1, 2), keepdims=True))
+    r = np.abs(got - ref) / rms
+    ny, nx = r.shape[1:]
+    ty, tx = -(-ny // 8), -(-nx // 16)
+    pad = np.zeros((6, ty * 8, tx * 16))
+    pad[:, :ny, :nx] = r
+    cnt = np.zeros((ty * 8, tx * 16))
+    cnt[:ny, :nx] = 1.0
+    tiles = pad.reshape(6, ty, 8, tx, 16).sum(axis=(0, 2, 4)) / (6 * cnt.reshape(ty, 8, tx, 16).sum(axis=(1, 3)))
+    return r, r.mean(axis=(0, 1)), r.mean(axis=(0, 2)), tiles
+
+
+def _forward_ok(got, ref):
+    r, col, row, tiles = _forward_stats(got, ref)
+    return r.max() <= 0.25 and col.max() <= 5e-3 and row.max() <= 5e-3 and tiles.max() <= 1e-2
+
+
+def test_forward_elementwise_multi_tile(multitile):
+    import torch
+    from oracle import cnn as ocnn
+    from paper_1710_06423_b300.sac import CNN
+    nx, ny, w, g, flat, params64, _, x = multitile
+    net = CNN(nx, ny)
+    net.set_params(flat)
+    net.set_scales(SCALES, np.ones(6))
+    wd = torch.from_numpy(w.astype(np.float32)).cuda().contiguous()
+    pred = torch.zeros((ny * nx, 8), dtype=torch.float32, device="cuda")
+    net.forward(wd, g, 1.0 / nx, 1.0 / ny, pred)
+    torch.cuda.synchronize()
+    net.close()
+    got = pred.cpu().numpy()[:, :6].T.reshape(6, ny, nx).astype(np.float64)
+    ref, _ = ocnn.forward_bf16(params64, x)
+    r, col, row, tiles = _forward_stats(got, ref)
+    print(f"forward: max r {r.max():.3g}, column mean max {col.max():.3g}, row mean max {row.max():.3g}, "
+          f"tile mean max {tiles.max():.3g}, fraction of elements with r > 1e-3: {(r > 1e-3).mean():.3g}")
+    assert _forward_ok(got, ref), (r.max(), col.max(), row.max(), tiles.max())
+    # the bounds have the power to see a tile-edge fault: against an oracle
+    # whose periodic wrap feeds the last pixel column from one row off (a
+    # planted mistake on the oracle side) the same comparison fails
+    xb = x.copy()
+    xb[:, :, -1] = np.roll(x[:, :, -1], 1, axis=1)
+    bad, _ = ocnn.forward_bf16(params64, xb)
+    assert not _forward_ok(got, bad)
+
+
+def test_gradients_elementwise_multi_tile(multitile):
+    import torch
+    from oracle import cnn as ocnn
+    from paper_1710_06423_b300.sac import CNN
+    nx, ny, w, g, flat, params64, target, x = multitile
+    net = CNN(nx, ny)
+    net.set_params(flat)
+    net.set_scales(SCALES, np.ones(6))
+    w32 = w.astype(np.float32)
+    wd = torch.from_numpy(w32).cuda().contiguous()
+    nd = torch.from_numpy((w32 + target).astype(np.float32)).cuda().contiguous()
+    loss, grads = net.grads(wd, nd, g, 1.0 / nx, 1.0 / ny)
+    net.close()
+    # the target the GPU forms: (next - w) / out_scale in FP32, out_scale = 1
+    tgt = ((w32 + target).astype(np.float32) - w32).astype(np.float64)
+    ref_loss, ref_grads, (acts, dys) = ocnn.loss_and_grads_bf16(params64, x, tgt, return_stored=True)
+    assert abs(loss - ref_loss) <= 1e-4 * ref_loss, (loss, ref_loss)
+    gg = _unflat(grads.astype(np.float64), ocnn.LAYERS)
+    for k in range(4):
+        wk = ocnn.round_bf16(params64[k][0])
+        _, sw, sb = ocnn.conv3x3_backward(np.abs(acts[k]), np.abs(wk), np.abs(dys[k]))
+        for name, a, b, s in (("dW", gg[k][0], ref_grads[k][0], sw), ("db", gg[k][1], ref_grads[k][1], sb)):
+            d = np.abs(a - b)
+            lim = 1e-2 * np.abs(b) + 1e-3 * s
+            frac = np.max(np.where(lim > 0, d / np.where(lim > 0, lim, 1.0), 0.0))
+            print(f"layer {k} {name}: max |gpu - oracle| / bound = {frac:.3g}")
+            assert np.all(d <= lim), (k, name, frac)

@@ -88,9 +88,13 @@ def test_brio_wu_fp64_full_config(oracle_mod, inputs_mod):
 
 
 def test_brio_wu_fp32(oracle_mod, inputs_mod):
-    """Same shock tube in FP32 (the Brio-Wu workload itself is an FP64 case).  Over ~1040
-    steps the shocks amplify single-precision rounding to a few 1e-4 of the momentum
-    L1 norm; the bound is 1e-3 per field and the step count may differ by one."""
+    """Same shock tube in FP32 (the Brio-Wu workload itself is an FP64 case), all
+    six fields.  The bound is 1e-3 relative L1 per field, not the smooth-flow
+    1e-5: the FP64 oracle started from this state with a 2^-24 relative
+    perturbation (one FP32 rounding of each value, nothing else) already ends
+    up to 4.5e-4 away from itself in m_x at t = 0.1, because the shocks turn
+    a perturbation of the state into a shift of their positions
+    (test_oracle_sensitivity.py pins that).  The step count may differ by one."""
     kw = problem_kwargs(800, 1, gamma=2.0, bc_x=1)
     pr = oracle_problem(oracle_mod, kw)
     w0 = inputs_mod.brio_wu()
@@ -101,7 +105,9 @@ def test_brio_wu_fp32(oracle_mod, inputs_mod):
         got, t = s.get_state()
     assert t == 0.1 and abs(n - n_ref) <= 1
     err = l1rel(got, ref)
-    assert np.all(err[[0, 1, 3, 5]] <= 1e-3), err
+    print("Brio-Wu FP32 relative L1 per field:", err)
+    assert np.all(err <= 1e-3), err
+    assert np.all(got[4] == 0.75)      # B_x has no flux and no difference: exact
 
 
 def test_run_to_lands_on_t_end_and_matches_step_count(oracle_mod, inputs_mod):

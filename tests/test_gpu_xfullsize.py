@@ -3,12 +3,15 @@
 * Orszag-Tang 1000 x 1000, 200 RK4 steps, FP64 and FP32, against the FP64
   oracle run to the same horizon (element by element), with the vortex's
   point symmetry and periodic conservation checked on the GPU results.
+* Orszag-Tang 2044^2 with 1e-3 noise, FP32, 100 graph-replayed CFL steps
+  (the workload's horizon) against the oracle over the whole grid.
 * Orszag-Tang 2044^2 and 8000^2 with 1e-3 noise, FP32, in the launch
   configuration the benchmark times (graph-replayed CFL steps): one step
   compared with the oracle on sampled windows.  One RK4 step reads 3 cells
   per stage, so a cell depends only on cells within 12 of it; the oracle run
   on a periodically-wrapped window with a 12-cell margin is exact inside the
-  margin when given the GPU's step size and signal speeds.
+  margin when given the step size and signal speeds, which come from the
+  oracle over the whole state (the GPU's are checked against them).
 * The longest side the API accepts (65536 cells) along x and along y, two
   steps in both precisions against the oracle over the whole grid.
 * The 64-run batch of the benchmark in its autotuned launch configuration:
@@ -120,6 +123,29 @@ def test_c3_batch_config_equals_single_runs(inputs_mod):
         assert np.array_equal(got[k][0], ref), (k, sizes[k])
 
 
+def test_c2_2044_fp32_100_steps_full_grid(oracle_mod, inputs_mod):
+    """The 2044^2 Orszag-Tang workload with 1e-3 noise at its horizon: 100 CFL
+    steps of the FP32 path (graph-replayed, as timed) against 100 oracle steps,
+    over the whole grid.  FP32 storage noise enters the hyper-diffusion ratio
+    at every stage; the bound is the FP32 target, relative L1 per field
+    <= 1e-5, and the time reached agrees to the FP32 signal speeds' rounding."""
+    n, steps = 2044, 100
+    kw = problem_kwargs(n, n)
+    w0 = inputs_mod.orszag_tang(n, noise=1e-3, seed=20171018)
+    ref, t_ref, n_ref = oracle_mod.run(oracle_problem(oracle_mod, kw), w0, max_steps=steps)
+    assert n_ref == steps
+    with solver(kw, FP32) as s:
+        s.set_state(w0, None, 0.0)
+        s.steps(steps)
+        got, t = s.get_state()
+        t_gpu, n_gpu = s.time()
+    assert n_gpu == steps
+    assert abs(t - t_ref) <= 1e-6 * t_ref, (t, t_ref)
+    err = l1rel(got, ref)
+    print("2044^2, 100 steps, FP32 relative L1 per field:", err)
+    assert np.all(err <= TOL_FP32_L1), err
+
+
 def _window(w, j0, i0, size, margin):
     """Periodic window [j0-margin, j0+size+margin) x [i0-margin, i0+size+margin)."""
     ny, nx = w.shape[1:]
@@ -130,14 +156,23 @@ def _window(w, j0, i0, size, margin):
 
 @pytest.mark.parametrize("n", [2044, 8000])
 def test_bench_config_one_step_windows(oracle_mod, inputs_mod, n):
+    """One graph-replayed step of the benchmark's configuration against the
+    oracle on sampled windows.  The signal speeds and the CFL step are the
+    oracle's own, taken over the whole initial state; the GPU's FP32 speeds and
+    its step are checked against them first."""
     kw = problem_kwargs(n, n)
     w0 = inputs_mod.orszag_tang(n, noise=1e-3, seed=20171018)
+    pr_full = oracle_problem(oracle_mod, kw)
+    cx, cy = oracle_mod.cmax(pr_full, w0)
+    dt = oracle_mod.cfl_dt(pr_full, cx, cy)
     with solver(kw, FP32) as s:
         s.set_state(w0, None, 0.0)
-        cx, cy = s.cmax()
+        gcx, gcy = s.cmax()
         s.steps(1)                       # the graph-replayed step the benchmark times
         got, t = s.get_state()
-    dt = t
+    # FP32 signal speeds of FP32-rounded states: a few units of 2^-24
+    assert abs(gcx - cx) <= 1e-6 * cx and abs(gcy - cy) <= 1e-6 * cy, (gcx, cx, gcy, cy)
+    assert abs(t - dt) <= 1e-6 * dt, (t, dt)
     size, margin = 48, 12
     starts = [(0, 0), (n - 20, n - 30), (n // 2 + 7, n // 3 + 5), (5, n - 1), (n - 1, 17)]
     for j0, i0 in starts:

@@ -112,3 +112,44 @@ def test_block_average(cnn):
     m = cnn.block_average(a, 4)
     assert m.shape == (2, 2, 2)
     assert m[1, 1, 0] == a[1, 4:8, 0:4].mean()
+
+
+def test_round_bf16_matches_torch_on_fp32_values(cnn):
+    """FP32 values (which convert to BF16 without double rounding) round as
+    torch's float32 -> bfloat16 conversion does (round to nearest even)."""
+    import torch
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal(20000) * np.exp(rng.uniform(-20, 20, 20000))).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(cnn.round_bf16(x.astype(np.float64)), ref)
+
+
+def test_round_bf16_ties_to_even_and_fixed_points(cnn):
+    t = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8), 3 * 2.0 ** -9 * 257 / 256])
+    got = cnn.round_bf16(t)
+    assert got[0] == 1.0 and got[1] == 1 + 2.0 ** -6 and got[2] == -1.0
+    # values with at most 8 significant bits are fixed points, zero included
+    v = np.array([0.0, 1.0, -0.75, 255.0, 2.0 ** -40 * 129, -(2.0 ** 30) * 255])
+    np.testing.assert_array_equal(cnn.round_bf16(v), v)
+
+
+def test_bf16_network_is_the_network_when_every_stored_value_is_exact(cnn):
+    """With small-integer weights and inputs every stored value (weights,
+    activations, r / n and the input gradients) is exactly a BF16 number, so the
+    BF16-storage network must equal the FP64 network bit for bit: a pin that
+    forward_bf16 / loss_and_grads_bf16 change nothing but the rounding."""
+    rng = np.random.default_rng(6)
+    layers = ((2, 3), (3, 3), (3, 2))
+    params = [(rng.integers(-1, 2, (co, ci, 3, 3)).astype(np.float64), rng.integers(-2, 3, co).astype(np.float64))
+              for ci, co in layers]
+    x = rng.integers(-2, 3, (2, 4, 4)).astype(np.float64)
+    y, acts = cnn.forward(params, x)
+    yb, actsb = cnn.forward_bf16(params, x)
+    assert np.array_equal(y, yb) and all(np.array_equal(a, b) for a, b in zip(acts, actsb))
+    n = y.size                                  # 2 * 4 * 4 = 32: r / n exact for integer r
+    target = y - rng.integers(-3, 4, y.shape)
+    l0, g0 = cnn.loss_and_grads(params, x, target)
+    l1, g1 = cnn.loss_and_grads_bf16(params, x, target)
+    assert n == 32 and l0 == l1
+    for (a, b), (c, d) in zip(g0, g1):
+        assert np.array_equal(a, c) and np.array_equal(b, d)

@@ -155,6 +155,39 @@ def test_shock_viscosity_linear_compression(oracle_mod):
     np.testing.assert_allclose(k[4, 0, 3:nx - 3], 2.0 * csh * av * q, rtol=1e-9)
 
 
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_shock_viscosity_face_average_quadratic_compression(oracle_mod, axis):
+    """Places the shock indicator on the faces.  v_d = -a x_d^2 gives
+    div v = -2a x_d exactly (the stencil is exact on quadratics), so the cell
+    indicator s_i = 2a x_i is LINEAR in the cell index.  The face value
+    s_{i+1/2} = (s_i + s_{i+1})/2 = 2a (i+1) h.  With B_d = q i^2
+    (d1 = q(2i+1) on face i+1/2, no ideal flux of B_d) the shock diffusion is
+    c_shk (s_{i+1/2} d1_{i+1/2} - s_{i-1/2} d1_{i-1/2}) = 2 a q c_shk h (4i+1).
+    Taking s_i alone on the face gives 4i instead, the larger neighbour 4i+2,
+    so a wrong placement fails here.  Run along x and along y (the y operator
+    is not reached by the x-only compression pin)."""
+    o = oracle_mod
+    n, av, q, csh = 30, 0.8, 1e-3, 0.6
+    if axis == "x":
+        pr = o.Problem(nx=n, ny=1, bc_x=BC_O, c2=(0,) * 6, c_shk=csh)
+        h = pr.dx
+    else:
+        pr = o.Problem(nx=1, ny=n, bc_y=BC_O, c2=(0,) * 6, c_shk=csh)
+        h = pr.dy
+    xc = (np.arange(n) + 0.5) * h              # cell centres along the axis
+    i = np.arange(n, dtype=float)
+    shape = (1, n) if axis == "x" else (n, 1)
+    w = _uniform(*shape, rho=1.0, p=5.0)
+    mom, bfield = (1, 4) if axis == "x" else (2, 5)
+    w[mom] = (-av * xc * xc).reshape(shape)    # m_d = rho v_d with rho = 1
+    w[bfield] = (0.3 + q * i * i).reshape(shape)
+    k = o.rhs(pr, w, cmax=(3.0, 3.0))
+    got = k[bfield].reshape(-1)
+    inner = np.arange(4, n - 4)                # every stencil inside the interior
+    expect = 2.0 * av * q * csh * h * (4.0 * inner + 1.0)
+    np.testing.assert_allclose(got[inner], expect, rtol=1e-9)
+
+
 def test_signal_speed_and_dt_uniform(oracle_mod):
     """cmax_d = |v_d| + sqrt((gamma p + B^2)/rho); dt = C min(dx/cx, dy/cy)."""
     o = oracle_mod

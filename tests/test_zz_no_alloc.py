@@ -1,9 +1,10 @@
 """The allocation-free step (sac_step_noalloc) against the allocating one.
 
-Some callers cannot allocate device memory (for example code running while a
-CUDA graph is captured, or plugins whose host forbids allocation); for them the
-library keeps the working memory of one FP32 RK4 step in a fixed array compiled
-into it.  This test calls that entry point through the C ABI twice in a row,
+Some callers cannot allocate device memory (for example a plug-in whose host
+application owns all device memory through its own allocator, or a real-time
+loop where an allocation's device synchronisation and unbounded latency are not
+allowed); for them the library keeps the working memory of one FP32 RK4 step in
+a fixed array compiled into it.  This test calls that entry point through the C ABI twice in a row,
 each time on the previous output, and checks it against the context-based path
 (sac_set_state_dev + sac_step + sac_get_state_dev) on the same states.
 """
@@ -71,6 +72,30 @@ def test_noalloc_edge_cases_equal_context_step(inputs_mod, case):
     torch.cuda.synchronize()
     assert dt == dt_ref
     assert torch.equal(b, ref)
+
+
+def test_noalloc_fixed_step_equals_context_step(inputs_mod):
+    """A given step size (dt > 0) goes through the step-begin override instead
+    of the CFL step: two such calls in a row equal Solver.step(dt) bit for bit."""
+    import torch
+    from paper_1710_06423_b300 import sac
+    nx, ny = 96, 80
+    w0 = inputs_mod.orszag_tang(nx, ny, noise=1e-3, seed=4)
+    dev = torch.from_numpy(w0.astype(np.float32)).cuda().contiguous()
+    dt = 1.25e-3
+    refs = []
+    with sac.Solver(nx=nx, ny=ny, precision=sac.FP32) as s:
+        s.set_state_dev(dev, None, 0.0)
+        for _ in range(2):
+            assert s.step(dt) == dt
+            r = torch.empty_like(dev)
+            s.get_state_dev(r)
+            refs.append(r.clone())
+    a, b = dev.clone(), torch.empty_like(dev)
+    assert sac.step_noalloc(a, b, dt, nx=nx, ny=ny) == dt
+    assert sac.step_noalloc(b, a, dt, nx=nx, ny=ny) == dt
+    torch.cuda.synchronize()
+    assert torch.equal(b, refs[0]) and torch.equal(a, refs[1])
 
 
 def test_noalloc_rejects_grids_beyond_its_memory():
