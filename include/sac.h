@@ -384,6 +384,21 @@ long sac_cnn_param_count(void);
 int sac_cnn_init(int nx, int ny, int device, void *stream, sac_cnn **out);
 void sac_cnn_free(sac_cnn *c);
 const char *sac_cnn_last_error(const sac_cnn *c);
+/* Tensor-core path of the convolutions: 1 = tcgen05 (5th-generation tensor
+ * cores: BF16 operands staged in shared memory, FP32 accumulators in tensor
+ * memory, 128-pixel row tiles), 0 = mma.sync (warp-level BF16 MMA, 8 x 16-pixel
+ * tiles).  Both accumulate in FP32 and store the same BF16 activations; they
+ * differ only in the order of the FP32 sums.  Waits for the stream.
+ * Errors: SAC_ERR_ARG. */
+int sac_cnn_set_tensor_path(sac_cnn *c, int path);
+/* Limit of the correction sac_cnn_apply adds: clip > 0 clamps every network
+ * output to [-clip, clip] before the mean is removed and out_scale applied (a
+ * correction of at most clip residual scales per field and step); 0 (the
+ * default) applies it unlimited.  Errors: SAC_ERR_ARG. */
+int sac_cnn_set_clip(sac_cnn *c, double clip);
+/* Wait for the network's stream and report a tensor-core accumulator wait
+ * that gave up (about one second; SAC_ERR_TIMEOUT, flag cleared). */
+int sac_cnn_sync(sac_cnn *c);
 /* Host FP32 parameters in/out (n must equal sac_cnn_param_count()); setting
  * them also resets the optimiser state.  Synchronous. */
 int sac_cnn_set_params(sac_cnn *c, const float *params, long n);

@@ -192,6 +192,238 @@ __global__ void __launch_bounds__(NTHR) conv3x3_kernel(const ConvArgs a)
     }
 }
 
+// ---- tcgen05 implicit-GEMM periodic 3x3 convolution ------------------------------
+// The same convolution on the 5th-generation tensor cores.  One CTA of 128
+// threads owns a tile of TP = 128 consecutive pixels of one image row: the GEMM
+// has M = 128 (pixels), N = NC (output channels, COUT padded to 16 or 32) and
+// K = 9 taps x CIN channels.  Per tap and 16-channel step one
+// tcgen05.mma.cta_group::1.kind::f16 (BF16 operands in shared memory, FP32
+// accumulator of 128 lanes x NC columns in tensor memory) is issued by one
+// thread; the epilogue reads the accumulator back with tcgen05.ld (warp w owns
+// lanes 32w .. 32w+31, i.e. pixels 32w .. 32w+31 of the tile).
+// Shared-memory operands use the K-major layout without swizzle, in 8-row x
+// 16-byte core matrices:
+//   halo  [3 rows][CIN/8 chunks][HP pixels][8 ch]: the A operand of tap (dy, dx)
+//         starts at row dy, pixel dx; consecutive pixels are 16 B apart, so 8
+//         pixels form one core matrix (SBO = 128 B between pixel groups) and the
+//         next 8 channels are HP * 16 B away (LBO);
+//   wts   [9 taps][CIN/8 chunks][NC/8 groups][8 out ch][8 ch]: the B operand
+//         (SBO = 128 B between output-channel groups, LBO = NC/8 * 128 B).
+namespace tcv {
+constexpr int TP = 128, HP = TP + 2, NTHR_TC = 128;
+
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    // start address, leading / stride byte offsets (16-byte units), descriptor
+    // version 1 (bits 46-47), no swizzle, base offset 0
+    return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = n, M = 128
+__host__ __device__ constexpr unsigned idesc_bf16(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16_tc(unsigned tmem_d, unsigned long long adesc, unsigned long long bdesc,
+                                            unsigned idesc, int accumulate)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void mbar_init_tc(unsigned long long* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_wait_tc(unsigned long long* bar, unsigned parity)
+{
+    unsigned long long t0 = 0;
+    for (;;) {
+        unsigned ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (ok) return true;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > 1000000000ull) return false;   // about one second
+    }
+}
+
+template <int CIN, int NC>
+struct TcSmem {
+    static constexpr int CPP = CIN / 8, NG = NC / 8;
+    static constexpr int HALO_BYTES = 3 * CPP * HP * 16;
+    static constexpr int W_BYTES = 9 * CPP * NG * 128;
+    static constexpr int BYTES = 2 * HALO_BYTES + W_BYTES + 64;   // two halo buffers + mbarrier, TMEM address
+};
+
+// Copy the halo of tile `tile` (rows y-1 .. y+1, pixels x0-1 .. x0+TP, periodic)
+// into one halo buffer with 16-byte cp.async; the caller commits the group.
+template <int CIN>
+__device__ __forceinline__ void stage_halo_tc(const ConvArgs& a, int tile, int tiles_x, unsigned char* halo)
+{
+    constexpr int CPP = CIN / 8;
+    const int y = tile / tiles_x, x0 = (tile - y * tiles_x) * TP;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        int gy = y - 1 + r;
+        gy = gy < 0 ? gy + a.H : (gy >= a.H ? gy - a.H : gy);
+        const __nv_bfloat16* row = a.in + (long long)gy * a.W * CIN;
+        for (int v = threadIdx.x; v < CPP * HP; v += NTHR_TC) {
+            const int ch = v / HP, px = v - ch * HP;
+            int gx = x0 - 1 + px;
+            gx = gx < 0 ? gx + a.W : (gx >= a.W ? gx - a.W : gx);
+            cp16(halo + ((r * CPP + ch) * HP + px) * 16, row + (long long)gx * CIN + ch * 8);
+        }
+    }
+}
+
+// COUT: channels stored (<= NC); the weight rows COUT .. NC-1 are zero.  Two
+// halo buffers: the next tile's halo is copied while the current tile's MMAs
+// and epilogue run.
+template <int CIN, int COUT, int NC, int MODE>
+__global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, int* err)
+{
+    using L = TcSmem<CIN, NC>;
+    constexpr int CPP = L::CPP, NG = L::NG;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* halo[2] = {smem, smem + L::HALO_BYTES};
+    unsigned char* wts = smem + 2 * L::HALO_BYTES;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 2 * L::HALO_BYTES + L::W_BYTES);
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem + 2 * L::HALO_BYTES + L::W_BYTES + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // weights: 16-byte chunks (o, tap, chunk) of the [COUT][9][CIN] layout
+    for (int v = tid; v < NC * 9 * CPP; v += NTHR_TC) {
+        const int o = v / (9 * CPP), rem = v - o * 9 * CPP, tap = rem / CPP, ch = rem - tap * CPP;
+        unsigned char* dst = wts + ((tap * CPP + ch) * NG + (o >> 3)) * 128 + (o & 7) * 16;
+        if (o < COUT) cp16(dst, a.w + ((long long)o * 9 + tap) * CIN + ch * 8);
+        else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+    }
+    const int tiles_x = (a.W + TP - 1) / TP, ntiles = tiles_x * a.H;
+    if ((int)blockIdx.x < ntiles) stage_halo_tc<CIN>(a, blockIdx.x, tiles_x, halo[0]);
+    asm volatile("cp.async.commit_group;" ::: "memory");   // group 0: weights and the first halo
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;"
+                     :: "r"(smem_u32(tmem_slot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) mbar_init_tc(bar);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+    const unsigned wbase = smem_u32(wts);
+    constexpr unsigned IDESC = idesc_bf16(NC);
+
+    unsigned phase = 0;
+    int buf = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+        const int y = tile / tiles_x, x0 = (tile - y * tiles_x) * TP;
+        // the next tile's halo streams into the other buffer meanwhile
+        const int next = tile + gridDim.x;
+        if (next < ntiles) stage_halo_tc<CIN>(a, next, tiles_x, halo[buf ^ 1]);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's group has landed
+        // make the generic-proxy writes visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned hbase = smem_u32(halo[buf]);
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap - dy * 3;
+#pragma unroll
+                for (int ks = 0; ks < CPP / 2; ++ks) {
+                    const unsigned aaddr = hbase + ((dy * CPP + 2 * ks) * HP + dx) * 16;
+                    const unsigned baddr = wbase + ((tap * CPP + 2 * ks) * NG) * 128;
+                    mma_bf16_tc(tmem, smem_desc(aaddr, HP * 16, 128), smem_desc(baddr, NG * 128, 128), IDESC,
+                                (tap | ks) != 0);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(bar)) : "memory");
+        }
+        __syncwarp();
+        const bool done = mbar_wait_tc(bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!done)) {   // the accumulator never arrived: report, do not read it
+            if (tid == 0) atomicExch(err, 1);
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: this thread's pixel, all NC accumulator columns
+        float acc[NC];
+        {
+            unsigned r[NC];
+            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16);
+            if constexpr (NC == 32) {
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                               "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                               "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                               "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                             : "r"(taddr) : "memory");
+            } else {
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                               "=r"(r[14]), "=r"(r[15])
+                             : "r"(taddr) : "memory");
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int o = 0; o < NC; ++o) acc[o] = __uint_as_float(r[o]);
+        }
+        // the accumulator may be overwritten by the next tile's MMAs once every warp has read it
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        const int gx = x0 + tid;
+        if (gx < a.W) {
+            const long long pix = (long long)y * a.W + gx;
+            if (MODE == MODE_LINEAR_F32) {
+                float* out = reinterpret_cast<float*>(a.out) + pix * COUT;
+#pragma unroll
+                for (int o = 0; o < COUT; o += 4)
+                    *reinterpret_cast<float4*>(out + o) =
+                        make_float4(acc[o] + a.bias[o], acc[o + 1] + a.bias[o + 1], acc[o + 2] + a.bias[o + 2],
+                                    acc[o + 3] + a.bias[o + 3]);
+            } else {
+                __align__(16) __nv_bfloat162 ov[COUT / 2];
+#pragma unroll
+                for (int o = 0; o < COUT; o += 2) {
+                    float v0 = acc[o], v1 = acc[o + 1];
+                    if (MODE == MODE_RELU) {
+                        if (a.bias) { v0 += a.bias[o]; v1 += a.bias[o + 1]; }
+                        v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f);
+                    } else {   // MODE_MASK: keep where the layer's activation is positive
+                        const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + pix * COUT + o);
+                        if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                        if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                    }
+                    ov[o / 2] = __floats2bfloat162_rn(v0, v1);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + pix * COUT);
+#pragma unroll
+                for (int q = 0; q < COUT / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(ov)[q];
+            }
+        }
+        __syncthreads();   // accumulator read and this halo buffer consumed before they are reused
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy is left in flight
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" :: "r"(tmem) : "memory");
+}
+}  // namespace tcv
+
 // ---- weight gradient: dW[o][tap][c] = sum_p dY[p][o] X[p + tap][c] ---------------
 struct DwArgs {
     const __nv_bfloat16* dy;   // [H*W][MO]
@@ -445,15 +677,20 @@ __global__ void export_paired_kernel(const float* __restrict__ u0, Layout L, flo
     }
 }
 
-// Per-block partial sums of the 6 output channels (fixed order; the final sum is
-// taken in add_correction_kernel's prologue by every block, in the same order).
-__global__ void pred_sum_kernel(const float* __restrict__ pred, long long n, float* __restrict__ part)
+// The network output applied to the state, limited to [-clip, clip] (units of
+// out_scale) when clip > 0.
+__device__ __forceinline__ float limited(float v, float clip) { return clip > 0.f ? fminf(fmaxf(v, -clip), clip) : v; }
+
+// Per-block partial sums of the 6 (limited) output channels (fixed order; the
+// final sum is taken in add_correction_kernel's prologue by every block, in the
+// same order).
+__global__ void pred_sum_kernel(const float* __restrict__ pred, long long n, float clip, float* __restrict__ part)
 {
     __shared__ float red[6][NTHR / 32];
     float s[6] = {0, 0, 0, 0, 0, 0};
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
 #pragma unroll
-        for (int c = 0; c < 6; ++c) s[c] += pred[p * 8 + c];
+        for (int c = 0; c < 6; ++c) s[c] += limited(pred[p * 8 + c], clip);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         float x = s[c];
@@ -468,12 +705,13 @@ __global__ void pred_sum_kernel(const float* __restrict__ pred, long long n, flo
     }
 }
 
-// u += out_scale * (pred - mean(pred)) on the interior and on every periodic ghost
-// copy: the correction is conservative (it moves no mass, momentum, energy or flux
-// in or out of the periodic domain, as the fine and coarse runs conserve them).
+// u += out_scale * (p - mean(p)), p = the limited network output, on the interior
+// and on every periodic ghost copy: the correction is conservative (it moves no
+// mass, momentum, energy or flux in or out of the periodic domain, as the fine
+// and coarse runs conserve them).
 __global__ void add_correction_kernel(float* __restrict__ u0, Layout L, const float* __restrict__ pred,
                                       const float* __restrict__ out_scale, const float* __restrict__ part,
-                                      int nblk, DevScalars* sc)
+                                      int nblk, float clip, DevScalars* sc)
 {
     __shared__ float mean[6];
     if (threadIdx.x < 6) {
@@ -489,7 +727,7 @@ __global__ void add_correction_kernel(float* __restrict__ u0, Layout L, const fl
         const long long r = v - (long long)f * ex * ey;
         const int j = (int)(r / ex) - GY, i = (int)(r % ex) - GY;
         const int si = wrapm(i, L.nx), sj = wrapm(j, L.ny);
-        u0[L.idx(f, i, j, false)] += out_scale[f] * (pred[((long long)sj * L.nx + si) * 8 + f] - mean[f]);
+        u0[L.idx(f, i, j, false)] += out_scale[f] * (limited(pred[((long long)sj * L.nx + si) * 8 + f], clip) - mean[f]);
     }
 }
 
@@ -535,6 +773,9 @@ int grid_n(long long n, int cap) { long long g = (n + 255) / 256; return (int)(g
 
 struct sac_cnn {
     int H = 0, W = 0, device = 0, nsm = 148, conv_grid = 0;
+    int tensor_path = 0;                // 1: tcgen05 convolutions, 0: mma.sync convolutions
+    float clip = 0.f;                   // > 0: sac_cnn_apply limits the output to [-clip, clip]
+    int* tc_err = nullptr;              // device flag: a tcgen05 accumulator wait gave up
     cudaStream_t stream = nullptr;
     float* params = nullptr;      // FP32 master [kParams]
     float* grads = nullptr;       // [kParams]
@@ -577,13 +818,26 @@ static int cfail(sac_cnn* c, int code, const char* fmt, ...)
                          "%s failed: %s", #call, cudaGetErrorString(e_));                 \
     } while (0)
 
+// The convolutions run on the tcgen05 kernel (N = COUT rounded up to 16);
+// the mma.sync kernel stays as the timed baseline (sac_cnn_set_tensor_path).
 template <int CIN, int COUT, int MODE>
 static cudaError_t run_conv(sac_cnn* c, const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, void* out,
                             const __nv_bfloat16* mask)
 {
     ConvArgs a;
     a.in = in; a.w = w; a.bias = bias; a.out = out; a.mask = mask; a.H = c->H; a.W = c->W;
-    conv3x3_kernel<CIN, COUT, MODE><<<c->conv_grid, NTHR, conv_smem<CIN, COUT>(), c->stream>>>(a);
+    if (c->tensor_path == 1) {
+        constexpr int NC = COUT < 16 ? 16 : COUT;
+        // resident CTAs per SM as the shared memory allows (two halo buffers each)
+        constexpr int per_sm = (227 * 1024) / tcv::TcSmem<CIN, NC>::BYTES < 8 ? (227 * 1024) / tcv::TcSmem<CIN, NC>::BYTES : 8;
+        const int tiles = ((c->W + tcv::TP - 1) / tcv::TP) * c->H;
+        const int cap = per_sm * c->nsm;
+        const int grid = tiles < cap ? tiles : cap;
+        tcv::conv3x3_tc_kernel<CIN, COUT, NC, MODE>
+            <<<grid, tcv::NTHR_TC, tcv::TcSmem<CIN, NC>::BYTES, c->stream>>>(a, c->tc_err);
+    } else {
+        conv3x3_kernel<CIN, COUT, MODE><<<c->conv_grid, NTHR, conv_smem<CIN, COUT>(), c->stream>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -659,6 +913,12 @@ static cudaError_t conv_attr()
     return cudaFuncSetAttribute(conv3x3_kernel<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)conv_smem<CIN, COUT>());
 }
+template <int CIN, int COUT, int NC, int MODE>
+static cudaError_t tc_attr()
+{
+    return cudaFuncSetAttribute(tcv::conv3x3_tc_kernel<CIN, COUT, NC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tcv::TcSmem<CIN, NC>::BYTES);
+}
 template <int CIN, int MO>
 static cudaError_t dw_attr()
 {
@@ -680,7 +940,7 @@ void sac_cnn_free(sac_cnn* c)
     for (int k = 0; k < NLAYER; ++k) { cudaFree(c->wf[k]); cudaFree(c->wt[k]); cudaFree(c->bias[k]); }
     cudaFree(c->feat); for (int k = 0; k < 3; ++k) { cudaFree(c->act[k]); cudaFree(c->dact[k]); }
     cudaFree(c->pred); cudaFree(c->dy3); cudaFree(c->part); cudaFree(c->dbpart); cudaFree(c->loss_part);
-    cudaFree(c->state); cudaFree(c->in_scale); cudaFree(c->out_scale);
+    cudaFree(c->state); cudaFree(c->in_scale); cudaFree(c->out_scale); cudaFree(c->tc_err);
     delete c;
 }
 
@@ -713,6 +973,7 @@ int sac_cnn_init(int nx, int ny, int device, void* stream, sac_cnn** out)
         A((void**)&c->loss_part, 1024 * 4);
         A((void**)&c->state, P * NF * 4);
         A((void**)&c->in_scale, 8 * 4); A((void**)&c->out_scale, 6 * 4);
+        A((void**)&c->tc_err, 4);
         if (!ok) { rc = cfail(c, SAC_ERR_OOM, "network buffers"); break; }
         cudaError_t e = conv_attr<16, 32, MODE_RELU>();
         if (e == cudaSuccess) e = conv_attr<32, 32, MODE_RELU>();
@@ -722,6 +983,11 @@ int sac_cnn_init(int nx, int ny, int device, void* stream, sac_cnn** out)
         if (e == cudaSuccess) e = dw_attr<32, 16>();
         if (e == cudaSuccess) e = dw_attr<32, 32>();
         if (e == cudaSuccess) e = dw_attr<16, 32>();
+        if (e == cudaSuccess) e = tc_attr<16, 32, 32, MODE_RELU>();
+        if (e == cudaSuccess) e = tc_attr<32, 32, 32, MODE_RELU>();
+        if (e == cudaSuccess) e = tc_attr<32, 8, 16, MODE_LINEAR_F32>();
+        if (e == cudaSuccess) e = tc_attr<16, 32, 32, MODE_MASK>();
+        if (e == cudaSuccess) e = tc_attr<32, 32, 32, MODE_MASK>();
         if (e != cudaSuccess) { rc = cfail(c, SAC_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e)); break; }
         const float ones[8] = {1, 1, 1, 1, 1, 1, 1, 1};
         if (cudaMemcpy(c->in_scale, ones, 32, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -731,6 +997,36 @@ int sac_cnn_init(int nx, int ny, int device, void* stream, sac_cnn** out)
     } while (0);
     if (rc != SAC_OK) { sac_cnn_free(c); return rc; }
     *out = c;
+    return SAC_OK;
+}
+
+int sac_cnn_set_tensor_path(sac_cnn* c, int path)
+{
+    if (!c || (path != 0 && path != 1)) return SAC_ERR_ARG;
+    CC(cudaSetDevice(c->device));
+    CC(cudaStreamSynchronize(c->stream));
+    c->tensor_path = path;
+    return SAC_OK;
+}
+
+int sac_cnn_set_clip(sac_cnn* c, double clip)
+{
+    if (!c || !(clip >= 0.0) || !std::isfinite(clip)) return SAC_ERR_ARG;
+    c->clip = (float)clip;
+    return SAC_OK;
+}
+
+int sac_cnn_sync(sac_cnn* c)
+{
+    if (!c) return SAC_ERR_ARG;
+    CC(cudaSetDevice(c->device));
+    int h = 0;
+    CC(cudaMemcpyAsync(&h, c->tc_err, 4, cudaMemcpyDeviceToHost, c->stream));
+    CC(cudaStreamSynchronize(c->stream));
+    if (h) {
+        CC(cudaMemsetAsync(c->tc_err, 0, 4, c->stream));
+        return cfail(c, SAC_ERR_TIMEOUT, "a tensor-core accumulator wait gave up");
+    }
     return SAC_OK;
 }
 
@@ -822,11 +1118,11 @@ int sac_cnn_apply(sac_ctx* ctx, sac_cnn* c)
     CC(cudaGetLastError());
     CC(forward_all(c, c->state, ctx->p.gamma, ctx->dx, ctx->dy));
     const int nsum = 148;
-    pred_sum_kernel<<<nsum, NTHR, 0, c->stream>>>(c->pred, P, c->loss_part);
+    pred_sum_kernel<<<nsum, NTHR, 0, c->stream>>>(c->pred, P, c->clip, c->loss_part);
     CC(cudaGetLastError());
     const long long ng = (long long)NF * (ctx->p.nx + 2 * GY) * (ctx->p.ny + 2 * GY);
     add_correction_kernel<<<grid_n(ng, 4096), 256, 0, c->stream>>>(u0, ctx->L, c->pred, c->out_scale, c->loss_part,
-                                                                   nsum, ctx->sc);
+                                                                   nsum, c->clip, ctx->sc);
     CC(cudaGetLastError());
     cmax_paired_kernel<<<grid_n(P, 2048), NTHR, 0, c->stream>>>(u0, ctx->L, (float)ctx->p.gamma, ctx->sc);
     CC(cudaGetLastError());

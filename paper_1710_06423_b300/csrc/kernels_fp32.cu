@@ -76,6 +76,8 @@ namespace {
 
 __global__ void halo_fp32(const StageArgs<float> a, long long n)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     if (a.sc->skip) return;
     float2* w = reinterpret_cast<float2*>(a.sout);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
@@ -91,13 +93,15 @@ cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
     CUtensorMap tm;
     const cudaError_t te = encode_stage_tensor_map(a, &tm);
     if (te != cudaSuccess) return te;
-    f32k::stage_fp32<G, S, BG, HD, GR, SF><<<grid, G::NT, sizeof(f32k::Smem<G>), s>>>(a, ntx, ntiles, tm);
-    if (a.bc_x != BC_FIXED || a.bc_y != BC_FIXED) {
+    // both kernels may be scheduled while their predecessor runs (see pdl_wait)
+    cudaError_t e = launch_pdl(f32k::stage_fp32<G, S, BG, HD, GR, SF>, dim3(grid), dim3(G::NT), sizeof(f32k::Smem<G>),
+                               s, a, ntx, ntiles, tm);
+    if (e == cudaSuccess && (a.bc_x != BC_FIXED || a.bc_y != BC_FIXED)) {
         const long long n = f32k::halo_count(a.L);
         const int hb = (int)std::min<long long>((n + 255) / 256, 4 * g_nsm);
-        halo_fp32<<<hb, 256, 0, s>>>(a, n);
+        e = launch_pdl(halo_fp32, dim3(hb), dim3(256), 0, s, a, n);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 template <class G, bool BG, bool HD, bool GR = false, bool SF = false>

@@ -128,6 +128,8 @@ __global__ void control_kernel(DevScalars* sc, double t_end)
 __global__ void begin_step_kernel(DevScalars* sc, double dx, double dy, double courant, int fp32,
                                   double dt_override)
 {
+    pdl_launch_dependents();
+    pdl_wait();
     step_begin(sc, dx, dy, courant, fp32, dt_override);
 }
 
@@ -370,8 +372,11 @@ static cudaError_t enqueue_stages(sac_ctx* c, cudaStream_t s)
 static cudaError_t enqueue_step(sac_ctx* c, cudaStream_t s, double dt_override)
 {
     const double dx = c->dx, dy = c->dy;
-    begin_step_kernel<<<1, 1, 0, s>>>(c->sc, dx, dy, c->p.courant, c->fp32 ? 1 : 0, dt_override);
-    cudaError_t e = cudaGetLastError();
+    // FP32: the step-control kernel and the stage kernels overlap their launches (pdl_wait)
+    cudaError_t e = c->fp32 ? launch_pdl(begin_step_kernel, dim3(1), dim3(1), 0, s, c->sc, dx, dy, c->p.courant, 1,
+                                         dt_override)
+                            : (begin_step_kernel<<<1, 1, 0, s>>>(c->sc, dx, dy, c->p.courant, 0, dt_override),
+                               cudaGetLastError());
     if (e != cudaSuccess) return e;
     return enqueue_stages(c, s);
 }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace sac {
 
 constexpr int NF = 6;   // conserved perturbation fields: rho~, m_x, m_y, e~, B~x, B~y
@@ -68,6 +70,35 @@ struct DevScalars {
     float fdt[4];             // FP32 kernels: dt/2, dt, dt/3, dt/6 of the current step (rounded once)
     float fcmax[2];           // FP32 kernels: cmax_step rounded to float
 };
+
+// Programmatic dependent launch (kernels launched with the programmatic
+// stream-serialisation attribute): launch_dependents lets the next kernel in the
+// stream be scheduled while this one runs; wait blocks until the previous
+// kernel has completed and its memory is visible.  A kernel calls wait before it
+// reads anything an earlier kernel wrote, so the order of results is that of a
+// plain stream; only the launch latency between kernels overlaps.  Both are
+// no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch `kernel` on stream s with the programmatic stream-serialisation
+// attribute (see pdl_wait).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 __device__ __forceinline__ double decode_speed(unsigned long long b, int fp32)
 {

@@ -835,6 +835,8 @@ template <class G, int STAGE, bool BG, bool HD, bool GRAV, bool SF = false>
 __global__ void __launch_bounds__(G::NT, G::MINB) stage_fp32(const StageArgs<float> a, const int ntx, const int ntiles,
                                                              const __grid_constant__ CUtensorMap tm)
 {
+    pdl_launch_dependents();
+    pdl_wait();   // the previous kernel's output (stage input, scalars) is complete
     if (a.sc->skip || a.sc->status != ST_OK) return;   // skipped step, or an earlier stage gave up
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ unsigned long long red[2][G::NW];

@@ -35,16 +35,22 @@ OPPOSITE = {LEFT: RIGHT, RIGHT: LEFT, BOTTOM: TOP, TOP: BOTTOM}
 HALO = 3    # cells each stage reads beyond its own (the stencil reach, section 2)
 
 
-def split(n: int, parts: int) -> list[tuple[int, int]]:
-    """(start, count) of `parts` nearly equal pieces of n cells (the first ones
-    one cell longer when n does not divide)."""
-    base, extra = divmod(n, parts)
-    out, s = [], 0
-    for k in range(parts):
-        c = base + (1 if k < extra else 0)
-        out.append((s, c))
-        s += c
-    return out
+ALIGN = 4  # block origins are multiples of the stage kernel's 4-cell sweep segment
+
+
+def split(n: int, parts: int, align: int = ALIGN) -> list[tuple[int, int]]:
+    """(start, count) of `parts` nearly equal pieces of n cells whose inner
+    boundaries are multiples of `align` (the nearest multiple of align to
+    k n / parts).
+
+    The FP32 stage kernel sweeps each row and column in 4-cell segments, and a
+    cell's last-place rounding can depend on its position inside its segment
+    (measured: one cell in ~6400 differs by one unit in the last place when the
+    grid is shifted by a cell count that is not a multiple of 4).  Aligning every
+    block to the segment length keeps each cell where the undivided grid has
+    it, so the decomposed run stays bit-for-bit the single-grid run."""
+    bounds = [0] + [int(round(k * n / parts / align)) * align for k in range(1, parts)] + [n]
+    return [(bounds[k], bounds[k + 1] - bounds[k]) for k in range(parts)]
 
 
 @dataclass(frozen=True)

@@ -35,7 +35,8 @@ EXPORTS = (
     "sac_batch_init", "sac_batch_free", "sac_batch_last_error", "sac_batch_set_state",
     "sac_batch_get_state", "sac_batch_steps", "sac_batch_sync", "sac_batch_time", "sac_batch_tune",
     "sac_batch_set_config", "sac_batch_set_tile", "sac_batch_get_config",
-    "sac_cnn_param_count", "sac_cnn_init", "sac_cnn_free", "sac_cnn_last_error", "sac_cnn_set_params",
+    "sac_cnn_param_count", "sac_cnn_init", "sac_cnn_free", "sac_cnn_last_error", "sac_cnn_set_tensor_path",
+    "sac_cnn_set_clip", "sac_cnn_sync", "sac_cnn_set_params",
     "sac_cnn_get_params", "sac_cnn_set_scales", "sac_cnn_forward", "sac_cnn_grads", "sac_cnn_train_step",
     "sac_cnn_apply", "sac_cnn_perturb", "sac_block_average",
     "sac_step_noalloc",
@@ -149,6 +150,9 @@ def load() -> ctypes.CDLL:
         "sac_cnn_init": (i, [i, i, i, vp, ctypes.POINTER(vp)]),
         "sac_cnn_free": (None, [vp]),
         "sac_cnn_last_error": (ctypes.c_char_p, [vp]),
+        "sac_cnn_set_tensor_path": (i, [vp, i]),
+        "sac_cnn_set_clip": (i, [vp, d]),
+        "sac_cnn_sync": (i, [vp]),
         "sac_cnn_set_params": (i, [vp, ctypes.POINTER(ctypes.c_float), L]),
         "sac_cnn_get_params": (i, [vp, ctypes.POINTER(ctypes.c_float), L]),
         "sac_cnn_set_scales": (i, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
@@ -524,6 +528,17 @@ class CNN:
             self.close()
         except Exception:
             pass
+
+    def set_tensor_path(self, path: int):
+        """1: tcgen05 convolutions; 0: mma.sync convolutions."""
+        self._check(load().sac_cnn_set_tensor_path(self._c, int(path)), "sac_cnn_set_tensor_path")
+
+    def sync(self):
+        self._check(load().sac_cnn_sync(self._c), "sac_cnn_sync")
+
+    def set_clip(self, clip: float):
+        """Limit applied corrections to clip residual scales per field and step (0: off)."""
+        self._check(load().sac_cnn_set_clip(self._c, float(clip)), "sac_cnn_set_clip")
 
     def set_params(self, flat):
         flat = np.ascontiguousarray(flat, dtype=np.float32)

@@ -68,14 +68,18 @@ def test_decomposed_oracle_run_equals_single_grid(oracle_mod, inputs_mod, px, py
 
 def test_process_grid_neighbours_and_split():
     from paper_1710_06423_b300 import decomp
-    g = decomp.ProcessGrid(10, 9, 3, 2)
-    assert [c for _, c in g.xs] == [4, 3, 3] and [c for _, c in g.ys] == [5, 4]
+    g = decomp.ProcessGrid(30, 9, 3, 2)
+    # inner block boundaries on multiples of the 4-cell sweep segment
+    assert g.xs == [(0, 8), (8, 12), (20, 10)] and g.ys == [(0, 4), (4, 5)]
     assert g.neighbor(0, decomp.LEFT) == 2 and g.neighbor(2, decomp.RIGHT) == 0
     assert g.neighbor(1, decomp.BOTTOM) == 4 and g.neighbor(4, decomp.TOP) == 1
     assert g.phases() == [(decomp.LEFT, decomp.RIGHT), (decomp.BOTTOM, decomp.TOP)]
-    w = np.arange(6 * 9 * 10, dtype=float).reshape(6, 9, 10)
+    w = np.arange(6 * 9 * 30, dtype=float).reshape(6, 9, 30)
     assert np.array_equal(g.gather({r: g.scatter(w, r) for r in range(6)}), w)
+    for n, parts in ((97, 2), (130, 3), (26, 4), (1000, 7)):
+        sp = decomp.split(n, parts)
+        assert sum(c for _, c in sp) == n and all(s0 % 4 == 0 for s0, _ in sp)
     with pytest.raises(ValueError):
-        decomp.ProcessGrid(5, 8, 2, 1)          # a block of 2 cells cannot feed a 3-cell halo
+        decomp.ProcessGrid(6, 8, 2, 1)          # a block of 2 cells cannot feed a 3-cell halo
     with pytest.raises(ValueError):
         g.local_bc(1, 0)                        # a split direction must be periodic

@@ -212,18 +212,20 @@ def _forward_ok(got, ref):
     return r.max() <= 0.25 and col.max() <= 5e-3 and row.max() <= 5e-3 and tiles.max() <= 1e-2
 
 
-def test_forward_elementwise_multi_tile(multitile):
+@pytest.mark.parametrize("path", [0, 1], ids=["mma_sync", "tcgen05"])
+def test_forward_elementwise_multi_tile(multitile, path):
     import torch
     from oracle import cnn as ocnn
     from paper_1710_06423_b300.sac import CNN
     nx, ny, w, g, flat, params64, _, x = multitile
     net = CNN(nx, ny)
+    net.set_tensor_path(path)
     net.set_params(flat)
     net.set_scales(SCALES, np.ones(6))
     wd = torch.from_numpy(w.astype(np.float32)).cuda().contiguous()
     pred = torch.zeros((ny * nx, 8), dtype=torch.float32, device="cuda")
     net.forward(wd, g, 1.0 / nx, 1.0 / ny, pred)
-    torch.cuda.synchronize()
+    net.sync()
     net.close()
     got = pred.cpu().numpy()[:, :6].T.reshape(6, ny, nx).astype(np.float64)
     ref, _ = ocnn.forward_bf16(params64, x)
@@ -240,18 +242,21 @@ def test_forward_elementwise_multi_tile(multitile):
     assert not _forward_ok(got, bad)
 
 
-def test_gradients_elementwise_multi_tile(multitile):
+@pytest.mark.parametrize("path", [0, 1], ids=["mma_sync", "tcgen05"])
+def test_gradients_elementwise_multi_tile(multitile, path):
     import torch
     from oracle import cnn as ocnn
     from paper_1710_06423_b300.sac import CNN
     nx, ny, w, g, flat, params64, target, x = multitile
     net = CNN(nx, ny)
+    net.set_tensor_path(path)
     net.set_params(flat)
     net.set_scales(SCALES, np.ones(6))
     w32 = w.astype(np.float32)
     wd = torch.from_numpy(w32).cuda().contiguous()
     nd = torch.from_numpy((w32 + target).astype(np.float32)).cuda().contiguous()
     loss, grads = net.grads(wd, nd, g, 1.0 / nx, 1.0 / ny)
+    net.sync()
     net.close()
     # the target the GPU forms: (next - w) / out_scale in FP32, out_scale = 1
     tgt = ((w32 + target).astype(np.float32) - w32).astype(np.float64)
