@@ -44,8 +44,8 @@ MODEL_BYTES_PER_CELL_STAGE = 96
 # per RK register), with the SHA-256 of the FP32 stage sources at the time of that
 # capture: when the sources differ, the figures no longer describe the kernel and
 # `roofline.traffic` is reported as null.
-STAGE_TRAFFIC_B_PER_CELL_FP32 = (45.6, 93.8, 120.2, 97.6)
-STAGE_TRAFFIC_SOURCES_SHA = None
+STAGE_TRAFFIC_B_PER_CELL_FP32 = (46.0, 94.3, 120.3, 98.2)
+STAGE_TRAFFIC_SOURCES_SHA = "7bee94cb8581bdda"
 STAGE_SOURCES = ("stage_fp32.cuh", "kernels_fp32.cu", "speed.cuh", "sac_internal.cuh")
 
 
@@ -331,50 +331,68 @@ def run_batched(args, ws, local, pg, torch, per_size=True):
             "per_size": per_size_res, "gpu_launches": LAUNCHES_PER_STEP * args.batch_steps}
 
 
-def run_learned(args, local):
-    """Learned 1000^2 coarse run vs plain FP32 runs at equal L1 error against the
-    block-averaged 4000^2 plain run (Orszag-Tang family, horizon t_end)."""
+def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=6000, noise=1.0, alpha=0.5,
+                       clip=3.0, keep_positive=True, plain_sizes=None, pairs_per_member=100, tensor_path=0,
+                       rounds=1):
+    """Learned nc^2 coarse run vs plain FP32 runs at equal L1 error against the
+    block-averaged (ratio nc)^2 plain run (Orszag-Tang family, horizon t_end);
+    returns the result record."""
     import torch
     from paper_1710_06423_b300 import learned
     from paper_1710_06423_b300.sac import CNN, FP32, SacError, Solver
     torch.cuda.set_device(local)
-    nc, ratio = 1000, 4
     nf = nc * ratio
     dx = 1.0 / nc
     dt_c = 0.25 * dx / 3.0                      # fixed coarse step: Courant 0.25 at a signal speed of 3
-    steps = int(round(args.t_end / dt_c))
-    every = max(1, steps // 200)
+    steps = int(round(t_end / dt_c))
+    every = max(1, steps // pairs_per_member)
     # shock viscosity 4 (default 0.5): with 0.5 the family's 2000^2-4000^2 runs turn
     # non-finite before t = 0.5 (in FP64 as in FP32), with 2 one member still does at
     # 4000^2; every run of this experiment uses the same value
     kw = dict(c_shk=4.0)
     t0 = time.perf_counter()
     pairs = learned.Pairs()
-    train_members = (0, 1, 2)
     completed = {}
     for k in train_members:
         completed[k] = learned.generate_pairs(pairs, 2024, k, nc, ratio, dt_c, steps, every, torch, solver_kw=kw)
     t_data = time.perf_counter() - t0
     osc = learned.out_scales(pairs, torch)
     net = CNN(nc, nc)
+    net.set_tensor_path(tensor_path)
     net.set_params(learned.init_params(1))
     net.set_scales(learned.FEATURE_SCALES, osc)
     t0 = time.perf_counter()
     # noise-injected training (inputs perturbed by out_scale * U[-1,1) every other step)
-    losses = learned.train(net, pairs, osc, dx, iters=3000, lr=1e-3, torch=torch, log_every=500, noise=1.0)
+    losses = learned.train(net, pairs, osc, dx, iters=iters, lr=1e-3, torch=torch, log_every=max(1, iters // 6),
+                           noise=noise)
+    n_pairs, agg_pairs = len(pairs), []
+    # dataset aggregation: pairs on the corrected run's own states, then more training
+    for r in range(rounds):
+        net.set_scales(learned.FEATURE_SCALES, osc * alpha)
+        net.set_limiter(clip, keep_positive)
+        agg = learned.rollout_pairs(net, pairs, 2024, train_members, nc, ratio, dt_c, torch, solver_kw=kw)
+        net.set_scales(learned.FEATURE_SCALES, osc)
+        net.set_limiter(0.0, False)
+        # states the corrected run reached far from the fine solution carry residuals
+        # many times out_scale; those pairs would dominate the loss: keep the pairs
+        # whose loss is within a few times the loss on the fine-started pairs
+        ref = np.median(learned.pair_losses(net, pairs, dx))
+        agg = learned.select(agg, learned.pair_losses(net, agg, dx) <= 4.0 * ref)
+        agg_pairs.append(len(agg))
+        losses += learned.train(net, learned.merged(pairs, agg), osc, dx, iters=iters, lr=5e-4, torch=torch,
+                                log_every=max(1, iters // 6), noise=noise, seed=r + 1)
+        del agg
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     del pairs
     torch.cuda.empty_cache()
-    held_pairs = learned.Pairs()                # one-step gain on the held-out member (first fifth of the horizon)
-    learned.generate_pairs(held_pairs, 2024, 20, nc, ratio, dt_c, steps // 5, max(1, steps // 100), torch,
-                           solver_kw=kw)
+    held_pairs = learned.Pairs()                # one-step gain on the held-out member over the horizon
+    learned.generate_pairs(held_pairs, 2024, held, nc, ratio, dt_c, steps, max(1, steps // 20), torch, solver_kw=kw)
     held_gain = learned.residual_gain(net, held_pairs, osc, dx, torch)
     del held_pairs
-    alpha = 0.5                                  # relaxation of the applied correction
-    net.set_scales(learned.FEATURE_SCALES, osc * alpha)
+    net.set_scales(learned.FEATURE_SCALES, osc * alpha)   # relaxation of the applied correction
+    net.set_limiter(clip, keep_positive)
 
-    held = 20                                    # held-out family member
     w0f, gamma = learned.family_state(2024, held, nf)
     fine_out = torch.empty((6, nf, nf), dtype=torch.float32, device="cuda")
     with Solver(nx=nf, ny=nf, precision=FP32, gamma=gamma, **kw) as fine:
@@ -382,11 +400,12 @@ def run_learned(args, local):
         fine.set_fixed_dt(dt_c / ratio)
         fine.steps(steps * ratio)
         fine.get_state_dev(fine_out)
+        fine.sync()
     truth = learned.downsample(fine_out, nc, torch)
     del fine_out
     wf_dev = torch.from_numpy(w0f.astype(np.float32)).cuda().contiguous()
     curve, plain = [], {}
-    for n in (1000, 2000, 3000):
+    for n in plain_sizes or (nc, 2 * nc, 3 * nc):
         w0n = learned.downsample(wf_dev, n, torch) if nf % n == 0 else None
         if w0n is None:
             w0n_np, _ = learned.family_state(2024, held, n)
@@ -404,17 +423,26 @@ def run_learned(args, local):
         # the plain coarse solver is the fallback of the learned run
         fell_back = True
         out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, solver_kw=kw)
+    net.close()
     err = learned.l1_error(out, truth)
-    t_eq = learned.equal_error_time(curve, float(err.mean()))
-    res = {"metric": "learned-vs-plain time at equal L1 error", "t_end": args.t_end, "coarse": nc, "fine": nf,
-           "dt_coarse": dt_c, "steps_coarse": steps, "train_members": list(train_members), "held_out_member": held,
-           "c_shk": kw["c_shk"], "member_steps_completed": completed,
-           "pairs": int(sum(len(range(0, completed[k], every)) for k in train_members)), "data_seconds": t_data,
-           "train_seconds": t_train, "losses": losses, "noise": 1.0, "alpha": alpha,
-           "held_out_one_step_residual_ratio": held_gain,
-           "learned": {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec, "fell_back_to_plain": fell_back},
-           "plain": plain, "plain_time_at_learned_error": t_eq,
-           "speedup_at_equal_error": (t_eq / sec) if t_eq else None}
+    t_eq = None if fell_back else learned.equal_error_time(curve, float(err.mean()))
+    return {"metric": "learned-vs-plain time at equal L1 error", "t_end": t_end, "coarse": nc, "fine": nf,
+            "dt_coarse": dt_c, "steps_coarse": steps, "train_members": list(train_members), "held_out_member": held,
+            "c_shk": kw["c_shk"], "member_steps_completed": completed, "pairs": n_pairs, "data_seconds": t_data,
+            "train_iters": iters, "train_seconds": t_train, "losses": losses, "noise": noise, "alpha": alpha,
+            "aggregation_rounds": rounds, "aggregated_pairs": agg_pairs,
+            "limiter": {"clip": clip, "keep_positive": keep_positive},
+            "cnn_tensor_path": "tcgen05" if tensor_path == 1 else "mma.sync",
+            "held_out_one_step_residual_ratio": held_gain,
+            "learned": {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec,
+                        "fell_back_to_plain": fell_back},
+            "plain": plain, "plain_time_at_learned_error": t_eq,
+            "speedup_at_equal_error": (t_eq / sec) if t_eq else None}
+
+
+def run_learned(args, local):
+    """The full experiment: 1000^2 coarse from 4000^2 fine runs, horizon t_end."""
+    res = learned_experiment(local, 1000, 4, args.t_end, train_members=(0, 1, 2, 3, 4, 5))
     print(json.dumps(res), flush=True)
 
 
@@ -582,6 +610,13 @@ def run_ours(args, ws, rank, local, pg):
         extra["stratified_gravity"] = run_stratified(args, ws, local, pg, torch)
         extra["batched"] = run_batched(args, ws, local, pg, torch)
         extra["ot3d_256"] = run_3d(args, ws, local, pg, torch)
+        if ws == 1:
+            # the learned coarse-grid correction at a reduced scale (250^2 coarse from
+            # 1000^2 fine runs, horizon 0.5); --learned runs the 1000^2 / 4000^2 form
+            small = learned_experiment(local, 250, 4, 0.5, train_members=(0, 1, 2, 3, 4, 5), iters=3000,
+                                       plain_sizes=(250, 500, 750))
+            small["scale"] = "reduced: 250^2 coarse from 1000^2 fine (the full form is 1000^2 from 4000^2)"
+            extra["learned_250"] = small
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

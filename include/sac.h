@@ -391,11 +391,13 @@ const char *sac_cnn_last_error(const sac_cnn *c);
  * differ only in the order of the FP32 sums.  Waits for the stream.
  * Errors: SAC_ERR_ARG. */
 int sac_cnn_set_tensor_path(sac_cnn *c, int path);
-/* Limit of the correction sac_cnn_apply adds: clip > 0 clamps every network
- * output to [-clip, clip] before the mean is removed and out_scale applied (a
- * correction of at most clip residual scales per field and step); 0 (the
- * default) applies it unlimited.  Errors: SAC_ERR_ARG. */
-int sac_cnn_set_clip(sac_cnn *c, double clip);
+/* Limiter of the correction sac_cnn_apply adds (defaults: off).  clip > 0
+ * clamps every network output to [-clip, clip] (a correction of at most clip
+ * residual scales per field and step).  keep_positive = 1 drops the correction
+ * of a cell whose corrected density or kinetic pressure would fall below half
+ * of its value.  The per-field mean of the limited correction is removed, so
+ * the correction still conserves every periodic sum.  Errors: SAC_ERR_ARG. */
+int sac_cnn_set_limiter(sac_cnn *c, double clip, int keep_positive);
 /* Wait for the network's stream and report a tensor-core accumulator wait
  * that gave up (about one second; SAC_ERR_TIMEOUT, flag cleared). */
 int sac_cnn_sync(sac_cnn *c);

@@ -252,24 +252,26 @@ __device__ __forceinline__ bool mbar_wait_tc(unsigned long long* bar, unsigned p
     }
 }
 
+constexpr int ROWS = 4;   // image rows per tile: four independent 128 x NC accumulators
+
 template <int CIN, int NC>
 struct TcSmem {
     static constexpr int CPP = CIN / 8, NG = NC / 8;
-    static constexpr int HALO_BYTES = 3 * CPP * HP * 16;
+    static constexpr int HALO_BYTES = (ROWS + 2) * CPP * HP * 16;
     static constexpr int W_BYTES = 9 * CPP * NG * 128;
-    static constexpr int BYTES = 2 * HALO_BYTES + W_BYTES + 64;   // two halo buffers + mbarrier, TMEM address
+    static constexpr int BYTES = HALO_BYTES + W_BYTES + 64;   // + mbarrier, TMEM address
+    static constexpr int TMEM_COLS = ROWS * NC <= 32 ? 32 : (ROWS * NC <= 64 ? 64 : 128);
 };
 
-// Copy the halo of tile `tile` (rows y-1 .. y+1, pixels x0-1 .. x0+TP, periodic)
-// into one halo buffer with 16-byte cp.async; the caller commits the group.
+// Copy the halo of a tile (rows y0-1 .. y0+ROWS, pixels x0-1 .. x0+TP, periodic)
+// with 16-byte cp.async.
 template <int CIN>
-__device__ __forceinline__ void stage_halo_tc(const ConvArgs& a, int tile, int tiles_x, unsigned char* halo)
+__device__ __forceinline__ void stage_halo_tc(const ConvArgs& a, int y0, int x0, unsigned char* halo)
 {
     constexpr int CPP = CIN / 8;
-    const int y = tile / tiles_x, x0 = (tile - y * tiles_x) * TP;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        int gy = y - 1 + r;
+    for (int r = 0; r < ROWS + 2; ++r) {
+        int gy = y0 - 1 + r;
         gy = gy < 0 ? gy + a.H : (gy >= a.H ? gy - a.H : gy);
         const __nv_bfloat16* row = a.in + (long long)gy * a.W * CIN;
         for (int v = threadIdx.x; v < CPP * HP; v += NTHR_TC) {
@@ -281,19 +283,22 @@ __device__ __forceinline__ void stage_halo_tc(const ConvArgs& a, int tile, int t
     }
 }
 
-// COUT: channels stored (<= NC); the weight rows COUT .. NC-1 are zero.  Two
-// halo buffers: the next tile's halo is copied while the current tile's MMAs
-// and epilogue run.
+// COUT: channels stored (<= NC); the weight rows COUT .. NC-1 are zero.  A tile
+// is ROWS image rows x TP pixels: row q accumulates into tensor-memory columns
+// q*NC .. q*NC+NC-1, and its MMAs are issued interleaved with the other rows'
+// (independent accumulators keep the tensor pipe busy).  Rows past the image
+// (the last tile of a height that ROWS does not divide) are computed on wrapped
+// rows and not stored.
 template <int CIN, int COUT, int NC, int MODE>
 __global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, int* err)
 {
     using L = TcSmem<CIN, NC>;
     constexpr int CPP = L::CPP, NG = L::NG;
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* halo[2] = {smem, smem + L::HALO_BYTES};
-    unsigned char* wts = smem + 2 * L::HALO_BYTES;
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 2 * L::HALO_BYTES + L::W_BYTES);
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem + 2 * L::HALO_BYTES + L::W_BYTES + 8);
+    unsigned char* halo = smem;
+    unsigned char* wts = smem + L::HALO_BYTES;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + L::HALO_BYTES + L::W_BYTES);
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem + L::HALO_BYTES + L::W_BYTES + 8);
     const int tid = threadIdx.x, warp = tid >> 5;
 
     // weights: 16-byte chunks (o, tap, chunk) of the [COUT][9][CIN] layout
@@ -303,12 +308,9 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, i
         if (o < COUT) cp16(dst, a.w + ((long long)o * 9 + tap) * CIN + ch * 8);
         else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
     }
-    const int tiles_x = (a.W + TP - 1) / TP, ntiles = tiles_x * a.H;
-    if ((int)blockIdx.x < ntiles) stage_halo_tc<CIN>(a, blockIdx.x, tiles_x, halo[0]);
-    asm volatile("cp.async.commit_group;" ::: "memory");   // group 0: weights and the first halo
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;"
-                     :: "r"(smem_u32(tmem_slot)) : "memory");
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_slot)), "r"(L::TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) mbar_init_tc(bar);
@@ -316,33 +318,32 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, i
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
-    const unsigned wbase = smem_u32(wts);
+    const unsigned wbase = smem_u32(wts), hbase = smem_u32(halo);
     constexpr unsigned IDESC = idesc_bf16(NC);
 
+    const int tiles_x = (a.W + TP - 1) / TP, tiles_y = (a.H + ROWS - 1) / ROWS, ntiles = tiles_x * tiles_y;
     unsigned phase = 0;
-    int buf = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
-        const int y = tile / tiles_x, x0 = (tile - y * tiles_x) * TP;
-        // the next tile's halo streams into the other buffer meanwhile
-        const int next = tile + gridDim.x;
-        if (next < ntiles) stage_halo_tc<CIN>(a, next, tiles_x, halo[buf ^ 1]);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's group has landed
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int ty = tile / tiles_x, x0 = (tile - ty * tiles_x) * TP, y0 = ty * ROWS;
+        stage_halo_tc<CIN>(a, y0, x0, halo);
+        cp_wait();
         // make the generic-proxy writes visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned hbase = smem_u32(halo[buf]);
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
                 const int dy = tap / 3, dx = tap - dy * 3;
 #pragma unroll
                 for (int ks = 0; ks < CPP / 2; ++ks) {
-                    const unsigned aaddr = hbase + ((dy * CPP + 2 * ks) * HP + dx) * 16;
                     const unsigned baddr = wbase + ((tap * CPP + 2 * ks) * NG) * 128;
-                    mma_bf16_tc(tmem, smem_desc(aaddr, HP * 16, 128), smem_desc(baddr, NG * 128, 128), IDESC,
-                                (tap | ks) != 0);
+                    const unsigned long long bdesc = smem_desc(baddr, NG * 128, 128);
+#pragma unroll
+                    for (int q = 0; q < ROWS; ++q) {
+                        const unsigned aaddr = hbase + (((q + dy) * CPP + 2 * ks) * HP + dx) * 16;
+                        mma_bf16_tc(tmem + q * NC, smem_desc(aaddr, HP * 16, 128), bdesc, IDESC, (tap | ks) != 0);
+                    }
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -351,76 +352,81 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, i
         __syncwarp();
         const bool done = mbar_wait_tc(bar, phase);
         phase ^= 1u;
-        if (__syncthreads_or(!done)) {   // the accumulator never arrived: report, do not read it
+        if (__syncthreads_or(!done)) {   // the accumulators never arrived: report, do not read them
             if (tid == 0) atomicExch(err, 1);
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: this thread's pixel, all NC accumulator columns
-        float acc[NC];
-        {
-            unsigned r[NC];
-            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16);
-            if constexpr (NC == 32) {
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                               "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-                               "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-                               "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                             : "r"(taddr) : "memory");
-            } else {
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                               "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                               "=r"(r[14]), "=r"(r[15])
-                             : "r"(taddr) : "memory");
-            }
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-            for (int o = 0; o < NC; ++o) acc[o] = __uint_as_float(r[o]);
-        }
-        // the accumulator may be overwritten by the next tile's MMAs once every warp has read it
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         const int gx = x0 + tid;
-        if (gx < a.W) {
-            const long long pix = (long long)y * a.W + gx;
-            if (MODE == MODE_LINEAR_F32) {
-                float* out = reinterpret_cast<float*>(a.out) + pix * COUT;
-#pragma unroll
-                for (int o = 0; o < COUT; o += 4)
-                    *reinterpret_cast<float4*>(out + o) =
-                        make_float4(acc[o] + a.bias[o], acc[o + 1] + a.bias[o + 1], acc[o + 2] + a.bias[o + 2],
-                                    acc[o + 3] + a.bias[o + 3]);
-            } else {
-                __align__(16) __nv_bfloat162 ov[COUT / 2];
-#pragma unroll
-                for (int o = 0; o < COUT; o += 2) {
-                    float v0 = acc[o], v1 = acc[o + 1];
-                    if (MODE == MODE_RELU) {
-                        if (a.bias) { v0 += a.bias[o]; v1 += a.bias[o + 1]; }
-                        v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f);
-                    } else {   // MODE_MASK: keep where the layer's activation is positive
-                        const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + pix * COUT + o);
-                        if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
-                        if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
-                    }
-                    ov[o / 2] = __floats2bfloat162_rn(v0, v1);
+#pragma unroll 1
+        for (int q = 0; q < ROWS; ++q) {
+            // epilogue of row q: this thread's pixel, all NC accumulator columns
+            float acc[NC];
+            {
+                unsigned r[NC];
+                const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + q * NC;
+                if constexpr (NC == 32) {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                                   "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+                                   "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+                                   "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+                                   "=r"(r[31])
+                                 : "r"(taddr) : "memory");
+                } else {
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                                   "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                                 : "r"(taddr) : "memory");
                 }
-                uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + pix * COUT);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int q = 0; q < COUT / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(ov)[q];
+                for (int o = 0; o < NC; ++o) acc[o] = __uint_as_float(r[o]);
+            }
+            const int gy = y0 + q;
+            if (gx < a.W && gy < a.H) {
+                const long long pix = (long long)gy * a.W + gx;
+                if (MODE == MODE_LINEAR_F32) {
+                    float* out = reinterpret_cast<float*>(a.out) + pix * COUT;
+#pragma unroll
+                    for (int o = 0; o < COUT; o += 4)
+                        *reinterpret_cast<float4*>(out + o) =
+                            make_float4(acc[o] + a.bias[o], acc[o + 1] + a.bias[o + 1], acc[o + 2] + a.bias[o + 2],
+                                        acc[o + 3] + a.bias[o + 3]);
+                } else {
+                    __align__(16) __nv_bfloat162 ov[COUT / 2];
+#pragma unroll
+                    for (int o = 0; o < COUT; o += 2) {
+                        float v0 = acc[o], v1 = acc[o + 1];
+                        if (MODE == MODE_RELU) {
+                            if (a.bias) { v0 += a.bias[o]; v1 += a.bias[o + 1]; }
+                            v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f);
+                        } else {   // MODE_MASK: keep where the layer's activation is positive
+                            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + pix * COUT + o);
+                            if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                            if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+                        }
+                        ov[o / 2] = __floats2bfloat162_rn(v0, v1);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + pix * COUT);
+#pragma unroll
+                    for (int k = 0; k < COUT / 8; ++k) dst[k] = reinterpret_cast<const uint4*>(ov)[k];
+                }
             }
         }
-        __syncthreads();   // accumulator read and this halo buffer consumed before they are reused
+        // the accumulators and the halo are reused by the next tile once every warp is done
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy is left in flight
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" :: "r"(tmem) : "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::TMEM_COLS) : "memory");
 }
 }  // namespace tcv
 
@@ -667,13 +673,27 @@ __global__ void block_average_kernel(const float* __restrict__ fine, int nf, int
 }
 
 // ---- correction of a solver context ---------------------------------------------
+// fields of the three float2 planes of the FP32 layout: (rho, e), (m_x, m_y), (B_x, B_y)
+__device__ __forceinline__ void plane_fields(int p, int& f0, int& f1)
+{
+    f0 = p == 0 ? 0 : (p == 1 ? 1 : 4);
+    f1 = p == 0 ? 3 : (p == 1 ? 2 : 5);
+}
+
+// Packed [6][ny][nx] copy of the interior: one thread per (plane, cell), one
+// 8-byte read of the field pair, two 4-byte writes.
 __global__ void export_paired_kernel(const float* __restrict__ u0, Layout L, float* __restrict__ dst)
 {
     const long long n = (long long)L.nx * L.ny;
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n * NF; v += (long long)gridDim.x * blockDim.x) {
-        const int f = (int)(v / n);
-        const long long r = v - (long long)f * n;
-        dst[v] = u0[L.idx(f, (int)(r % L.nx), (int)(r / L.nx), false)];
+    const float2* w = reinterpret_cast<const float2*>(u0);
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < 3 * n; v += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(v / n);
+        const long long r = v - (long long)p * n;
+        const float2 q = w[p * L.fstride + L.at((int)(r % L.nx), (int)(r / L.nx))];
+        int f0, f1;
+        plane_fields(p, f0, f1);
+        dst[f0 * n + r] = q.x;
+        dst[f1 * n + r] = q.y;
     }
 }
 
@@ -681,16 +701,38 @@ __global__ void export_paired_kernel(const float* __restrict__ u0, Layout L, flo
 // out_scale) when clip > 0.
 __device__ __forceinline__ float limited(float v, float clip) { return clip > 0.f ? fminf(fmaxf(v, -clip), clip) : v; }
 
+// Limiter of the correction of cell p (positive != 0): 1 if the corrected cell
+// keeps at least half of its density and of its kinetic pressure
+// p_k = (gamma-1)(e - |m|^2/(2 rho) - |B|^2/2), else 0 (no correction there).
+__device__ __forceinline__ float keep_factor(const float* __restrict__ state, long long p, long long n,
+                                             const float* __restrict__ pred, const float* __restrict__ osc, float clip,
+                                             float gm1, int positive)
+{
+    if (!positive) return 1.f;
+    float u[NF], v[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        u[f] = state[f * n + p];
+        v[f] = u[f] + osc[f] * limited(pred[p * 8 + f], clip);
+    }
+    const float pk0 = gm1 * (u[3] - 0.5f * (u[1] * u[1] + u[2] * u[2]) / u[0] - 0.5f * (u[4] * u[4] + u[5] * u[5]));
+    const float pk1 = gm1 * (v[3] - 0.5f * (v[1] * v[1] + v[2] * v[2]) / v[0] - 0.5f * (v[4] * v[4] + v[5] * v[5]));
+    return (v[0] > 0.5f * u[0] && pk1 > 0.5f * pk0) ? 1.f : 0.f;
+}
+
 // Per-block partial sums of the 6 (limited) output channels (fixed order; the
 // final sum is taken in add_correction_kernel's prologue by every block, in the
 // same order).
-__global__ void pred_sum_kernel(const float* __restrict__ pred, long long n, float clip, float* __restrict__ part)
+__global__ void pred_sum_kernel(const float* __restrict__ pred, long long n, float clip, const float* __restrict__ state,
+                                const float* __restrict__ osc, float gm1, int positive, float* __restrict__ part)
 {
     __shared__ float red[6][NTHR / 32];
     float s[6] = {0, 0, 0, 0, 0, 0};
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const float k = keep_factor(state, p, n, pred, osc, clip, gm1, positive);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) s[c] += limited(pred[p * 8 + c], clip);
+        for (int c = 0; c < 6; ++c) s[c] += k * limited(pred[p * 8 + c], clip);
+    }
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         float x = s[c];
@@ -711,7 +753,8 @@ __global__ void pred_sum_kernel(const float* __restrict__ pred, long long n, flo
 // and coarse runs conserve them).
 __global__ void add_correction_kernel(float* __restrict__ u0, Layout L, const float* __restrict__ pred,
                                       const float* __restrict__ out_scale, const float* __restrict__ part,
-                                      int nblk, float clip, DevScalars* sc)
+                                      int nblk, float clip, const float* __restrict__ state, float gm1, int positive,
+                                      DevScalars* sc)
 {
     __shared__ float mean[6];
     if (threadIdx.x < 6) {
@@ -721,13 +764,24 @@ __global__ void add_correction_kernel(float* __restrict__ u0, Layout L, const fl
     }
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) { sc->cmax_bits[0] = 0ull; sc->cmax_bits[1] = 0ull; }
-    const long long ex = L.nx + 2 * GY, ey = L.ny + 2 * GY, total = (long long)NF * ex * ey;
+    // one thread per ghost-extended cell: the limiter once, then the three field pairs
+    float2* w = reinterpret_cast<float2*>(u0);
+    const long long n = (long long)L.nx * L.ny;
+    const long long ex = L.nx + 2 * GY, total = ex * (L.ny + 2 * GY);
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < total; v += (long long)gridDim.x * blockDim.x) {
-        const int f = (int)(v / (ex * ey));
-        const long long r = v - (long long)f * ex * ey;
-        const int j = (int)(r / ex) - GY, i = (int)(r % ex) - GY;
-        const int si = wrapm(i, L.nx), sj = wrapm(j, L.ny);
-        u0[L.idx(f, i, j, false)] += out_scale[f] * (limited(pred[((long long)sj * L.nx + si) * 8 + f], clip) - mean[f]);
+        const int j = (int)(v / ex) - GY, i = (int)(v % ex) - GY;
+        const long long p = (long long)wrapm(j, L.ny) * L.nx + wrapm(i, L.nx);
+        const float k = keep_factor(state, p, n, pred, out_scale, clip, gm1, positive);
+        const long long e = L.at(i, j);
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+            int f0, f1;
+            plane_fields(pl, f0, f1);
+            float2 q = w[pl * L.fstride + e];
+            q.x += out_scale[f0] * (k * limited(pred[p * 8 + f0], clip) - mean[f0]);
+            q.y += out_scale[f1] * (k * limited(pred[p * 8 + f1], clip) - mean[f1]);
+            w[pl * L.fstride + e] = q;
+        }
     }
 }
 
@@ -775,6 +829,7 @@ struct sac_cnn {
     int H = 0, W = 0, device = 0, nsm = 148, conv_grid = 0;
     int tensor_path = 0;                // 1: tcgen05 convolutions, 0: mma.sync convolutions
     float clip = 0.f;                   // > 0: sac_cnn_apply limits the output to [-clip, clip]
+    int positive = 0;                   // 1: no correction where it would halve density or pressure
     int* tc_err = nullptr;              // device flag: a tcgen05 accumulator wait gave up
     cudaStream_t stream = nullptr;
     float* params = nullptr;      // FP32 master [kParams]
@@ -830,7 +885,7 @@ static cudaError_t run_conv(sac_cnn* c, const __nv_bfloat16* in, const __nv_bflo
         constexpr int NC = COUT < 16 ? 16 : COUT;
         // resident CTAs per SM as the shared memory allows (two halo buffers each)
         constexpr int per_sm = (227 * 1024) / tcv::TcSmem<CIN, NC>::BYTES < 8 ? (227 * 1024) / tcv::TcSmem<CIN, NC>::BYTES : 8;
-        const int tiles = ((c->W + tcv::TP - 1) / tcv::TP) * c->H;
+        const int tiles = ((c->W + tcv::TP - 1) / tcv::TP) * ((c->H + tcv::ROWS - 1) / tcv::ROWS);
         const int cap = per_sm * c->nsm;
         const int grid = tiles < cap ? tiles : cap;
         tcv::conv3x3_tc_kernel<CIN, COUT, NC, MODE>
@@ -1009,10 +1064,11 @@ int sac_cnn_set_tensor_path(sac_cnn* c, int path)
     return SAC_OK;
 }
 
-int sac_cnn_set_clip(sac_cnn* c, double clip)
+int sac_cnn_set_limiter(sac_cnn* c, double clip, int keep_positive)
 {
-    if (!c || !(clip >= 0.0) || !std::isfinite(clip)) return SAC_ERR_ARG;
+    if (!c || !(clip >= 0.0) || !std::isfinite(clip) || (keep_positive != 0 && keep_positive != 1)) return SAC_ERR_ARG;
     c->clip = (float)clip;
+    c->positive = keep_positive;
     return SAC_OK;
 }
 
@@ -1114,15 +1170,17 @@ int sac_cnn_apply(sac_ctx* ctx, sac_cnn* c)
     CC(cudaSetDevice(c->device));
     const long long P = (long long)c->H * c->W;
     float* u0 = (float*)ctx->u0;
-    export_paired_kernel<<<grid_n(P * NF, 4096), 256, 0, c->stream>>>(u0, ctx->L, c->state);
+    export_paired_kernel<<<grid_n(P * 3, 4096), 256, 0, c->stream>>>(u0, ctx->L, c->state);
     CC(cudaGetLastError());
     CC(forward_all(c, c->state, ctx->p.gamma, ctx->dx, ctx->dy));
     const int nsum = 148;
-    pred_sum_kernel<<<nsum, NTHR, 0, c->stream>>>(c->pred, P, c->clip, c->loss_part);
+    const float gm1 = (float)(ctx->p.gamma - 1.0);
+    pred_sum_kernel<<<nsum, NTHR, 0, c->stream>>>(c->pred, P, c->clip, c->state, c->out_scale, gm1, c->positive,
+                                                  c->loss_part);
     CC(cudaGetLastError());
-    const long long ng = (long long)NF * (ctx->p.nx + 2 * GY) * (ctx->p.ny + 2 * GY);
+    const long long ng = (long long)(ctx->p.nx + 2 * GY) * (ctx->p.ny + 2 * GY);
     add_correction_kernel<<<grid_n(ng, 4096), 256, 0, c->stream>>>(u0, ctx->L, c->pred, c->out_scale, c->loss_part,
-                                                                   nsum, c->clip, ctx->sc);
+                                                                   nsum, c->clip, c->state, gm1, c->positive, ctx->sc);
     CC(cudaGetLastError());
     cmax_paired_kernel<<<grid_n(P, 2048), NTHR, 0, c->stream>>>(u0, ctx->L, (float)ctx->p.gamma, ctx->sc);
     CC(cudaGetLastError());

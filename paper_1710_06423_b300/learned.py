@@ -59,6 +59,7 @@ class Pairs:
 
     def __init__(self):
         self.x, self.next, self.gamma = [], [], []
+        self.meta = []   # (family member, coarse step index of the pair's start)
 
     def __len__(self):
         return len(self.x)
@@ -97,6 +98,7 @@ def generate_pairs(pairs: Pairs, seed: int, k: int, n_coarse: int, ratio: int, d
                 pairs.x.append(xp)
                 pairs.next.append(a1)
                 pairs.gamma.append(gamma)
+                pairs.meta.append((k, coarse_steps))
                 coarse_steps += 1
                 skip = min(every - 1, n_steps - coarse_steps)
                 if skip > 0:
@@ -105,6 +107,82 @@ def generate_pairs(pairs: Pairs, seed: int, k: int, n_coarse: int, ratio: int, d
         except SacError:
             pass
     return coarse_steps
+
+
+def rollout_pairs(net: CNN, pairs: Pairs, seed: int, members, n_coarse: int, ratio: int, dt_c: float, torch,
+                  solver_kw=None) -> Pairs:
+    """Pairs on the network's own trajectories (dataset aggregation): for each
+    member, the corrected coarse run (the network applied after every step, with
+    its current scales and limiter) is started from the block-averaged fine
+    initial state; at the coarse step of each stored pair of that member, its
+    state is stepped once more by the plain coarse solver, and that state is
+    paired with the pair's fine target.  The network so also learns to pull
+    the states its own rollout reaches back toward the fine solution.  A member
+    whose corrected run turns non-finite stops contributing there."""
+    kw = dict(solver_kw or {})
+    nf = n_coarse * ratio
+    out = Pairs()
+    for k in members:
+        idx = [j for j, (m, _) in enumerate(pairs.meta) if m == k]
+        if not idx:
+            continue
+        at = {pairs.meta[j][1]: j for j in idx}
+        w0f, gamma = family_state(seed, k, nf)
+        wf = torch.from_numpy(w0f.astype(np.float32)).cuda().contiguous()
+        w0c = torch.empty((6, n_coarse, n_coarse), dtype=torch.float32, device="cuda")
+        block_average(wf, 6, nf, nf, ratio, w0c)
+        del wf
+        with Solver(nx=n_coarse, ny=n_coarse, precision=FP32, gamma=gamma, **kw) as roll, \
+                Solver(nx=n_coarse, ny=n_coarse, precision=FP32, gamma=gamma, **kw) as one:
+            roll.set_state_dev(w0c, None, 0.0)
+            roll.set_fixed_dt(dt_c)
+            try:
+                for step in range(max(at) + 1):
+                    if step in at:
+                        xr = torch.empty_like(w0c)
+                        roll.get_state_dev(xr)
+                        one.set_state_dev(xr, None, 0.0)
+                        one.step(dt_c)
+                        one.get_state_dev(xr)
+                        j = at[step]
+                        out.x.append(xr)
+                        out.next.append(pairs.next[j])
+                        out.gamma.append(gamma)
+                        out.meta.append((k, step))
+                    roll.steps(1)
+                    net.apply(roll)
+                roll.sync()
+            except SacError:
+                pass
+    return out
+
+
+def pair_losses(net: CNN, pairs: Pairs, dx: float) -> np.ndarray:
+    """The network's loss on each pair (sac_cnn_grads: forward, loss, backward)."""
+    out = np.empty(len(pairs))
+    for j, (x, nx_, g) in enumerate(zip(pairs.x, pairs.next, pairs.gamma)):
+        out[j], _ = net.grads(x, nx_, g, dx, dx)
+    return out
+
+
+def select(pairs: Pairs, keep) -> Pairs:
+    out = Pairs()
+    for j in np.flatnonzero(keep):
+        out.x.append(pairs.x[j])
+        out.next.append(pairs.next[j])
+        out.gamma.append(pairs.gamma[j])
+        out.meta.append(pairs.meta[j])
+    return out
+
+
+def merged(a: Pairs, b: Pairs) -> Pairs:
+    m = Pairs()
+    for p in (a, b):
+        m.x += p.x
+        m.next += p.next
+        m.gamma += p.gamma
+        m.meta += p.meta
+    return m
 
 
 def _host(x):

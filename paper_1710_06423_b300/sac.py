@@ -36,7 +36,7 @@ EXPORTS = (
     "sac_batch_get_state", "sac_batch_steps", "sac_batch_sync", "sac_batch_time", "sac_batch_tune",
     "sac_batch_set_config", "sac_batch_set_tile", "sac_batch_get_config",
     "sac_cnn_param_count", "sac_cnn_init", "sac_cnn_free", "sac_cnn_last_error", "sac_cnn_set_tensor_path",
-    "sac_cnn_set_clip", "sac_cnn_sync", "sac_cnn_set_params",
+    "sac_cnn_set_limiter", "sac_cnn_sync", "sac_cnn_set_params",
     "sac_cnn_get_params", "sac_cnn_set_scales", "sac_cnn_forward", "sac_cnn_grads", "sac_cnn_train_step",
     "sac_cnn_apply", "sac_cnn_perturb", "sac_block_average",
     "sac_step_noalloc",
@@ -151,7 +151,7 @@ def load() -> ctypes.CDLL:
         "sac_cnn_free": (None, [vp]),
         "sac_cnn_last_error": (ctypes.c_char_p, [vp]),
         "sac_cnn_set_tensor_path": (i, [vp, i]),
-        "sac_cnn_set_clip": (i, [vp, d]),
+        "sac_cnn_set_limiter": (i, [vp, d, i]),
         "sac_cnn_sync": (i, [vp]),
         "sac_cnn_set_params": (i, [vp, ctypes.POINTER(ctypes.c_float), L]),
         "sac_cnn_get_params": (i, [vp, ctypes.POINTER(ctypes.c_float), L]),
@@ -536,9 +536,10 @@ class CNN:
     def sync(self):
         self._check(load().sac_cnn_sync(self._c), "sac_cnn_sync")
 
-    def set_clip(self, clip: float):
-        """Limit applied corrections to clip residual scales per field and step (0: off)."""
-        self._check(load().sac_cnn_set_clip(self._c, float(clip)), "sac_cnn_set_clip")
+    def set_limiter(self, clip: float = 0.0, keep_positive: bool = False):
+        """Limit applied corrections to clip residual scales per field and step (0: off) and,
+        with keep_positive, drop them where density or pressure would halve."""
+        self._check(load().sac_cnn_set_limiter(self._c, float(clip), int(bool(keep_positive))), "sac_cnn_set_limiter")
 
     def set_params(self, flat):
         flat = np.ascontiguousarray(flat, dtype=np.float32)
