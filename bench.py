@@ -38,6 +38,7 @@ STAGE_VALUES_FP32 = (12, 24, 30, 24)
 # algorithmic bytes per cell-stage of the hot path's byte model (classical RK4,
 # three registers plus a ping-pong pair, 24 FP32 values per cell-stage on
 # average, no background): the figure the roofline fraction divides by
+CNN_PATH_NAMES = {0: "mma.sync", 1: "tcgen05", 2: "tcgen05-tma"}
 MODEL_BYTES_PER_CELL_STAGE = 96
 # DRAM bytes per cell of each stage_fp32 launch (stages 1..4) measured by ncu as
 # dram__bytes_read.sum + dram__bytes_write.sum on the 4000^2 workload (three times L2
@@ -78,12 +79,18 @@ def parse():
     ap.add_argument("--learned", action="store_true",
                     help="run the learned coarse-grid correction experiment instead (several minutes)")
     ap.add_argument("--t-end", type=float, default=0.5, help="horizon of the learned experiment")
+    ap.add_argument("--learned-coarse", type=int, default=1000,
+                    help="coarse grid of --learned (fine = 4x; 250 is the reduced leg of the default line)")
     ap.add_argument("--only-batched", action="store_true",
                     help="time only the 64-run batched workload (one JSON line)")
     ap.add_argument("--no-per-size", action="store_true",
                     help="with --only-batched: skip the per-size batches")
     ap.add_argument("--only-3d", type=int, default=0, metavar="N",
                     help="time only the 3D form on an N^3 box and print its line (for profiling)")
+    ap.add_argument("--only-cnn", type=int, default=0, metavar="N",
+                    help="time only coarse steps and network applications on an N^2 grid (for profiling)")
+    ap.add_argument("--cnn-path", type=int, default=0, choices=[0, 1, 2],
+                    help="convolution kernel of --only-cnn: 0 mma.sync, 1 tcgen05, 2 tcgen05 with tensor-map halo")
     return ap.parse_args()
 
 
@@ -331,12 +338,17 @@ def run_batched(args, ws, local, pg, torch, per_size=True):
             "per_size": per_size_res, "gpu_launches": LAUNCHES_PER_STEP * args.batch_steps}
 
 
-def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=6000, noise=1.0, alpha=0.5,
+RELAXATIONS = (0.0, 0.125, 0.25, 0.5, 1.0)
+
+
+def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=6000, noise=1.0, alpha=None,
                        clip=3.0, keep_positive=True, plain_sizes=None, pairs_per_member=100, tensor_path=0,
-                       rounds=1):
+                       rounds=1, select_members=2):
     """Learned nc^2 coarse run vs plain FP32 runs at equal L1 error against the
     block-averaged (ratio nc)^2 plain run (Orszag-Tang family, horizon t_end);
-    returns the result record."""
+    returns the result record.  alpha None: the relaxation of the applied
+    correction is chosen among RELAXATIONS on the first `select_members`
+    training members' horizon errors (0 = the plain coarse run)."""
     import torch
     from paper_1710_06423_b300 import learned
     from paper_1710_06423_b300.sac import CNN, FP32, SacError, Solver
@@ -368,7 +380,7 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
     n_pairs, agg_pairs = len(pairs), []
     # dataset aggregation: pairs on the corrected run's own states, then more training
     for r in range(rounds):
-        net.set_scales(learned.FEATURE_SCALES, osc * alpha)
+        net.set_scales(learned.FEATURE_SCALES, osc * (alpha if alpha else 0.25))
         net.set_limiter(clip, keep_positive)
         agg = learned.rollout_pairs(net, pairs, 2024, train_members, nc, ratio, dt_c, torch, solver_kw=kw)
         net.set_scales(learned.FEATURE_SCALES, osc)
@@ -384,14 +396,22 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
         del agg
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    finals = pairs.final
     del pairs
     torch.cuda.empty_cache()
     held_pairs = learned.Pairs()                # one-step gain on the held-out member over the horizon
     learned.generate_pairs(held_pairs, 2024, held, nc, ratio, dt_c, steps, max(1, steps // 20), torch, solver_kw=kw)
     held_gain = learned.residual_gain(net, held_pairs, osc, dx, torch)
     del held_pairs
-    net.set_scales(learned.FEATURE_SCALES, osc * alpha)   # relaxation of the applied correction
     net.set_limiter(clip, keep_positive)
+    alpha_errs = None
+    if alpha is None:                           # relaxation of the applied correction
+        sel = [k for k in train_members if k in finals][:select_members]
+        alpha, alpha_errs = learned.choose_relaxation(net, finals, osc, 2024, sel, nc, ratio, dt_c, steps,
+                                                      RELAXATIONS, torch, solver_kw=kw)
+    else:
+        net.set_scales(learned.FEATURE_SCALES, osc * alpha)
+    del finals
 
     w0f, gamma = learned.family_state(2024, held, nf)
     fine_out = torch.empty((6, nf, nf), dtype=torch.float32, device="cuda")
@@ -418,7 +438,8 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
     w0c = learned.downsample(wf_dev, nc, torch).double().cpu().numpy()
     fell_back = False
     try:
-        out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, net=net, solver_kw=kw)
+        out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, net=net if alpha > 0 else None,
+                                     solver_kw=kw)
     except SacError:
         # the plain coarse solver is the fallback of the learned run
         fell_back = True
@@ -430,9 +451,10 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
             "dt_coarse": dt_c, "steps_coarse": steps, "train_members": list(train_members), "held_out_member": held,
             "c_shk": kw["c_shk"], "member_steps_completed": completed, "pairs": n_pairs, "data_seconds": t_data,
             "train_iters": iters, "train_seconds": t_train, "losses": losses, "noise": noise, "alpha": alpha,
+            "alpha_selection_l1": alpha_errs,
             "aggregation_rounds": rounds, "aggregated_pairs": agg_pairs,
             "limiter": {"clip": clip, "keep_positive": keep_positive},
-            "cnn_tensor_path": "tcgen05" if tensor_path == 1 else "mma.sync",
+            "cnn_tensor_path": CNN_PATH_NAMES[tensor_path],
             "held_out_one_step_residual_ratio": held_gain,
             "learned": {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec,
                         "fell_back_to_plain": fell_back},
@@ -441,9 +463,52 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
 
 
 def run_learned(args, local):
-    """The full experiment: 1000^2 coarse from 4000^2 fine runs, horizon t_end."""
-    res = learned_experiment(local, 1000, 4, args.t_end, train_members=(0, 1, 2, 3, 4, 5))
+    """The experiment: n^2 coarse from (4n)^2 fine runs, horizon t_end (n = 1000:
+    the full form; 250: the reduced leg of the default line)."""
+    n = args.learned_coarse
+    kw = {} if n >= 1000 else dict(iters=3000, plain_sizes=(n, 2 * n, 3 * n))
+    res = learned_experiment(local, n, 4, args.t_end, train_members=(0, 1, 2, 3, 4, 5), **kw)
     print(json.dumps(res), flush=True)
+
+
+def run_cnn_apply(args, local, n):
+    """CUDA-event times of a coarse RK4 step and of one application of the network
+    (features, four convolutions, limited conservative correction) on an n^2
+    Orszag-Tang state, untrained network with small output scales."""
+    import torch
+    from paper_1710_06423_b300 import inputs, learned
+    from paper_1710_06423_b300.sac import CNN, FP32, Solver
+    torch.cuda.set_device(local)
+    net = CNN(n, n)
+    net.set_tensor_path(args.cnn_path)
+    net.set_params(learned.init_params(1))
+    net.set_scales(learned.FEATURE_SCALES, np.full(6, 1e-6, dtype=np.float32))
+    res = {"metric": "learned-correction kernel times", "n": n,
+           "cnn_path": CNN_PATH_NAMES[args.cnn_path]}
+    with Solver(nx=n, ny=n, precision=FP32, device=local) as s:
+        s.set_state(inputs.orszag_tang(n), None, 0.0)
+        s.set_fixed_dt(0.25 / n / 3.0)
+        for _ in range(args.warmup):
+            s.steps(1)
+            net.apply(s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            s.steps(1)
+        e1.record()
+        e1.synchronize()
+        res["plain_step_ms"] = e0.elapsed_time(e1) / args.steps
+        e0.record()
+        for _ in range(args.steps):
+            net.apply(s)
+        e1.record()
+        e1.synchronize()
+        res["cnn_apply_ms"] = e0.elapsed_time(e1) / args.steps
+        s.sync()
+    net.sync()
+    net.close()
+    return res
 
 
 def run_stratified(args, ws, local, pg, torch, n=4000):
@@ -660,6 +725,9 @@ def main():
             res = run_batched(args, ws, local, pg, torch, per_size=not args.no_per_size)
             if rank == 0:
                 print(json.dumps({"metric": "batched cell-updates/s per RK step", **res}), flush=True)
+        elif args.only_cnn:
+            if rank == 0:
+                print(json.dumps(run_cnn_apply(args, local, args.only_cnn)), flush=True)
         elif args.only_3d:
             import torch
             torch.cuda.set_device(local)

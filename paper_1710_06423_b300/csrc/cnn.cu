@@ -10,6 +10,7 @@
 // gradient they are bf16 [cin][tap'][cout] with tap' = 8 - tap (flipped).
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -283,6 +284,69 @@ __device__ __forceinline__ void stage_halo_tc(const ConvArgs& a, int y0, int x0,
     }
 }
 
+// Epilogue of one accumulator row: tensor-memory columns q*NC .. q*NC+NC-1 of
+// this warp's 32 lanes (pixels), bias / ReLU / mask, stored as NHWC (BF16 or
+// FP32); image row gy, this thread's pixel gx (nothing is stored outside the image).
+template <int COUT, int NC, int MODE>
+__device__ __forceinline__ void epilogue_row(const ConvArgs& a, unsigned tmem, int warp, int q, int gy, int gx)
+{
+    float acc[NC];
+    {
+        unsigned r[NC];
+        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + q * NC;
+        if constexpr (NC == 32) {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                           "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+                           "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+                           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+                           "=r"(r[31])
+                         : "r"(taddr) : "memory");
+        } else {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                           "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                         : "r"(taddr) : "memory");
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int o = 0; o < NC; ++o) acc[o] = __uint_as_float(r[o]);
+    }
+    if (gx >= a.W || gy >= a.H) return;
+    const long long pix = (long long)gy * a.W + gx;
+    if (MODE == MODE_LINEAR_F32) {
+        float* out = reinterpret_cast<float*>(a.out) + pix * COUT;
+#pragma unroll
+        for (int o = 0; o < COUT; o += 4)
+            *reinterpret_cast<float4*>(out + o) =
+                make_float4(acc[o] + a.bias[o], acc[o + 1] + a.bias[o + 1], acc[o + 2] + a.bias[o + 2],
+                            acc[o + 3] + a.bias[o + 3]);
+    } else {
+        __align__(16) __nv_bfloat162 ov[COUT / 2];
+#pragma unroll
+        for (int o = 0; o < COUT; o += 2) {
+            float v0 = acc[o], v1 = acc[o + 1];
+            if (MODE == MODE_RELU) {
+                if (a.bias) { v0 += a.bias[o]; v1 += a.bias[o + 1]; }
+                v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f);
+            } else {   // MODE_MASK: keep where the layer's activation is positive
+                const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + pix * COUT + o);
+                if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+                if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+            }
+            ov[o / 2] = __floats2bfloat162_rn(v0, v1);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + pix * COUT);
+#pragma unroll
+        for (int k = 0; k < COUT / 8; ++k) dst[k] = reinterpret_cast<const uint4*>(ov)[k];
+    }
+}
+
 // COUT: channels stored (<= NC); the weight rows COUT .. NC-1 are zero.  A tile
 // is ROWS image rows x TP pixels: row q accumulates into tensor-memory columns
 // q*NC .. q*NC+NC-1, and its MMAs are issued interleaved with the other rows'
@@ -359,66 +423,7 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, i
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int gx = x0 + tid;
 #pragma unroll 1
-        for (int q = 0; q < ROWS; ++q) {
-            // epilogue of row q: this thread's pixel, all NC accumulator columns
-            float acc[NC];
-            {
-                unsigned r[NC];
-                const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + q * NC;
-                if constexpr (NC == 32) {
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-                                   "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-                                   "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-                                   "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-                                   "=r"(r[31])
-                                 : "r"(taddr) : "memory");
-                } else {
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-                                   "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                                 : "r"(taddr) : "memory");
-                }
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int o = 0; o < NC; ++o) acc[o] = __uint_as_float(r[o]);
-            }
-            const int gy = y0 + q;
-            if (gx < a.W && gy < a.H) {
-                const long long pix = (long long)gy * a.W + gx;
-                if (MODE == MODE_LINEAR_F32) {
-                    float* out = reinterpret_cast<float*>(a.out) + pix * COUT;
-#pragma unroll
-                    for (int o = 0; o < COUT; o += 4)
-                        *reinterpret_cast<float4*>(out + o) =
-                            make_float4(acc[o] + a.bias[o], acc[o + 1] + a.bias[o + 1], acc[o + 2] + a.bias[o + 2],
-                                        acc[o + 3] + a.bias[o + 3]);
-                } else {
-                    __align__(16) __nv_bfloat162 ov[COUT / 2];
-#pragma unroll
-                    for (int o = 0; o < COUT; o += 2) {
-                        float v0 = acc[o], v1 = acc[o + 1];
-                        if (MODE == MODE_RELU) {
-                            if (a.bias) { v0 += a.bias[o]; v1 += a.bias[o + 1]; }
-                            v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f);
-                        } else {   // MODE_MASK: keep where the layer's activation is positive
-                            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + pix * COUT + o);
-                            if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
-                            if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
-                        }
-                        ov[o / 2] = __floats2bfloat162_rn(v0, v1);
-                    }
-                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + pix * COUT);
-#pragma unroll
-                    for (int k = 0; k < COUT / 8; ++k) dst[k] = reinterpret_cast<const uint4*>(ov)[k];
-                }
-            }
-        }
+        for (int q = 0; q < ROWS; ++q) epilogue_row<COUT, NC, MODE>(a, tmem, warp, q, y0 + q, gx);
         // the accumulators and the halo are reused by the next tile once every warp is done
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -428,6 +433,160 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, i
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::TMEM_COLS) : "memory");
 }
+// The same convolution fed by tensor-map copies: a tile is RT image rows x TP
+// pixels, its halo (RT+2 rows) arrives by one 4D tensor copy per row
+// ((8 channels, pixel, 8-channel chunk, row) of the NHWC image, so the copy lands
+// in the [chunk][pixel][8 ch] core-matrix layout directly) into one of two halo
+// buffers, while the other buffer's tile is multiplied and written back.  Pixels
+// left of column 0 or right of column W-1 read zeros and are then patched with
+// the periodic neighbour column.
+template <int CIN, int NC, int RT>
+struct TmaSmem {
+    static constexpr int CPP = CIN / 8, NG = NC / 8;
+    static constexpr int ROW_BYTES = CPP * HP * 16;                 // one row's copy (dense)
+    static constexpr int ROW_STRIDE = (ROW_BYTES + 127) / 128 * 128;   // row copies start 128-byte aligned
+    static constexpr int HALO_BYTES = (RT + 2) * ROW_STRIDE;
+    static constexpr int W_BYTES = 9 * CPP * NG * 128;
+    static constexpr int BYTES = 128 + 2 * HALO_BYTES + W_BYTES + 64;   // + alignment of the base
+    static constexpr int TMEM_COLS = RT * NC <= 32 ? 32 : (RT * NC <= 64 ? 64 : 128);
+};
+
+__device__ __forceinline__ void mbar_expect_tc(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+template <int CIN, int NC, int RT>
+__device__ __forceinline__ void issue_halo_tma(const CUtensorMap* tm, const ConvArgs& a, int y0, int x0,
+                                               unsigned char* halo, unsigned long long* bar)
+{
+    using L = TmaSmem<CIN, NC, RT>;
+    mbar_expect_tc(bar, (unsigned)((RT + 2) * L::ROW_BYTES));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+    for (int r = 0; r < RT + 2; ++r) {
+        int gy = y0 - 1 + r;
+        gy = gy < 0 ? gy + a.H : (gy >= a.H ? gy - a.H : gy);
+        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                     :: "r"(smem_u32(halo + r * L::ROW_STRIDE)), "l"(tm), "r"(0), "r"(x0 - 1), "r"(0), "r"(gy),
+                        "r"(smem_u32(bar)) : "memory");
+    }
+}
+
+template <int CIN, int COUT, int NC, int MODE, int RT>
+__global__ void __launch_bounds__(NTHR_TC) conv3x3_tma_kernel(const ConvArgs a, const __grid_constant__ CUtensorMap tm,
+                                                              int* err)
+{
+    using L = TmaSmem<CIN, NC, RT>;
+    constexpr int CPP = L::CPP, NG = L::NG;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);   // 128-byte aligned base
+    unsigned char* halo[2] = {smem, smem + L::HALO_BYTES};
+    unsigned char* wts = smem + 2 * L::HALO_BYTES;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 2 * L::HALO_BYTES + L::W_BYTES);
+    // bar[0], bar[1]: halo buffers landed; bar[2]: accumulators complete
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem + 2 * L::HALO_BYTES + L::W_BYTES + 32);
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    for (int v = tid; v < NC * 9 * CPP; v += NTHR_TC) {
+        const int o = v / (9 * CPP), rem = v - o * 9 * CPP, tap = rem / CPP, ch = rem - tap * CPP;
+        unsigned char* dst = wts + ((tap * CPP + ch) * NG + (o >> 3)) * 128 + (o & 7) * 16;
+        if (o < COUT) cp16(dst, a.w + ((long long)o * 9 + tap) * CIN + ch * 8);
+        else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+    }
+    cp_wait();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_slot)), "r"(L::TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) { mbar_init_tc(&bar[0]); mbar_init_tc(&bar[1]); mbar_init_tc(&bar[2]); }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the weights, for the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+    const unsigned wbase = smem_u32(wts);
+    constexpr unsigned IDESC = idesc_bf16(NC);
+
+    const int tiles_x = (a.W + TP - 1) / TP, tiles_y = (a.H + RT - 1) / RT, ntiles = tiles_x * tiles_y;
+    int tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles)
+        issue_halo_tma<CIN, NC, RT>(&tm, a, (tile / tiles_x) * RT, (tile % tiles_x) * TP, halo[0], &bar[0]);
+    unsigned lphase[2] = {0u, 0u}, mphase = 0u;
+    bool inflight[2] = {tile < ntiles, false};
+    for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+        const int buf = i & 1;
+        const int y0 = (tile / tiles_x) * RT, x0 = (tile % tiles_x) * TP;
+        const int next = tile + gridDim.x;
+        if (next < ntiles) {
+            if (tid == 0)
+                issue_halo_tma<CIN, NC, RT>(&tm, a, (next / tiles_x) * RT, (next % tiles_x) * TP, halo[buf ^ 1], &bar[buf ^ 1]);
+            inflight[buf ^ 1] = true;
+        }
+        const bool landed = mbar_wait_tc(&bar[buf], lphase[buf]);
+        if (landed) { lphase[buf] ^= 1u; inflight[buf] = false; }
+        if (__syncthreads_or(!landed)) {
+            if (tid == 0) atomicExch(err, 1);
+            break;
+        }
+        // periodic columns: halo pixel 0 when the tile starts at column 0, and the
+        // pixel just right of column W-1 when the tile reaches it (zeros from the copy)
+        const int pr = a.W - x0 + 1;
+        for (int v = tid; v < 2 * (RT + 2) * CPP; v += NTHR_TC) {
+            const int side = v / ((RT + 2) * CPP), rem = v - side * (RT + 2) * CPP, r = rem / CPP, ch = rem - r * CPP;
+            const int px = side == 0 ? 0 : pr;
+            if ((side == 0 && x0 != 0) || (side == 1 && pr > HP - 1)) continue;
+            int gy = y0 - 1 + r;
+            gy = gy < 0 ? gy + a.H : (gy >= a.H ? gy - a.H : gy);
+            const int gx = side == 0 ? a.W - 1 : 0;
+            *reinterpret_cast<uint4*>(halo[buf] + r * L::ROW_STRIDE + (ch * HP + px) * 16) =
+                *reinterpret_cast<const uint4*>(a.in + ((long long)gy * a.W + gx) * CIN + ch * 8);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned hbase = smem_u32(halo[buf]);
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap - dy * 3;
+#pragma unroll
+                for (int ks = 0; ks < CPP / 2; ++ks) {
+                    const unsigned long long bdesc = smem_desc(wbase + ((tap * CPP + 2 * ks) * NG) * 128, NG * 128, 128);
+#pragma unroll
+                    for (int q = 0; q < RT; ++q) {
+                        const unsigned aaddr = hbase + (q + dy) * L::ROW_STRIDE + ((2 * ks) * HP + dx) * 16;
+                        mma_bf16_tc(tmem + q * NC, smem_desc(aaddr, HP * 16, 128), bdesc, IDESC, (tap | ks) != 0);
+                    }
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&bar[2])) : "memory");
+        }
+        __syncwarp();
+        const bool done = mbar_wait_tc(&bar[2], mphase);
+        mphase ^= 1u;
+        if (__syncthreads_or(!done)) {
+            if (tid == 0) atomicExch(err, 1);
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+        for (int q = 0; q < RT; ++q) epilogue_row<COUT, NC, MODE>(a, tmem, warp, q, y0 + q, x0 + tid);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    // no copy may land after the CTA has left: wait (bounded) for any still in flight
+    for (int b = 0; b < 2; ++b)
+        if (inflight[b]) mbar_wait_tc(&bar[b], lphase[b]);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::TMEM_COLS) : "memory");
+}
+
 }  // namespace tcv
 
 // ---- weight gradient: dW[o][tap][c] = sum_p dY[p][o] X[p + tap][c] ---------------
@@ -827,7 +986,11 @@ int grid_n(long long n, int cap) { long long g = (n + 255) / 256; return (int)(g
 
 struct sac_cnn {
     int H = 0, W = 0, device = 0, nsm = 148, conv_grid = 0;
-    int tensor_path = 0;                // 1: tcgen05 convolutions, 0: mma.sync convolutions
+    int tensor_path = 0;                // 0: mma.sync, 1: tcgen05 (cp.async halo), 2: tcgen05 (tensor-map halo)
+    CUtensorMap tmaps[8];               // tensor maps of the convolution inputs (path 2)
+    const void* tmap_ptr[8] = {nullptr};
+    int tmap_c[8] = {0};
+    int ntmap = 0;
     float clip = 0.f;                   // > 0: sac_cnn_apply limits the output to [-clip, clip]
     int positive = 0;                   // 1: no correction where it would halve density or pressure
     int* tc_err = nullptr;              // device flag: a tcgen05 accumulator wait gave up
@@ -881,7 +1044,19 @@ static cudaError_t run_conv(sac_cnn* c, const __nv_bfloat16* in, const __nv_bflo
 {
     ConvArgs a;
     a.in = in; a.w = w; a.bias = bias; a.out = out; a.mask = mask; a.H = c->H; a.W = c->W;
-    if (c->tensor_path == 1) {
+    if (c->tensor_path == 2) {
+        constexpr int NC = COUT < 16 ? 16 : COUT, RT = 2;
+        const CUtensorMap* tm = nullptr;
+        for (int k = 0; k < c->ntmap; ++k)
+            if (c->tmap_ptr[k] == in && c->tmap_c[k] == CIN) tm = &c->tmaps[k];
+        if (!tm) return cudaErrorInvalidValue;
+        constexpr int bytes = tcv::TmaSmem<CIN, NC, RT>::BYTES;
+        constexpr int per_sm = (227 * 1024) / bytes < 8 ? (227 * 1024) / bytes : 8;
+        const int tiles = ((c->W + tcv::TP - 1) / tcv::TP) * ((c->H + RT - 1) / RT);
+        const int cap = per_sm * c->nsm;
+        tcv::conv3x3_tma_kernel<CIN, COUT, NC, MODE, RT>
+            <<<tiles < cap ? tiles : cap, tcv::NTHR_TC, bytes, c->stream>>>(a, *tm, c->tc_err);
+    } else if (c->tensor_path == 1) {
         constexpr int NC = COUT < 16 ? 16 : COUT;
         // resident CTAs per SM as the shared memory allows (two halo buffers each)
         constexpr int per_sm = (227 * 1024) / tcv::TcSmem<CIN, NC>::BYTES < 8 ? (227 * 1024) / tcv::TcSmem<CIN, NC>::BYTES : 8;
@@ -969,6 +1144,36 @@ static cudaError_t conv_attr()
                                 (int)conv_smem<CIN, COUT>());
 }
 template <int CIN, int COUT, int NC, int MODE>
+static cudaError_t tma_attr()
+{
+    return cudaFuncSetAttribute(tcv::conv3x3_tma_kernel<CIN, COUT, NC, MODE, 2>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcv::TmaSmem<CIN, NC, 2>::BYTES);
+}
+
+// Tensor map of an NHWC BF16 image with C channels as the 4D tensor (8 channels,
+// pixel, 8-channel chunk, row) and a box of (8, 130, C/8, 1): one copy lands one
+// halo row in the [chunk][pixel][8 ch] layout of the tcgen05 convolution.
+static cudaError_t encode_nhwc_map(const void* img, int C, int W, int H, CUtensorMap* out)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !encode)
+            return cudaErrorNotSupported;
+    }
+    const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)(C / 8), (cuuint64_t)H};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, 16, (cuuint64_t)W * C * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)tcv::HP, (cuuint32_t)(C / 8), 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(img), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+template <int CIN, int COUT, int NC, int MODE>
 static cudaError_t tc_attr()
 {
     return cudaFuncSetAttribute(tcv::conv3x3_tc_kernel<CIN, COUT, NC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1043,6 +1248,24 @@ int sac_cnn_init(int nx, int ny, int device, void* stream, sac_cnn** out)
         if (e == cudaSuccess) e = tc_attr<32, 8, 16, MODE_LINEAR_F32>();
         if (e == cudaSuccess) e = tc_attr<16, 32, 32, MODE_MASK>();
         if (e == cudaSuccess) e = tc_attr<32, 32, 32, MODE_MASK>();
+        if (e == cudaSuccess) e = tma_attr<16, 32, 32, MODE_RELU>();
+        if (e == cudaSuccess) e = tma_attr<32, 32, 32, MODE_RELU>();
+        if (e == cudaSuccess) e = tma_attr<32, 8, 16, MODE_LINEAR_F32>();
+        if (e == cudaSuccess) e = tma_attr<16, 32, 32, MODE_MASK>();
+        if (e == cudaSuccess) e = tma_attr<32, 32, 32, MODE_MASK>();
+        if (e == cudaSuccess) {
+            // the convolution inputs: features, the three hidden activations, the output
+            // gradient and the two hidden input gradients the backward pass convolves
+            const void* img[7] = {c->feat, c->act[0], c->act[1], c->act[2], c->dy3, c->dact[2], c->dact[1]};
+            const int ch[7] = {16, 32, 32, 32, 16, 32, 32};
+            c->ntmap = 0;
+            for (int k = 0; k < 7; ++k)
+                if (encode_nhwc_map(img[k], ch[k], nx, ny, &c->tmaps[c->ntmap]) == cudaSuccess) {
+                    c->tmap_ptr[c->ntmap] = img[k];
+                    c->tmap_c[c->ntmap++] = ch[k];
+                }
+            cudaGetLastError();
+        }
         if (e != cudaSuccess) { rc = cfail(c, SAC_ERR_CUDA, "kernel set-up: %s", cudaGetErrorString(e)); break; }
         const float ones[8] = {1, 1, 1, 1, 1, 1, 1, 1};
         if (cudaMemcpy(c->in_scale, ones, 32, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1057,7 +1280,8 @@ int sac_cnn_init(int nx, int ny, int device, void* stream, sac_cnn** out)
 
 int sac_cnn_set_tensor_path(sac_cnn* c, int path)
 {
-    if (!c || (path != 0 && path != 1)) return SAC_ERR_ARG;
+    if (!c || path < 0 || path > 2) return SAC_ERR_ARG;
+    if (path == 2 && c->ntmap < 7) return cfail(c, SAC_ERR_CUDA, "tensor maps of the activations could not be encoded");
     CC(cudaSetDevice(c->device));
     CC(cudaStreamSynchronize(c->stream));
     c->tensor_path = path;

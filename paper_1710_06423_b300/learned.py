@@ -60,6 +60,7 @@ class Pairs:
     def __init__(self):
         self.x, self.next, self.gamma = [], [], []
         self.meta = []   # (family member, coarse step index of the pair's start)
+        self.final = {}  # member -> block-averaged fine state at the horizon (members that reached it)
 
     def __len__(self):
         return len(self.x)
@@ -69,9 +70,10 @@ def generate_pairs(pairs: Pairs, seed: int, k: int, n_coarse: int, ratio: int, d
                    every: int, torch, solver_kw=None):
     """Run the fine solver of family member (seed, k) for n_steps coarse steps and
     collect a pair every `every` coarse steps (solver_kw: extra sac_params fields,
-    e.g. the diffusion coefficients, used by both grids).  If the fine run turns
-    non-finite, the pairs collected before stay and the member ends there;
-    returns the number of coarse steps the member completed."""
+    e.g. the diffusion coefficients, used by both grids).  A member that reaches
+    the horizon keeps its block-averaged final state in pairs.final[k].  If the
+    fine run turns non-finite, the pairs collected before stay and the member
+    ends there; returns the number of coarse steps the member completed."""
     kw = dict(solver_kw or {})
     nf = n_coarse * ratio
     w0, gamma = family_state(seed, k, nf)
@@ -104,6 +106,11 @@ def generate_pairs(pairs: Pairs, seed: int, k: int, n_coarse: int, ratio: int, d
                 if skip > 0:
                     fine.steps(ratio * skip)
                     coarse_steps += skip
+            fine.get_state_dev(fine_buf)
+            fine.sync()
+            final = torch.empty_like(a0)
+            block_average(fine_buf, 6, nf, nf, ratio, final)
+            pairs.final[k] = final
         except SacError:
             pass
     return coarse_steps
@@ -182,7 +189,41 @@ def merged(a: Pairs, b: Pairs) -> Pairs:
         m.next += p.next
         m.gamma += p.gamma
         m.meta += p.meta
+        m.final.update(p.final)
     return m
+
+
+def choose_relaxation(net: CNN, finals: dict, osc: np.ndarray, seed: int, members, n_coarse: int, ratio: int,
+                      dt_c: float, steps: int, alphas, torch, solver_kw=None):
+    """Relaxation of the applied correction (u <- u + alpha out_scale f), chosen
+    on training members: each alpha's corrected run of every given member that
+    reached the horizon is compared with that member's block-averaged fine state
+    there (finals: member -> that state, as Pairs.final holds it) (mean relative L1 over the fields); alpha = 0 is the plain coarse run.
+    A run that turns non-finite counts as infinite error.  Leaves the network's
+    output scales at alpha_best * osc; returns (alpha_best, {alpha: error})."""
+    nf = n_coarse * ratio
+    errs = {}
+    for alpha in alphas:
+        e = []
+        for k in members:
+            if k not in finals:
+                continue
+            w0f, gamma = family_state(seed, k, nf)
+            wf = _dev(w0f, torch)
+            w0c = _host(downsample(wf, n_coarse, torch))
+            del wf
+            net.set_scales(FEATURE_SCALES, osc * alpha)
+            try:
+                out, _ = run_plain(w0c, gamma, n_coarse, dt_c, steps, torch, net=net if alpha > 0 else None,
+                                   solver_kw=solver_kw)
+                e.append(float(l1_error(out, finals[k]).mean()))
+            except SacError:
+                e.append(math.inf)
+        if e:
+            errs[float(alpha)] = float(np.mean(e))
+    best = min(errs, key=errs.get) if errs else 0.0
+    net.set_scales(FEATURE_SCALES, osc * best)
+    return best, errs
 
 
 def _host(x):

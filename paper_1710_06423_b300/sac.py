@@ -530,7 +530,8 @@ class CNN:
             pass
 
     def set_tensor_path(self, path: int):
-        """1: tcgen05 convolutions; 0: mma.sync convolutions."""
+        """Convolution kernel: 0 mma.sync, 1 tcgen05 (asynchronous-copy halo),
+        2 tcgen05 (tensor-map halo, double-buffered)."""
         self._check(load().sac_cnn_set_tensor_path(self._c, int(path)), "sac_cnn_set_tensor_path")
 
     def sync(self):

@@ -212,7 +212,7 @@ def _forward_ok(got, ref):
     return r.max() <= 0.25 and col.max() <= 5e-3 and row.max() <= 5e-3 and tiles.max() <= 1e-2
 
 
-@pytest.mark.parametrize("path", [0, 1], ids=["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("path", [0, 1, 2], ids=["mma_sync", "tcgen05", "tcgen05_tma"])
 def test_forward_elementwise_multi_tile(multitile, path):
     import torch
     from oracle import cnn as ocnn
@@ -242,7 +242,7 @@ def test_forward_elementwise_multi_tile(multitile, path):
     assert not _forward_ok(got, bad)
 
 
-@pytest.mark.parametrize("path", [0, 1], ids=["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("path", [0, 1, 2], ids=["mma_sync", "tcgen05", "tcgen05_tma"])
 def test_gradients_elementwise_multi_tile(multitile, path):
     import torch
     from oracle import cnn as ocnn
@@ -335,7 +335,7 @@ def test_tensor_paths_agree(multitile):
     nx, ny, w, g, flat, _, _, _ = multitile
     wd = torch.from_numpy(w.astype(np.float32)).cuda().contiguous()
     outs = []
-    for path in (0, 1):
+    for path in (0, 1, 2):
         net = CNN(nx, ny)
         net.set_tensor_path(path)
         net.set_params(flat)
@@ -346,9 +346,10 @@ def test_tensor_paths_agree(multitile):
         net.close()
         outs.append(pred[:, :6].double().cpu().numpy())
     rms = np.sqrt((outs[0] ** 2).mean(axis=0))
-    r = np.abs(outs[1] - outs[0]) / rms
-    print(f"tcgen05 vs mma.sync: bitwise equal {np.array_equal(outs[0], outs[1])}, "
-          f"max diff / rms {r.max():.3g}, mean {r.mean():.3g}")
-    # a different FP32 summation order can flip BF16 roundings of hidden
-    # activations (the bounds of the element-by-element tests)
-    assert r.max() <= 0.25 and r.mean() <= 1e-3, (r.max(), r.mean())
+    for k in (1, 2):
+        r = np.abs(outs[k] - outs[0]) / rms
+        print(f"path {k} vs mma.sync: bitwise equal {np.array_equal(outs[0], outs[k])}, "
+              f"max diff / rms {r.max():.3g}, mean {r.mean():.3g}")
+        # a different FP32 summation order can flip BF16 roundings of hidden
+        # activations (the bounds of the element-by-element tests)
+        assert r.max() <= 0.25 and r.mean() <= 1e-3, (k, r.max(), r.mean())
