@@ -79,6 +79,12 @@ def parse():
     ap.add_argument("--learned", action="store_true",
                     help="run the learned coarse-grid correction experiment instead (several minutes)")
     ap.add_argument("--t-end", type=float, default=0.5, help="horizon of the learned experiment")
+    ap.add_argument("--substeps", type=int, default=1,
+                    help="coarse steps per training pair of --learned (per-step share of the m-step correction)")
+    ap.add_argument("--target", choices=["share", "whole"], default="share",
+                    help="--learned with --substeps m: per-step share applied every step, or the whole "
+                         "m-step correction applied every m steps")
+    ap.add_argument("--pairs-per-member", type=int, default=100, help="training pairs per family member of --learned")
     ap.add_argument("--learned-coarse", type=int, default=1000,
                     help="coarse grid of --learned (fine = 4x; 250 is the reduced leg of the default line)")
     ap.add_argument("--only-batched", action="store_true",
@@ -343,12 +349,15 @@ RELAXATIONS = (0.0, 0.125, 0.25, 0.5, 1.0)
 
 def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=6000, noise=1.0, alpha=None,
                        clip=3.0, keep_positive=True, plain_sizes=None, pairs_per_member=100, tensor_path=0,
-                       rounds=1, select_members=2):
+                       rounds=1, select_members=2, substeps=1, share=True):
     """Learned nc^2 coarse run vs plain FP32 runs at equal L1 error against the
     block-averaged (ratio nc)^2 plain run (Orszag-Tang family, horizon t_end);
     returns the result record.  alpha None: the relaxation of the applied
     correction is chosen among RELAXATIONS on the first `select_members`
-    training members' horizon errors (0 = the plain coarse run)."""
+    training members' horizon errors (0 = the plain coarse run).  substeps m:
+    training pairs over m coarse steps with the per-step share of the missed
+    correction as target, the network applied after every step (share), or the
+    whole missed correction, applied after every m-th step (learned.Pairs)."""
     import torch
     from paper_1710_06423_b300 import learned
     from paper_1710_06423_b300.sac import CNN, FP32, SacError, Solver
@@ -358,12 +367,15 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
     dt_c = 0.25 * dx / 3.0                      # fixed coarse step: Courant 0.25 at a signal speed of 3
     steps = int(round(t_end / dt_c))
     every = max(1, steps // pairs_per_member)
+    if not share:   # pairs start right after an application of the network
+        every = max(substeps, every // substeps * substeps)
     # shock viscosity 4 (default 0.5): with 0.5 the family's 2000^2-4000^2 runs turn
     # non-finite before t = 0.5 (in FP64 as in FP32), with 2 one member still does at
     # 4000^2; every run of this experiment uses the same value
     kw = dict(c_shk=4.0)
     t0 = time.perf_counter()
-    pairs = learned.Pairs()
+    pairs = learned.Pairs(substeps, share)
+    every_apply = pairs.apply_every
     completed = {}
     for k in train_members:
         completed[k] = learned.generate_pairs(pairs, 2024, k, nc, ratio, dt_c, steps, every, torch, solver_kw=kw)
@@ -408,7 +420,7 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
     if alpha is None:                           # relaxation of the applied correction
         sel = [k for k in train_members if k in finals][:select_members]
         alpha, alpha_errs = learned.choose_relaxation(net, finals, osc, 2024, sel, nc, ratio, dt_c, steps,
-                                                      RELAXATIONS, torch, solver_kw=kw)
+                                                      RELAXATIONS, torch, solver_kw=kw, every=every_apply)
     else:
         net.set_scales(learned.FEATURE_SCALES, osc * alpha)
     del finals
@@ -439,7 +451,7 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
     fell_back = False
     try:
         out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, net=net if alpha > 0 else None,
-                                     solver_kw=kw)
+                                     solver_kw=kw, every=every_apply)
     except SacError:
         # the plain coarse solver is the fallback of the learned run
         fell_back = True
@@ -452,7 +464,8 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
             "c_shk": kw["c_shk"], "member_steps_completed": completed, "pairs": n_pairs, "data_seconds": t_data,
             "train_iters": iters, "train_seconds": t_train, "losses": losses, "noise": noise, "alpha": alpha,
             "alpha_selection_l1": alpha_errs,
-            "aggregation_rounds": rounds, "aggregated_pairs": agg_pairs,
+            "aggregation_rounds": rounds, "aggregated_pairs": agg_pairs, "substeps": substeps,
+            "target": "per-step share, applied every step" if share else f"whole {substeps}-step correction, applied every {substeps} steps",
             "limiter": {"clip": clip, "keep_positive": keep_positive},
             "cnn_tensor_path": CNN_PATH_NAMES[tensor_path],
             "held_out_one_step_residual_ratio": held_gain,
@@ -467,7 +480,8 @@ def run_learned(args, local):
     the full form; 250: the reduced leg of the default line)."""
     n = args.learned_coarse
     kw = {} if n >= 1000 else dict(iters=3000, plain_sizes=(n, 2 * n, 3 * n))
-    res = learned_experiment(local, n, 4, args.t_end, train_members=(0, 1, 2, 3, 4, 5), **kw)
+    res = learned_experiment(local, n, 4, args.t_end, train_members=(0, 1, 2, 3, 4, 5), substeps=args.substeps,
+                             share=args.target == "share", pairs_per_member=args.pairs_per_member, **kw)
     print(json.dumps(res), flush=True)
 
 

@@ -10,9 +10,11 @@ the second, divided by out_scale.  The plain fine solver is both the source of
 the training data and the reference for the error (relative L1 per field against
 its block average at the horizon).
 
-Every array operation runs in the library's CUDA kernels (solver steps, block
-averages, network forward/backward/update, correction); this module only
-sequences the calls and keeps device tensors (torch is used for device memory).
+Every array operation of the solver and the network runs in the library's CUDA
+kernels (solver steps, block averages, network forward/backward/update,
+correction); this module sequences the calls and keeps device tensors.  The one
+torch arithmetic is the per-step share of an m-step target (a lerp per pair,
+training-data preparation only).
 """
 from __future__ import annotations
 
@@ -52,13 +54,20 @@ def family_state(seed: int, k: int, n: int):
 
 
 class Pairs:
-    """Training pairs on the device: x' (the coarse state after one coarse step
-    from avg(fine(t))) and next = avg(fine(t + dt_c)), the state the corrected
-    step should reach; the network's target (next - x') / out_scale is formed
-    inside the loss kernel."""
+    """Training pairs on the device: x' (the coarse state after m coarse steps
+    from avg(fine(t))) and next, the state the corrected step should reach; the
+    network's target (next - x') / out_scale is formed inside the loss kernel.
+    With m = 1, next = avg(fine(t + dt_c)).  With m > 1 (substeps), raw =
+    avg(fine(t + m dt_c)), and either (share) next = x' + (raw - x') / m, the
+    per-step share of the correction the m plain steps missed, for a network
+    applied after every step; or (not share) next = raw, the whole missed
+    correction, for a network applied after every m-th step (apply_every)."""
 
-    def __init__(self):
+    def __init__(self, substeps: int = 1, share: bool = True):
+        self.substeps, self.share = substeps, share
+        self.apply_every = 1 if share else substeps
         self.x, self.next, self.gamma = [], [], []
+        self.raw = []    # avg(fine) at the end of the pair's m steps (= next when m = 1)
         self.meta = []   # (family member, coarse step index of the pair's start)
         self.final = {}  # member -> block-averaged fine state at the horizon (members that reached it)
 
@@ -66,16 +75,26 @@ class Pairs:
         return len(self.x)
 
 
+def _target(pairs: "Pairs", xp, raw, torch):
+    """The pair's target: x' + (raw - x') / m (share), else raw."""
+    m = pairs.substeps
+    return raw if m == 1 or not pairs.share else torch.lerp(xp, raw, 1.0 / m)
+
+
 def generate_pairs(pairs: Pairs, seed: int, k: int, n_coarse: int, ratio: int, dt_c: float, n_steps: int,
                    every: int, torch, solver_kw=None):
     """Run the fine solver of family member (seed, k) for n_steps coarse steps and
-    collect a pair every `every` coarse steps (solver_kw: extra sac_params fields,
+    collect a pair every `every` coarse steps (pairs.substeps coarse steps per
+    pair, at most `every`; solver_kw: extra sac_params fields,
     e.g. the diffusion coefficients, used by both grids).  A member that reaches
     the horizon keeps its block-averaged final state in pairs.final[k].  If the
     fine run turns non-finite, the pairs collected before stay and the member
     ends there; returns the number of coarse steps the member completed."""
     kw = dict(solver_kw or {})
     nf = n_coarse * ratio
+    m = pairs.substeps
+    if not 1 <= m <= every:
+        raise ValueError("substeps must be in 1 .. every")
     w0, gamma = family_state(seed, k, nf)
     fine_buf = torch.empty((6, nf, nf), dtype=torch.float32, device="cuda")
     a0 = torch.empty((6, n_coarse, n_coarse), dtype=torch.float32, device="cuda")
@@ -85,24 +104,26 @@ def generate_pairs(pairs: Pairs, seed: int, k: int, n_coarse: int, ratio: int, d
         fine.set_fixed_dt(dt_c / ratio)
         coarse_steps = 0
         try:
-            while coarse_steps + 1 <= n_steps:
+            while coarse_steps + m <= n_steps:
                 fine.get_state_dev(fine_buf)
                 block_average(fine_buf, 6, nf, nf, ratio, a0)
-                fine.steps(ratio)
+                fine.steps(ratio * m)
                 fine.get_state_dev(fine_buf)
                 fine.sync()                      # a non-finite fine state stops here
                 a1 = torch.empty_like(a0)
                 block_average(fine_buf, 6, nf, nf, ratio, a1)
                 coarse.set_state_dev(a0, None, 0.0)
-                coarse.step(dt_c)
+                for _ in range(m):
+                    coarse.step(dt_c)
                 xp = torch.empty_like(a0)
                 coarse.get_state_dev(xp)
                 pairs.x.append(xp)
-                pairs.next.append(a1)
+                pairs.next.append(_target(pairs, xp, a1, torch))
+                pairs.raw.append(a1)
                 pairs.gamma.append(gamma)
                 pairs.meta.append((k, coarse_steps))
-                coarse_steps += 1
-                skip = min(every - 1, n_steps - coarse_steps)
+                coarse_steps += m
+                skip = min(every - m, n_steps - coarse_steps)
                 if skip > 0:
                     fine.steps(ratio * skip)
                     coarse_steps += skip
@@ -121,14 +142,16 @@ def rollout_pairs(net: CNN, pairs: Pairs, seed: int, members, n_coarse: int, rat
     """Pairs on the network's own trajectories (dataset aggregation): for each
     member, the corrected coarse run (the network applied after every step, with
     its current scales and limiter) is started from the block-averaged fine
-    initial state; at the coarse step of each stored pair of that member, its
-    state is stepped once more by the plain coarse solver, and that state is
-    paired with the pair's fine target.  The network so also learns to pull
+    initial state (applied every pairs.apply_every steps); at the coarse step of
+    each stored pair of that member, its state is stepped pairs.substeps more
+    times by the plain coarse solver, and that state is paired with the pair's
+    fine target (as Pairs forms it).  The network so also learns to pull
     the states its own rollout reaches back toward the fine solution.  A member
     whose corrected run turns non-finite stops contributing there."""
     kw = dict(solver_kw or {})
     nf = n_coarse * ratio
-    out = Pairs()
+    m, every = pairs.substeps, pairs.apply_every
+    out = Pairs(m, pairs.share)
     for k in members:
         idx = [j for j, (m, _) in enumerate(pairs.meta) if m == k]
         if not idx:
@@ -149,15 +172,18 @@ def rollout_pairs(net: CNN, pairs: Pairs, seed: int, members, n_coarse: int, rat
                         xr = torch.empty_like(w0c)
                         roll.get_state_dev(xr)
                         one.set_state_dev(xr, None, 0.0)
-                        one.step(dt_c)
+                        for _ in range(m):
+                            one.step(dt_c)
                         one.get_state_dev(xr)
                         j = at[step]
                         out.x.append(xr)
-                        out.next.append(pairs.next[j])
+                        out.next.append(_target(pairs, xr, pairs.raw[j], torch))
+                        out.raw.append(pairs.raw[j])
                         out.gamma.append(gamma)
                         out.meta.append((k, step))
                     roll.steps(1)
-                    net.apply(roll)
+                    if (step + 1) % every == 0:
+                        net.apply(roll)
                 roll.sync()
             except SacError:
                 pass
@@ -173,20 +199,22 @@ def pair_losses(net: CNN, pairs: Pairs, dx: float) -> np.ndarray:
 
 
 def select(pairs: Pairs, keep) -> Pairs:
-    out = Pairs()
+    out = Pairs(pairs.substeps, pairs.share)
     for j in np.flatnonzero(keep):
         out.x.append(pairs.x[j])
         out.next.append(pairs.next[j])
+        out.raw.append(pairs.raw[j])
         out.gamma.append(pairs.gamma[j])
         out.meta.append(pairs.meta[j])
     return out
 
 
 def merged(a: Pairs, b: Pairs) -> Pairs:
-    m = Pairs()
+    m = Pairs(a.substeps, a.share)
     for p in (a, b):
         m.x += p.x
         m.next += p.next
+        m.raw += p.raw
         m.gamma += p.gamma
         m.meta += p.meta
         m.final.update(p.final)
@@ -194,12 +222,13 @@ def merged(a: Pairs, b: Pairs) -> Pairs:
 
 
 def choose_relaxation(net: CNN, finals: dict, osc: np.ndarray, seed: int, members, n_coarse: int, ratio: int,
-                      dt_c: float, steps: int, alphas, torch, solver_kw=None):
-    """Relaxation of the applied correction (u <- u + alpha out_scale f), chosen
-    on training members: each alpha's corrected run of every given member that
-    reached the horizon is compared with that member's block-averaged fine state
-    there (finals: member -> that state, as Pairs.final holds it) (mean relative L1 over the fields); alpha = 0 is the plain coarse run.
-    A run that turns non-finite counts as infinite error.  Leaves the network's
+                      dt_c: float, steps: int, alphas, torch, solver_kw=None, every: int = 1):
+    """Relaxation of the applied correction (u <- u + alpha out_scale f, after
+    every `every`-th step), chosen on training members: each alpha's corrected
+    run of every given member that reached the horizon is compared with that
+    member's block-averaged fine state there (finals: member -> that state, as
+    Pairs.final holds it; mean relative L1 over the fields); alpha = 0 is the
+    plain coarse run.  A run that turns non-finite counts as infinite error.  Leaves the network's
     output scales at alpha_best * osc; returns (alpha_best, {alpha: error})."""
     nf = n_coarse * ratio
     errs = {}
@@ -215,7 +244,7 @@ def choose_relaxation(net: CNN, finals: dict, osc: np.ndarray, seed: int, member
             net.set_scales(FEATURE_SCALES, osc * alpha)
             try:
                 out, _ = run_plain(w0c, gamma, n_coarse, dt_c, steps, torch, net=net if alpha > 0 else None,
-                                   solver_kw=solver_kw)
+                                   solver_kw=solver_kw, every=every)
                 e.append(float(l1_error(out, finals[k]).mean()))
             except SacError:
                 e.append(math.inf)
@@ -282,31 +311,37 @@ def residual_gain(net: CNN, pairs: Pairs, osc: np.ndarray, dx: float, torch) -> 
     return num / den
 
 
-def run_plain(w0, gamma, n, dt, steps, torch, net=None, solver_kw=None):
+def run_plain(w0, gamma, n, dt, steps, torch, net=None, solver_kw=None, every: int = 1):
     """Coarse (or plain) run of `steps` fixed steps; with `net`, the correction after
-    every step.  Returns the final state (device) and the device time in seconds."""
+    every `every`-th step.  Returns the final state (device) and the device time in
+    seconds (the first `every` steps are untimed; the time is scaled to `steps`)."""
     out = torch.empty((6, n, n), dtype=torch.float32, device="cuda")
     with Solver(nx=n, ny=n, precision=FP32, gamma=gamma, **(solver_kw or {})) as s:
         s.set_state(w0, None, 0.0)
         s.set_fixed_dt(dt)
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.steps(1)
-        if net is not None:
+        first = min(every, steps)
+        s.steps(first)
+        if net is not None and first == every:
             net.apply(s)
         e0.record(stream)
         if net is None:
-            s.steps(steps - 1)
+            s.steps(steps - first)
         else:
-            for _ in range(steps - 1):
-                s.steps(1)
-                net.apply(s)
+            done = first
+            while done < steps:
+                k = min(every, steps - done)
+                s.steps(k)
+                done += k
+                if k == every:
+                    net.apply(s)
         e1.record(stream)
         e1.synchronize()
         s.sync()
         s.get_state_dev(out)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) * steps / max(1, steps - 1)
+        ms = e0.elapsed_time(e1) * steps / max(1, steps - first)
     return out, ms * 1e-3
 
 

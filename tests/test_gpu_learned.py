@@ -69,3 +69,41 @@ def test_learned_rollout_beats_plain_coarse(trained):
     e_plain = learned.l1_error(plain, truth)
     e_corr = learned.l1_error(corr, truth)
     assert e_corr.mean() < e_plain.mean(), (e_corr, e_plain)
+
+
+def test_multi_step_pairs():
+    """Pairs over m = 4 coarse steps: one pair every 6 steps over 24 steps, the
+    coarse input is 4 plain steps from the block-averaged fine state, and the
+    target is the per-step share x' + (avg fine(t + 4 dt) - x') / 4; the final
+    block-averaged fine state is kept for the member."""
+    import torch
+    from paper_1710_06423_b300 import learned
+    from paper_1710_06423_b300.sac import FP32, Solver, block_average
+    nc, ratio = 32, 4
+    dt_c = 0.2 / nc / 2.5
+    pairs = learned.Pairs(4)
+    done = learned.generate_pairs(pairs, 77, 0, nc, ratio, dt_c, n_steps=24, every=6, torch=torch)
+    assert done == 24 and len(pairs) == 4 and [m for _, m in pairs.meta] == [0, 6, 12, 18]
+    assert 0 in pairs.final
+    for xp, nxt, raw in zip(pairs.x, pairs.next, pairs.raw):
+        want = xp.double() + (raw.double() - xp.double()) / 4
+        assert torch.allclose(nxt.double(), want, rtol=1e-6, atol=1e-7)
+    # the second pair's input: 4 plain coarse steps from avg(fine) at coarse step 6
+    nf = nc * ratio
+    w0f, gamma = learned.family_state(77, 0, nf)
+    fine_buf = torch.empty((6, nf, nf), dtype=torch.float32, device="cuda")
+    a0 = torch.empty((6, nc, nc), dtype=torch.float32, device="cuda")
+    xp = torch.empty_like(a0)
+    with Solver(nx=nf, ny=nf, precision=FP32, gamma=gamma) as fine, \
+            Solver(nx=nc, ny=nc, precision=FP32, gamma=gamma) as coarse:
+        fine.set_state(w0f, None, 0.0)
+        fine.set_fixed_dt(dt_c / ratio)
+        fine.steps(6 * ratio)
+        fine.get_state_dev(fine_buf)
+        block_average(fine_buf, 6, nf, nf, ratio, a0)
+        coarse.set_state_dev(a0, None, 0.0)
+        for _ in range(4):
+            coarse.step(dt_c)
+        coarse.get_state_dev(xp)
+        coarse.sync()
+    assert torch.equal(xp, pairs.x[1])
