@@ -693,7 +693,8 @@ def run_ours(args, ws, rank, local, pg):
             # the learned coarse-grid correction at a reduced scale (250^2 coarse from
             # 1000^2 fine runs, horizon 0.5); --learned runs the 1000^2 / 4000^2 form
             small = learned_experiment(local, 250, 4, 0.5, train_members=(0, 1, 2, 3, 4, 5), iters=3000,
-                                       plain_sizes=(250, 500, 750))
+                                       plain_sizes=(250, 500, 750), substeps=60, share=False,
+                                       pairs_per_member=25)
             small["scale"] = "reduced: 250^2 coarse from 1000^2 fine (the full form is 1000^2 from 4000^2)"
             extra["learned_250"] = small
 
@@ -704,6 +705,11 @@ def run_ours(args, ws, rank, local, pg):
         cpu = {"value": rate, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
                "sample": f"orszag-tang 1000x1000 window of the workload, {done} RK4 steps in {el:.1f} s (FP64 oracle, OpenMP over rows)",
                "one_thread": {"value": rate1, "sample": f"the same window, {done1} RK4 steps in {el1:.1f} s on one thread"}}
+        rate2, _, done2, el2 = cpu_oracle_rate(2044, 2, budget_s=6.0)
+        rate3, _, done3, el3 = cpu_oracle_rate(2044, 1, budget_s=6.0, threads=1)
+        cpu["orszag_tang_2044"] = {
+            "value": rate2, "sample": f"orszag-tang 2044x2044 with the same noise, {done2} RK4 steps in {el2:.1f} s",
+            "one_thread": {"value": rate3, "sample": f"{done3} RK4 step in {el3:.1f} s on one thread"}}
 
     line = {
         "metric": "cell-updates/s per RK step", "value": value, "unit": "cell-updates/s",

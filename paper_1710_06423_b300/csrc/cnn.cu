@@ -434,20 +434,23 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, i
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::TMEM_COLS) : "memory");
 }
 // The same convolution fed by tensor-map copies: a tile is RT image rows x TP
-// pixels, its halo (RT+2 rows) arrives by one 4D tensor copy per row
-// ((8 channels, pixel, 8-channel chunk, row) of the NHWC image, so the copy lands
-// in the [chunk][pixel][8 ch] core-matrix layout directly) into one of two halo
-// buffers, while the other buffer's tile is multiplied and written back.  Pixels
-// left of column 0 or right of column W-1 read zeros and are then patched with
-// the periodic neighbour column.
+// pixels.  Each of its RT+2 halo rows arrives by one 3D tensor copy of the
+// NHWC image (box: C channels x 130 pixels x 1 row, 8320 contiguous bytes for
+// C = 32) into a staging buffer; the threads then transpose it into the
+// [chunk][pixel][8 ch] core-matrix layout the MMAs read, and the next tile's
+// rows are copied into the staging buffer while this tile is multiplied and
+// written back.  Pixels left of column 0 or right of column W-1 arrive as zeros
+// and take their periodic neighbour column (read from the image) during the
+// transpose.
 template <int CIN, int NC, int RT>
 struct TmaSmem {
     static constexpr int CPP = CIN / 8, NG = NC / 8;
-    static constexpr int ROW_BYTES = CPP * HP * 16;                 // one row's copy (dense)
-    static constexpr int ROW_STRIDE = (ROW_BYTES + 127) / 128 * 128;   // row copies start 128-byte aligned
+    static constexpr int ROW_BYTES = CPP * HP * 16;                    // one halo row, either layout
+    static constexpr int ROW_STRIDE = (ROW_BYTES + 127) / 128 * 128;   // rows start 128-byte aligned
     static constexpr int HALO_BYTES = (RT + 2) * ROW_STRIDE;
     static constexpr int W_BYTES = 9 * CPP * NG * 128;
-    static constexpr int BYTES = 128 + 2 * HALO_BYTES + W_BYTES + 64;   // + alignment of the base
+    // staging, core-matrix halo, weights, mbarriers + TMEM address, alignment of the base
+    static constexpr int BYTES = 128 + 2 * HALO_BYTES + W_BYTES + 64;
     static constexpr int TMEM_COLS = RT * NC <= 32 ? 32 : (RT * NC <= 64 ? 64 : 128);
 };
 
@@ -456,20 +459,23 @@ __device__ __forceinline__ void mbar_expect_tc(unsigned long long* bar, unsigned
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// One thread: the RT+2 row copies of the tile whose top-left output pixel is
+// (x0, y0) into the staging buffer; completion on bar.  The reads of the
+// staging buffer by the previous transpose are ordered before these writes.
 template <int CIN, int NC, int RT>
 __device__ __forceinline__ void issue_halo_tma(const CUtensorMap* tm, const ConvArgs& a, int y0, int x0,
-                                               unsigned char* halo, unsigned long long* bar)
+                                               unsigned char* stage, unsigned long long* bar)
 {
     using L = TmaSmem<CIN, NC, RT>;
-    mbar_expect_tc(bar, (unsigned)((RT + 2) * L::ROW_BYTES));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tc(bar, (unsigned)((RT + 2) * L::ROW_BYTES));
 #pragma unroll
     for (int r = 0; r < RT + 2; ++r) {
         int gy = y0 - 1 + r;
         gy = gy < 0 ? gy + a.H : (gy >= a.H ? gy - a.H : gy);
-        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                     " [%0], [%1, {%2, %3, %4, %5}], [%6];"
-                     :: "r"(smem_u32(halo + r * L::ROW_STRIDE)), "l"(tm), "r"(0), "r"(x0 - 1), "r"(0), "r"(gy),
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4}], [%5];"
+                     :: "r"(smem_u32(stage + r * L::ROW_STRIDE)), "l"(tm), "r"(0), "r"(x0 - 1), "r"(gy),
                         "r"(smem_u32(bar)) : "memory");
     }
 }
@@ -482,11 +488,12 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tma_kernel(const ConvArgs a, 
     constexpr int CPP = L::CPP, NG = L::NG;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);   // 128-byte aligned base
-    unsigned char* halo[2] = {smem, smem + L::HALO_BYTES};
+    unsigned char* stage = smem;                       // [row][pixel][CIN], as copied
+    unsigned char* halo = smem + L::HALO_BYTES;        // [row][chunk][pixel][8 ch], read by the MMAs
     unsigned char* wts = smem + 2 * L::HALO_BYTES;
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 2 * L::HALO_BYTES + L::W_BYTES);
-    // bar[0], bar[1]: halo buffers landed; bar[2]: accumulators complete
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem + 2 * L::HALO_BYTES + L::W_BYTES + 32);
+    // bar[0]: staging rows landed; bar[1]: accumulators complete
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem + 2 * L::HALO_BYTES + L::W_BYTES + 16);
     const int tid = threadIdx.x, warp = tid >> 5;
 
     for (int v = tid; v < NC * 9 * CPP; v += NTHR_TC) {
@@ -501,54 +508,54 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tma_kernel(const ConvArgs a, 
                      :: "r"(smem_u32(tmem_slot)), "r"(L::TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) { mbar_init_tc(&bar[0]); mbar_init_tc(&bar[1]); mbar_init_tc(&bar[2]); }
+    if (tid == 0) { mbar_init_tc(&bar[0]); mbar_init_tc(&bar[1]); }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the weights, for the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
-    const unsigned wbase = smem_u32(wts);
+    const unsigned wbase = smem_u32(wts), hbase = smem_u32(halo);
     constexpr unsigned IDESC = idesc_bf16(NC);
 
     const int tiles_x = (a.W + TP - 1) / TP, tiles_y = (a.H + RT - 1) / RT, ntiles = tiles_x * tiles_y;
     int tile = blockIdx.x;
     if (tid == 0 && tile < ntiles)
-        issue_halo_tma<CIN, NC, RT>(&tm, a, (tile / tiles_x) * RT, (tile % tiles_x) * TP, halo[0], &bar[0]);
-    unsigned lphase[2] = {0u, 0u}, mphase = 0u;
-    bool inflight[2] = {tile < ntiles, false};
-    for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
-        const int buf = i & 1;
+        issue_halo_tma<CIN, NC, RT>(&tm, a, (tile / tiles_x) * RT, (tile % tiles_x) * TP, stage, &bar[0]);
+    unsigned lphase = 0u, mphase = 0u;
+    bool inflight = tile < ntiles;
+    for (; tile < ntiles; tile += gridDim.x) {
         const int y0 = (tile / tiles_x) * RT, x0 = (tile % tiles_x) * TP;
-        const int next = tile + gridDim.x;
-        if (next < ntiles) {
-            if (tid == 0)
-                issue_halo_tma<CIN, NC, RT>(&tm, a, (next / tiles_x) * RT, (next % tiles_x) * TP, halo[buf ^ 1], &bar[buf ^ 1]);
-            inflight[buf ^ 1] = true;
-        }
-        const bool landed = mbar_wait_tc(&bar[buf], lphase[buf]);
-        if (landed) { lphase[buf] ^= 1u; inflight[buf] = false; }
+        const bool landed = mbar_wait_tc(&bar[0], lphase);
+        if (landed) { lphase ^= 1u; inflight = false; }
         if (__syncthreads_or(!landed)) {
             if (tid == 0) atomicExch(err, 1);
             break;
         }
-        // periodic columns: halo pixel 0 when the tile starts at column 0, and the
-        // pixel just right of column W-1 when the tile reaches it (zeros from the copy)
+        // transpose into the core-matrix layout; the periodic columns: halo pixel 0
+        // when the tile starts at column 0, and the pixel just right of column W-1
+        // when the tile reaches it (zeros in the copy) come from the image
         const int pr = a.W - x0 + 1;
-        for (int v = tid; v < 2 * (RT + 2) * CPP; v += NTHR_TC) {
-            const int side = v / ((RT + 2) * CPP), rem = v - side * (RT + 2) * CPP, r = rem / CPP, ch = rem - r * CPP;
-            const int px = side == 0 ? 0 : pr;
-            if ((side == 0 && x0 != 0) || (side == 1 && pr > HP - 1)) continue;
-            int gy = y0 - 1 + r;
-            gy = gy < 0 ? gy + a.H : (gy >= a.H ? gy - a.H : gy);
-            const int gx = side == 0 ? a.W - 1 : 0;
-            *reinterpret_cast<uint4*>(halo[buf] + r * L::ROW_STRIDE + (ch * HP + px) * 16) =
-                *reinterpret_cast<const uint4*>(a.in + ((long long)gy * a.W + gx) * CIN + ch * 8);
+#pragma unroll 4
+        for (int v = tid; v < (RT + 2) * HP * CPP; v += NTHR_TC) {
+            const int r = v / (HP * CPP), rem = v - r * (HP * CPP), px = rem / CPP, ch = rem - px * CPP;
+            uint4 val;
+            if ((px == 0 && x0 == 0) || px == pr) {
+                int gy = y0 - 1 + r;
+                gy = gy < 0 ? gy + a.H : (gy >= a.H ? gy - a.H : gy);
+                const int gx = px == 0 ? a.W - 1 : 0;
+                val = *reinterpret_cast<const uint4*>(a.in + ((long long)gy * a.W + gx) * CIN + ch * 8);
+            } else {
+                val = *reinterpret_cast<const uint4*>(stage + r * L::ROW_STRIDE + px * (CIN * 2) + ch * 16);
+            }
+            *reinterpret_cast<uint4*>(halo + r * L::ROW_STRIDE + (ch * HP + px) * 16) = val;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the halo, for the tensor core
         __syncthreads();
         if (tid == 0) {
+            const int next = tile + gridDim.x;
+            if (next < ntiles)
+                issue_halo_tma<CIN, NC, RT>(&tm, a, (next / tiles_x) * RT, (next % tiles_x) * TP, stage, &bar[0]);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned hbase = smem_u32(halo[buf]);
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
                 const int dy = tap / 3, dx = tap - dy * 3;
@@ -563,10 +570,11 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tma_kernel(const ConvArgs a, 
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(&bar[2])) : "memory");
+                         :: "r"(smem_u32(&bar[1])) : "memory");
         }
+        inflight = tile + (int)gridDim.x < ntiles;
         __syncwarp();
-        const bool done = mbar_wait_tc(&bar[2], mphase);
+        const bool done = mbar_wait_tc(&bar[1], mphase);
         mphase ^= 1u;
         if (__syncthreads_or(!done)) {
             if (tid == 0) atomicExch(err, 1);
@@ -575,12 +583,12 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tma_kernel(const ConvArgs a, 
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
         for (int q = 0; q < RT; ++q) epilogue_row<COUT, NC, MODE>(a, tmem, warp, q, y0 + q, x0 + tid);
+        // the accumulators and the core-matrix halo are reused by the next tile once every warp is done
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
-    // no copy may land after the CTA has left: wait (bounded) for any still in flight
-    for (int b = 0; b < 2; ++b)
-        if (inflight[b]) mbar_wait_tc(&bar[b], lphase[b]);
+    // no copy may land after the CTA has left: wait (bounded) for one still in flight
+    if (inflight) mbar_wait_tc(&bar[0], lphase);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -1150,9 +1158,9 @@ static cudaError_t tma_attr()
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcv::TmaSmem<CIN, NC, 2>::BYTES);
 }
 
-// Tensor map of an NHWC BF16 image with C channels as the 4D tensor (8 channels,
-// pixel, 8-channel chunk, row) and a box of (8, 130, C/8, 1): one copy lands one
-// halo row in the [chunk][pixel][8 ch] layout of the tcgen05 convolution.
+// Tensor map of an NHWC BF16 image with C channels (3D: channel, pixel, row)
+// whose box is one halo row of a tcgen05 tile: C channels x 130 pixels x 1 row,
+// contiguous in the image (pixels left of 0 or right of W-1 read zeros).
 static cudaError_t encode_nhwc_map(const void* img, int C, int W, int H, CUtensorMap* out)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -1162,11 +1170,11 @@ static cudaError_t encode_nhwc_map(const void* img, int C, int W, int H, CUtenso
                 cudaSuccess || q != cudaDriverEntryPointSuccess || !encode)
             return cudaErrorNotSupported;
     }
-    const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)(C / 8), (cuuint64_t)H};
-    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, 16, (cuuint64_t)W * C * 2};
-    const cuuint32_t box[4] = {8, (cuuint32_t)tcv::HP, (cuuint32_t)(C / 8), 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    if (encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(img), dims, strides, box, estr,
+    const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)C, (cuuint32_t)tcv::HP, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(img), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
