@@ -411,8 +411,10 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
     finals = pairs.final
     del pairs
     torch.cuda.empty_cache()
-    held_pairs = learned.Pairs()                # one-step gain on the held-out member over the horizon
-    learned.generate_pairs(held_pairs, 2024, held, nc, ratio, dt_c, steps, max(1, steps // 20), torch, solver_kw=kw)
+    # gain on the held-out member's pairs of the same kind (m steps, same target) over the horizon
+    held_pairs = learned.Pairs(substeps, share)
+    learned.generate_pairs(held_pairs, 2024, held, nc, ratio, dt_c, steps, max(substeps, steps // 20), torch,
+                           solver_kw=kw)
     held_gain = learned.residual_gain(net, held_pairs, osc, dx, torch)
     del held_pairs
     net.set_limiter(clip, keep_positive)
@@ -458,7 +460,10 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
         out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, solver_kw=kw)
     net.close()
     err = learned.l1_error(out, truth)
-    t_eq = None if fell_back else learned.equal_error_time(curve, float(err.mean()))
+    if alpha == 0:      # the relaxation chosen on the training members switched the correction off
+        t_eq = sec
+    else:
+        t_eq = None if fell_back else learned.equal_error_time(curve, float(err.mean()))
     return {"metric": "learned-vs-plain time at equal L1 error", "t_end": t_end, "coarse": nc, "fine": nf,
             "dt_coarse": dt_c, "steps_coarse": steps, "train_members": list(train_members), "held_out_member": held,
             "c_shk": kw["c_shk"], "member_steps_completed": completed, "pairs": n_pairs, "data_seconds": t_data,
@@ -468,7 +473,8 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
             "target": "per-step share, applied every step" if share else f"whole {substeps}-step correction, applied every {substeps} steps",
             "limiter": {"clip": clip, "keep_positive": keep_positive},
             "cnn_tensor_path": CNN_PATH_NAMES[tensor_path],
-            "held_out_one_step_residual_ratio": held_gain,
+            "held_out_residual_ratio": held_gain,
+            "correction_off": alpha == 0,
             "learned": {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec,
                         "fell_back_to_plain": fell_back},
             "plain": plain, "plain_time_at_learned_error": t_eq,
