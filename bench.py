@@ -85,6 +85,8 @@ def parse():
                     help="--learned with --substeps m: per-step share applied every step, or the whole "
                          "m-step correction applied every m steps")
     ap.add_argument("--pairs-per-member", type=int, default=100, help="training pairs per family member of --learned")
+    ap.add_argument("--iters", type=int, default=0, help="Adam iterations per training pass of --learned (0: default)")
+    ap.add_argument("--members", type=int, default=6, help="family members 0 .. N-1 that --learned trains on")
     ap.add_argument("--learned-coarse", type=int, default=1000,
                     help="coarse grid of --learned (fine = 4x; 250 is the reduced leg of the default line)")
     ap.add_argument("--only-batched", action="store_true",
@@ -486,7 +488,9 @@ def run_learned(args, local):
     the full form; 250: the reduced leg of the default line)."""
     n = args.learned_coarse
     kw = {} if n >= 1000 else dict(iters=3000, plain_sizes=(n, 2 * n, 3 * n))
-    res = learned_experiment(local, n, 4, args.t_end, train_members=(0, 1, 2, 3, 4, 5), substeps=args.substeps,
+    if args.iters:
+        kw["iters"] = args.iters
+    res = learned_experiment(local, n, 4, args.t_end, train_members=tuple(range(args.members)), substeps=args.substeps,
                              share=args.target == "share", pairs_per_member=args.pairs_per_member, **kw)
     print(json.dumps(res), flush=True)
 

@@ -388,9 +388,9 @@ const char *sac_cnn_last_error(const sac_cnn *c);
  * 8 x 16-pixel tiles); 1 = tcgen05 (5th-generation tensor cores: BF16 operands
  * staged in shared memory by 16-byte asynchronous copies, FP32 accumulators in
  * tensor memory, 4 rows x 128 pixels per tile); 2 = tcgen05 fed by tensor-map
- * copies of contiguous halo rows, transposed in shared memory (2 rows x 128
- * pixels per tile, the next tile's rows copied while the current one is
- * multiplied).  All accumulate in FP32 over the same tap and channel order
+ * copies, pipelined over two halo buffers and two accumulators (2 rows x 128
+ * pixels per tile: a tile's MMAs run while the previous tile is written back
+ * and the next one's halo is copied).  All accumulate in FP32 over the same tap and channel order
  * and store BF16 activations; on the B300 their outputs are bitwise equal.
  * Waits for the stream.  Errors: SAC_ERR_ARG (path not 0..2); SAC_ERR_CUDA (path 2 when the
  * driver could not encode the activations' tensor maps). */

@@ -242,10 +242,13 @@ __device__ __forceinline__ bool mbar_wait_tc(unsigned long long* bar, unsigned p
 {
     unsigned long long t0 = 0;
     for (;;) {
-        unsigned ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-        if (ok) return true;
+        // the clock is read once per 32 polls: polling is what finds the phase complete
+        for (int k = 0; k < 32; ++k) {
+            unsigned ok;
+            asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+            if (ok) return true;
+        }
         unsigned long long t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
         if (t0 == 0) t0 = t;
@@ -286,9 +289,11 @@ __device__ __forceinline__ void stage_halo_tc(const ConvArgs& a, int y0, int x0,
 
 // Epilogue of one accumulator row: tensor-memory columns q*NC .. q*NC+NC-1 of
 // this warp's 32 lanes (pixels), bias / ReLU / mask, stored as NHWC (BF16 or
-// FP32); image row gy, this thread's pixel gx (nothing is stored outside the image).
+// FP32); image row gy, this thread's pixel gx (nothing is stored outside the
+// image).  sb: the layer's bias staged in shared memory (read when a.bias is set).
 template <int COUT, int NC, int MODE>
-__device__ __forceinline__ void epilogue_row(const ConvArgs& a, unsigned tmem, int warp, int q, int gy, int gx)
+__device__ __forceinline__ void epilogue_row(const ConvArgs& a, const float* __restrict__ sb, unsigned tmem, int warp,
+                                             int q, int gy, int gx)
 {
     float acc[NC];
     {
@@ -324,15 +329,14 @@ __device__ __forceinline__ void epilogue_row(const ConvArgs& a, unsigned tmem, i
 #pragma unroll
         for (int o = 0; o < COUT; o += 4)
             *reinterpret_cast<float4*>(out + o) =
-                make_float4(acc[o] + a.bias[o], acc[o + 1] + a.bias[o + 1], acc[o + 2] + a.bias[o + 2],
-                            acc[o + 3] + a.bias[o + 3]);
+                make_float4(acc[o] + sb[o], acc[o + 1] + sb[o + 1], acc[o + 2] + sb[o + 2], acc[o + 3] + sb[o + 3]);
     } else {
         __align__(16) __nv_bfloat162 ov[COUT / 2];
 #pragma unroll
         for (int o = 0; o < COUT; o += 2) {
             float v0 = acc[o], v1 = acc[o + 1];
             if (MODE == MODE_RELU) {
-                if (a.bias) { v0 += a.bias[o]; v1 += a.bias[o + 1]; }
+                if (a.bias) { v0 += sb[o]; v1 += sb[o + 1]; }
                 v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f);
             } else {   // MODE_MASK: keep where the layer's activation is positive
                 const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(a.mask + pix * COUT + o);
@@ -372,6 +376,8 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, i
         if (o < COUT) cp16(dst, a.w + ((long long)o * 9 + tap) * CIN + ch * 8);
         else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
     }
+    __shared__ float s_bias[NC];
+    if (tid < NC) s_bias[tid] = (a.bias && tid < COUT) ? a.bias[tid] : 0.f;   // visible after the barrier below
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(tmem_slot)), "r"(L::TMEM_COLS) : "memory");
@@ -423,7 +429,7 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, i
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int gx = x0 + tid;
 #pragma unroll 1
-        for (int q = 0; q < ROWS; ++q) epilogue_row<COUT, NC, MODE>(a, tmem, warp, q, y0 + q, gx);
+        for (int q = 0; q < ROWS; ++q) epilogue_row<COUT, NC, MODE>(a, s_bias, tmem, warp, q, y0 + q, gx);
         // the accumulators and the halo are reused by the next tile once every warp is done
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -433,25 +439,25 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tc_kernel(const ConvArgs a, i
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::TMEM_COLS) : "memory");
 }
-// The same convolution fed by tensor-map copies: a tile is RT image rows x TP
-// pixels.  Each of its RT+2 halo rows arrives by one 3D tensor copy of the
-// NHWC image (box: C channels x 130 pixels x 1 row, 8320 contiguous bytes for
-// C = 32) into a staging buffer; the threads then transpose it into the
-// [chunk][pixel][8 ch] core-matrix layout the MMAs read, and the next tile's
-// rows are copied into the staging buffer while this tile is multiplied and
-// written back.  Pixels left of column 0 or right of column W-1 arrive as zeros
-// and take their periodic neighbour column (read from the image) during the
-// transpose.
+// The same convolution fed by tensor-map copies and software-pipelined: a tile
+// is RT image rows x TP pixels; each of its RT+2 halo rows arrives by one 4D
+// tensor copy ((8 channels, pixel, 8-channel chunk, row) of the NHWC image, so
+// the copy lands in the [chunk][pixel][8 ch] core-matrix layout directly) into
+// one of two halo buffers, and the tile's MMAs accumulate into one of two
+// tensor-memory accumulators.  While the MMAs of tile i run, the threads write
+// back tile i-1 and the copies of tile i+1 are in flight.  Pixels left of
+// column 0 or right of column W-1 read zeros and are then patched with the
+// periodic neighbour column.
 template <int CIN, int NC, int RT>
 struct TmaSmem {
     static constexpr int CPP = CIN / 8, NG = NC / 8;
-    static constexpr int ROW_BYTES = CPP * HP * 16;                    // one halo row, either layout
-    static constexpr int ROW_STRIDE = (ROW_BYTES + 127) / 128 * 128;   // rows start 128-byte aligned
+    static constexpr int ROW_BYTES = CPP * HP * 16;                    // one row's copy (dense)
+    static constexpr int ROW_STRIDE = (ROW_BYTES + 127) / 128 * 128;   // row copies start 128-byte aligned
     static constexpr int HALO_BYTES = (RT + 2) * ROW_STRIDE;
     static constexpr int W_BYTES = 9 * CPP * NG * 128;
-    // staging, core-matrix halo, weights, mbarriers + TMEM address, alignment of the base
-    static constexpr int BYTES = 128 + 2 * HALO_BYTES + W_BYTES + 64;
-    static constexpr int TMEM_COLS = RT * NC <= 32 ? 32 : (RT * NC <= 64 ? 64 : 128);
+    static constexpr int BYTES = 128 + 2 * HALO_BYTES + W_BYTES + 64;   // + alignment of the base
+    static constexpr int ACC_COLS = RT * NC;                           // one accumulator
+    static constexpr int TMEM_COLS = 2 * ACC_COLS <= 32 ? 32 : (2 * ACC_COLS <= 64 ? 64 : 128);
 };
 
 __device__ __forceinline__ void mbar_expect_tc(unsigned long long* bar, unsigned bytes)
@@ -460,11 +466,10 @@ __device__ __forceinline__ void mbar_expect_tc(unsigned long long* bar, unsigned
 }
 
 // One thread: the RT+2 row copies of the tile whose top-left output pixel is
-// (x0, y0) into the staging buffer; completion on bar.  The reads of the
-// staging buffer by the previous transpose are ordered before these writes.
+// (x0, y0) into a halo buffer; completion on bar.
 template <int CIN, int NC, int RT>
 __device__ __forceinline__ void issue_halo_tma(const CUtensorMap* tm, const ConvArgs& a, int y0, int x0,
-                                               unsigned char* stage, unsigned long long* bar)
+                                               unsigned char* halo, unsigned long long* bar)
 {
     using L = TmaSmem<CIN, NC, RT>;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -473,9 +478,9 @@ __device__ __forceinline__ void issue_halo_tma(const CUtensorMap* tm, const Conv
     for (int r = 0; r < RT + 2; ++r) {
         int gy = y0 - 1 + r;
         gy = gy < 0 ? gy + a.H : (gy >= a.H ? gy - a.H : gy);
-        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                     " [%0], [%1, {%2, %3, %4}], [%5];"
-                     :: "r"(smem_u32(stage + r * L::ROW_STRIDE)), "l"(tm), "r"(0), "r"(x0 - 1), "r"(gy),
+        asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                     :: "r"(smem_u32(halo + r * L::ROW_STRIDE)), "l"(tm), "r"(0), "r"(x0 - 1), "r"(0), "r"(gy),
                         "r"(smem_u32(bar)) : "memory");
     }
 }
@@ -488,12 +493,10 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tma_kernel(const ConvArgs a, 
     constexpr int CPP = L::CPP, NG = L::NG;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);   // 128-byte aligned base
-    unsigned char* stage = smem;                       // [row][pixel][CIN], as copied
-    unsigned char* halo = smem + L::HALO_BYTES;        // [row][chunk][pixel][8 ch], read by the MMAs
     unsigned char* wts = smem + 2 * L::HALO_BYTES;
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + 2 * L::HALO_BYTES + L::W_BYTES);
-    // bar[0]: staging rows landed; bar[1]: accumulators complete
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem + 2 * L::HALO_BYTES + L::W_BYTES + 16);
+    // bar[0], bar[1]: halo buffer landed; bar[2], bar[3]: accumulator complete
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem + 2 * L::HALO_BYTES + L::W_BYTES + 32);
     const int tid = threadIdx.x, warp = tid >> 5;
 
     for (int v = tid; v < NC * 9 * CPP; v += NTHR_TC) {
@@ -503,92 +506,113 @@ __global__ void __launch_bounds__(NTHR_TC) conv3x3_tma_kernel(const ConvArgs a, 
         else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
     }
     cp_wait();
+    __shared__ float s_bias[NC];
+    if (tid < NC) s_bias[tid] = (a.bias && tid < COUT) ? a.bias[tid] : 0.f;   // visible after the barrier below
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(tmem_slot)), "r"(L::TMEM_COLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid == 0) { mbar_init_tc(&bar[0]); mbar_init_tc(&bar[1]); }
+    if (tid == 0)
+        for (int k = 0; k < 4; ++k) mbar_init_tc(&bar[k]);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the weights, for the tensor core
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
-    const unsigned wbase = smem_u32(wts), hbase = smem_u32(halo);
+    const unsigned wbase = smem_u32(wts);
     constexpr unsigned IDESC = idesc_bf16(NC);
 
     const int tiles_x = (a.W + TP - 1) / TP, tiles_y = (a.H + RT - 1) / RT, ntiles = tiles_x * tiles_y;
-    int tile = blockIdx.x;
-    if (tid == 0 && tile < ntiles)
-        issue_halo_tma<CIN, NC, RT>(&tm, a, (tile / tiles_x) * RT, (tile % tiles_x) * TP, stage, &bar[0]);
-    unsigned lphase = 0u, mphase = 0u;
-    bool inflight = tile < ntiles;
-    for (; tile < ntiles; tile += gridDim.x) {
-        const int y0 = (tile / tiles_x) * RT, x0 = (tile % tiles_x) * TP;
-        const bool landed = mbar_wait_tc(&bar[0], lphase);
-        if (landed) { lphase ^= 1u; inflight = false; }
-        if (__syncthreads_or(!landed)) {
-            if (tid == 0) atomicExch(err, 1);
-            break;
-        }
-        // transpose into the core-matrix layout; the periodic columns: halo pixel 0
-        // when the tile starts at column 0, and the pixel just right of column W-1
-        // when the tile reaches it (zeros in the copy) come from the image
-        const int pr = a.W - x0 + 1;
-#pragma unroll 4
-        for (int v = tid; v < (RT + 2) * HP * CPP; v += NTHR_TC) {
-            const int r = v / (HP * CPP), rem = v - r * (HP * CPP), px = rem / CPP, ch = rem - px * CPP;
-            uint4 val;
-            if ((px == 0 && x0 == 0) || px == pr) {
+    const int first = blockIdx.x, n = first < ntiles ? (ntiles - 1 - first) / (int)gridDim.x + 1 : 0;
+    auto tile_of = [&](int i) { return first + i * (int)gridDim.x; };
+    // per buffer / accumulator k (bit k): phase of the next wait on its copies
+    // (lph) and on its MMAs (mph), copies in flight (infl), MMAs not yet waited (pend)
+    unsigned lph = 0u, mph = 0u, infl = 0u, pend = 0u;
+    auto halo = [&](int k) { return smem + k * L::HALO_BYTES; };
+    if (n > 0) {
+        if (tid == 0) issue_halo_tma<CIN, NC, RT>(&tm, a, (first / tiles_x) * RT, (first % tiles_x) * TP, halo(0), &bar[0]);
+        infl |= 1u;
+    }
+    bool ok = true;
+    for (int i = 0; i <= n && ok; ++i) {
+        const int b = i & 1;
+        if (i < n) {
+            // ---- tile i: copies landed, periodic columns, MMAs into accumulator b
+            const int t = tile_of(i), y0 = (t / tiles_x) * RT, x0 = (t % tiles_x) * TP;
+            const bool landed = mbar_wait_tc(&bar[b], (lph >> b) & 1u);
+            if (landed) { lph ^= 1u << b; infl &= ~(1u << b); }
+            if (__syncthreads_or(!landed)) { ok = false; break; }
+            const int pr = a.W - x0 + 1;
+            for (int v = tid; v < 2 * (RT + 2) * CPP; v += NTHR_TC) {
+                const int side = v / ((RT + 2) * CPP), rem = v - side * (RT + 2) * CPP, r = rem / CPP, ch = rem - r * CPP;
+                if ((side == 0 && x0 != 0) || (side == 1 && pr > HP - 1)) continue;
                 int gy = y0 - 1 + r;
                 gy = gy < 0 ? gy + a.H : (gy >= a.H ? gy - a.H : gy);
-                const int gx = px == 0 ? a.W - 1 : 0;
-                val = *reinterpret_cast<const uint4*>(a.in + ((long long)gy * a.W + gx) * CIN + ch * 8);
-            } else {
-                val = *reinterpret_cast<const uint4*>(stage + r * L::ROW_STRIDE + px * (CIN * 2) + ch * 16);
+                const int px = side == 0 ? 0 : pr, gx = side == 0 ? a.W - 1 : 0;
+                *reinterpret_cast<uint4*>(halo(b) + r * L::ROW_STRIDE + (ch * HP + px) * 16) =
+                    *reinterpret_cast<const uint4*>(a.in + ((long long)gy * a.W + gx) * CIN + ch * 8);
             }
-            *reinterpret_cast<uint4*>(halo + r * L::ROW_STRIDE + (ch * HP + px) * 16) = val;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the halo, for the tensor core
-        __syncthreads();
-        if (tid == 0) {
-            const int next = tile + gridDim.x;
-            if (next < ntiles)
-                issue_halo_tma<CIN, NC, RT>(&tm, a, (next / tiles_x) * RT, (next % tiles_x) * TP, stage, &bar[0]);
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned hbase = smem_u32(halo(b)), acc = tmem + b * L::ACC_COLS;
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap - dy * 3;
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap - dy * 3;
 #pragma unroll
-                for (int ks = 0; ks < CPP / 2; ++ks) {
-                    const unsigned long long bdesc = smem_desc(wbase + ((tap * CPP + 2 * ks) * NG) * 128, NG * 128, 128);
+                    for (int ks = 0; ks < CPP / 2; ++ks) {
+                        const unsigned long long bdesc = smem_desc(wbase + ((tap * CPP + 2 * ks) * NG) * 128, NG * 128, 128);
 #pragma unroll
-                    for (int q = 0; q < RT; ++q) {
-                        const unsigned aaddr = hbase + (q + dy) * L::ROW_STRIDE + ((2 * ks) * HP + dx) * 16;
-                        mma_bf16_tc(tmem + q * NC, smem_desc(aaddr, HP * 16, 128), bdesc, IDESC, (tap | ks) != 0);
+                        for (int q = 0; q < RT; ++q) {
+                            const unsigned aaddr = hbase + (q + dy) * L::ROW_STRIDE + ((2 * ks) * HP + dx) * 16;
+                            mma_bf16_tc(acc + q * NC, smem_desc(aaddr, HP * 16, 128), bdesc, IDESC, (tap | ks) != 0);
+                        }
                     }
                 }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_u32(&bar[2 + b])) : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(&bar[1])) : "memory");
+            pend |= 1u << b;
         }
-        inflight = tile + (int)gridDim.x < ntiles;
-        __syncwarp();
-        const bool done = mbar_wait_tc(&bar[1], mphase);
-        mphase ^= 1u;
-        if (__syncthreads_or(!done)) {
-            if (tid == 0) atomicExch(err, 1);
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (i >= 1) {
+            // ---- tile i-1: its MMAs are done, so its halo buffer takes tile i+1's
+            // copies; then its accumulator is written back
+            const int pb = b ^ 1, t = tile_of(i - 1), y0 = (t / tiles_x) * RT, x0 = (t % tiles_x) * TP;
+            __syncwarp();
+            const bool done = mbar_wait_tc(&bar[2 + pb], (mph >> pb) & 1u);
+            if (done) { mph ^= 1u << pb; pend &= ~(1u << pb); }
+            if (__syncthreads_or(!done)) { ok = false; break; }
+            if (i + 1 < n) {
+                const int nt = tile_of(i + 1);
+                if (tid == 0)
+                    issue_halo_tma<CIN, NC, RT>(&tm, a, (nt / tiles_x) * RT, (nt % tiles_x) * TP, halo(pb), &bar[pb]);
+                infl |= 1u << pb;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll 1
-        for (int q = 0; q < RT; ++q) epilogue_row<COUT, NC, MODE>(a, tmem, warp, q, y0 + q, x0 + tid);
-        // the accumulators and the core-matrix halo are reused by the next tile once every warp is done
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+            for (int q = 0; q < RT; ++q)
+                epilogue_row<COUT, NC, MODE>(a, s_bias, tmem + pb * L::ACC_COLS, warp, q, y0 + q, x0 + tid);
+            // accumulator pb is reused by tile i+1 once every warp has read it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        } else if (n > 1) {
+            // tile 1's copies go to the second halo buffer, unused so far
+            if (tid == 0) {
+                const int nt = tile_of(1);
+                issue_halo_tma<CIN, NC, RT>(&tm, a, (nt / tiles_x) * RT, (nt % tiles_x) * TP, halo(1), &bar[1]);
+            }
+            infl |= 2u;
+        }
     }
-    // no copy may land after the CTA has left: wait (bounded) for one still in flight
-    if (inflight) mbar_wait_tc(&bar[0], lphase);
+    if (!ok && tid == 0) atomicExch(err, 1);
+    // nothing may land in shared or tensor memory after the CTA has left: wait
+    // (bounded) for copies and MMAs still in flight
+    for (int k = 0; k < 2; ++k) {
+        if ((infl >> k) & 1u) mbar_wait_tc(&bar[k], (lph >> k) & 1u);
+        if ((pend >> k) & 1u) mbar_wait_tc(&bar[2 + k], (mph >> k) & 1u);
+    }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -1059,15 +1083,19 @@ static cudaError_t run_conv(sac_cnn* c, const __nv_bfloat16* in, const __nv_bflo
             if (c->tmap_ptr[k] == in && c->tmap_c[k] == CIN) tm = &c->tmaps[k];
         if (!tm) return cudaErrorInvalidValue;
         constexpr int bytes = tcv::TmaSmem<CIN, NC, RT>::BYTES;
-        constexpr int per_sm = (227 * 1024) / bytes < 8 ? (227 * 1024) / bytes : 8;
+        // resident CTAs per SM: as many as shared memory and the 512 tensor-memory columns allow
+        constexpr int by_smem = (227 * 1024) / (bytes + 1024), by_tmem = 512 / tcv::TmaSmem<CIN, NC, RT>::TMEM_COLS;
+        constexpr int per_sm = by_smem < by_tmem ? by_smem : by_tmem;
         const int tiles = ((c->W + tcv::TP - 1) / tcv::TP) * ((c->H + RT - 1) / RT);
         const int cap = per_sm * c->nsm;
         tcv::conv3x3_tma_kernel<CIN, COUT, NC, MODE, RT>
             <<<tiles < cap ? tiles : cap, tcv::NTHR_TC, bytes, c->stream>>>(a, *tm, c->tc_err);
     } else if (c->tensor_path == 1) {
         constexpr int NC = COUT < 16 ? 16 : COUT;
-        // resident CTAs per SM as the shared memory allows (two halo buffers each)
-        constexpr int per_sm = (227 * 1024) / tcv::TcSmem<CIN, NC>::BYTES < 8 ? (227 * 1024) / tcv::TcSmem<CIN, NC>::BYTES : 8;
+        // resident CTAs per SM: as many as shared memory and the 512 tensor-memory columns allow
+        constexpr int by_smem = (227 * 1024) / (tcv::TcSmem<CIN, NC>::BYTES + 1024);
+        constexpr int by_tmem = 512 / tcv::TcSmem<CIN, NC>::TMEM_COLS;
+        constexpr int per_sm = by_smem < by_tmem ? by_smem : by_tmem;
         const int tiles = ((c->W + tcv::TP - 1) / tcv::TP) * ((c->H + tcv::ROWS - 1) / tcv::ROWS);
         const int cap = per_sm * c->nsm;
         const int grid = tiles < cap ? tiles : cap;
@@ -1158,9 +1186,10 @@ static cudaError_t tma_attr()
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcv::TmaSmem<CIN, NC, 2>::BYTES);
 }
 
-// Tensor map of an NHWC BF16 image with C channels (3D: channel, pixel, row)
-// whose box is one halo row of a tcgen05 tile: C channels x 130 pixels x 1 row,
-// contiguous in the image (pixels left of 0 or right of W-1 read zeros).
+// Tensor map of an NHWC BF16 image with C channels as the 4D tensor
+// (8 channels, pixel, 8-channel chunk, row) and a box of (8, 130, C/8, 1): one
+// copy lands one halo row in the [chunk][pixel][8 ch] layout of the tcgen05
+// convolution (pixels left of 0 or right of W-1 read zeros).
 static cudaError_t encode_nhwc_map(const void* img, int C, int W, int H, CUtensorMap* out)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -1170,11 +1199,11 @@ static cudaError_t encode_nhwc_map(const void* img, int C, int W, int H, CUtenso
                 cudaSuccess || q != cudaDriverEntryPointSuccess || !encode)
             return cudaErrorNotSupported;
     }
-    const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H};
-    const cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)C, (cuuint32_t)tcv::HP, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    if (encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(img), dims, strides, box, estr,
+    const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)(C / 8), (cuuint64_t)H};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, 16, (cuuint64_t)W * C * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)tcv::HP, (cuuint32_t)(C / 8), 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (encode(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(img), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
