@@ -79,14 +79,15 @@ def parse():
     ap.add_argument("--learned", action="store_true",
                     help="run the learned coarse-grid correction experiment instead (several minutes)")
     ap.add_argument("--t-end", type=float, default=0.5, help="horizon of the learned experiment")
-    ap.add_argument("--substeps", type=int, default=1,
-                    help="coarse steps per training pair of --learned (per-step share of the m-step correction)")
-    ap.add_argument("--target", choices=["share", "whole"], default="share",
-                    help="--learned with --substeps m: per-step share applied every step, or the whole "
-                         "m-step correction applied every m steps")
-    ap.add_argument("--pairs-per-member", type=int, default=100, help="training pairs per family member of --learned")
-    ap.add_argument("--iters", type=int, default=0, help="Adam iterations per training pass of --learned (0: default)")
-    ap.add_argument("--members", type=int, default=6, help="family members 0 .. N-1 that --learned trains on")
+    ap.add_argument("--substeps", type=int, default=0,
+                    help="coarse steps m per training pair of --learned (0: 4%% of the horizon's steps)")
+    ap.add_argument("--target", choices=["share", "whole"], default="whole",
+                    help="--learned: the whole m-step correction applied every m steps, or its per-step "
+                         "share applied every step")
+    ap.add_argument("--pairs-per-member", type=int, default=25, help="training pairs per family member of --learned")
+    ap.add_argument("--iters", type=int, default=0,
+                    help="Adam iterations per training pass of --learned (0: LEARNED_ITERS for the grid)")
+    ap.add_argument("--members", type=int, default=12, help="family members 0 .. N-1 that --learned trains on")
     ap.add_argument("--learned-coarse", type=int, default=1000,
                     help="coarse grid of --learned (fine = 4x; 250 is the reduced leg of the default line)")
     ap.add_argument("--only-batched", action="store_true",
@@ -347,6 +348,8 @@ def run_batched(args, ws, local, pg, torch, per_size=True):
 
 
 RELAXATIONS = (0.0, 0.125, 0.25, 0.5, 1.0)
+# Adam iterations per training pass by coarse grid (longer training kept paying off at both sizes)
+LEARNED_ITERS = {250: 30000, 1000: 96000}
 
 
 def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=6000, noise=1.0, alpha=None,
@@ -483,14 +486,20 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
             "speedup_at_equal_error": (t_eq / sec) if t_eq else None}
 
 
+def learned_substeps(n: int, t_end: float) -> int:
+    """Default m: 4% of the coarse steps to t_end (the coarse step is 0.25 dx / 3)."""
+    return max(1, int(round(0.04 * t_end * 12.0 * n)))
+
+
 def run_learned(args, local):
     """The experiment: n^2 coarse from (4n)^2 fine runs, horizon t_end (n = 1000:
     the full form; 250: the reduced leg of the default line)."""
     n = args.learned_coarse
-    kw = {} if n >= 1000 else dict(iters=3000, plain_sizes=(n, 2 * n, 3 * n))
-    if args.iters:
-        kw["iters"] = args.iters
-    res = learned_experiment(local, n, 4, args.t_end, train_members=tuple(range(args.members)), substeps=args.substeps,
+    kw = dict(iters=args.iters or LEARNED_ITERS.get(n, 30000))
+    if n < 1000:
+        kw["plain_sizes"] = (n, 2 * n, 3 * n)
+    m = args.substeps or learned_substeps(n, args.t_end)
+    res = learned_experiment(local, n, 4, args.t_end, train_members=tuple(range(args.members)), substeps=m,
                              share=args.target == "share", pairs_per_member=args.pairs_per_member, **kw)
     print(json.dumps(res), flush=True)
 
@@ -702,9 +711,9 @@ def run_ours(args, ws, rank, local, pg):
         if ws == 1:
             # the learned coarse-grid correction at a reduced scale (250^2 coarse from
             # 1000^2 fine runs, horizon 0.5); --learned runs the 1000^2 / 4000^2 form
-            small = learned_experiment(local, 250, 4, 0.5, train_members=(0, 1, 2, 3, 4, 5), iters=3000,
-                                       plain_sizes=(250, 500, 750), substeps=60, share=False,
-                                       pairs_per_member=25)
+            small = learned_experiment(local, 250, 4, 0.5, train_members=tuple(range(12)), iters=LEARNED_ITERS[250],
+                                       plain_sizes=(250, 500, 750), substeps=learned_substeps(250, 0.5),
+                                       share=False, pairs_per_member=25)
             small["scale"] = "reduced: 250^2 coarse from 1000^2 fine (the full form is 1000^2 from 4000^2)"
             extra["learned_250"] = small
 
