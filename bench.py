@@ -352,7 +352,7 @@ RELAXATIONS = (0.0, 0.125, 0.25, 0.5, 1.0)
 LEARNED_ITERS = {250: 30000, 1000: 96000}
 
 
-def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=6000, noise=1.0, alpha=None,
+def learned_experiment(local, nc, ratio, t_end, train_members, held=(20, 21, 22), iters=6000, noise=1.0, alpha=None,
                        clip=3.0, keep_positive=True, plain_sizes=None, pairs_per_member=100, tensor_path=0,
                        rounds=1, select_members=2, substeps=1, share=True):
     """Learned nc^2 coarse run vs plain FP32 runs at equal L1 error against the
@@ -416,9 +416,9 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
     finals = pairs.final
     del pairs
     torch.cuda.empty_cache()
-    # gain on the held-out member's pairs of the same kind (m steps, same target) over the horizon
+    # gain on the first held-out member's pairs of the same kind (m steps, same target) over the horizon
     held_pairs = learned.Pairs(substeps, share)
-    learned.generate_pairs(held_pairs, 2024, held, nc, ratio, dt_c, steps, max(substeps, steps // 20), torch,
+    learned.generate_pairs(held_pairs, 2024, held[0], nc, ratio, dt_c, steps, max(substeps, steps // 20), torch,
                            solver_kw=kw)
     held_gain = learned.residual_gain(net, held_pairs, osc, dx, torch)
     del held_pairs
@@ -432,45 +432,57 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
         net.set_scales(learned.FEATURE_SCALES, osc * alpha)
     del finals
 
-    w0f, gamma = learned.family_state(2024, held, nf)
-    fine_out = torch.empty((6, nf, nf), dtype=torch.float32, device="cuda")
-    with Solver(nx=nf, ny=nf, precision=FP32, gamma=gamma, **kw) as fine:
-        fine.set_state(w0f, None, 0.0)
-        fine.set_fixed_dt(dt_c / ratio)
-        fine.steps(steps * ratio)
-        fine.get_state_dev(fine_out)
-        fine.sync()
-    truth = learned.downsample(fine_out, nc, torch)
-    del fine_out
-    wf_dev = torch.from_numpy(w0f.astype(np.float32)).cuda().contiguous()
-    curve, plain = [], {}
-    for n in plain_sizes or (nc, 2 * nc, 3 * nc):
-        w0n = learned.downsample(wf_dev, n, torch) if nf % n == 0 else None
-        if w0n is None:
-            w0n_np, _ = learned.family_state(2024, held, n)
+    def evaluate(member):
+        """The learned and plain runs of one held-out member against its fine run."""
+        w0f, gamma = learned.family_state(2024, member, nf)
+        fine_out = torch.empty((6, nf, nf), dtype=torch.float32, device="cuda")
+        with Solver(nx=nf, ny=nf, precision=FP32, gamma=gamma, **kw) as fine:
+            fine.set_state(w0f, None, 0.0)
+            fine.set_fixed_dt(dt_c / ratio)
+            fine.steps(steps * ratio)
+            fine.get_state_dev(fine_out)
+            fine.sync()
+        truth = learned.downsample(fine_out, nc, torch)
+        del fine_out
+        wf_dev = torch.from_numpy(w0f.astype(np.float32)).cuda().contiguous()
+        curve, plain = [], {}
+        for n in plain_sizes or (nc, 2 * nc, 3 * nc):
+            w0n = learned.downsample(wf_dev, n, torch) if nf % n == 0 else None
+            if w0n is None:
+                w0n_np, _ = learned.family_state(2024, member, n)
+            else:
+                w0n_np = w0n.double().cpu().numpy()
+            out, sec = learned.run_plain(w0n_np, gamma, n, dt_c * nc / n, steps * n // nc, torch, solver_kw=kw)
+            err = learned.l1_error(learned.downsample(out, nc, torch), truth)   # n is a multiple of nc
+            plain[n] = {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec}
+            curve.append((sec, float(err.mean())))
+        w0c = learned.downsample(wf_dev, nc, torch).double().cpu().numpy()
+        fell_back = False
+        try:
+            out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, net=net if alpha > 0 else None,
+                                         solver_kw=kw, every=every_apply)
+        except SacError:
+            # the plain coarse solver is the fallback of the learned run
+            fell_back = True
+            out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, solver_kw=kw)
+        err = learned.l1_error(out, truth)
+        if alpha == 0:      # the relaxation chosen on the training members switched the correction off
+            t_eq = sec
         else:
-            w0n_np = w0n.double().cpu().numpy()
-        out, sec = learned.run_plain(w0n_np, gamma, n, dt_c * nc / n, steps * n // nc, torch, solver_kw=kw)
-        err = learned.l1_error(learned.downsample(out, nc, torch), truth)   # n is a multiple of nc
-        plain[n] = {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec}
-        curve.append((sec, float(err.mean())))
-    w0c = learned.downsample(wf_dev, nc, torch).double().cpu().numpy()
-    fell_back = False
-    try:
-        out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, net=net if alpha > 0 else None,
-                                     solver_kw=kw, every=every_apply)
-    except SacError:
-        # the plain coarse solver is the fallback of the learned run
-        fell_back = True
-        out, sec = learned.run_plain(w0c, gamma, nc, dt_c, steps, torch, solver_kw=kw)
+            t_eq = None if fell_back else learned.equal_error_time(curve, float(err.mean()))
+        return {"member": member,
+                "learned": {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec,
+                            "fell_back_to_plain": fell_back},
+                "plain": plain, "plain_time_at_learned_error": t_eq,
+                "speedup_at_equal_error": (t_eq / sec) if t_eq else None}
+
+    evals = [evaluate(m) for m in held]
     net.close()
-    err = learned.l1_error(out, truth)
-    if alpha == 0:      # the relaxation chosen on the training members switched the correction off
-        t_eq = sec
-    else:
-        t_eq = None if fell_back else learned.equal_error_time(curve, float(err.mean()))
+    sp = [e["speedup_at_equal_error"] for e in evals]
+    geomean = float(np.exp(np.mean(np.log(sp)))) if all(v is not None for v in sp) else None
+    first = evals[0]
     return {"metric": "learned-vs-plain time at equal L1 error", "t_end": t_end, "coarse": nc, "fine": nf,
-            "dt_coarse": dt_c, "steps_coarse": steps, "train_members": list(train_members), "held_out_member": held,
+            "dt_coarse": dt_c, "steps_coarse": steps, "train_members": list(train_members), "held_out_member": held[0],
             "c_shk": kw["c_shk"], "member_steps_completed": completed, "pairs": n_pairs, "data_seconds": t_data,
             "train_iters": iters, "train_seconds": t_train, "losses": losses, "noise": noise, "alpha": alpha,
             "alpha_selection_l1": alpha_errs,
@@ -480,10 +492,10 @@ def learned_experiment(local, nc, ratio, t_end, train_members, held=20, iters=60
             "cnn_tensor_path": CNN_PATH_NAMES[tensor_path],
             "held_out_residual_ratio": held_gain,
             "correction_off": alpha == 0,
-            "learned": {"l1": err.tolist(), "l1_mean": float(err.mean()), "seconds": sec,
-                        "fell_back_to_plain": fell_back},
-            "plain": plain, "plain_time_at_learned_error": t_eq,
-            "speedup_at_equal_error": (t_eq / sec) if t_eq else None}
+            "learned": first["learned"], "plain": first["plain"],
+            "plain_time_at_learned_error": first["plain_time_at_learned_error"],
+            "speedup_at_equal_error": first["speedup_at_equal_error"],
+            "held_out": evals, "speedup_geomean_over_held_out": geomean}
 
 
 def learned_substeps(n: int, t_end: float) -> int:
