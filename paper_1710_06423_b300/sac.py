@@ -195,6 +195,25 @@ def _dp(a):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+_F32, _F64, _I64 = ("torch.float32",), ("torch.float64",), ("torch.int64", "torch.uint64")
+
+
+def _dev_ptr(t, name: str, numel: int, dtypes, device: int) -> ctypes.c_void_p:
+    """Device address of tensor ``t`` for a C call that receives only a bare
+    pointer.  The library cannot see how large the buffer is, so a tensor that
+    is too small, strided, of another dtype or on another device would be read
+    or written past its end on the GPU: refuse it here, before the call."""
+    if t.numel() != numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, {numel} needed")
+    if str(t.dtype) not in dtypes:
+        raise ValueError(f"{name} has dtype {t.dtype}, not {' or '.join(dtypes)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if not t.is_cuda or t.device.index != device:
+        raise ValueError(f"{name} must live on cuda:{device}, not {t.device}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 class Solver:
     """One run on one GPU: ``Solver(nx=..., ny=..., precision=FP32, ...)``.
 
@@ -275,15 +294,18 @@ class Solver:
         self._check(load().sac_get_state(self._ctx, _dp(w), ctypes.byref(t)), "sac_get_state")
         return t.value
 
+    def _state_ptr(self, t, name: str, nfields: int = NF) -> ctypes.c_void_p:
+        return _dev_ptr(t, name, nfields * self.nx * self.ny, _F32 if self.fp32 else _F64, self.params.device)
+
     def set_state_dev(self, w, bg=None, t: float = 0.0):
         """Device tensors of the context's dtype, shape (6, ny, nx) / (4, ny, nx), contiguous."""
-        self._check(load().sac_set_state_dev(self._ctx, ctypes.c_void_p(w.data_ptr()),
-                                             None if bg is None else ctypes.c_void_p(bg.data_ptr()),
-                                             float(t)), "sac_set_state_dev")
+        wp = self._state_ptr(w, "w")
+        bp = None if bg is None else self._state_ptr(bg, "bg", NB)
+        self._check(load().sac_set_state_dev(self._ctx, wp, bp, float(t)), "sac_set_state_dev")
 
     def get_state_dev(self, w) -> None:
-        self._check(load().sac_get_state_dev(self._ctx, ctypes.c_void_p(w.data_ptr()), None),
-                    "sac_get_state_dev")
+        wp = self._state_ptr(w, "w")
+        self._check(load().sac_get_state_dev(self._ctx, wp, None), "sac_get_state_dev")
 
     def step(self, dt: float = 0.0) -> float:
         out = ctypes.c_double()
@@ -364,19 +386,26 @@ class Solver:
         self._check(load().sac_halo_size(self._ctx, int(side), ctypes.byref(n)), "sac_halo_size")
         return n.value
 
+    def _strip_ptr(self, side: int, strip) -> ctypes.c_void_p:
+        return _dev_ptr(strip, "strip", self.halo_size(side), _F32 if self.fp32 else _F64, self.params.device)
+
     def halo_pack(self, side: int, strip):
         """Pack the strip next to `side` into a device tensor of halo_size(side) elements."""
-        self._check(load().sac_halo_pack(self._ctx, int(side), ctypes.c_void_p(strip.data_ptr())), "sac_halo_pack")
+        sp = self._strip_ptr(side, strip)
+        self._check(load().sac_halo_pack(self._ctx, int(side), sp), "sac_halo_pack")
 
     def halo_unpack(self, side: int, strip):
-        self._check(load().sac_halo_unpack(self._ctx, int(side), ctypes.c_void_p(strip.data_ptr())), "sac_halo_unpack")
+        sp = self._strip_ptr(side, strip)
+        self._check(load().sac_halo_unpack(self._ctx, int(side), sp), "sac_halo_unpack")
 
     def get_cmax_bits(self, bits):
         """Copy the two running signal-speed keys into a device int64/uint64 tensor of 2."""
-        self._check(load().sac_get_cmax_bits(self._ctx, ctypes.c_void_p(bits.data_ptr())), "sac_get_cmax_bits")
+        bp = _dev_ptr(bits, "bits", 2, _I64, self.params.device)
+        self._check(load().sac_get_cmax_bits(self._ctx, bp), "sac_get_cmax_bits")
 
     def set_cmax_bits(self, bits):
-        self._check(load().sac_set_cmax_bits(self._ctx, ctypes.c_void_p(bits.data_ptr())), "sac_set_cmax_bits")
+        bp = _dev_ptr(bits, "bits", 2, _I64, self.params.device)
+        self._check(load().sac_set_cmax_bits(self._ctx, bp), "sac_set_cmax_bits")
 
     def debug_drop_copies(self, on: bool):
         """Test hook of the bounded copy waits (see sac_debug_drop_copies)."""
@@ -556,37 +585,45 @@ class CNN:
         b = np.ascontiguousarray(out_scale, dtype=np.float32)
         self._check(load().sac_cnn_set_scales(self._c, _fp(a), _fp(b)), "sac_cnn_set_scales")
 
+    def _ptr(self, t, name: str, per_cell: int = NF) -> ctypes.c_void_p:
+        """Device address of a float32 tensor of per_cell values per cell of the grid."""
+        return _dev_ptr(t, name, per_cell * self.nx * self.ny, _F32, self.device)
+
     def forward(self, w_dev, gamma, dx, dy, pred_dev):
-        self._check(load().sac_cnn_forward(self._c, ctypes.c_void_p(w_dev.data_ptr()), gamma, dx, dy,
-                                           ctypes.c_void_p(pred_dev.data_ptr())), "sac_cnn_forward")
+        wp, pp = self._ptr(w_dev, "w_dev"), self._ptr(pred_dev, "pred_dev", 8)
+        self._check(load().sac_cnn_forward(self._c, wp, gamma, dx, dy, pp), "sac_cnn_forward")
 
     def grads(self, w_dev, next_dev, gamma, dx, dy):
+        wp, np_ = self._ptr(w_dev, "w_dev"), self._ptr(next_dev, "next_dev")
         g = np.zeros(self.nparams, dtype=np.float32)
         loss = ctypes.c_double()
-        self._check(load().sac_cnn_grads(self._c, ctypes.c_void_p(w_dev.data_ptr()),
-                                         ctypes.c_void_p(next_dev.data_ptr()), gamma, dx, dy, _fp(g),
-                                         ctypes.byref(loss)), "sac_cnn_grads")
+        self._check(load().sac_cnn_grads(self._c, wp, np_, gamma, dx, dy, _fp(g), ctypes.byref(loss)),
+                    "sac_cnn_grads")
         return loss.value, g
 
     def train_step(self, w_dev, next_dev, gamma, dx, dy, lr, want_loss=True):
+        wp, np_ = self._ptr(w_dev, "w_dev"), self._ptr(next_dev, "next_dev")
         loss = ctypes.c_double()
-        self._check(load().sac_cnn_train_step(self._c, ctypes.c_void_p(w_dev.data_ptr()),
-                                              ctypes.c_void_p(next_dev.data_ptr()), gamma, dx, dy, lr,
+        self._check(load().sac_cnn_train_step(self._c, wp, np_, gamma, dx, dy, lr,
                                               ctypes.byref(loss) if want_loss else None), "sac_cnn_train_step")
         return loss.value
 
     def perturb(self, w_dev, out_dev, amp, seed: int):
+        wp, op = self._ptr(w_dev, "w_dev"), self._ptr(out_dev, "out_dev")
         a = np.ascontiguousarray(amp, dtype=np.float32)
-        self._check(load().sac_cnn_perturb(self._c, ctypes.c_void_p(w_dev.data_ptr()),
-                                           ctypes.c_void_p(out_dev.data_ptr()), _fp(a), int(seed)), "sac_cnn_perturb")
+        self._check(load().sac_cnn_perturb(self._c, wp, op, _fp(a), int(seed)), "sac_cnn_perturb")
 
     def apply(self, solver):
         self._check(load().sac_cnn_apply(solver._ctx, self._c), "sac_cnn_apply")
 
 
 def block_average(fine_dev, nfields, nxf, nyf, r, coarse_dev, stream="current"):
-    rc = load().sac_block_average(ctypes.c_void_p(fine_dev.data_ptr()), nfields, nxf, nyf, r,
-                                  ctypes.c_void_p(coarse_dev.data_ptr()), _stream_handle(stream))
+    if r < 1 or nxf % r or nyf % r:
+        raise ValueError(f"block size {r} does not divide {nxf} x {nyf}")
+    dev = fine_dev.device.index if fine_dev.is_cuda else -1
+    fp = _dev_ptr(fine_dev, "fine_dev", nfields * nxf * nyf, _F32, dev)
+    cp = _dev_ptr(coarse_dev, "coarse_dev", nfields * (nxf // r) * (nyf // r), _F32, dev)
+    rc = load().sac_block_average(fp, nfields, nxf, nyf, r, cp, _stream_handle(stream, max(dev, 0)))
     if rc != SAC_OK:
         raise SacError(rc, "sac_block_average")
 
