@@ -151,7 +151,9 @@ int sac_get_state_dev(sac_ctx *c, void *w_dev, double *t);
 int sac_step(sac_ctx *c, double dt, double *dt_taken);
 
 /* nsteps CFL steps.  ASYNC: no host synchronisation; errors surface at the
- * next synchronising call.  Steps are CUDA-graph replays after the first. */
+ * next synchronising call.  Steps are replays of a one-step and a 16-step
+ * CUDA graph, both captured by the first call (and again after a change of
+ * tile configuration or cell size), whatever its step count. */
 int sac_steps(sac_ctx *c, long nsteps);
 
 /*
@@ -210,23 +212,33 @@ int sac_sync(sac_ctx *c);
  * SAC_TILE_32x32: 32 x 32 cells, 256 threads, 2 CTAs per SM (the default);
  * SAC_TILE_64x16: 64 x 16 cells, 256 threads, 2 CTAs per SM;
  * SAC_TILE_32x16: 32 x 16 cells, 128 threads, 3 CTAs per SM.
- * Every shape gives bit-for-bit the same results (each cell's arithmetic does
- * not depend on where the tile boundaries fall); they differ in halo overhead
- * per cell and in how evenly the tiles fill the GPU. */
-enum { SAC_TILE_32x32 = 0, SAC_TILE_64x16 = 1, SAC_TILE_32x16 = 2 };
+ * SAC_TILE_KERNEL_GHOSTS + shape (3, 4, 5): the same shape, with the ghost
+ * frame of every stage output (periodic and outflow copies) written by the
+ * stage kernel itself after each tile next to a side, instead of by a separate
+ * ghost-frame kernel after each stage (one launch per stage instead of two);
+ * runs with a background, gravity or the single-face variant use the separate
+ * kernel whatever the setting.
+ * Every configuration gives bit-for-bit the same results (each cell's
+ * arithmetic does not depend on where the tile boundaries fall, and the ghost
+ * cells receive the same copies); they differ in halo overhead per cell, in
+ * how evenly the tiles fill the GPU and in launches per step. */
+enum { SAC_TILE_32x32 = 0, SAC_TILE_64x16 = 1, SAC_TILE_32x16 = 2, SAC_TILE_KERNEL_GHOSTS = 3 };
 
-/* Use tile shape `tile` (SAC_TILE_*) for the later steps of an FP32 context
- * (the gravity and single-face variants always run 32 x 32).  Waits for the
- * context's stream.  Errors: SAC_ERR_ARG (unknown shape, FP64 context). */
+/* Use tile configuration `tile` (SAC_TILE_* shape, plus SAC_TILE_KERNEL_GHOSTS
+ * for the in-kernel ghost frame) for the later steps of an FP32 context (the
+ * gravity and single-face variants always run 32 x 32).  Waits for the
+ * context's stream.  Errors: SAC_ERR_ARG (unknown configuration, FP64 context). */
 int sac_set_tile(sac_ctx *c, int tile);
 
-/* The context's current tile shape.  Errors: SAC_ERR_ARG. */
+/* The context's current tile configuration.  Errors: SAC_ERR_ARG. */
 int sac_get_tile(const sac_ctx *c, int *tile);
 
-/* Autotuner of the tile shape: for every shape, one warm-up CFL step and
+/* Autotuner of the tile configuration: for every shape, with and without the
+ * in-kernel ghost frame (shapes only for runs with a background or the
+ * single-face variant), one warm-up CFL step and
  * `trials` timed CFL steps (CUDA events on the context's stream) from the
  * current state, which is restored afterwards together with time, step count
- * and signal speeds; the fastest shape is kept, reported in *tile (may be
+ * and signal speeds; the fastest configuration is kept, reported in *tile (may be
  * NULL) with its mean step time in *ms (may be NULL), and remembered for
  * contexts of the same grid size, hyper-diffusion and background flags that
  * this process creates later (they start with it).  Allocates one state-sized
@@ -323,7 +335,8 @@ const char *sac_batch_last_error(const sac_batch *b);
 int sac_batch_set_state(sac_batch *b, int run, const double *w, const double *bg, double t);
 int sac_batch_get_state(sac_batch *b, int run, double *w, double *t);
 
-/* nsteps CFL steps of every run (each with its own dt).  ASYNC. */
+/* nsteps CFL steps of every run (each with its own dt).  ASYNC.  The first
+ * call captures the one-step and 16-step graphs it replays. */
 int sac_batch_steps(sac_batch *b, long nsteps);
 
 /* Wait for the batch's stream; report the first run in error. */

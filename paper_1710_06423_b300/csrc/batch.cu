@@ -361,7 +361,7 @@ static cudaError_t capture_batch(sac_batch* b, int nsteps, cudaGraphExec_t* out)
 // maps' boxes follow the shape); without tensor maps the kernel copies rows.
 static int set_tile_tables(sac_batch* b, int tile)
 {
-    for (auto& a : b->h_args) a.tile = tile;
+    for (auto& a : b->h_args) { a.tile = tile; a.kernel_ghosts = 0; }
     BK(cudaMemcpy(b->d_args, b->h_args.data(), b->h_args.size() * sizeof(StageArgs<float>), cudaMemcpyHostToDevice));
     if (b->d_tmaps) {
         std::vector<CUtensorMap> maps(b->h_args.size());
@@ -525,8 +525,9 @@ int sac_batch_steps(sac_batch* b, long nsteps)
     if (nsteps < 0) return bfail(b, SAC_ERR_ARG, "nsteps < 0");
     for (int i = 0; i < b->n; ++i)
         if (!b->runs[i]->have_state) return bfail(b, SAC_ERR_STATE, "run %d has no state", i);
+    // both step graphs are captured by the first call (a one-time set-up)
     if (!b->g1) BK(capture_batch(b, 1, &b->g1));
-    if (!b->gN && nsteps >= kChunk) BK(capture_batch(b, kChunk, &b->gN));
+    if (!b->gN) BK(capture_batch(b, kChunk, &b->gN));
     long left = nsteps;
     while (left >= kChunk) { BK(cudaGraphLaunch(b->gN, b->stream)); left -= kChunk; }
     while (left > 0) { BK(cudaGraphLaunch(b->g1, b->stream)); --left; }

@@ -11,14 +11,14 @@
 namespace sac {
 namespace {
 
-template <class G, int S, bool BG, bool HD, bool GR, bool SF>
+template <class G, int S, bool BG, bool HD, bool GR, bool SF, bool KG = false>
 cudaError_t set_attr()
 {
-    cudaError_t e = cudaFuncSetAttribute(f32k::stage_fp32<G, S, BG, HD, GR, SF>,
+    cudaError_t e = cudaFuncSetAttribute(f32k::stage_fp32<G, S, BG, HD, GR, SF, KG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(f32k::Smem<G>));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(f32k::stage_fp32<G, S, BG, HD, GR, SF>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
+        e = cudaFuncSetAttribute(f32k::stage_fp32<G, S, BG, HD, GR, SF, KG>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     return e;
 }
 
@@ -84,7 +84,7 @@ __global__ void halo_fp32(const StageArgs<float> a, long long n)
         f32k::halo_cell(w, a.L, a.bc_x, a.bc_y, t);
 }
 
-template <class G, int S, bool BG, bool HD, bool GR, bool SF>
+template <class G, int S, bool BG, bool HD, bool GR, bool SF, bool KG>
 cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
 {
     const int ntx = (a.L.nx + G::TX - 1) / G::TX, nty = (a.L.ny + G::TY - 1) / G::TY, ntiles = ntx * nty;
@@ -94,9 +94,9 @@ cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
     const cudaError_t te = encode_stage_tensor_map(a, &tm);
     if (te != cudaSuccess) return te;
     // both kernels may be scheduled while their predecessor runs (see pdl_wait)
-    cudaError_t e = launch_pdl(f32k::stage_fp32<G, S, BG, HD, GR, SF>, dim3(grid), dim3(G::NT), sizeof(f32k::Smem<G>),
-                               s, a, ntx, ntiles, tm);
-    if (e == cudaSuccess && (a.bc_x != BC_FIXED || a.bc_y != BC_FIXED)) {
+    cudaError_t e = launch_pdl(f32k::stage_fp32<G, S, BG, HD, GR, SF, KG>, dim3(grid), dim3(G::NT),
+                               sizeof(f32k::Smem<G>), s, a, ntx, ntiles, tm);
+    if (!KG && e == cudaSuccess && (a.bc_x != BC_FIXED || a.bc_y != BC_FIXED)) {
         const long long n = f32k::halo_count(a.L);
         const int hb = (int)std::min<long long>((n + 255) / 256, 4 * g_nsm);
         e = launch_pdl(halo_fp32, dim3(hb), dim3(256), 0, s, a, n);
@@ -104,36 +104,45 @@ cudaError_t launch(const StageArgs<float>& a, cudaStream_t s)
     return e;
 }
 
-template <class G, bool BG, bool HD, bool GR = false, bool SF = false>
+template <class G, bool BG, bool HD, bool GR = false, bool SF = false, bool KG = false>
 cudaError_t by_stage(const StageArgs<float>& a, int stage, cudaStream_t s)
 {
     switch (stage) {
-        case 1: return launch<G, 1, BG, HD, GR, SF>(a, s);
-        case 2: return launch<G, 2, BG, HD, GR, SF>(a, s);
-        case 3: return launch<G, 3, BG, HD, GR, SF>(a, s);
-        default: return launch<G, 4, BG, HD, GR, SF>(a, s);
+        case 1: return launch<G, 1, BG, HD, GR, SF, KG>(a, s);
+        case 2: return launch<G, 2, BG, HD, GR, SF, KG>(a, s);
+        case 3: return launch<G, 3, BG, HD, GR, SF, KG>(a, s);
+        default: return launch<G, 4, BG, HD, GR, SF, KG>(a, s);
     }
 }
 
-// the tile shapes are instantiated for the plain and background variants; the
-// gravity and single-face variants run 32 x 32 tiles
+// the tile shapes are instantiated for the plain and background variants, the
+// in-kernel ghost frame for the plain variants only (a background run ignores
+// it); the gravity and single-face variants run 32 x 32 tiles
+template <class G, bool BG, bool HD>
+cudaError_t by_ghosts(const StageArgs<float>& a, int stage, cudaStream_t s)
+{
+    if constexpr (!BG) {
+        if (a.kernel_ghosts) return by_stage<G, BG, HD, false, false, true>(a, stage, s);
+    }
+    return by_stage<G, BG, HD>(a, stage, s);
+}
 template <bool BG, bool HD>
 cudaError_t by_tile(const StageArgs<float>& a, int stage, cudaStream_t s)
 {
     switch (a.tile) {
-        case TILE_64x16: return by_stage<f32k::G64x16, BG, HD>(a, stage, s);
-        case TILE_32x16: return by_stage<f32k::G32x16, BG, HD>(a, stage, s);
-        default: return by_stage<f32k::G32x32, BG, HD>(a, stage, s);
+        case TILE_64x16: return by_ghosts<f32k::G64x16, BG, HD>(a, stage, s);
+        case TILE_32x16: return by_ghosts<f32k::G32x16, BG, HD>(a, stage, s);
+        default: return by_ghosts<f32k::G32x32, BG, HD>(a, stage, s);
     }
 }
 
-template <class G, bool BG, bool HD, bool GR = false, bool SF = false>
+template <class G, bool BG, bool HD, bool GR = false, bool SF = false, bool KG = false>
 cudaError_t attr_all()
 {
-    cudaError_t e = set_attr<G, 1, BG, HD, GR, SF>();
-    if (e == cudaSuccess) e = set_attr<G, 2, BG, HD, GR, SF>();
-    if (e == cudaSuccess) e = set_attr<G, 3, BG, HD, GR, SF>();
-    if (e == cudaSuccess) e = set_attr<G, 4, BG, HD, GR, SF>();
+    cudaError_t e = set_attr<G, 1, BG, HD, GR, SF, KG>();
+    if (e == cudaSuccess) e = set_attr<G, 2, BG, HD, GR, SF, KG>();
+    if (e == cudaSuccess) e = set_attr<G, 3, BG, HD, GR, SF, KG>();
+    if (e == cudaSuccess) e = set_attr<G, 4, BG, HD, GR, SF, KG>();
     return e;
 }
 template <class G>
@@ -143,6 +152,8 @@ cudaError_t attr_geometry()
     if (e == cudaSuccess) e = attr_all<G, false, true>();
     if (e == cudaSuccess) e = attr_all<G, true, false>();
     if (e == cudaSuccess) e = attr_all<G, true, true>();
+    if (e == cudaSuccess) e = attr_all<G, false, false, false, false, true>();
+    if (e == cudaSuccess) e = attr_all<G, false, true, false, false, true>();
     return e;
 }
 }  // namespace

@@ -339,7 +339,8 @@ static void fill_stage_args(const sac_ctx* c, int stage, StageArgs<T>* a)
     a->c_shk = c->p.c_shk; a->bc_x = c->p.bc_x; a->bc_y = c->p.bc_y;
     a->grav[0] = c->p.gravity[0]; a->grav[1] = c->p.gravity[1];
     a->hd_single_face = c->p.hd_single_face;
-    a->tile = c->tile;
+    a->tile = c->tile % NTILE_SHAPES;
+    a->kernel_ghosts = c->tile >= NTILE_SHAPES;
     a->derive_f32();
 }
 
@@ -722,8 +723,10 @@ int sac_steps(sac_ctx* c, long nsteps)
         int rc = set_t_end(c, std::numeric_limits<double>::infinity());
         if (rc != SAC_OK) return rc;
     }
+    // both step graphs are captured by the first call, whatever its step count, so
+    // that a later, longer call does not pay the capture (a one-time set-up)
     if (!c->g1) CK(capture(c, 1, &c->g1));
-    if (!c->gN && nsteps >= kChunk) CK(capture(c, kChunk, &c->gN));
+    if (!c->gN) CK(capture(c, kChunk, &c->gN));
     long left = nsteps;
     while (left >= kChunk) { CK(cudaGraphLaunch(c->gN, c->stream)); left -= kChunk; }
     while (left > 0) { CK(cudaGraphLaunch(c->g1, c->stream)); --left; }
@@ -744,6 +747,7 @@ int sac_run_to(sac_ctx* c, double t_end, long max_steps, long* steps_taken)
     rc = set_t_end(c, t_end);
     if (rc != SAC_OK) return rc;
     if (!c->g1) CK(capture(c, 1, &c->g1));
+    if (!c->gN) CK(capture(c, kChunk, &c->gN));
     long launched = 0;
     double t = c->hsc->t, dt_last = c->hsc->dt;
     while ((max_steps < 0 || launched < max_steps) && t < t_end) {
@@ -754,7 +758,6 @@ int sac_run_to(sac_ctx* c, double t_end, long max_steps, long* steps_taken)
             want = est > 4096.0 ? 4096 : (long)est + 1;
         }
         if (max_steps >= 0 && want > max_steps - launched) want = max_steps - launched;
-        if (want >= kChunk && !c->gN) CK(capture(c, kChunk, &c->gN));
         long n = 0;
         while (want - n >= kChunk) { CK(cudaGraphLaunch(c->gN, c->stream)); n += kChunk; }
         while (n < want) { CK(cudaGraphLaunch(c->g1, c->stream)); ++n; }
@@ -921,7 +924,7 @@ int sac_sync(sac_ctx* c)
 int sac_set_tile(sac_ctx* c, int tile)
 {
     if (!c) return SAC_ERR_ARG;
-    if (tile < 0 || tile >= NTILE_SHAPES) return fail(c, SAC_ERR_ARG, "unknown tile shape %d", tile);
+    if (tile < 0 || tile >= NTILE_CONFIGS) return fail(c, SAC_ERR_ARG, "unknown tile configuration %d", tile);
     if (!c->fp32) return fail(c, SAC_ERR_ARG, "tile shapes apply to FP32 contexts");
     if (tile != c->tile) {
         CK(cudaSetDevice(c->p.device));
@@ -965,7 +968,10 @@ int sac_tune(sac_ctx* c, int trials, int* tile_out, double* ms_out)
     const int keep = c->tile;
     double best = 1e300;
     int bi = keep;
-    for (int t = 0; t < NTILE_SHAPES && e == cudaSuccess; ++t) {
+    // the in-kernel ghost frame exists for the plain kernels only (no background,
+    // gravity or single-face variant), which otherwise ignore it
+    const int nconf = c->p.has_background || c->p.hd_single_face ? (int)NTILE_SHAPES : (int)NTILE_CONFIGS;
+    for (int t = 0; t < nconf && e == cudaSuccess; ++t) {
         c->tile = t;
         e = enqueue_step(c, c->stream, 0.0);                   // warm-up (tensor maps, caches)
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);

@@ -21,6 +21,10 @@ enum { ST_OK = 0, ST_ERR_NONFINITE = -5, ST_ERR_TIMEOUT = -6 };
 // tile shapes of the FP32 stage kernels (SAC_TILE_* of sac.h): 32 x 32 cells
 // with 256 threads, 64 x 16 with 256 threads, 32 x 16 with 128 threads
 enum { TILE_32x32 = 0, TILE_64x16 = 1, TILE_32x16 = 2, NTILE_SHAPES = 3 };
+// single-run FP32 tile configurations: NTILE_SHAPES + s is shape s with the
+// ghost frame of each stage output written by the stage kernel itself (no
+// ghost-frame launch); the batch runs use the shapes only
+enum { NTILE_CONFIGS = 2 * NTILE_SHAPES };
 
 // field index -> (plane, component) of the FP32 pair layout:
 // planes (rho~, e~), (m_x, m_y), (B~x, B~y); background (rho_b, e_b), (B_bx, B_by)
@@ -150,6 +154,7 @@ struct StageArgs {
     double c_shk;
     int bc_x, bc_y;
     int hd_single_face;   // 1: hyper-diffusion ratio from the face itself (no max over 3 faces)
+    int kernel_ghosts = 0;   // FP32 single-run kernel: 1 = it writes the ghost frame of sout itself
     double grav[2];    // gravitational acceleration; sources rt g (momentum), m.g (energy)
     int tile = TILE_32x32;   // FP32 kernels: tile shape (TILE_*)
     __host__ __device__ bool has_grav() const { return grav[0] != 0.0 || grav[1] != 0.0; }

@@ -31,7 +31,9 @@
 // The RK registers U0/D of a thread's Y-sweep cells are prefetched into L2
 // when the tile starts and loaded into registers ahead of their use.
 // A small kernel after each stage fills the ghost frame of the output
-// (periodic/outflow copies), so the tile code has no boundary cases.
+// (periodic/outflow copies), so the tile code has no boundary cases; in the
+// tile configurations with in-kernel ghosts the stage kernel writes that frame
+// itself after each tile near a side (tile_ghosts).
 //
 // RK registers (D scheme, 22.5 values moved per cell-stage):
 //   s1: S1 = U0 + dt/2 k1
@@ -272,6 +274,78 @@ __device__ __forceinline__ void halo_cell(float2* __restrict__ w, const Layout& 
     const long long src = L.at(sx, sy), dst = L.at(gx, gy);
 #pragma unroll
     for (int p = 0; p < 3; ++p) w[p * L.fstride + dst] = w[p * L.fstride + src];
+}
+
+// The same ghost frame written by the stage kernel itself (tile
+// configurations with in-kernel ghosts, KG): after a tile, each thread copies
+// its own Y-sweep cells (column x0 + tid % TX, rows y0 + SEG (tid / TX) + q),
+// which it has just stored into w, to every ghost cell whose
+// (map(gx), map(gy)) is that cell.  Along one direction the coordinates that
+// hold interior coordinate i are the candidates k = 0 .. 2 GY: k = 0 is i
+// itself, k = 1..GY the ghost -k and k = GY+1..2GY the ghost n+k-GY-1, a ghost
+// taken when its side is not fixed and halo_map sends it to i; the cell's
+// ghosts are the products of its x and y candidates other than the cell
+// itself.  No kernel of the same stage reads w, and the next stage reads it
+// after this kernel has completed.
+__device__ __forceinline__ int ghost_coord(int k, int i, int n)
+{
+    return k == 0 ? i : (k <= GY ? -k : n + (k - GY - 1));
+}
+// Bit k set: candidate k holds i.
+__device__ __forceinline__ unsigned ghost_mask(int i, int n, int bc)
+{
+    unsigned m = 1u;
+    if (bc == BC_FIXED) return m;
+    if (bc == BC_OUTFLOW) {
+        if (i == 0) m |= ((1u << GY) - 1u) << 1;              // ghosts -1 .. -GY
+        if (i == n - 1) m |= ((1u << GY) - 1u) << (GY + 1);   // ghosts n .. n+GY-1
+        return m;
+    }
+    if (n >= GY) {   // periodic: ghost -k holds n - k, ghost n + k holds k
+        if (i >= n - GY) m |= 1u << (n - i);
+        if (i < GY) m |= 1u << (GY + 1 + i);
+        return m;
+    }
+    for (int k = 1; k <= 2 * GY; ++k)   // periodic with fewer than GY cells: several wraps
+        if (halo_map(ghost_coord(k, i, n), n, bc) == i) m |= 1u << k;
+    return m;
+}
+// The copies of one tile near a non-fixed side.  A separate function: the
+// rarely taken path then leaves the code of the tile loop as it is.
+template <class G>
+__device__ __noinline__ void tile_ghosts_copy(float2* __restrict__ w, const Layout L, const int bc_x, const int bc_y,
+                                              const int x0, const int y0, const bool near_x, const bool near_y)
+{
+    const int tid = threadIdx.x, gi = x0 + tid % G::TX, j0 = y0 + (tid / G::TX) * SEG;
+    if (gi >= L.nx) return;
+    const unsigned mx = near_x && (gi < GY || gi >= L.nx - GY) ? ghost_mask(gi, L.nx, bc_x) : 1u;
+#pragma unroll 1
+    for (int q = 0; q < SEG; ++q) {
+        const int gj = j0 + q;
+        if (gj >= L.ny) break;
+        const unsigned my = near_y && (gj < GY || gj >= L.ny - GY) ? ghost_mask(gj, L.ny, bc_y) : 1u;
+        if ((mx | my) == 1u) continue;   // no ghost holds this cell
+        const long long src = L.at(gi, gj);
+        const float2 v0 = w[src], v1 = w[L.fstride + src], v2 = w[2 * L.fstride + src];
+        for (unsigned bx = mx; bx; bx &= bx - 1u) {
+            const int kx = __ffs(bx) - 1, gx = ghost_coord(kx, gi, L.nx);
+            for (unsigned by = my; by; by &= by - 1u) {
+                const int ky = __ffs(by) - 1;
+                if ((kx | ky) == 0) continue;
+                const long long dst = L.at(gx, ghost_coord(ky, gj, L.ny));
+                w[dst] = v0; w[L.fstride + dst] = v1; w[2 * L.fstride + dst] = v2;
+            }
+        }
+    }
+}
+// Tile-uniform test: only tiles within GY cells of a non-fixed side copy.
+template <class G>
+__device__ __forceinline__ void tile_ghosts(float2* __restrict__ w, const Layout& L, int bc_x, int bc_y,
+                                            const int x0, const int y0)
+{
+    const bool near_x = bc_x != BC_FIXED && (x0 < GY || x0 + G::TX > L.nx - GY);
+    const bool near_y = bc_y != BC_FIXED && (y0 < GY || y0 + G::TY > L.ny - GY);
+    if (near_x || near_y) tile_ghosts_copy<G>(w, L, bc_x, bc_y, x0, y0, near_x, near_y);
 }
 
 // The shock part of the face coefficients, bh (s_f + s_{f+1}) with
@@ -831,7 +905,9 @@ __device__ __forceinline__ void tile_body(const StageArgs<float>& a, const int x
 // copies while it finishes the current one.
 // The step constants are read once; stage 4 keeps the signal-speed maximum of
 // all its tiles in registers and reduces it once at the end.
-template <class G, int STAGE, bool BG, bool HD, bool GRAV, bool SF = false>
+// KG: the kernel also writes the ghost frame of its output (tile_ghosts);
+// otherwise a ghost-frame kernel follows it.
+template <class G, int STAGE, bool BG, bool HD, bool GRAV, bool SF = false, bool KG = false>
 __global__ void __launch_bounds__(G::NT, G::MINB) stage_fp32(const StageArgs<float> a, const int ntx, const int ntiles,
                                                              const __grid_constant__ CUtensorMap tm)
 {
@@ -867,9 +943,16 @@ __global__ void __launch_bounds__(G::NT, G::MINB) stage_fp32(const StageArgs<flo
         const int tn = t + gridDim.x;
         NextTile nt = next_tile(a, tn < ntiles, (tn % ntx) * G::TX, (tn / ntx) * G::TY);
         nt.tm = tmp;
-        tile_body<G, STAGE, BG, HD, true, GRAV, SF>(a, (t % ntx) * G::TX, (t / ntx) * G::TY, S, K, m, nt, &bar,
-                                                     &phase, &failed);
-        if (failed) return;
+        if constexpr (KG) {
+            const int x0 = (t % ntx) * G::TX, y0 = (t / ntx) * G::TY;
+            tile_body<G, STAGE, BG, HD, true, GRAV, SF>(a, x0, y0, S, K, m, nt, &bar, &phase, &failed);
+            if (failed) return;
+            tile_ghosts<G>(reinterpret_cast<float2*>(a.sout), a.L, a.bc_x, a.bc_y, x0, y0);
+        } else {
+            tile_body<G, STAGE, BG, HD, true, GRAV, SF>(a, (t % ntx) * G::TX, (t / ntx) * G::TY, S, K, m, nt, &bar,
+                                                         &phase, &failed);
+            if (failed) return;
+        }
     }
     if (STAGE == 4) block_speed_max(m, red, a.sc);
 }

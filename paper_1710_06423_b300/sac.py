@@ -20,7 +20,9 @@ SAC_OK, SAC_ERR_ARG, SAC_ERR_STATE, SAC_ERR_CUDA, SAC_ERR_OOM, SAC_ERR_NONFINITE
 SAC_ERR_TOO_LARGE = -7
 BC_PERIODIC, BC_FIXED, BC_OUTFLOW = 0, 1, 2
 TILE_32x32, TILE_64x16, TILE_32x16 = 0, 1, 2
+TILE_KERNEL_GHOSTS = 3   # + shape: the stage kernel writes the ghost frame itself (single runs)
 TILE_NAMES = {TILE_32x32: "32x32", TILE_64x16: "64x16", TILE_32x16: "32x16"}
+TILE_NAMES.update({TILE_KERNEL_GHOSTS + t: f"{n}, in-kernel ghosts" for t, n in list(TILE_NAMES.items())})
 FP64, FP32 = 0, 1
 NF, NB = 6, 4
 
@@ -360,7 +362,8 @@ class Solver:
         self._check(load().sac_sync(self._ctx), "sac_sync")
 
     def set_tile(self, tile: int):
-        """FP32 tile shape (TILE_32x32, TILE_64x16, TILE_32x16) of the later steps."""
+        """FP32 tile configuration of the later steps: a shape (TILE_32x32, TILE_64x16,
+        TILE_32x16), plus TILE_KERNEL_GHOSTS for the in-kernel ghost frame."""
         self._check(load().sac_set_tile(self._ctx, int(tile)), "sac_set_tile")
 
     def tile(self) -> int:
@@ -369,7 +372,7 @@ class Solver:
         return out.value
 
     def tune(self, trials: int = 3):
-        """Autotune the tile shape on the current state (restored); returns (tile, ms per step)."""
+        """Autotune the tile configuration on the current state (restored); returns (tile, ms per step)."""
         t, ms = ctypes.c_int(), ctypes.c_double()
         self._check(load().sac_tune(self._ctx, int(trials), ctypes.byref(t), ctypes.byref(ms)), "sac_tune")
         return t.value, ms.value

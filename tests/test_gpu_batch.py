@@ -131,7 +131,7 @@ def test_tuner_keeps_states(small_batch):
         after = [b.get_state(i) for i in range(len(runs))]
         b.steps(3)
         cont = [b.get_state(i)[0] for i in range(len(runs))]
-    assert ms > 0 and cfg[0] in (0, 1) and cfg[1] in (1, 2) and cfg[2] in (0, 1, 2)
+    assert ms > 0 and cfg[0] in (0, 1, 2) and cfg[1] in (1, 2) and cfg[2] in (0, 1, 2)
     for x, y in zip(before, after):
         assert np.array_equal(x[0], y[0]) and x[1] == y[1]
     for i, (kw, w) in enumerate(zip(runs, states)):

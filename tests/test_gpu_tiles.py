@@ -1,8 +1,10 @@
 """Tile shapes of the FP32 stage kernel and their autotuner.
 
-Every shape (32 x 32, 64 x 16, 32 x 16 cells) must give bit for bit the results
-of the default 32 x 32 tiles: a cell's arithmetic is the same whatever tile it
-falls in, so only the work distribution changes.  Checked on ragged grids
+Every shape (32 x 32, 64 x 16, 32 x 16 cells), with the ghost frame written by
+a separate kernel or by the stage kernel itself, must give bit for bit the
+results of the default 32 x 32 tiles: a cell's arithmetic is the same whatever
+tile it falls in, and the ghost cells receive the same copies, so only the work
+distribution changes.  Checked on ragged grids
 (several tiles plus partial ones in both directions), with every boundary
 kind, with a background, in single runs and in batches; one non-default shape
 is also compared with the oracle directly.  The tuner must restore the state
@@ -17,6 +19,7 @@ from gpu_helpers import TOL_FP32_L1, l1rel, oracle_problem, problem_kwargs, smoo
 pytestmark = pytest.mark.gpu
 FP32 = 1
 SHAPES = (0, 1, 2)   # SAC_TILE_32x32, SAC_TILE_64x16, SAC_TILE_32x16
+CONFIGS = SHAPES + (3, 4, 5)   # the same shapes with the in-kernel ghost frame
 
 CASES = [
     # nx, ny, kwargs, background
@@ -26,6 +29,12 @@ CASES = [
     (33, 1, {}, False),
     (1, 40, {"bc_y": 2}, False),
     (200, 150, {"hyperdiffusion": 0}, False),
+    # for the in-kernel ghost frame (grids narrower than the 3-cell frame are
+    # the 33 x 1 and 1 x 40 cases): a fixed side beside a periodic one, last
+    # tiles narrower than the frame, outflow on both sides
+    (66, 70, {"bc_x": 1}, False),
+    (65, 34, {}, False),
+    (35, 19, {"bc_x": 2, "bc_y": 2}, False),
 ]
 
 
@@ -57,7 +66,7 @@ def test_every_tile_shape_equals_the_default_bitwise(inputs_mod, nx, ny, kw, has
     kw = problem_kwargs(nx, ny, **kw)
     w, bg = _state(inputs_mod, nx, ny, has_bg)
     ref, t_ref = _run(kw, w, bg, 0, 6)
-    for tile in SHAPES[1:]:
+    for tile in CONFIGS[1:]:
         got, t = _run(kw, w, bg, tile, 6)
         assert t == t_ref
         assert np.array_equal(got, ref), (tile, np.abs(got - ref).max())
@@ -67,7 +76,7 @@ def test_non_default_tile_against_the_oracle(oracle_mod, inputs_mod):
     kw = problem_kwargs(150, 90)
     w, _ = _state(inputs_mod, 150, 90, False)
     ref, t_ref, _ = oracle_mod.run(oracle_problem(oracle_mod, kw), w, max_steps=10)
-    for tile in (1, 2):
+    for tile in (1, 2, 4):
         got, t = _run(kw, w, None, tile, 10)
         assert abs(t - t_ref) <= 1e-6 * t_ref
         assert np.all(l1rel(got, ref) <= TOL_FP32_L1), (tile, l1rel(got, ref))
@@ -84,7 +93,7 @@ def test_tuner_restores_the_state_and_keeps_the_fastest_shape(inputs_mod):
         before, t0 = s.get_state()
         tile, ms = s.tune(trials=2)
         after, t1 = s.get_state()
-        assert tile in SHAPES and ms > 0 and s.tile() == tile
+        assert tile in CONFIGS and ms > 0 and s.tile() == tile
         assert t1 == t0 and s.time() == (t0, 2)
         assert np.array_equal(after, before)
         s.steps(3)
@@ -99,8 +108,9 @@ def test_tuner_restores_the_state_and_keeps_the_fastest_shape(inputs_mod):
 def test_tile_api_rejects_bad_shapes_and_fp64(inputs_mod):
     from paper_1710_06423_b300.sac import FP64, SacError, Solver
     with Solver(nx=16, ny=16, precision=FP32) as s:
-        with pytest.raises(SacError):
-            s.set_tile(3)
+        for bad in (-1, 6):
+            with pytest.raises(SacError):
+                s.set_tile(bad)
     with Solver(nx=16, ny=16, precision=FP64) as s:
         with pytest.raises(SacError):
             s.set_tile(1)
