@@ -44,9 +44,12 @@ MODEL_BYTES_PER_CELL_STAGE = 96
 # dram__bytes_read.sum + dram__bytes_write.sum on the 4000^2 workload (three times L2
 # per RK register), with the SHA-256 of the FP32 stage sources at the time of that
 # capture: when the sources differ, the figures no longer describe the kernel and
-# `roofline.traffic` is reported as null.
-STAGE_TRAFFIC_B_PER_CELL_FP32 = (46.0, 94.3, 120.3, 98.2)
-STAGE_TRAFFIC_SOURCES_SHA = "7bee94cb8581bdda"
+# `roofline.traffic` is reported as null.  Captured on the configuration the tuner
+# kept in that run, 64 x 16 tiles with the in-kernel ghost frame (the tile code is
+# that of every configuration; the ghost copies add ~0.1 B per cell at 4000^2).
+STAGE_TRAFFIC_B_PER_CELL_FP32 = (47.3, 96.5, 121.1, 98.2)
+STAGE_TRAFFIC_SOURCES_SHA = "afce6b56d3f87bd3"
+STAGE_TRAFFIC_CONFIG = "64x16, in-kernel ghosts"
 STAGE_SOURCES = ("stage_fp32.cuh", "kernels_fp32.cu", "speed.cuh", "sac_internal.cuh")
 
 
@@ -656,8 +659,8 @@ def run_ours(args, ws, rank, local, pg):
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per average stage launch",
                 "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the stage kernel on the "
-                                   "4000^2 workload, per-cell figures x the cells of one 8000^2 launch; stage "
-                                   f"sources sha {STAGE_TRAFFIC_SOURCES_SHA}") if fresh else
+                                   f"4000^2 workload ({STAGE_TRAFFIC_CONFIG}), per-cell figures x the cells of "
+                                   f"one 8000^2 launch; stage sources sha {STAGE_TRAFFIC_SOURCES_SHA}") if fresh else
                                   f"null: the stage sources (sha {sha}) changed since the last capture",
                 "kernel": "stage_fp32 (all four RK stages)",
                 "bytes_per_cell_stage": MODEL_BYTES_PER_CELL_STAGE,
