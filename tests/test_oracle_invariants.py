@@ -5,7 +5,8 @@ conservation of mass, momentum, energy and flux; the 180-degree point symmetry
 of the Orszag-Tang vortex; a y-uniform 2D run equal to the 1D run; x/y
 transposition symmetry; the perturbation/background split equal to the
 unsplit system for a uniform background; discrete div B preserved by the
-ideal central scheme; fourth-order convergence on smooth linear waves.
+ideal central scheme; fourth-order convergence on smooth linear waves; the
+Brio-Wu integrals following the fluxes through its fixed ends.
 """
 import math
 
@@ -179,3 +180,37 @@ def test_brio_wu_runs_to_horizon(oracle_mod, inputs_mod):
     assert 0.10 < w[0].min() and w[0].max() < 1.02
     # the far ends are still the initial left and right states
     assert abs(w[0, 0, 0] - 1.0) < 1e-9 and abs(w[0, 0, -1] - 0.125) < 1e-9
+
+
+def test_brio_wu_integrals_follow_the_end_fluxes(oracle_mod, inputs_mod):
+    """Brio-Wu to t = 0.1 with fixed ends: while both ends keep their initial
+    states at rest, each field's integral changes only by the flux difference
+    between the ends, F(left) - F(right), times t.  At rest F_rho = F_e = F_By =
+    F_Bx = 0, F_mx = p_t - B_x^2 and F_my = -B_x B_y (section 2's fluxes), so mass,
+    energy and both field components keep their initial integrals, the x momentum
+    gains t (p_tL - p_tR) = 0.1 * 0.9 and the y momentum t (-B_x)(B_yL - B_yR) =
+    -0.1 * 1.5.  The fourth-order flux difference and the hyper-diffusion fluxes
+    telescope to those end values exactly when the cells next to each end are
+    uniform, so the scheme meets this to rounding."""
+    o, I = oracle_mod, inputs_mod
+    n, gamma, t_end = 800, 2.0, 0.1
+    pr = o.Problem(nx=n, ny=1, gamma=gamma, bc_x=BC_F)
+    w0 = I.brio_wu(n, 1, gamma=gamma)
+    w, t, _ = o.run(pr, w0, t_end=t_end)
+    assert t == t_end
+    bx, byl, byr = 0.75, 1.0, -1.0
+    ptl = 1.0 + 0.5 * (bx * bx + byl * byl)
+    ptr = 0.1 + 0.5 * (bx * bx + byr * byr)
+    el = 1.0 / (gamma - 1.0) + 0.5 * (bx * bx + byl * byl)
+    er = 0.1 / (gamma - 1.0) + 0.5 * (bx * bx + byr * byr)
+    want = np.array([0.5 * 1.0 + 0.5 * 0.125,            # rho
+                     t_end * (ptl - ptr),                 # m_x
+                     t_end * (-bx * byl + bx * byr),      # m_y
+                     0.5 * el + 0.5 * er,                 # e
+                     bx,                                  # B_x
+                     0.5 * byl + 0.5 * byr])              # B_y
+    got = _sums(w) / n
+    assert np.allclose(got, want, rtol=0.0, atol=1e-11), got - want
+    # the ends are still the initial states (the premise of the balance)
+    assert np.abs(w[:, 0, :3] - w0[:, 0, :3]).max() < 1e-12
+    assert np.abs(w[:, 0, -3:] - w0[:, 0, -3:]).max() < 1e-12
