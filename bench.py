@@ -667,6 +667,8 @@ def run_ours(args, ws, rank, local, pg):
                 "bytes_basis": "classical RK4 byte model: 24 FP32 values per cell-stage on average, no background",
                 "kernel_bytes_per_cell_stage": kernel_bpc,
                 "frac_kernel_bytes": kernel_bpc * cells / (sum(stage_ms) / 4 * 1e-3) / 1e9 / peak,
+                # the same byte model over the whole timed step (step control and launch gaps included)
+                "frac_step": 4 * MODEL_BYTES_PER_CELL_STAGE * cells / (ms / args.steps * 1e-3) / 1e9 / peak,
                 "stage_ms": stage_ms, "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "of fallback"}
     del s
